@@ -1,0 +1,211 @@
+"""CPU oracle for the variance-adaptive hashed TSDF map (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg import this package. It shares no code
+with the CUDA library: ``mrh_oracle.cpp`` is plain C++ compiled here with ``g++ -O2 -ffp-contract=off``.
+
+Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
+  segment cells (allocation)   pinned: brute force == ordered walk, closed forms, exact-rational spot checks
+  camera fusion (Eq. 2)        pinned: analytic ranges of a sphere / plane, Euclidean bound, f64 vs f32s
+  LiDAR fusion (Eq. 1)         pinned: normal-incidence plane, analytic along-ray values
+  Welford (Eq. 5/6)            pinned: two-pass variance, S2 >= 0, W monotone, S2 == 0 for repeated noise-free views
+  merge / split payloads       pinned on linear fields (exact); the rule itself is a reading: parity unpinned
+  thresholds                   chosen values: parity unpinned
+  raycast                      pinned: analytic plane / sphere depth; step constants are a reading
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mrh_oracle.cpp")
+_SO = os.path.join(_HERE, "libmrh_oracle.so")
+_lib = None
+
+CFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile libmrh_oracle.so if it is missing or older than its source."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", *CFLAGS, "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("base_voxel", ctypes.c_float), ("n_levels", ctypes.c_int), ("truncation", ctypes.c_float),
+                ("var_threshold", ctypes.c_double * 2), ("split_hysteresis", ctypes.c_double),
+                ("min_obs", ctypes.c_int), ("precision", ctypes.c_int), ("fp16", ctypes.c_int),
+                ("has_color", ctypes.c_int), ("min_range", ctypes.c_float), ("max_range", ctypes.c_float)]
+
+
+class Pinhole(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("min_depth", ctypes.c_float),
+                ("max_depth", ctypes.c_float)]
+
+
+class FrameStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("valid_rays", "touched", "new_blocks", "merged", "split", "fp64_rechecks", "observations")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        vp = ctypes.c_void_p
+        lib.orc_create.restype = vp
+        lib.orc_create.argtypes = [ctypes.POINTER(Params)]
+        lib.orc_destroy.argtypes = [vp]
+        lib.orc_integrate_depth.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, ctypes.POINTER(FrameStats)]
+        lib.orc_integrate_points.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(FrameStats)]
+        lib.orc_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp]
+        lib.orc_count_blocks.restype = ctypes.c_int64
+        lib.orc_count_blocks.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_extract.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.orc_block_stats.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.orc_segment_cells.restype = ctypes.c_int64
+        lib.orc_segment_cells.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int64]
+        lib.orc_resample_block.argtypes = [vp, ctypes.c_int, ctypes.c_int] + [vp] * 8
+        lib.orc_half_round.restype = ctypes.c_float
+        lib.orc_half_round.argtypes = [ctypes.c_float]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def params_from(wl, precision: str = "f32s", fp16: bool | None = None, var_threshold=None, split_hysteresis=None,
+                min_obs=None) -> Params:
+    """Oracle parameters for a ``synth.Workload``."""
+    p = Params()
+    p.base_voxel = wl.base_voxel
+    p.n_levels = wl.n_levels
+    p.truncation = wl.truncation
+    th = list(wl.var_threshold if var_threshold is None else var_threshold) + [0.0, 0.0]
+    p.var_threshold[0], p.var_threshold[1] = th[0], th[1]
+    p.split_hysteresis = wl.split_hysteresis if split_hysteresis is None else split_hysteresis
+    p.min_obs = wl.min_obs if min_obs is None else min_obs
+    p.precision = 1 if precision == "f64" else 0
+    p.fp16 = int(wl.fp16 if fp16 is None else fp16) if precision != "f64" else 0
+    p.has_color = int(wl.has_color)
+    p.min_range, p.max_range = wl.r_min, wl.r_max
+    return p
+
+
+def pinhole_from(wl) -> Pinhole:
+    k = Pinhole()
+    k.fx, k.fy, k.cx, k.cy = wl.fx, wl.fy, wl.cx, wl.cy
+    k.width, k.height = wl.width, wl.height
+    k.min_depth, k.max_depth = wl.min_depth, wl.max_depth
+    return k
+
+
+class OracleMap:
+    """One oracle map. ``precision`` is "f32s" (float, literal op order) or "f64" (double truth)."""
+
+    def __init__(self, params: Params):
+        self._lib = _load()
+        self.params = params
+        self._h = self._lib.orc_create(ctypes.byref(params))
+        if not self._h:
+            raise ValueError("invalid oracle parameters")
+
+    def close(self):
+        if self._h:
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate_depth(self, K: Pinhole, T_wc: np.ndarray, depth: np.ndarray, rgb: np.ndarray | None = None):
+        T = np.ascontiguousarray(T_wc, dtype=np.float64)
+        d = np.ascontiguousarray(depth, dtype=np.float32)
+        c = None if rgb is None else np.ascontiguousarray(rgb, dtype=np.uint8)
+        st = FrameStats()
+        self._lib.orc_integrate_depth(self._h, ctypes.byref(K), _p(T), _p(d), _p(c), ctypes.byref(st))
+        return st.as_dict()
+
+    def integrate_points(self, T_ws: np.ndarray, xyz: np.ndarray):
+        T = np.ascontiguousarray(T_ws, dtype=np.float64)
+        x = np.ascontiguousarray(xyz, dtype=np.float32)
+        st = FrameStats()
+        self._lib.orc_integrate_points(self._h, _p(T), _p(x), x.shape[0], ctypes.byref(st))
+        return st.as_dict()
+
+    def raycast(self, K: Pinhole, T_wc: np.ndarray) -> np.ndarray:
+        T = np.ascontiguousarray(T_wc, dtype=np.float64)
+        out = np.zeros((K.height, K.width), dtype=np.float32)
+        self._lib.orc_raycast(self._h, ctypes.byref(K), _p(T), _p(out))
+        return out
+
+    def count(self):
+        nv = ctypes.c_int64()
+        nb = self._lib.orc_count_blocks(self._h, ctypes.byref(nv))
+        return nb, nv.value
+
+    def extract(self) -> dict:
+        """All blocks sorted by key: keys (n,3) int32, levels (n,) uint8, offsets (n+1,) int64, D/W/S2 (V,) float64,
+        C (V,3) float64. Voxel i of a block of side n is at x + n (y + n z)."""
+        nb, nv = self.count()
+        out = dict(keys=np.zeros((nb, 3), np.int32), levels=np.zeros(nb, np.uint8), offsets=np.zeros(nb + 1, np.int64),
+                   D=np.zeros(nv), W=np.zeros(nv), S2=np.zeros(nv), C=np.zeros((nv, 3)))
+        self._lib.orc_extract(self._h, _p(out["keys"]), _p(out["levels"]), _p(out["offsets"]), _p(out["D"]),
+                              _p(out["W"]), _p(out["S2"]), _p(out["C"]))
+        return out
+
+    def resample_block(self, level: int, direction: int, D, W, S2, C=None) -> dict:
+        """Apply the merge (direction +1) or split (direction -1) payload rule to one block of ``level``."""
+        n_in = len(W)
+        n_out = n_in // 8 if direction > 0 else n_in * 8
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (D, W, S2)]
+        c = np.ascontiguousarray(np.zeros((n_in, 3)) if C is None else C, dtype=np.float64)
+        out = dict(D=np.zeros(n_out), W=np.zeros(n_out), S2=np.zeros(n_out), C=np.zeros((n_out, 3)))
+        rc = self._lib.orc_resample_block(self._h, level, direction, *[_p(x) for x in a], _p(c), _p(out["D"]),
+                                          _p(out["W"]), _p(out["S2"]), _p(out["C"]))
+        if rc != 0:
+            raise ValueError("invalid level/direction")
+        return out
+
+    def block_stats(self) -> dict:
+        """Per block (sorted by key): level, mean variance over observed voxels (double), observed count, weight sum."""
+        nb, _ = self.count()
+        out = dict(keys=np.zeros((nb, 3), np.int32), levels=np.zeros(nb, np.uint8), vbar=np.zeros(nb),
+                   n_obs=np.zeros(nb, np.int64), sum_w=np.zeros(nb, np.int64))
+        self._lib.orc_block_stats(self._h, _p(out["keys"]), _p(out["levels"]), _p(out["vbar"]), _p(out["n_obs"]),
+                                  _p(out["sum_w"]))
+        return out
+
+
+def segment_cells(A, B, unit: int, mode: str = "bruteforce") -> np.ndarray:
+    """Cells (edge ``unit``) met by the closed fixed-point segment A -> B. mode "bruteforce" or "walk"."""
+    lib = _load()
+    a = np.ascontiguousarray(A, dtype=np.int64)
+    b = np.ascontiguousarray(B, dtype=np.int64)
+    cap = 1 << 16
+    out = np.zeros((cap, 3), np.int64)
+    n = lib.orc_segment_cells(_p(a), _p(b), unit, 0 if mode == "bruteforce" else 1, _p(out), cap)
+    return out[:min(n, cap)].copy()
+
+
+def half_round(x: float) -> float:
+    return _load().orc_half_round(x)
+
+
+BLOCK_UNIT = 1 << 16      # fixed-point units per block edge
+VOXEL_UNIT = BLOCK_UNIT // 8

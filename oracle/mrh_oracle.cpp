@@ -1,0 +1,920 @@
+/*
+ * CPU oracle for the variance-adaptive multi-resolution TSDF map (MrHash, arXiv 2511.21459).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow reference that the CUDA library is checked against. Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg load it. It shares no code, header or table with
+ * the CUDA library.
+ *
+ * What it computes, step by step, per frame (paper section in brackets):
+ *   rays                    camera: pixel ray and range; LiDAR: sensor origin to point       [Sec. 3.1, Eq. 1/2]
+ *   allocation              every voxel block whose cell meets the ray's truncation band      [Sec. 3.2, DDA]
+ *   fusion                  truncated signed distance per voxel, running mean and weight     [Eq. 1, Eq. 2, Eq. 3]
+ *   Welford variance        S2 += (d - D_old)(d - D_new), sigma^2 = S2 / k                   [Sec. 3.2.1, Eq. 5/6]
+ *   block variance          mean of voxel variances over observed voxels of a block          [Sec. 3.2.1]
+ *   re-levelling            low-variance block -> coarser level (merge); high-variance block [Sec. 3.2.1, Fig. 2/4]
+ *                           -> finer level (split, an extension with hysteresis)
+ *   raycast                 first zero crossing of the trilinear field along each pixel ray  [Fig. 2 "render"]
+ * The readings taken where the paper is silent are written next to the code that takes them.
+ *
+ * Two arithmetic modes:
+ *   f64  - all voxel arithmetic and storage in double: the accuracy truth.
+ *   f32s - float storage and float arithmetic in the literal operation order written below. Compile with
+ *          -ffp-contract=off so no multiply-add is fused. Optional half storage of D and colour.
+ * Block keys are decided by exact integer arithmetic on fixed-point segment endpoints in both modes, so the key set
+ * does not depend on the mode.
+ *
+ * Plain containers only: std::unordered_map from block key to block, std::vector voxel arrays.
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+// ------------------------------------------------------------------------------------------------ constants
+
+constexpr int kFineDim = 8;           // voxels per block side at the finest level (512-voxel blocks, Sec. 5.1)
+constexpr int kFracBits = 16;         // fixed-point fraction bits per block edge for segment endpoints
+constexpr int64_t kBlockUnit = int64_t(1) << kFracBits;
+constexpr int64_t kVoxelUnit = kBlockUnit / kFineDim;  // one finest voxel
+constexpr int64_t kKeyLimit = (int64_t(1) << 20) - 2;  // |block coordinate| bound (21-bit packed keys)
+constexpr int kMaxLevels = 3;
+constexpr int kRaycastMaxIter = 8192;
+
+struct Key {
+  int64_t x, y, z;
+  bool operator==(const Key& o) const { return x == o.x && y == o.y && z == o.z; }
+  bool operator<(const Key& o) const {
+    if (x != o.x) return x < o.x;
+    if (y != o.y) return y < o.y;
+    return z < o.z;
+  }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = (uint64_t)k.x * 0x9E3779B97F4A7C15ULL;
+    h ^= (uint64_t)k.y * 0xC2B2AE3D27D4EB4FULL + (h << 6) + (h >> 2);
+    h ^= (uint64_t)k.z * 0x165667B19E3779F9ULL + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+  int64_t q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+
+// ------------------------------------------------------------------------------------------------ exact segment geometry
+//
+// Allocation (Sec. 3.2, "leverage DDA ... to allocate all intersected voxel blocks") needs the set of cells a segment
+// meets. Cells are half-open [c U, (c+1) U)^3. Endpoints are fixed-point integers, so "the closed segment meets the
+// cell" is decided exactly with integer arithmetic.
+
+struct Frac {  // num / den with den > 0, plus whether the bound is attained
+  __int128 num, den;
+  bool closed;
+};
+
+int frac_cmp(const Frac& a, const Frac& b) {
+  __int128 l = a.num * b.den, r = b.num * a.den;
+  return l < r ? -1 : (l > r ? 1 : 0);
+}
+
+// True iff the closed segment A -> B meets the half-open cell [c U, (c+1) U)^3.
+bool segment_meets_cell(const int64_t A[3], const int64_t B[3], const int64_t c[3], int64_t U) {
+  Frac lo{0, 1, true}, hi{1, 1, true};
+  for (int i = 0; i < 3; ++i) {
+    int64_t d = B[i] - A[i];
+    int64_t L = c[i] * U, H = (c[i] + 1) * U;
+    if (d == 0) {
+      if (A[i] < L || A[i] >= H) return false;
+      continue;
+    }
+    Frac cand_lo, cand_hi;
+    if (d > 0) {  // A + s d >= L  <=>  s >= (L - A)/d ;  A + s d < H  <=>  s < (H - A)/d
+      cand_lo = Frac{(__int128)(L - A[i]), (__int128)d, true};
+      cand_hi = Frac{(__int128)(H - A[i]), (__int128)d, false};
+    } else {      // A + s d >= L  <=>  s <= (A - L)/|d| ;  A + s d < H  <=>  s > (A - H)/|d|
+      cand_hi = Frac{(__int128)(A[i] - L), (__int128)(-d), true};
+      cand_lo = Frac{(__int128)(A[i] - H), (__int128)(-d), false};
+    }
+    int cl = frac_cmp(cand_lo, lo);
+    if (cl > 0 || (cl == 0 && !cand_lo.closed)) lo = cand_lo;
+    int ch = frac_cmp(cand_hi, hi);
+    if (ch < 0 || (ch == 0 && !cand_hi.closed)) hi = cand_hi;
+  }
+  int cmp = frac_cmp(lo, hi);
+  return cmp < 0 || (cmp == 0 && lo.closed && hi.closed);
+}
+
+// Every cell (edge U) the closed segment A -> B meets, by testing each cell of the bounding box.
+std::vector<Key> cells_bruteforce(const int64_t A[3], const int64_t B[3], int64_t U) {
+  int64_t lo[3], hi[3];
+  for (int i = 0; i < 3; ++i) {
+    int64_t a = floor_div(A[i], U), b = floor_div(B[i], U);
+    lo[i] = std::min(a, b);
+    hi[i] = std::max(a, b);
+  }
+  std::vector<Key> out;
+  for (int64_t x = lo[0]; x <= hi[0]; ++x)
+    for (int64_t y = lo[1]; y <= hi[1]; ++y)
+      for (int64_t z = lo[2]; z <= hi[2]; ++z) {
+        int64_t c[3] = {x, y, z};
+        if (segment_meets_cell(A, B, c, U)) out.push_back(Key{x, y, z});
+      }
+  return out;
+}
+
+// The same cells in the order the segment visits them: an Amanatides-Woo walk whose boundary crossings are compared
+// exactly. Crossing a boundary upward enters the next cell at the crossing point itself; crossing downward enters it
+// just after (cells are half-open). When crossings coincide, the upward ones are taken together first, then the
+// downward ones together.
+std::vector<Key> cells_dda(const int64_t A[3], const int64_t B[3], int64_t U) {
+  int64_t cell[3], end[3], D[3], N[3];
+  for (int i = 0; i < 3; ++i) {
+    cell[i] = floor_div(A[i], U);
+    end[i] = floor_div(B[i], U);
+    D[i] = B[i] - A[i];
+    // distance along axis i from A to the next boundary crossing (always >= 0)
+    if (D[i] > 0) N[i] = (cell[i] + 1) * U - A[i];
+    else if (D[i] < 0) N[i] = A[i] - cell[i] * U;
+    else N[i] = 0;
+  }
+  std::vector<Key> out;
+  out.push_back(Key{cell[0], cell[1], cell[2]});
+  for (int guard = 0; guard < 1 << 20; ++guard) {
+    if (cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2]) break;
+    // smallest crossing parameter N_i / |D_i| among moving axes
+    int best = -1;
+    for (int i = 0; i < 3; ++i) {
+      if (D[i] == 0) continue;
+      if (best < 0) { best = i; continue; }
+      __int128 l = (__int128)N[i] * (D[best] < 0 ? -D[best] : D[best]);
+      __int128 r = (__int128)N[best] * (D[i] < 0 ? -D[i] : D[i]);
+      if (l < r) best = i;
+    }
+    bool tie[3] = {false, false, false};
+    for (int i = 0; i < 3; ++i) {
+      if (D[i] == 0) continue;
+      __int128 l = (__int128)N[i] * (D[best] < 0 ? -D[best] : D[best]);
+      __int128 r = (__int128)N[best] * (D[i] < 0 ? -D[i] : D[i]);
+      tie[i] = (l == r);
+    }
+    bool any_up = false, any_down = false;
+    for (int i = 0; i < 3; ++i) {
+      if (!tie[i]) continue;
+      if (D[i] > 0) any_up = true; else any_down = true;
+    }
+    if (any_up) {
+      for (int i = 0; i < 3; ++i)
+        if (tie[i] && D[i] > 0) { cell[i] += 1; N[i] += U; }
+      out.push_back(Key{cell[0], cell[1], cell[2]});
+    }
+    if (any_down) {
+      if (cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2]) break;
+      for (int i = 0; i < 3; ++i)
+        if (tie[i] && D[i] < 0) { cell[i] -= 1; N[i] += U; }
+      out.push_back(Key{cell[0], cell[1], cell[2]});
+    }
+  }
+  return out;
+}
+
+bool key_in_range(const Key& k) {
+  return k.x >= -kKeyLimit && k.x <= kKeyLimit && k.y >= -kKeyLimit && k.y <= kKeyLimit && k.z >= -kKeyLimit &&
+         k.z <= kKeyLimit;
+}
+
+// float -> fixed point: floor(x * S), only for |x * S| < 2^40 (otherwise the ray is dropped)
+bool to_fixed_f(float v, float S, int64_t* out) {
+  float p = v * S;
+  if (!(std::fabs(p) < 1099511627776.0f)) return false;
+  *out = (int64_t)std::floor(p);
+  return true;
+}
+bool to_fixed_d(double v, double S, int64_t* out) {
+  double p = v * S;
+  if (!(std::fabs(p) < 1099511627776.0)) return false;
+  *out = (int64_t)std::floor(p);
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------------ half storage
+
+float half_round(float x) { return (float)(_Float16)x; }
+
+template <class S> struct Store;
+template <> struct Store<double> {
+  static double put(double x) { return x; }
+  static double get(double x) { return x; }
+};
+template <> struct Store<float> {
+  static float put(float x) { return x; }
+  static float get(float x) { return x; }
+};
+template <> struct Store<_Float16> {
+  static _Float16 put(float x) { return (_Float16)x; }
+  static float get(_Float16 x) { return (float)x; }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------ C interface types
+
+extern "C" {
+
+struct orc_params {
+  float base_voxel;        // coarsest-level voxel edge [m]
+  int n_levels;            // 1..3
+  float truncation;        // tau [m]
+  double var_threshold[2]; // theta_l: merge l -> l+1 when the block variance is below it [m^2]
+  double split_hysteresis; // h: split l -> l-1 when the block variance exceeds h * theta_{l-1}; 0 disables
+  int min_obs;             // k_min: mean weight over observed voxels needed before a block may change level
+  int precision;           // 0 = f32s, 1 = f64
+  int fp16;                // f32s only: D and colour stored as half
+  int has_color;
+  float min_range, max_range;  // LiDAR validity of |x_s| [m]
+};
+
+struct orc_pinhole {
+  float fx, fy, cx, cy;
+  int width, height;
+  float min_depth, max_depth;
+};
+
+struct orc_frame_stats {
+  int64_t valid_rays, touched, new_blocks, merged, split, fp64_rechecks, observations;
+};
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------------------------------------------ the map
+
+template <class R, class Sto>
+struct Block {
+  int level = 0;
+  std::vector<Sto> D;
+  std::vector<R> W, S2;
+  std::vector<Sto> C[3];
+  void resize(int n, bool color) {
+    size_t v = (size_t)n * n * n;
+    D.assign(v, Store<Sto>::put(0));
+    W.assign(v, 0);
+    S2.assign(v, 0);
+    for (int c = 0; c < 3; ++c) C[c].assign(color ? v : 0, Store<Sto>::put(0));
+  }
+};
+
+struct MapBase {
+  virtual ~MapBase() {}
+  virtual int integrate_depth(const orc_pinhole*, const double*, const float*, const uint8_t*, orc_frame_stats*) = 0;
+  virtual int integrate_points(const double*, const float*, int64_t, orc_frame_stats*) = 0;
+  virtual int raycast(const orc_pinhole*, const double*, float*) = 0;
+  virtual int64_t count_blocks(int64_t* n_voxels) = 0;
+  virtual int extract(int32_t*, uint8_t*, int64_t*, double*, double*, double*, double*) = 0;
+  virtual int block_stats(int32_t*, uint8_t*, double*, int64_t*, int64_t*) = 0;
+  virtual int resample(int, int, const double*, const double*, const double*, const double*, double*, double*,
+                       double*, double*) = 0;
+};
+
+template <class R, class Sto>
+struct Map : MapBase {
+  orc_params P;
+  int L;
+  R tau;
+  R v[kMaxLevels];        // voxel edge per level
+  int n[kMaxLevels];      // voxels per block side per level
+  float E_f;              // block edge (float), the unit of the fixed-point key coordinates
+  std::unordered_map<Key, Block<R, Sto>, KeyHash> blocks;
+
+  explicit Map(const orc_params& p) : P(p), L(p.n_levels) {
+    tau = (R)p.truncation;
+    float v0f = p.base_voxel / (float)(1 << (L - 1));
+    E_f = v0f * (float)kFineDim;
+    for (int l = 0; l < kMaxLevels; ++l) {
+      v[l] = (R)v0f * (R)(1 << l);
+      n[l] = kFineDim >> l;
+    }
+  }
+
+  static size_t vox(int n, int x, int y, int z) { return (size_t)x + (size_t)n * ((size_t)y + (size_t)n * z); }
+
+  // ---- allocation (Sec. 3.2): insert the blocks of a segment; new blocks start at the finest level (Sec. 3.2.1)
+  void allocate(const std::vector<Key>& cells, std::set<Key>& touched, orc_frame_stats* st) {
+    for (const Key& k : cells) {
+      touched.insert(k);
+      if (blocks.find(k) == blocks.end()) {
+        Block<R, Sto>& b = blocks[k];
+        b.level = 0;
+        b.resize(n[0], P.has_color != 0);
+        st->new_blocks++;
+      }
+    }
+  }
+
+  // ---- Eq. 3 with w_k = 1 in Welford's incremental form, and the Welford S2 update (Sec. 3.2.1).
+  // The running mean D + (d - D)/(W + 1) equals (W D + d)/(W + 1) of Eq. 3 in exact arithmetic; this form keeps a
+  // voxel that sees the same d again at exactly D, so its S2 stays exactly 0.
+  void update(Block<R, Sto>& b, size_t i, R d, const R* col) {
+    R W = b.W[i];
+    R D = (R)Store<Sto>::get(b.D[i]);
+    R Wn = W + (R)1;
+    R e = d - D;
+    R Dn = D + e / Wn;
+    b.S2[i] = b.S2[i] + e * (d - Dn);
+    b.D[i] = Store<Sto>::put(Dn);
+    b.W[i] = Wn;
+    if (col && P.has_color) {
+      for (int c = 0; c < 3; ++c) {
+        R C = (R)Store<Sto>::get(b.C[c][i]);
+        R ec = col[c] - C;
+        b.C[c][i] = Store<Sto>::put(C + ec / Wn);
+      }
+    }
+  }
+
+  // ---- block statistics (Sec. 3.2.1: "aggregated at the block level to obtain the mean variance of each block").
+  // Reading: the mean runs over observed voxels (W > 0); an unobserved voxel has no variance. Always double, voxel
+  // index order.
+  struct BStat {
+    int64_t n_obs, sum_w;
+    double vbar;
+  };
+  BStat stats(const Block<R, Sto>& b) const {
+    BStat s{0, 0, 0.0};
+    double acc = 0.0;
+    size_t nv = b.W.size();
+    for (size_t i = 0; i < nv; ++i) {
+      if (b.W[i] > (R)0) {
+        s.n_obs++;
+        s.sum_w += (int64_t)b.W[i];
+        acc += (double)b.S2[i] / (double)b.W[i];
+      }
+    }
+    s.vbar = s.n_obs ? acc / (double)s.n_obs : 0.0;
+    return s;
+  }
+
+  // ---- merge l -> l+1 (Sec. 3.2.1, Fig. 4a: a low-variance block is re-allocated at a coarser resolution).
+  // Reading: each coarse voxel pools its 2x2x2 observed children: D and colour are W-weighted means, sigma^2 is the
+  // W-weighted mean of child variances, W is the largest child weight, S2 = sigma^2 W.
+  void merge(Block<R, Sto>& b) {
+    int nf = n[b.level], nc = nf / 2;
+    Block<R, Sto> c;
+    c.level = b.level + 1;
+    c.resize(nc, P.has_color != 0);
+    for (int z = 0; z < nc; ++z)
+      for (int y = 0; y < nc; ++y)
+        for (int x = 0; x < nc; ++x) {
+          R sw = 0, swd = 0, ss2 = 0, wmax = 0, swc[3] = {0, 0, 0};
+          for (int k = 0; k < 8; ++k) {
+            size_t ch = vox(nf, 2 * x + (k & 1), 2 * y + ((k >> 1) & 1), 2 * z + (k >> 2));
+            R Wi = b.W[ch];
+            if (!(Wi > (R)0)) continue;
+            sw = sw + Wi;
+            swd = swd + Wi * (R)Store<Sto>::get(b.D[ch]);
+            ss2 = ss2 + b.S2[ch];
+            if (Wi > wmax) wmax = Wi;
+            if (P.has_color)
+              for (int q = 0; q < 3; ++q) swc[q] = swc[q] + Wi * (R)Store<Sto>::get(b.C[q][ch]);
+          }
+          size_t o = vox(nc, x, y, z);
+          if (sw > (R)0) {
+            R var = ss2 / sw;
+            c.D[o] = Store<Sto>::put(swd / sw);
+            c.W[o] = wmax;
+            c.S2[o] = var * wmax;
+            if (P.has_color)
+              for (int q = 0; q < 3; ++q) c.C[q][o] = Store<Sto>::put(swc[q] / sw);
+          }
+        }
+    b = std::move(c);
+  }
+
+  // ---- split l -> l-1 (extension: the inverse of the merge, for blocks whose variance has grown again).
+  // Reading: each fine voxel takes the trilinear interpolation of the coarse D and colour at its centre over observed
+  // coarse voxels of this block (clamped to the block, weights renormalised); W and S2 are copied from the coarse
+  // voxel that contains it.
+  void split(Block<R, Sto>& b) {
+    int nc = n[b.level], nf = nc * 2;
+    Block<R, Sto> f;
+    f.level = b.level - 1;
+    f.resize(nf, P.has_color != 0);
+    for (int z = 0; z < nf; ++z)
+      for (int y = 0; y < nf; ++y)
+        for (int x = 0; x < nf; ++x) {
+          int fi[3] = {x, y, z}, i0[3];
+          R fr[3];
+          for (int a = 0; a < 3; ++a) {
+            R p = (R)fi[a] * (R)0.5 - (R)0.25;  // fine centre in coarse voxel-index coordinates
+            if (p < (R)0) p = (R)0;
+            if (p > (R)(nc - 1)) p = (R)(nc - 1);
+            int i = (int)std::floor(p);
+            if (i > nc - 2) i = nc - 2;
+            i0[a] = i;
+            fr[a] = p - (R)i;
+          }
+          R sw = 0, sd = 0, sc[3] = {0, 0, 0};
+          for (int k = 0; k < 8; ++k) {
+            int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+            size_t cv = vox(nc, i0[0] + ax, i0[1] + ay, i0[2] + az);
+            if (!(b.W[cv] > (R)0)) continue;
+            R wx = ax ? fr[0] : (R)1 - fr[0];
+            R wy = ay ? fr[1] : (R)1 - fr[1];
+            R wz = az ? fr[2] : (R)1 - fr[2];
+            R w = (wx * wy) * wz;
+            sw = sw + w;
+            sd = sd + w * (R)Store<Sto>::get(b.D[cv]);
+            if (P.has_color)
+              for (int q = 0; q < 3; ++q) sc[q] = sc[q] + w * (R)Store<Sto>::get(b.C[q][cv]);
+          }
+          size_t own = vox(nc, x >> 1, y >> 1, z >> 1);
+          size_t o = vox(nf, x, y, z);
+          if (sw > (R)0) {
+            f.D[o] = Store<Sto>::put(sd / sw);
+            if (P.has_color)
+              for (int q = 0; q < 3; ++q) f.C[q][o] = Store<Sto>::put(sc[q] / sw);
+          } else {
+            f.D[o] = b.D[own];
+            if (P.has_color)
+              for (int q = 0; q < 3; ++q) f.C[q][o] = b.C[q][own];
+          }
+          f.W[o] = b.W[own];
+          f.S2[o] = b.S2[own];
+        }
+    b = std::move(f);
+  }
+
+  // ---- re-level every touched block once (Sec. 3.2.1). Reading: a block may change level only after its observed
+  // voxels carry a mean weight of at least k_min (one frame gives S2 = 0 everywhere), and at most once per frame.
+  void relevel(const std::set<Key>& touched, orc_frame_stats* st) {
+    for (const Key& k : touched) {
+      Block<R, Sto>& b = blocks[k];
+      BStat s = stats(b);
+      if (s.n_obs == 0) continue;
+      if (s.sum_w < (int64_t)P.min_obs * s.n_obs) continue;
+      if (b.level < L - 1 && s.vbar < P.var_threshold[b.level]) {
+        merge(b);
+        st->merged++;
+      } else if (P.split_hysteresis > 0.0 && b.level > 0 &&
+                 s.vbar > P.split_hysteresis * P.var_threshold[b.level - 1]) {
+        split(b);
+        st->split++;
+      }
+    }
+  }
+
+  // ---- pose as float (f32s) or double (f64) rotation + translation
+  void pose(const double* T, R Rm[9], R t[3]) const {
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) Rm[3 * r + c] = (R)T[4 * r + c];
+      t[r] = (R)T[4 * r + 3];
+    }
+  }
+
+  // ---- camera integration (Sec. 3.1.2, Eq. 2)
+  int integrate_depth(const orc_pinhole* K, const double* T, const float* depth, const uint8_t* rgb,
+                      orc_frame_stats* st) override {
+    std::memset(st, 0, sizeof(*st));
+    // (1) rays and allocation. The key endpoints always follow this float sequence.
+    float Rf[9], tf[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) Rf[3 * r + c] = (float)T[4 * r + c];
+      tf[r] = (float)T[4 * r + 3];
+    }
+    const float tauf = P.truncation;
+    const float Sfix = 65536.0f / E_f;
+    std::set<Key> touched;
+    for (int v_ = 0; v_ < K->height; ++v_) {
+      for (int u = 0; u < K->width; ++u) {
+        float z = depth[(size_t)v_ * K->width + u];
+        if (!(z >= K->min_depth && z <= K->max_depth)) continue;
+        float qx = ((float)u - K->cx) / K->fx;
+        float qy = ((float)v_ - K->cy) / K->fy;
+        float nq = std::sqrt(qx * qx + qy * qy + 1.0f);
+        float rho = z * nq;
+        float rc[3] = {qx / nq, qy / nq, 1.0f / nq};
+        float r[3];
+        for (int a = 0; a < 3; ++a) r[a] = Rf[3 * a + 0] * rc[0] + Rf[3 * a + 1] * rc[1] + Rf[3 * a + 2] * rc[2];
+        float t0 = rho - tauf;
+        if (t0 < 0.0f) t0 = 0.0f;
+        float t1 = rho + tauf;
+        int64_t A[3], B[3];
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+          ok = ok && to_fixed_f(tf[a] + t0 * r[a], Sfix, &A[a]);
+          ok = ok && to_fixed_f(tf[a] + t1 * r[a], Sfix, &B[a]);
+        }
+        if (!ok) continue;
+        Key ka{floor_div(A[0], kBlockUnit), floor_div(A[1], kBlockUnit), floor_div(A[2], kBlockUnit)};
+        Key kb{floor_div(B[0], kBlockUnit), floor_div(B[1], kBlockUnit), floor_div(B[2], kBlockUnit)};
+        if (!key_in_range(ka) || !key_in_range(kb)) continue;
+        st->valid_rays++;
+        allocate(cells_bruteforce(A, B, kBlockUnit), touched, st);
+      }
+    }
+    st->touched = (int64_t)touched.size();
+    // (2) projective fusion of every voxel of every touched block.
+    R Rm[9], t[3];
+    pose(T, Rm, t);
+    const R fx = (R)K->fx, fy = (R)K->fy, cx = (R)K->cx, cy = (R)K->cy;
+    const R E = (R)E_f;
+    for (const Key& k : touched) {
+      Block<R, Sto>& b = blocks[k];
+      int l = b.level, nl = n[l];
+      R vl = v[l];
+      R ob[3] = {(R)k.x * E - t[0], (R)k.y * E - t[1], (R)k.z * E - t[2]};  // block corner relative to the camera
+      for (int zi = 0; zi < nl; ++zi)
+        for (int yi = 0; yi < nl; ++yi)
+          for (int xi = 0; xi < nl; ++xi) {
+            R w[3] = {ob[0] + ((R)xi + (R)0.5) * vl, ob[1] + ((R)yi + (R)0.5) * vl, ob[2] + ((R)zi + (R)0.5) * vl};
+            R xc = Rm[0] * w[0] + Rm[3] * w[1] + Rm[6] * w[2];
+            R yc = Rm[1] * w[0] + Rm[4] * w[1] + Rm[7] * w[2];
+            R zc = Rm[2] * w[0] + Rm[5] * w[1] + Rm[8] * w[2];
+            if (!(zc > (R)0)) continue;
+            R uf = fx * xc / zc + cx + (R)0.5;
+            R vf = fy * yc / zc + cy + (R)0.5;
+            if (!(uf >= (R)0 && uf < (R)K->width && vf >= (R)0 && vf < (R)K->height)) continue;
+            int u = (int)std::floor(uf), vv = (int)std::floor(vf);
+            size_t pix = (size_t)vv * K->width + u;
+            float zm = depth[pix];
+            if (!(zm >= K->min_depth && zm <= K->max_depth)) continue;
+            R qx = ((R)u - cx) / fx, qy = ((R)vv - cy) / fy;
+            R rho = (R)zm * std::sqrt(qx * qx + qy * qy + (R)1);
+            R dist = std::sqrt(xc * xc + yc * yc + zc * zc);
+            // Eq. 2: d = rho - |x|. Reading: rho is the measured range along the pixel ray (z-depth times the ray
+            // length at unit z), so both terms are ranges. A voxel more than tau behind the surface is occluded and
+            // not updated; otherwise d is clipped to tau.
+            R eta = rho - dist;
+            if (eta < -tau) continue;
+            R d = eta < tau ? eta : tau;
+            R col[3];
+            if (rgb) for (int q = 0; q < 3; ++q) col[q] = (R)rgb[3 * pix + q];
+            update(b, vox(nl, xi, yi, zi), d, rgb ? col : nullptr);
+            st->observations++;
+          }
+    }
+    // (3) block variance and re-levelling
+    relevel(touched, st);
+    return 0;
+  }
+
+  // ---- LiDAR integration (Sec. 3.1.1, Eq. 1)
+  int integrate_points(const double* T, const float* xyz, int64_t npts, orc_frame_stats* st) override {
+    std::memset(st, 0, sizeof(*st));
+    const double tau_d = (double)P.truncation;
+    const double Sfix = 65536.0 / (double)E_f;
+    const double rmin2 = (double)P.min_range * (double)P.min_range, rmax2 = (double)P.max_range * (double)P.max_range;
+    struct RayRec {
+      int64_t A[3], B[3];
+      double rho, rhat[3];
+    };
+    std::vector<RayRec> rays;
+    std::vector<int64_t> ray_index;
+    std::set<Key> touched;
+    // (1) rays (double) and allocation
+    for (int64_t j = 0; j < npts; ++j) {
+      double xs[3] = {(double)xyz[3 * j], (double)xyz[3 * j + 1], (double)xyz[3 * j + 2]};
+      double n2 = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
+      if (!(n2 >= rmin2 && n2 <= rmax2)) continue;
+      double p[3], dv[3];
+      for (int a = 0; a < 3; ++a) {
+        p[a] = T[4 * a + 0] * xs[0] + T[4 * a + 1] * xs[1] + T[4 * a + 2] * xs[2] + T[4 * a + 3];
+        dv[a] = p[a] - T[4 * a + 3];
+      }
+      RayRec rr;
+      rr.rho = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      for (int a = 0; a < 3; ++a) rr.rhat[a] = dv[a] / rr.rho;
+      double t0 = rr.rho - tau_d;
+      if (t0 < 0.0) t0 = 0.0;
+      double t1 = rr.rho + tau_d;
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        ok = ok && to_fixed_d(T[4 * a + 3] + t0 * rr.rhat[a], Sfix, &rr.A[a]);
+        ok = ok && to_fixed_d(T[4 * a + 3] + t1 * rr.rhat[a], Sfix, &rr.B[a]);
+      }
+      if (!ok) continue;
+      Key ka{floor_div(rr.A[0], kBlockUnit), floor_div(rr.A[1], kBlockUnit), floor_div(rr.A[2], kBlockUnit)};
+      Key kb{floor_div(rr.B[0], kBlockUnit), floor_div(rr.B[1], kBlockUnit), floor_div(rr.B[2], kBlockUnit)};
+      if (!key_in_range(ka) || !key_in_range(kb)) continue;
+      st->valid_rays++;
+      allocate(cells_bruteforce(rr.A, rr.B, kBlockUnit), touched, st);
+      rays.push_back(rr);
+      ray_index.push_back(j);
+    }
+    st->touched = (int64_t)touched.size();
+    // (2) ray-based fusion: each ray walks the voxels of its truncation band in ascending point index; a voxel at
+    // level l is observed once per ray that crosses it (any of its finest-level cells).
+    R Rm[9], t[3];
+    pose(T, Rm, t);
+    (void)Rm;
+    const R E = (R)E_f;
+    for (size_t q = 0; q < rays.size(); ++q) {
+      const RayRec& rr = rays[q];
+      std::vector<Key> fine = cells_dda(rr.A, rr.B, kVoxelUnit);
+      R rho = (R)rr.rho;
+      R rh[3] = {(R)rr.rhat[0], (R)rr.rhat[1], (R)rr.rhat[2]};
+      bool have_prev = false;
+      Key prev_b{0, 0, 0};
+      int64_t prev_g[3] = {0, 0, 0};
+      for (const Key& f : fine) {
+        Key bk{floor_div(f.x, kFineDim), floor_div(f.y, kFineDim), floor_div(f.z, kFineDim)};
+        auto it = blocks.find(bk);
+        if (it == blocks.end()) continue;
+        Block<R, Sto>& b = it->second;
+        int l = b.level;
+        int64_t g[3] = {floor_div(f.x, (int64_t)1 << l), floor_div(f.y, (int64_t)1 << l),
+                        floor_div(f.z, (int64_t)1 << l)};
+        if (have_prev && prev_b == bk && prev_g[0] == g[0] && prev_g[1] == g[1] && prev_g[2] == g[2]) continue;
+        have_prev = true;
+        prev_b = bk;
+        std::memcpy(prev_g, g, sizeof(g));
+        int nl = n[l];
+        int li[3] = {(int)(g[0] - bk.x * nl), (int)(g[1] - bk.y * nl), (int)(g[2] - bk.z * nl)};
+        // Eq. 1: d = clip((p - x) . n, -tau, tau). With p = o + rho n and |n| = 1 this is rho - (x - o) . n.
+        R xr[3];
+        R ob[3] = {(R)bk.x * E - t[0], (R)bk.y * E - t[1], (R)bk.z * E - t[2]};
+        for (int a = 0; a < 3; ++a) xr[a] = ob[a] + ((R)li[a] + (R)0.5) * v[l];
+        R d = rho - (xr[0] * rh[0] + xr[1] * rh[1] + xr[2] * rh[2]);
+        if (d < -tau) d = -tau;
+        if (d > tau) d = tau;
+        update(b, vox(nl, li[0], li[1], li[2]), d, nullptr);
+        st->observations++;
+      }
+    }
+    relevel(touched, st);
+    return 0;
+  }
+
+  // ---- raycast (the rendering branch of Fig. 2): first +/- zero crossing of the trilinear TSDF along each pixel ray.
+  // Reading (the paper renders through Gaussian splats and gives no raycaster): march from min to max depth; skip
+  // whole unallocated blocks; inside a block of level l sample every min(v_l, tau/2); the field is trilinear over the
+  // 8 nearest voxel centres of that level's grid, a corner in another block uses that block's voxel containing the
+  // corner centre (any level); a sample counts only when all 8 corners are observed; on the first sign change take
+  // the linear root, evaluate there once more and take one more secant step. Output z-depth; 0 = no hit.
+  const Block<R, Sto>* find(const Key& k) const {
+    auto it = blocks.find(k);
+    return it == blocks.end() ? nullptr : &it->second;
+  }
+
+  bool field(const R x[3], int l, R* out) const {
+    R inv = (R)1 / v[l];
+    int64_t j0[3];
+    R fr[3];
+    for (int a = 0; a < 3; ++a) {
+      R g = x[a] * inv - (R)0.5;
+      R fl = std::floor(g);
+      j0[a] = (int64_t)fl;
+      fr[a] = g - fl;
+    }
+    R acc = 0;
+    for (int k = 0; k < 8; ++k) {
+      int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+      int64_t j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
+      int nl = n[l];
+      Key bk{floor_div(j[0], nl), floor_div(j[1], nl), floor_div(j[2], nl)};
+      const Block<R, Sto>* b = find(bk);
+      if (!b) return false;
+      size_t idx;
+      if (b->level == l) {
+        idx = vox(nl, (int)(j[0] - bk.x * nl), (int)(j[1] - bk.y * nl), (int)(j[2] - bk.z * nl));
+      } else {
+        // finest-level cell that holds the corner centre, then the voxel of block bk's level containing it
+        int lb = b->level, nb = n[lb];
+        int64_t cf[3];
+        for (int a = 0; a < 3; ++a) cf[a] = l == 0 ? j[a] : j[a] * ((int64_t)1 << l) + ((int64_t)1 << (l - 1));
+        idx = vox(nb, (int)(floor_div(cf[0], (int64_t)1 << lb) - bk.x * nb),
+                  (int)(floor_div(cf[1], (int64_t)1 << lb) - bk.y * nb),
+                  (int)(floor_div(cf[2], (int64_t)1 << lb) - bk.z * nb));
+      }
+      if (!(b->W[idx] > (R)0)) return false;
+      R wx = ax ? fr[0] : (R)1 - fr[0];
+      R wy = ay ? fr[1] : (R)1 - fr[1];
+      R wz = az ? fr[2] : (R)1 - fr[2];
+      acc = acc + ((wx * wy) * wz) * (R)Store<Sto>::get(b->D[idx]);
+    }
+    *out = acc;
+    return true;
+  }
+
+  // sample at parameter t: returns false when the block is unallocated; *valid tells whether the field exists
+  bool sample(const R o[3], const R r[3], R t, R invE, int* level, bool* valid, R* F) const {
+    R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+    Key bk{(int64_t)std::floor(x[0] * invE), (int64_t)std::floor(x[1] * invE), (int64_t)std::floor(x[2] * invE)};
+    const Block<R, Sto>* b = find(bk);
+    if (!b) return false;
+    *level = b->level;
+    *valid = field(x, b->level, F);
+    return true;
+  }
+
+  int raycast(const orc_pinhole* K, const double* T, float* out) override {
+    R Rm[9], o[3];
+    pose(T, Rm, o);
+    const R fx = (R)K->fx, fy = (R)K->fy, cx = (R)K->cx, cy = (R)K->cy;
+    const R E = (R)E_f, invE = (R)1 / E;
+    const R half_tau = tau * (R)0.5;
+    for (int vv = 0; vv < K->height; ++vv)
+      for (int u = 0; u < K->width; ++u) {
+        R qx = ((R)u - cx) / fx, qy = ((R)vv - cy) / fy;
+        R nq = std::sqrt(qx * qx + qy * qy + (R)1);
+        R rc[3] = {qx / nq, qy / nq, (R)1 / nq};
+        R r[3];
+        for (int a = 0; a < 3; ++a) r[a] = Rm[3 * a + 0] * rc[0] + Rm[3 * a + 1] * rc[1] + Rm[3 * a + 2] * rc[2];
+        R t = (R)K->min_depth * nq, t_far = (R)K->max_depth * nq;
+        bool have_prev = false;
+        R t_prev = 0, F_prev = 0, hit = 0;
+        for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
+          int l = 0;
+          bool valid = false;
+          R F = 0;
+          if (!sample(o, r, t, invE, &l, &valid, &F)) {
+            // leave the empty block: smallest parameter at which the ray reaches one of its far faces
+            R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+            R t_exit = t_far + (R)1;
+            for (int a = 0; a < 3; ++a) {
+              if (r[a] == (R)0) continue;
+              R bf = std::floor(x[a] * invE);
+              R face = (r[a] > (R)0 ? bf + (R)1 : bf) * E;
+              R ta = (face - o[a]) / r[a];
+              if (ta < t_exit) t_exit = ta;
+            }
+            R step_min = t + (R)1e-4 * E;
+            R tn = t_exit + (R)1e-4 * E;
+            t = tn > step_min ? tn : step_min;
+            have_prev = false;
+            continue;
+          }
+          if (valid && have_prev && F_prev > (R)0 && !(F > (R)0)) {
+            R ta = t_prev, Fa = F_prev, tb = t, Fb = F;
+            R ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+            int l2 = 0;
+            bool v2 = false;
+            R F2 = 0;
+            if (sample(o, r, ts, invE, &l2, &v2, &F2) && v2) {
+              if (F2 > (R)0) { ta = ts; Fa = F2; } else { tb = ts; Fb = F2; }
+              if (Fa - Fb > (R)0) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+            }
+            hit = ts * rc[2];
+            break;
+          }
+          have_prev = valid;
+          if (valid) { t_prev = t; F_prev = F; }
+          R s = v[l] < half_tau ? v[l] : half_tau;
+          t = t + s;
+        }
+        out[(size_t)vv * K->width + u] = (float)hit;
+      }
+    return 0;
+  }
+
+  // ---- read-out, sorted by key (x, then y, then z)
+  std::vector<Key> sorted_keys() const {
+    std::vector<Key> ks;
+    ks.reserve(blocks.size());
+    for (auto& kv : blocks) ks.push_back(kv.first);
+    std::sort(ks.begin(), ks.end());
+    return ks;
+  }
+
+  int64_t count_blocks(int64_t* n_voxels) override {
+    int64_t nv = 0;
+    for (auto& kv : blocks) nv += (int64_t)kv.second.W.size();
+    if (n_voxels) *n_voxels = nv;
+    return (int64_t)blocks.size();
+  }
+
+  int extract(int32_t* keys, uint8_t* levels, int64_t* offsets, double* D, double* W, double* S2,
+              double* C) override {
+    std::vector<Key> ks = sorted_keys();
+    int64_t off = 0;
+    for (size_t i = 0; i < ks.size(); ++i) {
+      const Block<R, Sto>& b = blocks.at(ks[i]);
+      keys[3 * i] = (int32_t)ks[i].x;
+      keys[3 * i + 1] = (int32_t)ks[i].y;
+      keys[3 * i + 2] = (int32_t)ks[i].z;
+      levels[i] = (uint8_t)b.level;
+      offsets[i] = off;
+      for (size_t j = 0; j < b.W.size(); ++j) {
+        D[off + j] = (double)Store<Sto>::get(b.D[j]);
+        W[off + j] = (double)b.W[j];
+        S2[off + j] = (double)b.S2[j];
+        if (C)
+          for (int q = 0; q < 3; ++q) C[3 * (off + j) + q] = P.has_color ? (double)Store<Sto>::get(b.C[q][j]) : 0.0;
+      }
+      off += (int64_t)b.W.size();
+    }
+    offsets[ks.size()] = off;
+    return 0;
+  }
+
+  int block_stats(int32_t* keys, uint8_t* levels, double* vbar, int64_t* n_obs, int64_t* sum_w) override {
+    std::vector<Key> ks = sorted_keys();
+    for (size_t i = 0; i < ks.size(); ++i) {
+      const Block<R, Sto>& b = blocks.at(ks[i]);
+      BStat s = stats(b);
+      keys[3 * i] = (int32_t)ks[i].x;
+      keys[3 * i + 1] = (int32_t)ks[i].y;
+      keys[3 * i + 2] = (int32_t)ks[i].z;
+      levels[i] = (uint8_t)b.level;
+      vbar[i] = s.vbar;
+      n_obs[i] = s.n_obs;
+      sum_w[i] = s.sum_w;
+    }
+    return 0;
+  }
+
+  // ---- test hook: load one block payload, apply merge (dir = +1) or split (dir = -1), read it back
+  int resample(int level, int dir, const double* D, const double* W, const double* S2, const double* C, double* oD,
+               double* oW, double* oS2, double* oC) {
+    if (level < 0 || level >= L || (dir > 0 && level >= L - 1) || (dir < 0 && level == 0)) return -1;
+    Block<R, Sto> b;
+    b.level = level;
+    b.resize(n[level], P.has_color != 0);
+    for (size_t i = 0; i < b.W.size(); ++i) {
+      b.D[i] = Store<Sto>::put((R)D[i]);
+      b.W[i] = (R)W[i];
+      b.S2[i] = (R)S2[i];
+      if (P.has_color)
+        for (int q = 0; q < 3; ++q) b.C[q][i] = Store<Sto>::put((R)C[3 * i + q]);
+    }
+    if (dir > 0) merge(b); else split(b);
+    for (size_t i = 0; i < b.W.size(); ++i) {
+      oD[i] = (double)Store<Sto>::get(b.D[i]);
+      oW[i] = (double)b.W[i];
+      oS2[i] = (double)b.S2[i];
+      if (oC)
+        for (int q = 0; q < 3; ++q) oC[3 * i + q] = P.has_color ? (double)Store<Sto>::get(b.C[q][i]) : 0.0;
+    }
+    return 0;
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------ C interface
+
+extern "C" {
+
+void* orc_create(const orc_params* p) {
+  if (!p || p->n_levels < 1 || p->n_levels > kMaxLevels || !(p->base_voxel > 0) || !(p->truncation > 0)) return nullptr;
+  if (p->precision == 1) return new Map<double, double>(*p);
+  if (p->fp16) return new Map<float, _Float16>(*p);
+  return new Map<float, float>(*p);
+}
+
+void orc_destroy(void* h) { delete (MapBase*)h; }
+
+int orc_integrate_depth(void* h, const orc_pinhole* K, const double* T_wc, const float* depth, const uint8_t* rgb,
+                        orc_frame_stats* st) {
+  return ((MapBase*)h)->integrate_depth(K, T_wc, depth, rgb, st);
+}
+
+int orc_integrate_points(void* h, const double* T_ws, const float* xyz, int64_t n, orc_frame_stats* st) {
+  return ((MapBase*)h)->integrate_points(T_ws, xyz, n, st);
+}
+
+int orc_raycast(void* h, const orc_pinhole* K, const double* T_wc, float* depth_out) {
+  return ((MapBase*)h)->raycast(K, T_wc, depth_out);
+}
+
+int64_t orc_count_blocks(void* h, int64_t* n_voxels) { return ((MapBase*)h)->count_blocks(n_voxels); }
+
+int orc_extract(void* h, int32_t* keys, uint8_t* levels, int64_t* offsets, double* D, double* W, double* S2,
+                double* C) {
+  return ((MapBase*)h)->extract(keys, levels, offsets, D, W, S2, C);
+}
+
+int orc_block_stats(void* h, int32_t* keys, uint8_t* levels, double* vbar, int64_t* n_obs, int64_t* sum_w) {
+  return ((MapBase*)h)->block_stats(keys, levels, vbar, n_obs, sum_w);
+}
+
+// Geometry helpers exposed for the pin tests: cells of the closed fixed-point segment A -> B with cell edge U.
+// mode 0 = bounding-box test of every cell, mode 1 = ordered walk. Returns the count (cells written up to cap).
+int64_t orc_segment_cells(const int64_t* A, const int64_t* B, int64_t U, int mode, int64_t* out, int64_t cap) {
+  std::vector<Key> c = mode == 0 ? cells_bruteforce(A, B, U) : cells_dda(A, B, U);
+  for (size_t i = 0; i < c.size() && (int64_t)i < cap; ++i) {
+    out[3 * i] = c[i].x;
+    out[3 * i + 1] = c[i].y;
+    out[3 * i + 2] = c[i].z;
+  }
+  return (int64_t)c.size();
+}
+
+float orc_half_round(float x) { return half_round(x); }
+
+// Test hook: the merge (dir = +1) or split (dir = -1) payload rule applied to one block of the given level.
+int orc_resample_block(void* h, int level, int dir, const double* D, const double* W, const double* S2,
+                       const double* C, double* oD, double* oW, double* oS2, double* oC) {
+  return ((MapBase*)h)->resample(level, dir, D, W, S2, C, oD, oW, oS2, oC);
+}
+
+}  // extern "C"
