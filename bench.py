@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame hot path: integrated points/s and frames/s on the RGB-D sequence (640x480, 3 levels
+1/2/4 cm, tau 12 cm, 2^20-slot hash, colour, FP32 storage; a 640x480 raycast every frame), with a LiDAR line
+(128 x 2048 = 262,144 points per scan, FP16 storage) and the HBM roofline of the fusion kernel.
+
+A step is one frame: allocation, fusion + block variance + re-levelling, heap release, and the raycast of that frame's
+view. Inputs are seeded synthetic frames (the paper's RGB-D and LiDAR datasets are not available), generated before
+timing and resident in HBM. Every step is timed with CUDA events on the launching stream; L2 is flushed (a 256 MiB
+write) between steps, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) each rank integrates its own replica of the sequence on its own
+GPU (no data exchange): weak scaling, value = all ranks' points / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "integrated points/s & frames/s (RGB-D 640x480, LiDAR 262k pts) vs HBM roofline"
+FALLBACK_HBM_GBS = 6400.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=290)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--lidar-steps", type=int, default=40)
+    ap.add_argument("--no-lidar", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------------------- helpers
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def camera_frames(wl, start, count):
+    scene = wl.scene()
+    return [synth.render_depth(wl, start + k, scene=scene) for k in range(count)]
+
+
+def fuse_bytes_camera(stats, wl, s_v):
+    """Algorithmic bytes of one camera fusion launch: the depth (+ colour) image once, every touched block's payload
+    read and written once, its 16-byte hash entry read, and the entry of every new block written."""
+    img = wl.width * wl.height * (4 + (3 if wl.has_color else 0))
+    payload = sum(2 * ((8 >> l) ** 3) * s_v * n for l, n in enumerate(stats["touched_level"]))
+    return img + payload + 16 * stats["touched"] + 16 * stats["new_blocks"]
+
+
+def voxel_bytes(wl):
+    if wl.fp16:
+        return 2 + (6 if wl.has_color else 0) + 8
+    return 12 + (12 if wl.has_color else 0)
+
+
+# ----------------------------------------------------------------------------------------------------- GPU arm
+
+def run_camera_gpu(wl, frames, warmup, steps, flush):
+    import torch
+    import paper_2511_21459_b300 as mrh
+    K = mrh.pinhole_from(wl)
+    m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
+    dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
+    out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(warmup):
+        d, c, T = dev[k]
+        m.integrate_depth(K, T, d, c)
+        m.raycast(K, T, out)
+    torch.cuda.synchronize()
+    m.set_profiling(True)
+    m.profile(reset=True)
+    times, rays, fbytes = [], 0, 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        d, c, T = dev[warmup + k]
+        ev[k][0].record(stream)
+        m.integrate_depth(K, T, d, c)
+        m.raycast(K, T, out)
+        ev[k][1].record(stream)
+        st = m.stats()  # synchronises (outside the timed events)
+        if st["status_code"] != 0:
+            raise RuntimeError(f"map status {st['status_code']} at step {k}")
+        rays += st["valid_rays"]
+        fbytes += fuse_bytes_camera(st, wl, voxel_bytes(wl))
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    prof = m.profile()
+    final = m.stats()
+    m.close()
+    return dict(ms=sum(times), ms_steps=times, rays=rays, fuse_bytes=fbytes, prof=prof, final=final)
+
+
+def run_camera_e2e(wl, frames, warmup, steps):
+    """Same workload through the public API with host buffers: pinned host frame -> device, integrate, raycast,
+    raycast depth -> pinned host, every step inside the timed events."""
+    import torch
+    import paper_2511_21459_b300 as mrh
+    K = mrh.pinhole_from(wl)
+    m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
+    host = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(c).pin_memory(), T) for d, c, T in frames]
+    d_dev = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    c_dev = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    out_host = torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        d, c, T = host[k]
+        d_dev.copy_(d, non_blocking=True)
+        c_dev.copy_(c, non_blocking=True)
+        m.integrate_depth(K, T, d_dev, c_dev)
+        m.raycast(K, T, out)
+        out_host.copy_(out, non_blocking=True)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        step(warmup + k)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    m.close()
+    h2d = wl.width * wl.height * (4 + 3)
+    d2h = wl.width * wl.height * 4
+    return ms, h2d, d2h
+
+
+def run_lidar_gpu(wl, warmup, steps, flush):
+    import torch
+    import paper_2511_21459_b300 as mrh
+    scene = wl.scene()
+    scans = [synth.render_lidar(wl, k, scene=scene) for k in range(warmup + steps)]
+    dev = [(torch.from_numpy(x).cuda(), T) for x, T in scans]
+    m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
+    for k in range(warmup):
+        m.integrate_points(dev[k][1], dev[k][0])
+    torch.cuda.synchronize()
+    m.set_profiling(True)
+    m.profile(reset=True)
+    stream = torch.cuda.current_stream()
+    rays, ms, fbytes = 0, 0.0, 0
+    for k in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.integrate_points(dev[warmup + k][1], dev[warmup + k][0])
+        b.record(stream)
+        st = m.stats()
+        if st["status_code"] != 0:
+            raise RuntimeError(f"LiDAR map status {st['status_code']} at step {k}")
+        ms += a.elapsed_time(b)
+        rays += st["valid_rays"]
+        # algorithmic bytes of the fusion kernel (distinct observed voxels are bounded by the touched blocks):
+        # every touched block's payload read + written, its hash entry, and the scan's points once
+        s_v = voxel_bytes(wl)
+        fbytes += (12 * wl.n_beams * wl.n_azimuth + 16 * st["touched"] +
+                   sum(2 * ((8 >> l) ** 3) * s_v * n for l, n in enumerate(st["touched_level"])))
+    prof = m.profile()
+    m.close()
+    return dict(ms=ms, rays=rays, steps=steps, prof=prof, fuse_bytes=fbytes)
+
+
+# ----------------------------------------------------------------------------------------------------- CPU oracle
+
+def oracle_camera_sample(wl, frames, budget_s, max_frames):
+    """The CPU oracle (f32s mode, single thread) on the first frames of the same sequence: integrate + raycast."""
+    import oracle
+    om = oracle.OracleMap(oracle.params_from(wl, "f32s"))
+    K = oracle.pinhole_from(wl)
+    rays, t_total, n = 0, 0.0, 0
+    for depth, rgb, T in frames[:max_frames]:
+        t0 = time.perf_counter()
+        st = om.integrate_depth(K, T, depth, rgb)
+        om.raycast(K, T)
+        t_total += time.perf_counter() - t0
+        rays += st["valid_rays"]
+        n += 1
+        if t_total > budget_s:
+            break
+    om.close()
+    return rays, t_total, n
+
+
+def main():
+    args = parse_args()
+    wl = synth.rgbd()
+    hbm, peak_kind = peaks()
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        warm = min(args.warmup, 1)
+        frames = camera_frames(wl, 0, warm + min(args.steps, 200))
+        import oracle
+        om = oracle.OracleMap(oracle.params_from(wl, "f32s"))
+        K = oracle.pinhole_from(wl)
+        for depth, rgb, T in frames[:warm]:
+            om.integrate_depth(K, T, depth, rgb)
+            om.raycast(K, T)
+        rays, t_total, n = 0, 0.0, 0
+        budget = 150.0
+        for depth, rgb, T in frames[warm:]:
+            t0 = time.perf_counter()
+            st = om.integrate_depth(K, T, depth, rgb)
+            om.raycast(K, T)
+            t_total += time.perf_counter() - t0
+            rays += st["valid_rays"]
+            n += 1
+            if t_total > budget:
+                break
+        value = rays / t_total
+        sample = (f"frames {warm}..{warm + n - 1} of the RGB-D sequence after {warm} untimed, integrate + full "
+                  f"640x480 raycast per frame, oracle f32s mode, 1 thread (time-boxed at {budget:.0f} s)")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+                "steps": n, "warmup": warm, "ms_per_step": 1000.0 * t_total / n, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm) + 640x480 raycast"},
+                "frames_per_s": n / t_total,
+                "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    from paper_2511_21459_b300 import build
+    if rank == 0 or local == 0:
+        build.build()
+    barrier(world)
+
+    n_frames = args.warmup + args.steps
+    frames = camera_frames(wl, 0, n_frames)
+
+    # CPU baseline first (host only, before the GPU work is timed)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rays_c, t_c, n_c = oracle_camera_sample(wl, frames, args.cpu_budget_s, 8)
+        cpu = {"value": rays_c / t_c, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_c} frames of the RGB-D sequence, integrate + full 640x480 raycast each, f32s "
+                         f"mode, single thread ({t_c:.1f} s)"}
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    res = run_camera_gpu(wl, frames, args.warmup, args.steps, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+
+    ms_max = max_over_ranks(res["ms"], world)
+    rays_all = sum_over_ranks(res["rays"], world)
+    value = rays_all / (ms_max / 1000.0)
+    fps = world * args.steps / (ms_max / 1000.0)
+
+    prof = res["prof"]
+    step_ms_sum = res["ms"]
+    kernels = {g: {"ms_total": round(v[0], 4), "launches": int(v[1]), "share": round(v[0] / step_ms_sum, 4)}
+               for g, v in prof.items() if v[1] > 0}
+    launches = sum(v[1] for v in prof.values())
+    fuse_ms = prof["fuse"][0]
+    achieved = res["fuse_bytes"] / (fuse_ms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "fuse_depth_rgbd.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2511_21459_b300", "csrc", "mrh_fuse.cu"), "rb").read()
+        if tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = tr.get("dram_bytes_per_launch")
+    roofline = {"kernel": "k_fuse_depth (fusion + block variance + re-level)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "peak_kind": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_launch": int(res["fuse_bytes"] / args.steps),
+                "launch_ms_avg": round(fuse_ms / args.steps, 5)}
+
+    e2e = None
+    if world >= 1:
+        e_ms, h2d, d2h = run_camera_e2e(wl, frames, args.warmup, args.steps)
+        e_ms = max_over_ranks(e_ms, world)
+        e2e = {"value": rays_all / (e_ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps}
+
+    lidar = None
+    if not args.no_lidar:
+        lw = synth.lidar()
+        lres = run_lidar_gpu(lw, 3, args.lidar_steps, flush)
+        l_ms = max_over_ranks(lres["ms"], world)
+        l_rays = sum_over_ranks(lres["rays"], world)
+        lprof = lres["prof"]
+        lidar = {"value": l_rays / (l_ms / 1000.0), "unit": "points/s", "frames_per_s": world * lres["steps"] /
+                 (l_ms / 1000.0), "steps": lres["steps"], "ms_per_step": l_ms / lres["steps"],
+                 "workload": "lidar-128x2048-street (3 levels 5/10/20 cm, tau 60 cm, FP16 storage)",
+                 "kernels": {g: {"ms_total": round(v[0], 3), "launches": int(v[1])} for g, v in lprof.items()
+                             if v[1] > 0},
+                 "fuse_achieved_GBps": round(lres["fuse_bytes"] / (lprof["fuse"][0] / 1000.0) / 1e9, 1)}
+
+    if rank == 0:
+        final = res["final"]
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded procedural RGB-D room sequence; stands in for ScanNet/Replica)",
+                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm, 2^20 hash, colour, FP32 "
+                                       "storage) + 640x480 raycast per frame",
+                           "frames": f"{args.warmup}..{args.warmup + args.steps - 1} timed after {args.warmup} warm-up",
+                           "l2": "flushed between steps (256 MiB write outside the timed events)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
+                "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
+                "lidar": lidar}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,258 @@
+"""B300 (sm_103a) variance-adaptive hashed TSDF map: thin Python binding of libmrhash's C ABI (include/mrhash.h).
+
+Every step of the per-frame path runs in the library's CUDA kernels; this module only marshals arguments. PyTorch is
+used for device buffers and streams. There is no CPU fallback: if ``libmrhash.so`` is missing or cannot be loaded,
+importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmrhash.so")
+_lib = None
+
+MRH_STORAGE_FP32, MRH_STORAGE_FP16 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash table probe limit reached",
+          4: "block heap empty", 5: "per-frame list full", 6: "CUDA error", 7: "output buffer too small"}
+
+
+class MrhError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, 'unknown')} ({code})")
+
+
+class Params(ctypes.Structure):
+    """mrh_map_params"""
+    _fields_ = [("base_voxel_size", ctypes.c_float), ("n_levels", ctypes.c_int32), ("truncation", ctypes.c_float),
+                ("var_threshold", ctypes.c_double * 2), ("split_hysteresis", ctypes.c_double),
+                ("min_obs", ctypes.c_int32), ("hash_slots_log2", ctypes.c_uint32),
+                ("max_blocks", ctypes.c_uint32 * 3), ("max_touched", ctypes.c_uint32),
+                ("max_observations", ctypes.c_uint32), ("storage", ctypes.c_int32), ("has_color", ctypes.c_int32),
+                ("min_range", ctypes.c_float), ("max_range", ctypes.c_float)]
+
+
+class Pinhole(ctypes.Structure):
+    """mrh_pinhole"""
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("min_depth", ctypes.c_float),
+                ("max_depth", ctypes.c_float)]
+
+
+class Stats(ctypes.Structure):
+    """mrh_stats"""
+    _fields_ = [("frame", ctypes.c_uint64), ("valid_rays", ctypes.c_uint64), ("touched", ctypes.c_uint64),
+                ("new_blocks", ctypes.c_uint64), ("merged", ctypes.c_uint64), ("split", ctypes.c_uint64),
+                ("fp64_rechecks", ctypes.c_uint64), ("live_blocks", ctypes.c_uint64 * 3),
+                ("touched_level", ctypes.c_uint64 * 3), ("observations", ctypes.c_uint64), ("status", ctypes.c_uint32)]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("live_blocks", "touched_level")}
+        d["live_blocks"] = list(self.live_blocks)
+        d["touched_level"] = list(self.touched_level)
+        return d
+
+
+KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast"]
+
+
+EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points", "mrh_raycast",
+           "mrh_count_blocks", "mrh_extract_blocks", "mrh_get_stats", "mrh_sync", "mrh_clear_status", "mrh_set_profiling",
+           "mrh_get_profile", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error", "mrh_version"]
+
+
+def lib():
+    """Load libmrhash.so (fails loudly when it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmrhash.so not built ({LIB_PATH}); run `python -m paper_2511_21459_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        L.mrh_map_create.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]
+        L.mrh_map_destroy.argtypes = [vp]
+        L.mrh_integrate_depth.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp]
+        L.mrh_integrate_points.argtypes = [vp, vp, vp, u64, vp]
+        L.mrh_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp]
+        L.mrh_count_blocks.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
+        L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
+                                         ctypes.POINTER(u64), vp]
+        L.mrh_get_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+        L.mrh_sync.argtypes = [vp, vp]
+        L.mrh_clear_status.argtypes = [vp, vp]
+        L.mrh_set_profiling.argtypes = [vp, i32]
+        L.mrh_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), i32, i32, vp]
+        L.mrh_hash_slot.restype = ctypes.c_uint32
+        L.mrh_hash_slot.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
+        L.mrh_status_string.restype = ctypes.c_char_p
+        L.mrh_last_cuda_error.restype = ctypes.c_char_p
+        L.mrh_version.restype = ctypes.c_char_p
+        for name in ("mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points",
+                     "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_get_stats", "mrh_sync",
+                     "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        err = lib().mrh_last_cuda_error().decode()
+        raise MrhError(code, what + (f" [{err}]" if code == 6 and err else ""))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _pose(T) -> np.ndarray:
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(4, 4))
+    return T
+
+
+def hash_slot(x: int, y: int, z: int, log2_slots: int) -> int:
+    """Eq. 4 slot of block key (x, y, z) (host helper, no GPU needed)."""
+    return int(lib().mrh_hash_slot(x, y, z, log2_slots))
+
+
+def params_from(wl, storage: int | None = None, max_observations: int | None = None) -> Params:
+    """Map parameters for a workload description (``synth.Workload``)."""
+    p = Params()
+    p.base_voxel_size = wl.base_voxel
+    p.n_levels = wl.n_levels
+    p.truncation = wl.truncation
+    th = list(wl.var_threshold) + [0.0, 0.0]
+    p.var_threshold[0], p.var_threshold[1] = th[0], th[1]
+    p.split_hysteresis = wl.split_hysteresis
+    p.min_obs = wl.min_obs
+    p.hash_slots_log2 = wl.hash_log2
+    mb = list(wl.max_blocks) + [1, 1, 1]
+    for l in range(3):
+        p.max_blocks[l] = mb[l]
+    p.max_touched = wl.max_touched
+    if max_observations is None:
+        max_observations = (1 << 25) if wl.sensor == "lidar" else 0
+    p.max_observations = max_observations
+    p.storage = (MRH_STORAGE_FP16 if wl.fp16 else MRH_STORAGE_FP32) if storage is None else storage
+    p.has_color = int(wl.has_color)
+    p.min_range, p.max_range = wl.r_min, wl.r_max
+    return p
+
+
+def pinhole_from(wl) -> Pinhole:
+    k = Pinhole()
+    k.fx, k.fy, k.cx, k.cy = wl.fx, wl.fy, wl.cx, wl.cy
+    k.width, k.height = wl.width, wl.height
+    k.min_depth, k.max_depth = wl.min_depth, wl.max_depth
+    return k
+
+
+class Map:
+    """A map on one CUDA device. Inputs are CUDA tensors on that device; poses are 4x4 (or 16) float64 host arrays."""
+
+    def __init__(self, params: Params, device: int = 0):
+        self._lib = lib()
+        self.params = params
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self._lib.mrh_map_create(ctypes.byref(params), device, ctypes.byref(h)), "mrh_map_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mrh_map_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def integrate_depth(self, K: Pinhole, T_wc, depth, rgb=None, stream=None):
+        T = _pose(T_wc)
+        _check(self._lib.mrh_integrate_depth(self._h, ctypes.byref(K), ctypes.c_void_p(T.ctypes.data), _ptr(depth),
+                                             _ptr(rgb), _stream(stream)), "mrh_integrate_depth")
+
+    def integrate_points(self, T_ws, xyz, stream=None):
+        T = _pose(T_ws)
+        _check(self._lib.mrh_integrate_points(self._h, ctypes.c_void_p(T.ctypes.data), _ptr(xyz), xyz.shape[0],
+                                              _stream(stream)), "mrh_integrate_points")
+
+    def raycast(self, K: Pinhole, T_wc, out=None, stream=None):
+        import torch
+        T = _pose(T_wc)
+        if out is None:
+            out = torch.empty((K.height, K.width), dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(self._lib.mrh_raycast(self._h, ctypes.byref(K), ctypes.c_void_p(T.ctypes.data), _ptr(out),
+                                     _stream(stream)), "mrh_raycast")
+        return out
+
+    def count(self, stream=None):
+        nb, nv = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.mrh_count_blocks(self._h, ctypes.byref(nb), ctypes.byref(nv), _stream(stream)),
+               "mrh_count_blocks")
+        return nb.value, nv.value
+
+    def extract(self, stream=None) -> dict:
+        """All blocks sorted by key: keys (n,3) int32, levels (n,) uint8, offsets (n+1,) int64, D/W/S2 (V,) float32,
+        C (V,3) float32 (CUDA tensors)."""
+        import torch
+        nb, nv = self.count(stream)
+        dev = f"cuda:{self.device}"
+        out = dict(keys=torch.empty((max(nb, 1), 3), dtype=torch.int32, device=dev),
+                   levels=torch.empty(max(nb, 1), dtype=torch.uint8, device=dev),
+                   offsets=torch.zeros(nb + 1, dtype=torch.int64, device=dev),
+                   D=torch.empty(max(nv, 1), dtype=torch.float32, device=dev),
+                   W=torch.empty(max(nv, 1), dtype=torch.float32, device=dev),
+                   S2=torch.empty(max(nv, 1), dtype=torch.float32, device=dev),
+                   C=torch.empty((max(nv, 1), 3), dtype=torch.float32, device=dev))
+        wb, wv = ctypes.c_uint64(), ctypes.c_uint64()
+        code = self._lib.mrh_extract_blocks(self._h, _ptr(out["keys"]), _ptr(out["levels"]), _ptr(out["offsets"]),
+                                            _ptr(out["D"]), _ptr(out["W"]), _ptr(out["S2"]), _ptr(out["C"]),
+                                            max(nb, 1), max(nv, 1), ctypes.byref(wb), ctypes.byref(wv),
+                                            _stream(stream))
+        _check(code, "mrh_extract_blocks")
+        n, v = wb.value, wv.value
+        return dict(keys=out["keys"][:n], levels=out["levels"][:n], offsets=out["offsets"], D=out["D"][:v],
+                    W=out["W"][:v], S2=out["S2"][:v], C=out["C"][:v])
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        code = self._lib.mrh_get_stats(self._h, ctypes.byref(s), _stream(stream))
+        d = s.as_dict()
+        d["status_code"] = code
+        return d
+
+    def sync(self, stream=None):
+        _check(self._lib.mrh_sync(self._h, _stream(stream)), "mrh_sync")
+
+    def set_profiling(self, enable: bool):
+        _check(self._lib.mrh_set_profiling(self._h, int(enable)), "mrh_set_profiling")
+
+    def profile(self, reset: bool = False, stream=None) -> dict:
+        """{group: (device ms, launches)} accumulated since the last reset."""
+        n = len(KERNEL_GROUPS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_uint64 * n)()
+        _check(self._lib.mrh_get_profile(self._h, ms, cnt, n, int(reset), _stream(stream)), "mrh_get_profile")
+        return {g: (ms[i], cnt[i]) for i, g in enumerate(KERNEL_GROUPS)}
+
+    def clear_status(self, stream=None):
+        _check(self._lib.mrh_clear_status(self._h, _stream(stream)), "mrh_clear_status")

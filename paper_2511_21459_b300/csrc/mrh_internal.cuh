@@ -1,0 +1,277 @@
+// Internal definitions of libmrhash (not part of the C ABI).
+//
+// Device data layout (all in the map's own device memory, sized at map creation):
+//   slots[2^k]           16-byte hash entries {packed key, value, frame stamp}: one flat table for every level
+//                        (Sec. 3.2 "single hash table"; the entry's level selects the heap, Fig. 3)
+//   heap[l]              block payloads of level l, struct-of-arrays inside a block so that every field is a
+//                        contiguous, 16-byte aligned run: FP32 storage [D | W | S2 | R | G | B] float each,
+//                        FP16 storage [D | R | G | B] half then [W | S2] float
+//   free_stack[l]        ids of free blocks of level l (pops and pushes never share a kernel)
+//   touched_all          slots touched by the current frame (unique: the slot's frame stamp dedups)
+//   touched[l]           the same slots binned by level, the fusion work lists
+//   retire               heap ids released by re-levelling in this frame, pushed back after fusion
+//   DevState             counters, frame number and the sticky status word
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mrhash.h"
+
+namespace mrh {
+
+constexpr int kFineDim = 8;                       // voxels per block side at the finest level (512-voxel blocks)
+constexpr int kMaxLevels = 3;
+constexpr int kFracBits = 16;                     // fixed-point fraction bits per block edge
+constexpr long long kBlockUnit = 1LL << kFracBits;
+constexpr long long kVoxelUnit = kBlockUnit / kFineDim;
+constexpr long long kKeyLimit = (1LL << 20) - 2;  // |block coordinate| bound of the 21-bit packed key
+constexpr unsigned long long kEmptyKey = ~0ULL;
+constexpr uint32_t kValPending = 0xFFFFFFFFu;     // key present, no heap block yet
+constexpr uint32_t kPtrMask = 0x0FFFFFFFu;
+constexpr uint32_t kValNew = 1u << 30;            // heap block not yet initialised: fusion starts from zero state
+constexpr int kMaxProbeWindows = 64;              // warp-cooperative probing: 64 x 32 slots
+constexpr int kMaxProbes = 2048;                  // single-thread probing
+constexpr int kMaxSegmentCells = 64;
+constexpr int kMaxVoxelCells = 256;
+constexpr int kRaycastMaxIter = 8192;
+
+// status bits (sticky)
+constexpr uint32_t kStHashFull = 1u << 0;
+constexpr uint32_t kStPoolEmpty = 1u << 1;
+constexpr uint32_t kStListFull = 1u << 2;
+constexpr uint32_t kStSegment = 1u << 3;
+constexpr uint32_t kStObsFull = 1u << 4;
+
+struct __align__(16) Slot {
+  unsigned long long key;
+  uint32_t val;    // heap id (28 bits) | level << 28 | kValNew, or kValPending
+  uint32_t stamp;  // frame number of the last frame that touched the block
+};
+
+struct DevState {
+  int free_top[4];
+  uint32_t touched_all;
+  uint32_t touched_count[4];
+  uint32_t retire_count;
+  uint32_t frame;
+  uint32_t status;
+  uint32_t new_blocks, merged, split, rechecks, valid_rays;
+  uint32_t pad;
+  unsigned long long observations;
+};
+
+// Everything a kernel needs, passed by value.
+struct MapDev {
+  Slot* slots;
+  uint32_t slot_mask;
+  int L;
+  int fp16, color;
+  int min_obs;
+  uint8_t* heap[kMaxLevels];
+  uint32_t* free_stack[kMaxLevels];
+  uint32_t max_blocks[kMaxLevels];
+  uint32_t block_bytes[kMaxLevels];
+  uint32_t* touched_all;
+  uint32_t* touched[kMaxLevels];
+  uint32_t max_touched;
+  uint32_t* retire;
+  uint32_t* slot_pos;         // per slot: level << 28 | position in touched[level] (written by k_bin)
+  // LiDAR observation buffers (per frame)
+  uint32_t* blk_count;        // per touched block (levels concatenated): observations
+  uint32_t* blk_off;          // exclusive prefix of blk_count, one extra entry = total
+  uint32_t* blk_fill;
+  uint32_t* obs_key;          // ray << 9 | voxel index within the block
+  float* obs_d;
+  uint32_t* obs_idx;          // per-voxel bins of observation indices
+  uint32_t max_obs;
+  DevState* st;
+  float v[kMaxLevels];  // voxel edge per level
+  float E;              // block edge
+  float tau;
+  float fix_scale;      // 65536 / E (float), camera key quantisation
+  double fix_scale64;   // 65536 / E (double), LiDAR key quantisation
+  double theta[2];
+  double split_h;
+  float min_range, max_range;
+};
+
+struct CamArgs {
+  float fx, fy, cx, cy;
+  int width, height;
+  float min_depth, max_depth;
+  float R[9];  // world <- camera rotation, row-major
+  float t[3];
+};
+
+// ---------------------------------------------------------------------------------------------------- payload layout
+
+__host__ __device__ inline uint32_t block_bytes_for(int nv, int fp16, int color) {
+  return fp16 ? (uint32_t)nv * (2u + (color ? 6u : 0u) + 8u) : (uint32_t)nv * (12u + (color ? 12u : 0u));
+}
+// byte offsets of the fields inside one block of nv voxels
+__host__ __device__ inline uint32_t off_W(int nv, int fp16, int color) {
+  return fp16 ? (uint32_t)nv * (color ? 8u : 2u) : (uint32_t)nv * 4u;
+}
+__host__ __device__ inline uint32_t off_S2(int nv, int fp16, int color) { return off_W(nv, fp16, color) + nv * 4u; }
+__host__ __device__ inline uint32_t off_C(int nv, int fp16, int q) {
+  return fp16 ? (uint32_t)nv * (2u + 2u * q) : (uint32_t)nv * (12u + 4u * q);
+}
+
+// ---------------------------------------------------------------------------------------------------- keys and hashing
+
+__host__ __device__ inline unsigned long long pack_key(long long x, long long y, long long z) {
+  const long long b = 1LL << 20;
+  return ((unsigned long long)(x + b) << 42) | ((unsigned long long)(y + b) << 21) | (unsigned long long)(z + b);
+}
+__host__ __device__ inline void unpack_key(unsigned long long k, int* x, int* y, int* z) {
+  const long long b = 1LL << 20;
+  *x = (int)((long long)((k >> 42) & 0x1FFFFF) - b);
+  *y = (int)((long long)((k >> 21) & 0x1FFFFF) - b);
+  *z = (int)((long long)(k & 0x1FFFFF) - b);
+}
+
+// Eq. 4: H(x, y, z) = (x p1 xor y p2 xor z p3) mod n_hash, 32-bit unsigned arithmetic, n_hash a power of two.
+__host__ __device__ inline uint32_t hash_xyz(int x, int y, int z, uint32_t mask) {
+  return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349669u) ^ ((uint32_t)z * 83492791u)) & mask;
+}
+__host__ __device__ inline uint32_t hash_key(unsigned long long k, uint32_t mask) {
+  int x, y, z;
+  unpack_key(k, &x, &y, &z);
+  return hash_xyz(x, y, z, mask);
+}
+
+__host__ __device__ inline long long floor_div(long long a, long long b) {  // b > 0
+  long long q = a / b;
+  if ((a % b != 0) && (a < 0)) --q;
+  return q;
+}
+__host__ __device__ inline bool key_ok(long long x, long long y, long long z) {
+  return x >= -kKeyLimit && x <= kKeyLimit && y >= -kKeyLimit && y <= kKeyLimit && z >= -kKeyLimit &&
+         z <= kKeyLimit;
+}
+
+// float -> fixed point floor(v * S), refused when |v S| >= 2^40
+__device__ inline bool to_fixed_f(float v, float S, long long* out) {
+  float p = v * S;
+  if (!(fabsf(p) < 1099511627776.0f)) return false;
+  *out = (long long)floorf(p);
+  return true;
+}
+__device__ inline bool to_fixed_d(double v, double S, long long* out) {
+  double p = v * S;
+  if (!(fabs(p) < 1099511627776.0)) return false;
+  *out = (long long)floor(p);
+  return true;
+}
+
+__device__ inline void set_status(DevState* st, uint32_t bit) { atomicOr(&st->status, bit); }
+
+// Single-thread lookup (linear probing from H). Returns the slot index or -1.
+__device__ inline int lookup_slot(const Slot* slots, uint32_t mask, unsigned long long key) {
+  uint32_t h = hash_key(key, mask);
+  for (int p = 0; p < kMaxProbes; ++p) {
+    uint32_t s = (h + (uint32_t)p) & mask;
+    unsigned long long k = slots[s].key;
+    if (k == key) return (int)s;
+    if (k == kEmptyKey) return -1;
+  }
+  return -1;
+}
+
+// Exact cell walk over cells of edge U from A to B (fixed point). visit(cell) is called for every cell in order.
+// Returns false if more than max_cells cells would be visited.
+template <class F>
+__device__ inline bool walk_cells(const long long A[3], const long long B[3], long long U, int max_cells, F&& visit) {
+  long long cell[3], end[3], D[3], aD[3], N[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cell[i] = floor_div(A[i], U);
+    end[i] = floor_div(B[i], U);
+    D[i] = B[i] - A[i];
+    aD[i] = D[i] < 0 ? -D[i] : D[i];
+    N[i] = D[i] > 0 ? (cell[i] + 1) * U - A[i] : (D[i] < 0 ? A[i] - cell[i] * U : 0);
+  }
+  visit(cell);
+  for (int n = 1; n < max_cells; ++n) {
+    if (cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2]) return true;
+    int best = -1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (D[i] == 0) continue;
+      if (best < 0 || N[i] * aD[best] < N[best] * aD[i]) best = i;
+    }
+    bool tie[3], up = false, down = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tie[i] = D[i] != 0 && N[i] * aD[best] == N[best] * aD[i];
+      up |= tie[i] && D[i] > 0;
+      down |= tie[i] && D[i] < 0;
+    }
+    if (up) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (tie[i] && D[i] > 0) { cell[i] += 1; N[i] += U; }
+      visit(cell);
+    }
+    if (down) {
+      if (cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2]) return true;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (tie[i] && D[i] < 0) { cell[i] -= 1; N[i] += U; }
+      visit(cell);
+    }
+  }
+  return cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2];
+}
+
+struct PoseD {
+  double T[16];  // world <- sensor, row-major
+};
+
+// LiDAR ray of point j in double (Sec. 3.1 "3D Point Cloud"): origin o = sensor position, p = T x_s,
+// rho = |p - o|, n = (p - o) / rho; band end points o + max(rho - tau, 0) n and o + (rho + tau) n as fixed point.
+// Returns false for a point outside [min_range, max_range], non-finite, or out of key range.
+__device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* xyz, uint64_t j, long long A[3],
+                                 long long B[3], double* rho_out, double rhat[3]) {
+  double xs[3] = {(double)xyz[3 * j], (double)xyz[3 * j + 1], (double)xyz[3 * j + 2]};
+  double n2 = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
+  double rmin2 = (double)m.min_range * (double)m.min_range, rmax2 = (double)m.max_range * (double)m.max_range;
+  if (!(n2 >= rmin2 && n2 <= rmax2)) return false;
+  const double* T = P.T;
+  double dv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double p = T[4 * a + 0] * xs[0] + T[4 * a + 1] * xs[1] + T[4 * a + 2] * xs[2] + T[4 * a + 3];
+    dv[a] = p - T[4 * a + 3];
+  }
+  double rho = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  double tau = (double)m.tau;
+  double t0 = rho - tau;
+  if (t0 < 0.0) t0 = 0.0;
+  double t1 = rho + tau;
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    rhat[a] = dv[a] / rho;
+    ok = ok && to_fixed_d(T[4 * a + 3] + t0 * rhat[a], m.fix_scale64, &A[a]);
+    ok = ok && to_fixed_d(T[4 * a + 3] + t1 * rhat[a], m.fix_scale64, &B[a]);
+  }
+  *rho_out = rho;
+  return ok && key_ok(floor_div(A[0], kBlockUnit), floor_div(A[1], kBlockUnit), floor_div(A[2], kBlockUnit)) &&
+         key_ok(floor_div(B[0], kBlockUnit), floor_div(B[1], kBlockUnit), floor_div(B[2], kBlockUnit));
+}
+
+// ---------------------------------------------------------------------------------------------------- host side
+
+// launch helpers implemented in the .cu files
+void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, cudaStream_t s);
+void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s);
+void launch_bin(const MapDev& m, cudaStream_t s, int sms);
+void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, cudaStream_t s,
+                       int sms);
+void launch_fuse_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s, int sms);
+void launch_lidar_observations(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s,
+                               int sms);
+void launch_raycast(const MapDev& m, const CamArgs& c, float* out, cudaStream_t s);
+
+}  // namespace mrh

@@ -1,0 +1,620 @@
+// Map lifetime, per-frame orchestration and read-out: the C ABI of include/mrhash.h.
+//
+// A depth frame is five stream-ordered launches with no host round trip:
+//   k_begin        frame number + 1, per-frame counters to zero
+//   k_alloc_*      ray -> block allocation into the hash table, touched list           (mrh_alloc.cu)
+//   k_bin          new blocks get a level-0 heap block; touched slots binned by level  (mrh_alloc.cu)
+//   k_fuse_*       fusion + block variance + re-levelling                              (mrh_fuse.cu, mrh_lidar.cu)
+//   k_release      heap blocks freed by re-levelling go back to their free stacks
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mrh_internal.cuh"
+
+using namespace mrh;
+
+struct mrh_map {
+  int device = 0;
+  int sms = 148;
+  mrh_map_params p{};
+  MapDev d{};
+  // owned device allocations
+  std::vector<void*> allocs;
+  // per-kernel-group accounting
+  bool profiling = false;
+  double prof_ms[MRH_K_COUNT] = {};
+  uint64_t launches[MRH_K_COUNT] = {};
+  struct Pending {
+    int kid;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+mrh_status cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return MRH_ERR_CUDA;
+}
+
+#define MRH_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool finite_pose(const double* T) {
+  if (!T) return false;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(T[i])) return false;
+  return true;
+}
+
+mrh_status status_from_bits(uint32_t bits) {
+  if (bits & kStHashFull) return MRH_ERR_HASH_FULL;
+  if (bits & kStPoolEmpty) return MRH_ERR_POOL_EMPTY;
+  if (bits & kStListFull) return MRH_ERR_LIST_FULL;
+  if (bits & kStObsFull) return MRH_ERR_LIST_FULL;
+  if (bits & kStSegment) return MRH_ERR_INVALID_ARG;
+  return MRH_OK;
+}
+
+cudaEvent_t take_event(mrh_map* m) {
+  if (!m->event_pool.empty()) {
+    cudaEvent_t e = m->event_pool.back();
+    m->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel group with events when profiling; counts launches always.
+struct KernelScope {
+  mrh_map* m;
+  int kid;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  KernelScope(mrh_map* m_, int kid_, cudaStream_t s_, int n_launches) : m(m_), kid(kid_), s(s_) {
+    m->launches[kid] += (uint64_t)n_launches;
+    if (m->profiling) {
+      a = take_event(m);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~KernelScope() {
+    if (a) {
+      cudaEvent_t b = take_event(m);
+      cudaEventRecord(b, s);
+      m->pending.push_back({kid, a, b});
+    }
+  }
+};
+
+mrh_status collect_profile(mrh_map* m) {
+  for (auto& p : m->pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    m->prof_ms[p.kid] += ms;
+    m->event_pool.push_back(p.a);
+    m->event_pool.push_back(p.b);
+  }
+  m->pending.clear();
+  return MRH_OK;
+}
+
+__global__ void k_init_stack(uint32_t* stack, uint32_t cap) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) stack[i] = cap - 1 - i;
+}
+
+__global__ void k_begin(DevState* st) {
+  st->frame += 1;
+  st->touched_all = 0;
+  for (int l = 0; l < 4; ++l) st->touched_count[l] = 0;
+  st->retire_count = 0;
+  st->new_blocks = st->merged = st->split = st->rechecks = st->valid_rays = 0;
+  st->observations = 0;
+}
+
+__global__ void __launch_bounds__(256) k_release(MapDev m) {
+  const uint32_t n = m.st->retire_count;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t r = m.retire[i];
+    uint32_t l = r >> 28, id = r & kPtrMask;
+    int t = atomicAdd(&m.st->free_top[l], 1);
+    m.free_stack[l][t] = id;
+  }
+}
+
+// ---- read-out kernels
+
+__global__ void k_compact(MapDev m, unsigned long long* keys, uint32_t* slots_out, uint32_t* count, uint32_t cap) {
+  const uint32_t n = m.slot_mask + 1;
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    Slot sl = m.slots[s];
+    if (sl.key != kEmptyKey && sl.val != kValPending) {
+      uint32_t i = atomicAdd(count, 1u);
+      if (i < cap) {
+        keys[i] = sl.key;
+        slots_out[i] = s;
+      }
+    }
+  }
+}
+
+__global__ void k_pad_keys(unsigned long long* keys, uint32_t from, uint32_t to) {
+  for (uint32_t i = from + blockIdx.x * blockDim.x + threadIdx.x; i < to; i += gridDim.x * blockDim.x)
+    keys[i] = kEmptyKey;
+}
+
+// one compare-exchange step (k, j) of a bitonic sort, ascending
+__global__ void k_bitonic_step(unsigned long long* keys, uint32_t* vals, uint32_t n, uint32_t k, uint32_t j) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t p = i ^ j;
+    if (p <= i) continue;
+    bool asc = (i & k) == 0;
+    unsigned long long a = keys[i], b = keys[p];
+    if ((a > b) == asc) {
+      keys[i] = b;
+      keys[p] = a;
+      uint32_t t = vals[i];
+      vals[i] = vals[p];
+      vals[p] = t;
+    }
+  }
+}
+
+// exclusive scan of voxel counts over the sorted blocks (one CTA, chunks of 1024)
+__global__ void __launch_bounds__(1024) k_voxel_offsets(MapDev m, const uint32_t* slots, uint32_t n,
+                                                        unsigned long long* off) {
+  __shared__ unsigned long long s[1024];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n; base += 1024) {
+    uint32_t i = base + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) {
+      uint32_t l = (m.slots[slots[i]].val >> 28) & 3u;
+      int nl = kFineDim >> l;
+      v = (unsigned long long)(nl * nl * nl);
+    }
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      unsigned long long t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n) off[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[n] = carry;
+}
+
+__global__ void k_extract(MapDev m, const uint32_t* slots, uint32_t n, const unsigned long long* off, int32_t* keys,
+                          uint8_t* levels, unsigned long long* off_out, float* D, float* W, float* S2, float* C) {
+  for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+    Slot sl = m.slots[slots[b]];
+    uint32_t l = (sl.val >> 28) & 3u, ptr = sl.val & kPtrMask;
+    int nl = kFineDim >> l, nv = nl * nl * nl;
+    const uint8_t* blk = m.heap[l] + (size_t)ptr * m.block_bytes[l];
+    unsigned long long o = off[b];
+    if (threadIdx.x == 0) {
+      int x, y, z;
+      unpack_key(sl.key, &x, &y, &z);
+      keys[3 * b] = x;
+      keys[3 * b + 1] = y;
+      keys[3 * b + 2] = z;
+      levels[b] = (uint8_t)l;
+      off_out[b] = o;
+      if (b == n - 1) off_out[n] = off[n];
+    }
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      float dv = m.fp16 ? __half2float(reinterpret_cast<const __half*>(blk)[i]) : reinterpret_cast<const float*>(blk)[i];
+      D[o + i] = dv;
+      W[o + i] = reinterpret_cast<const float*>(blk + off_W(nv, m.fp16, m.color))[i];
+      S2[o + i] = reinterpret_cast<const float*>(blk + off_S2(nv, m.fp16, m.color))[i];
+      if (C) {
+        for (int q = 0; q < 3; ++q) {
+          float cv = 0.f;
+          if (m.color) {
+            const uint8_t* pc = blk + off_C(nv, m.fp16, q);
+            cv = m.fp16 ? __half2float(reinterpret_cast<const __half*>(pc)[i]) : reinterpret_cast<const float*>(pc)[i];
+          }
+          C[3 * (o + i) + q] = cv;
+        }
+      }
+    }
+  }
+}
+
+mrh_status validate_params(const mrh_map_params* p) {
+  if (!p) return MRH_ERR_INVALID_ARG;
+  if (p->n_levels < 1 || p->n_levels > kMaxLevels) return MRH_ERR_INVALID_ARG;
+  if (!(p->base_voxel_size > 0.f) || !std::isfinite(p->base_voxel_size)) return MRH_ERR_INVALID_ARG;
+  if (!(p->truncation > 0.f) || !std::isfinite(p->truncation)) return MRH_ERR_INVALID_ARG;
+  float v0 = p->base_voxel_size / (float)(1 << (p->n_levels - 1));
+  float E = v0 * (float)kFineDim;
+  if (2.0f * p->truncation > 8.0f * E) return MRH_ERR_INVALID_ARG;
+  if (p->hash_slots_log2 < 10 || p->hash_slots_log2 > 28) return MRH_ERR_INVALID_ARG;
+  for (int l = 0; l < p->n_levels; ++l)
+    if (p->max_blocks[l] < 1 || p->max_blocks[l] > kPtrMask) return MRH_ERR_INVALID_ARG;
+  if (p->max_touched < 1 || p->max_touched > (1u << 28)) return MRH_ERR_INVALID_ARG;
+  if (p->storage != MRH_STORAGE_FP32 && p->storage != MRH_STORAGE_FP16) return MRH_ERR_INVALID_ARG;
+  if (p->has_color != 0 && p->has_color != 1) return MRH_ERR_INVALID_ARG;
+  for (int l = 0; l < 2; ++l)
+    if (!std::isfinite(p->var_threshold[l])) return MRH_ERR_INVALID_ARG;
+  if (!(p->split_hysteresis >= 0.0) || !std::isfinite(p->split_hysteresis)) return MRH_ERR_INVALID_ARG;
+  if (p->min_obs < 0) return MRH_ERR_INVALID_ARG;
+  if (!(p->min_range >= 0.f) || !(p->max_range >= p->min_range)) return MRH_ERR_INVALID_ARG;
+  return MRH_OK;
+}
+
+mrh_status validate_pinhole(const mrh_pinhole* K) {
+  if (!K) return MRH_ERR_INVALID_ARG;
+  if (K->width <= 0 || K->height <= 0 || (long long)K->width * K->height > (1LL << 28)) return MRH_ERR_INVALID_ARG;
+  if (!(K->fx > 0.f) || !(K->fy > 0.f) || !std::isfinite(K->fx) || !std::isfinite(K->fy)) return MRH_ERR_INVALID_ARG;
+  if (!std::isfinite(K->cx) || !std::isfinite(K->cy)) return MRH_ERR_INVALID_ARG;
+  if (!(K->min_depth >= 0.f) || !(K->max_depth >= K->min_depth) || !std::isfinite(K->max_depth))
+    return MRH_ERR_INVALID_ARG;
+  return MRH_OK;
+}
+
+CamArgs cam_args(const mrh_pinhole* K, const double* T) {
+  CamArgs c;
+  c.fx = K->fx; c.fy = K->fy; c.cx = K->cx; c.cy = K->cy;
+  c.width = K->width; c.height = K->height;
+  c.min_depth = K->min_depth; c.max_depth = K->max_depth;
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) c.R[3 * r + q] = (float)T[4 * r + q];
+    c.t[r] = (float)T[4 * r + 3];
+  }
+  return c;
+}
+
+template <class T>
+mrh_status dev_alloc(mrh_map* m, T** out, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "cudaMalloc");
+    return MRH_ERR_OUT_OF_MEMORY;
+  }
+  m->allocs.push_back(p);
+  *out = (T*)p;
+  return MRH_OK;
+}
+
+void free_all(mrh_map* m) {
+  for (void* p : m->allocs) cudaFree(p);
+  m->allocs.clear();
+  for (auto& p : m->pending) {
+    m->event_pool.push_back(p.a);
+    m->event_pool.push_back(p.b);
+  }
+  m->pending.clear();
+  for (cudaEvent_t e : m->event_pool) cudaEventDestroy(e);
+  m->event_pool.clear();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** out) {
+  if (!out) return MRH_ERR_INVALID_ARG;
+  *out = nullptr;
+  mrh_status st = validate_params(params);
+  if (st != MRH_OK) return st;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  mrh_map* m = new (std::nothrow) mrh_map();
+  if (!m) return MRH_ERR_OUT_OF_MEMORY;
+  m->device = device;
+  m->p = *params;
+  cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, device);
+  MapDev& d = m->d;
+  d.L = params->n_levels;
+  d.fp16 = params->storage == MRH_STORAGE_FP16;
+  d.color = params->has_color;
+  d.min_obs = params->min_obs;
+  float v0 = params->base_voxel_size / (float)(1 << (d.L - 1));
+  for (int l = 0; l < kMaxLevels; ++l) d.v[l] = v0 * (float)(1 << l);
+  d.E = v0 * (float)kFineDim;
+  d.tau = params->truncation;
+  d.fix_scale = 65536.0f / d.E;
+  d.fix_scale64 = 65536.0 / (double)d.E;
+  d.theta[0] = params->var_threshold[0];
+  d.theta[1] = params->var_threshold[1];
+  d.split_h = params->split_hysteresis;
+  d.min_range = params->min_range;
+  d.max_range = params->max_range;
+  d.max_touched = params->max_touched;
+  const uint32_t n_slots = 1u << params->hash_slots_log2;
+  d.slot_mask = n_slots - 1;
+#define TRY(x)               \
+  do {                       \
+    mrh_status s_ = (x);     \
+    if (s_ != MRH_OK) {      \
+      free_all(m);           \
+      delete m;              \
+      return s_;             \
+    }                        \
+  } while (0)
+  TRY(dev_alloc(m, &d.slots, n_slots));
+  TRY(dev_alloc(m, &d.st, 1));
+  TRY(dev_alloc(m, &d.touched_all, params->max_touched));
+  TRY(dev_alloc(m, &d.retire, params->max_touched));
+  TRY(dev_alloc(m, &d.slot_pos, n_slots));
+  TRY(dev_alloc(m, &d.blk_count, 3ull * params->max_touched));
+  TRY(dev_alloc(m, &d.blk_fill, 3ull * params->max_touched));
+  TRY(dev_alloc(m, &d.blk_off, 3ull * params->max_touched + 1));
+  d.max_obs = params->max_observations;
+  TRY(dev_alloc(m, &d.obs_key, d.max_obs));
+  TRY(dev_alloc(m, &d.obs_d, d.max_obs));
+  TRY(dev_alloc(m, &d.obs_idx, d.max_obs));
+  for (int l = 0; l < kMaxLevels; ++l) {
+    int nl = kFineDim >> l;
+    d.block_bytes[l] = block_bytes_for(nl * nl * nl, d.fp16, d.color);
+    d.max_blocks[l] = l < d.L ? params->max_blocks[l] : 0;
+    if (l < d.L) {
+      TRY(dev_alloc(m, &d.heap[l], (size_t)d.max_blocks[l] * d.block_bytes[l]));
+      TRY(dev_alloc(m, &d.free_stack[l], d.max_blocks[l]));
+      TRY(dev_alloc(m, &d.touched[l], params->max_touched));
+    } else {
+      d.heap[l] = nullptr;
+      d.free_stack[l] = nullptr;
+      d.touched[l] = nullptr;
+    }
+  }
+#undef TRY
+  cudaError_t e = cudaMemset(d.slots, 0xFF, (size_t)n_slots * sizeof(Slot));
+  DevState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  for (int l = 0; l < kMaxLevels; ++l) hs.free_top[l] = (int)d.max_blocks[l];
+  if (e == cudaSuccess) e = cudaMemcpy(d.st, &hs, sizeof(hs), cudaMemcpyHostToDevice);
+  for (int l = 0; l < d.L && e == cudaSuccess; ++l) {
+    k_init_stack<<<m->sms * 4, 256>>>(d.free_stack[l], d.max_blocks[l]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(m);
+    delete m;
+    return cuda_fail(e, "map initialisation");
+  }
+  *out = m;
+  return MRH_OK;
+}
+
+mrh_status mrh_map_destroy(mrh_map* m) {
+  if (!m) return MRH_OK;
+  DeviceGuard guard(m->device);
+  cudaDeviceSynchronize();
+  free_all(m);
+  delete m;
+  return MRH_OK;
+}
+
+mrh_status mrh_integrate_depth(mrh_map* m, const mrh_pinhole* K, const double* T_wc, const float* depth,
+                               const uint8_t* rgb, void* stream) {
+  if (!m || !depth || !finite_pose(T_wc)) return MRH_ERR_INVALID_ARG;
+  mrh_status st = validate_pinhole(K);
+  if (st != MRH_OK) return st;
+  DeviceGuard guard(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  CamArgs c = cam_args(K, T_wc);
+  { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
+  { KernelScope ks(m, MRH_K_ALLOC, s, 1); launch_alloc_depth(m->d, c, depth, s); }
+  { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
+  { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_depth(m->d, c, depth, m->p.has_color ? rgb : nullptr, s, m->sms); }
+  { KernelScope ks(m, MRH_K_RELEASE, s, 1); k_release<<<m->sms, 256, 0, s>>>(m->d); }
+  MRH_CUDA(cudaGetLastError());
+  return MRH_OK;
+}
+
+mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz, uint64_t n, void* stream) {
+  if (!m || (!xyz && n) || !finite_pose(T_ws) || n > (1ull << 23)) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
+  { KernelScope ks(m, MRH_K_ALLOC, s, n ? 1 : 0); launch_alloc_points(m->d, T_ws, xyz, n, s); }
+  { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
+  { KernelScope ks(m, MRH_K_LIDAR_OBS, s, n ? 4 : 2); launch_lidar_observations(m->d, T_ws, xyz, n, s, m->sms); }
+  { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_points(m->d, T_ws, xyz, n, s, m->sms); }
+  { KernelScope ks(m, MRH_K_RELEASE, s, 1); k_release<<<m->sms, 256, 0, s>>>(m->d); }
+  MRH_CUDA(cudaGetLastError());
+  return MRH_OK;
+}
+
+mrh_status mrh_raycast(mrh_map* m, const mrh_pinhole* K, const double* T_wc, float* depth_out, void* stream) {
+  if (!m || !depth_out || !finite_pose(T_wc)) return MRH_ERR_INVALID_ARG;
+  mrh_status st = validate_pinhole(K);
+  if (st != MRH_OK) return st;
+  DeviceGuard guard(m->device);
+  CamArgs c = cam_args(K, T_wc);
+  { KernelScope ks(m, MRH_K_RAYCAST, (cudaStream_t)stream, 1); launch_raycast(m->d, c, depth_out, (cudaStream_t)stream); }
+  MRH_CUDA(cudaGetLastError());
+  return MRH_OK;
+}
+
+mrh_status mrh_count_blocks(mrh_map* m, uint64_t* n_blocks, uint64_t* n_voxels, void* stream) {
+  if (!m) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  DevState hs;
+  MRH_CUDA(cudaMemcpyAsync(&hs, m->d.st, sizeof(hs), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  MRH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  uint64_t nb = 0, nv = 0;
+  for (int l = 0; l < m->d.L; ++l) {
+    uint64_t live = m->d.max_blocks[l] - (uint64_t)hs.free_top[l];
+    int nl = kFineDim >> l;
+    nb += live;
+    nv += live * (uint64_t)(nl * nl * nl);
+  }
+  if (n_blocks) *n_blocks = nb;
+  if (n_voxels) *n_voxels = nv;
+  return status_from_bits(hs.status);
+}
+
+mrh_status mrh_extract_blocks(mrh_map* m, int32_t* keys, uint8_t* levels, uint64_t* voxel_offset, float* tsdf,
+                              float* weight, float* s2, float* color, uint64_t cap_blocks, uint64_t cap_voxels,
+                              uint64_t* n_blocks_out, uint64_t* n_voxels_out, void* stream) {
+  if (!m || !keys || !levels || !voxel_offset || !tsdf || !weight || !s2) return MRH_ERR_INVALID_ARG;
+  uint64_t nb = 0, nv = 0;
+  mrh_status st = mrh_count_blocks(m, &nb, &nv, stream);
+  if (n_blocks_out) *n_blocks_out = nb;
+  if (n_voxels_out) *n_voxels_out = nv;
+  if (nb > cap_blocks || nv > cap_voxels) return MRH_ERR_CAPACITY;
+  DeviceGuard guard(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t npow = 1;
+  while (npow < nb) npow <<= 1;
+  unsigned long long *skeys = nullptr, *soff = nullptr;
+  uint32_t *sslots = nullptr, *scount = nullptr;
+  MRH_CUDA(cudaMallocAsync(&skeys, sizeof(unsigned long long) * npow + 16, s));
+  MRH_CUDA(cudaMallocAsync(&sslots, sizeof(uint32_t) * npow + 16, s));
+  MRH_CUDA(cudaMallocAsync(&soff, sizeof(unsigned long long) * (nb + 1), s));
+  MRH_CUDA(cudaMallocAsync(&scount, sizeof(uint32_t), s));
+  MRH_CUDA(cudaMemsetAsync(scount, 0, sizeof(uint32_t), s));
+  k_compact<<<m->sms * 8, 256, 0, s>>>(m->d, skeys, sslots, scount, npow);
+  uint32_t hcount = 0;
+  MRH_CUDA(cudaMemcpyAsync(&hcount, scount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  MRH_CUDA(cudaStreamSynchronize(s));
+  uint32_t n = std::min<uint32_t>(hcount, (uint32_t)nb);
+  if (npow > n) k_pad_keys<<<m->sms * 4, 256, 0, s>>>(skeys, n, npow);
+  for (uint32_t k = 2; k <= npow; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) k_bitonic_step<<<m->sms * 8, 256, 0, s>>>(skeys, sslots, npow, k, j);
+  if (n > 0) {
+    k_voxel_offsets<<<1, 1024, 0, s>>>(m->d, sslots, n, soff);
+    k_extract<<<m->sms * 8, 128, 0, s>>>(m->d, sslots, n, soff, keys, levels, (unsigned long long*)voxel_offset,
+                                          tsdf, weight, s2, color);
+  } else {
+    MRH_CUDA(cudaMemsetAsync(voxel_offset, 0, sizeof(uint64_t), s));
+  }
+  cudaFreeAsync(skeys, s);
+  cudaFreeAsync(sslots, s);
+  cudaFreeAsync(soff, s);
+  cudaFreeAsync(scount, s);
+  MRH_CUDA(cudaGetLastError());
+  MRH_CUDA(cudaStreamSynchronize(s));
+  if (n != nb) return MRH_ERR_CUDA;
+  return st;
+}
+
+mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
+  if (!m || !out) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  DevState hs;
+  MRH_CUDA(cudaMemcpyAsync(&hs, m->d.st, sizeof(hs), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  MRH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  std::memset(out, 0, sizeof(*out));
+  out->frame = hs.frame;
+  out->valid_rays = hs.valid_rays;
+  out->touched = std::min<uint32_t>(hs.touched_all, m->d.max_touched);
+  out->new_blocks = hs.new_blocks;
+  out->merged = hs.merged;
+  out->split = hs.split;
+  out->fp64_rechecks = hs.rechecks;
+  for (int l = 0; l < m->d.L; ++l) {
+    out->live_blocks[l] = m->d.max_blocks[l] - (uint64_t)hs.free_top[l];
+    out->touched_level[l] = std::min<uint32_t>(hs.touched_count[l], m->d.max_touched);
+  }
+  out->observations = hs.observations;
+  out->status = hs.status;
+  return status_from_bits(hs.status);
+}
+
+mrh_status mrh_sync(mrh_map* m, void* stream) {
+  mrh_stats s;
+  return mrh_get_stats(m, &s, stream);
+}
+
+mrh_status mrh_clear_status(mrh_map* m, void* stream) {
+  if (!m) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  MRH_CUDA(cudaMemsetAsync(&m->d.st->status, 0, sizeof(uint32_t), (cudaStream_t)stream));
+  return MRH_OK;
+}
+
+mrh_status mrh_set_profiling(mrh_map* m, int enable) {
+  if (!m) return MRH_ERR_INVALID_ARG;
+  m->profiling = enable != 0;
+  return MRH_OK;
+}
+
+mrh_status mrh_get_profile(mrh_map* m, double* ms_out, uint64_t* launches_out, int n, int reset, void* stream) {
+  if (!m || n < 0 || n > MRH_K_COUNT) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  MRH_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  mrh_status st = collect_profile(m);
+  if (st != MRH_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    if (ms_out) ms_out[i] = m->prof_ms[i];
+    if (launches_out) launches_out[i] = m->launches[i];
+  }
+  if (reset) {
+    for (int i = 0; i < MRH_K_COUNT; ++i) {
+      m->prof_ms[i] = 0.0;
+      m->launches[i] = 0;
+    }
+  }
+  return MRH_OK;
+}
+
+uint32_t mrh_hash_slot(int32_t x, int32_t y, int32_t z, uint32_t log2_slots) {
+  uint32_t mask = log2_slots >= 32 ? 0xFFFFFFFFu : ((1u << log2_slots) - 1u);
+  return hash_xyz(x, y, z, mask);
+}
+
+const char* mrh_status_string(mrh_status s) {
+  switch (s) {
+    case MRH_OK: return "ok";
+    case MRH_ERR_INVALID_ARG: return "invalid argument";
+    case MRH_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MRH_ERR_HASH_FULL: return "hash table probe limit reached";
+    case MRH_ERR_POOL_EMPTY: return "block heap empty";
+    case MRH_ERR_LIST_FULL: return "touched-block list full";
+    case MRH_ERR_CUDA: return "CUDA error";
+    case MRH_ERR_CAPACITY: return "output buffer too small";
+  }
+  return "unknown status";
+}
+
+const char* mrh_last_cuda_error(void) { return g_cuda_err; }
+
+const char* mrh_version(void) { return "mrhash 0.1.0 sm_103a"; }
+
+}  // extern "C"
