@@ -99,8 +99,11 @@ def lib():
     return _lib
 
 
-def _check(code: int, what: str):
-    if code != 0:
+DEVICE_CAPACITY_CODES = (3, 4, 5)  # sticky device statuses: the map stays valid, reported by stats() / sync()
+
+
+def _check(code: int, what: str, allow=()):
+    if code != 0 and code not in allow:
         err = lib().mrh_last_cuda_error().decode()
         raise MrhError(code, what + (f" [{err}]" if code == 6 and err else ""))
 
@@ -207,7 +210,7 @@ class Map:
     def count(self, stream=None):
         nb, nv = ctypes.c_uint64(), ctypes.c_uint64()
         _check(self._lib.mrh_count_blocks(self._h, ctypes.byref(nb), ctypes.byref(nv), _stream(stream)),
-               "mrh_count_blocks")
+               "mrh_count_blocks", allow=DEVICE_CAPACITY_CODES)
         return nb.value, nv.value
 
     def extract(self, stream=None) -> dict:
@@ -228,7 +231,7 @@ class Map:
                                             _ptr(out["D"]), _ptr(out["W"]), _ptr(out["S2"]), _ptr(out["C"]),
                                             max(nb, 1), max(nv, 1), ctypes.byref(wb), ctypes.byref(wv),
                                             _stream(stream))
-        _check(code, "mrh_extract_blocks")
+        _check(code, "mrh_extract_blocks", allow=DEVICE_CAPACITY_CODES)
         n, v = wb.value, wv.value
         return dict(keys=out["keys"][:n], levels=out["levels"][:n], offsets=out["offsets"], D=out["D"][:v],
                     W=out["W"][:v], S2=out["S2"][:v], C=out["C"][:v])
