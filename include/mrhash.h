@@ -49,7 +49,8 @@ typedef enum {
   MRH_ERR_LIST_FULL = 5,     /* a per-frame list overflowed (touched blocks > max_touched, or LiDAR observations >
                                 max_observations); the excess was not fused */
   MRH_ERR_CUDA = 6,          /* a CUDA runtime call failed (see mrh_last_cuda_error) */
-  MRH_ERR_CAPACITY = 7       /* caller-provided output buffers are too small */
+  MRH_ERR_CAPACITY = 7,      /* caller-provided output buffers are too small */
+  MRH_ERR_STATIC_LIMIT = 8   /* more blocks than mrh_extract_blocks_noalloc's fixed scratch holds */
 } mrh_status;
 
 enum { MRH_STORAGE_FP32 = 0, MRH_STORAGE_FP16 = 1 };
@@ -141,6 +142,24 @@ mrh_status mrh_extract_blocks(mrh_map* map, int32_t* keys_dev, uint8_t* levels_d
                               float* tsdf_dev, float* weight_dev, float* s2_dev, float* color_dev,
                               uint64_t capacity_blocks, uint64_t capacity_voxels, uint64_t* n_blocks_out,
                               uint64_t* n_voxels_out, void* stream);
+
+/* Same output as mrh_extract_blocks, but it allocates no device memory: no cudaMalloc, cudaMallocAsync or cudaFree.
+ * (The paper has no counterpart; this exists for callers of the library.) Meant for callers that cannot allocate
+ * at read-out time: a process that has handed all device memory to a fixed arena or to a framework's caching
+ * allocator, so a fresh allocation would fail, or a latency-bounded loop in which an allocation (which can
+ * synchronise the device) is not acceptable. Its sort and offset scratch is one file-scope device array of
+ * MRH_NOALLOC_MAX_BLOCKS blocks (about 5 MiB) that every GPU loading the library holds until the process exits;
+ * maps holding more blocks return MRH_ERR_STATIC_LIMIT before any work is queued.
+ * The first call on a device looks up that array's device address (once per device, with the map's device
+ * current); make that first call before any stream capture. Every call shares the one array per device and keeps
+ * the last call's contents (the call clears what must start at zero itself), so calls whose GPU work overlaps in
+ * time, on any stream or map of the same device, race: order them on one stream or synchronise between them.
+ * Arguments, outputs, ordering and the synchronisation of `stream` are those of mrh_extract_blocks. */
+#define MRH_NOALLOC_MAX_BLOCKS (1u << 18)
+mrh_status mrh_extract_blocks_noalloc(mrh_map* map, int32_t* keys_dev, uint8_t* levels_dev,
+                                      uint64_t* voxel_offset_dev, float* tsdf_dev, float* weight_dev, float* s2_dev,
+                                      float* color_dev, uint64_t capacity_blocks, uint64_t capacity_voxels,
+                                      uint64_t* n_blocks_out, uint64_t* n_voxels_out, void* stream);
 
 /* Counters of the last frame and map totals (synchronises `stream`); returns the sticky device status. */
 mrh_status mrh_get_stats(mrh_map* map, mrh_stats* out, void* stream);

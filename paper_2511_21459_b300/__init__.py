@@ -17,7 +17,8 @@ _lib = None
 
 MRH_STORAGE_FP32, MRH_STORAGE_FP16 = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash table probe limit reached",
-          4: "block heap empty", 5: "per-frame list full", 6: "CUDA error", 7: "output buffer too small"}
+          4: "block heap empty", 5: "per-frame list full", 6: "CUDA error", 7: "output buffer too small",
+          8: "more blocks than the no-allocation extract's fixed scratch holds"}
 
 
 class MrhError(RuntimeError):
@@ -61,8 +62,9 @@ KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "rayca
 
 
 EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points", "mrh_raycast",
-           "mrh_count_blocks", "mrh_extract_blocks", "mrh_get_stats", "mrh_sync", "mrh_clear_status", "mrh_set_profiling",
-           "mrh_get_profile", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error", "mrh_version"]
+           "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc", "mrh_get_stats", "mrh_sync",
+           "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_hash_slot", "mrh_status_string",
+           "mrh_last_cuda_error", "mrh_version"]
 
 
 def lib():
@@ -81,6 +83,7 @@ def lib():
         L.mrh_count_blocks.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
                                          ctypes.POINTER(u64), vp]
+        L.mrh_extract_blocks_noalloc.argtypes = L.mrh_extract_blocks.argtypes
         L.mrh_get_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
         L.mrh_sync.argtypes = [vp, vp]
         L.mrh_clear_status.argtypes = [vp, vp]
@@ -92,7 +95,8 @@ def lib():
         L.mrh_last_cuda_error.restype = ctypes.c_char_p
         L.mrh_version.restype = ctypes.c_char_p
         for name in ("mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points",
-                     "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_get_stats", "mrh_sync",
+                     "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc",
+                     "mrh_get_stats", "mrh_sync",
                      "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -328,6 +329,42 @@ void free_all(mrh_map* m) {
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------------------ static scratch
+//
+// mrh_extract_blocks_noalloc sorts and scans inside this one array instead of allocating. Host code must not use the
+// symbol as a pointer: its device address is looked up once per device (cudaGetSymbolAddress, with that device
+// current) and passed to the kernels.
+namespace {
+
+constexpr uint32_t kNoallocMaxBlocks = MRH_NOALLOC_MAX_BLOCKS;
+constexpr size_t kNoallocKeysOff = 0;                                               // u64 keys[max]
+constexpr size_t kNoallocSlotsOff = kNoallocKeysOff + 8ull * kNoallocMaxBlocks;      // u32 slots[max]
+constexpr size_t kNoallocOffsOff = kNoallocSlotsOff + 4ull * kNoallocMaxBlocks;      // u64 offsets[max + 1]
+constexpr size_t kNoallocCountOff = kNoallocOffsOff + 8ull * (kNoallocMaxBlocks + 1); // u32 count
+constexpr size_t kNoallocBytes = (kNoallocCountOff + 4 + 255) / 256 * 256;
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+uint8_t* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up on first use)
+mrh_status noalloc_scratch(int device, uint8_t** out) {
+  if (device < 0 || device >= kMaxDevices) return MRH_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[device] = (uint8_t*)ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return MRH_OK;
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -534,6 +571,52 @@ mrh_status mrh_extract_blocks(mrh_map* m, int32_t* keys, uint8_t* levels, uint64
   return st;
 }
 
+mrh_status mrh_extract_blocks_noalloc(mrh_map* m, int32_t* keys, uint8_t* levels, uint64_t* voxel_offset,
+                                      float* tsdf, float* weight, float* s2, float* color, uint64_t cap_blocks,
+                                      uint64_t cap_voxels, uint64_t* n_blocks_out, uint64_t* n_voxels_out,
+                                      void* stream) {
+  if (!m || !keys || !levels || !voxel_offset || !tsdf || !weight || !s2) return MRH_ERR_INVALID_ARG;
+  uint64_t nb = 0, nv = 0;
+  mrh_status st = mrh_count_blocks(m, &nb, &nv, stream);
+  if (n_blocks_out) *n_blocks_out = nb;
+  if (n_voxels_out) *n_voxels_out = nv;
+  if (st == MRH_ERR_CUDA) return st;
+  if (nb > kNoallocMaxBlocks) return MRH_ERR_STATIC_LIMIT;
+  if (nb > cap_blocks || nv > cap_voxels) return MRH_ERR_CAPACITY;
+  DeviceGuard guard(m->device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  uint8_t* base = nullptr;
+  mrh_status sst = noalloc_scratch(m->device, &base);
+  if (sst != MRH_OK) return sst;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* skeys = (unsigned long long*)(base + kNoallocKeysOff);
+  uint32_t* sslots = (uint32_t*)(base + kNoallocSlotsOff);
+  unsigned long long* soff = (unsigned long long*)(base + kNoallocOffsOff);
+  uint32_t* scount = (uint32_t*)(base + kNoallocCountOff);
+  uint32_t npow = 1;
+  while (npow < nb) npow <<= 1;
+  MRH_CUDA(cudaMemsetAsync(scount, 0, sizeof(uint32_t), s));
+  k_compact<<<m->sms * 8, 256, 0, s>>>(m->d, skeys, sslots, scount, npow);
+  uint32_t hcount = 0;
+  MRH_CUDA(cudaMemcpyAsync(&hcount, scount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  MRH_CUDA(cudaStreamSynchronize(s));
+  uint32_t n = std::min<uint32_t>(hcount, (uint32_t)nb);
+  if (npow > n) k_pad_keys<<<m->sms * 4, 256, 0, s>>>(skeys, n, npow);
+  for (uint32_t k = 2; k <= npow; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) k_bitonic_step<<<m->sms * 8, 256, 0, s>>>(skeys, sslots, npow, k, j);
+  if (n > 0) {
+    k_voxel_offsets<<<1, 1024, 0, s>>>(m->d, sslots, n, soff);
+    k_extract<<<m->sms * 8, 128, 0, s>>>(m->d, sslots, n, soff, keys, levels, (unsigned long long*)voxel_offset,
+                                          tsdf, weight, s2, color);
+  } else {
+    MRH_CUDA(cudaMemsetAsync(voxel_offset, 0, sizeof(uint64_t), s));
+  }
+  MRH_CUDA(cudaGetLastError());
+  MRH_CUDA(cudaStreamSynchronize(s));
+  if (n != nb) return MRH_ERR_CUDA;
+  return st;
+}
+
 mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
   if (!m || !out) return MRH_ERR_INVALID_ARG;
   DeviceGuard guard(m->device);
@@ -609,6 +692,7 @@ const char* mrh_status_string(mrh_status s) {
     case MRH_ERR_LIST_FULL: return "touched-block list full";
     case MRH_ERR_CUDA: return "CUDA error";
     case MRH_ERR_CAPACITY: return "output buffer too small";
+    case MRH_ERR_STATIC_LIMIT: return "more blocks than the no-allocation extract's fixed scratch holds";
   }
   return "unknown status";
 }
