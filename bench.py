@@ -46,7 +46,39 @@ def parse_args():
     ap.add_argument("--no-lidar", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--profile-case", choices=["rgbd", "lidar"], default=None,
+                    help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
     return ap.parse_args()
+
+
+def profile_case(kind: str) -> int:
+    """A few frames of the benchmark sequence on a map with reduced heap capacity (a few hundred MB on the device),
+    so that profiler captures of single launches stay small."""
+    import torch
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import build
+    build.build()
+    if kind == "rgbd":
+        wl = synth.rgbd()
+        wl.max_blocks = (1 << 15, 1 << 14, 1 << 14)
+        m = mrh.Map(mrh.params_from(wl))
+        K = mrh.pinhole_from(wl)
+        out = torch.empty((wl.height, wl.width), device="cuda")
+        for d, c, T in camera_frames(wl, 0, 6):
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+            m.raycast(K, T, out)
+    else:
+        wl = synth.lidar()
+        wl.max_blocks = (1 << 18, 1 << 16, 1 << 16)
+        m = mrh.Map(mrh.params_from(wl, max_observations=1 << 24))
+        scene = wl.scene()
+        for k in range(4):
+            xyz, T = synth.render_lidar(wl, k, scene=scene)
+            m.integrate_points(T, torch.from_numpy(xyz).cuda())
+    torch.cuda.synchronize()
+    st = m.stats()
+    print(json.dumps({"profile_case": kind, "status": st["status_code"], "touched_last": st["touched"]}))
+    return 0 if st["status_code"] == 0 else 1
 
 
 def peaks():
@@ -303,6 +335,8 @@ def oracle_camera_sample(wl, frames, budget_s, max_frames):
 
 def main():
     args = parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     wl = synth.rgbd()
     hbm, peak_kind = peaks()
 

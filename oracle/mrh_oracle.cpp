@@ -32,6 +32,7 @@
 #include <map>
 #include <set>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 namespace {
@@ -45,6 +46,7 @@ constexpr int64_t kVoxelUnit = kBlockUnit / kFineDim;  // one finest voxel
 constexpr int64_t kKeyLimit = (int64_t(1) << 20) - 2;  // |block coordinate| bound (21-bit packed keys)
 constexpr int kMaxLevels = 3;
 constexpr int kRaycastMaxIter = 8192;
+constexpr int64_t kBrick = 4;  // raycast empty-space skipping cell: 4 x 4 x 4 blocks
 
 struct Key {
   int64_t x, y, z;
@@ -294,6 +296,7 @@ struct Map : MapBase {
   int n[kMaxLevels];      // voxels per block side per level
   float E_f;              // block edge (float), the unit of the fixed-point key coordinates
   std::unordered_map<Key, Block<R, Sto>, KeyHash> blocks;
+  std::unordered_set<Key, KeyHash> bricks;  // 4x4x4-block cells holding at least one allocated block (raycast)
 
   explicit Map(const orc_params& p) : P(p), L(p.n_levels) {
     tau = (R)p.truncation;
@@ -316,6 +319,7 @@ struct Map : MapBase {
         b.level = 0;
         b.resize(n[0], P.has_color != 0);
         st->new_blocks++;
+        bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
       }
     }
   }
@@ -655,11 +659,14 @@ struct Map : MapBase {
   }
 
   // ---- raycast (the rendering branch of Fig. 2): first +/- zero crossing of the trilinear TSDF along each pixel ray.
-  // Reading (the paper renders through Gaussian splats and gives no raycaster): march from min to max depth; skip
-  // whole unallocated blocks; inside a block of level l sample every min(v_l, tau/2); the field is trilinear over the
-  // 8 nearest voxel centres of that level's grid, a corner in another block uses that block's voxel containing the
-  // corner centre (any level); a sample counts only when all 8 corners are observed; on the first sign change take
-  // the linear root, evaluate there once more and take one more secant step. Output z-depth; 0 = no hit.
+  // Reading (the paper renders through Gaussian splats and gives no raycaster): march from min to max depth; a
+  // sample in an empty 4x4x4-block brick jumps to the brick's exit face, a sample in an unallocated block of a
+  // non-empty brick to the block's exit face; inside a block of level l the field is trilinear over the 8 nearest
+  // voxel centres of that level's grid, a corner in another block uses that block's voxel containing the corner
+  // centre (any level), and a sample counts only when all 8 corners are observed; the next sample is
+  // min(v_l, tau/2) ahead, or 0.75 F ahead when the sample is valid with F larger than that (F <= tau underestimates
+  // the distance to the surface, so the step cannot cross the negative band); on the first sign change take the
+  // linear root, evaluate there once more and take one more secant step. Output z-depth; 0 = no hit.
   const Block<R, Sto>* find(const Key& k) const {
     auto it = blocks.find(k);
     return it == blocks.end() ? nullptr : &it->second;
@@ -722,37 +729,48 @@ struct Map : MapBase {
     const R fx = (R)K->fx, fy = (R)K->fy, cx = (R)K->cx, cy = (R)K->cy;
     const R E = (R)E_f, invE = (R)1 / E;
     const R half_tau = tau * (R)0.5;
+    const R eps = (R)1e-4 * E;
     for (int vv = 0; vv < K->height; ++vv)
       for (int u = 0; u < K->width; ++u) {
         R qx = ((R)u - cx) / fx, qy = ((R)vv - cy) / fy;
         R nq = std::sqrt(qx * qx + qy * qy + (R)1);
         R rc[3] = {qx / nq, qy / nq, (R)1 / nq};
-        R r[3];
-        for (int a = 0; a < 3; ++a) r[a] = Rm[3 * a + 0] * rc[0] + Rm[3 * a + 1] * rc[1] + Rm[3 * a + 2] * rc[2];
+        R r[3], inv_r[3];
+        for (int a = 0; a < 3; ++a) {
+          r[a] = Rm[3 * a + 0] * rc[0] + Rm[3 * a + 1] * rc[1] + Rm[3 * a + 2] * rc[2];
+          inv_r[a] = r[a] != (R)0 ? (R)1 / r[a] : (R)0;
+        }
         R t = (R)K->min_depth * nq, t_far = (R)K->max_depth * nq;
         bool have_prev = false;
         R t_prev = 0, F_prev = 0, hit = 0;
         for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
-          int l = 0;
-          bool valid = false;
-          R F = 0;
-          if (!sample(o, r, t, invE, &l, &valid, &F)) {
-            // leave the empty block: smallest parameter at which the ray reaches one of its far faces
-            R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+          R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+          int64_t bk[3] = {(int64_t)std::floor(x[0] * invE), (int64_t)std::floor(x[1] * invE),
+                           (int64_t)std::floor(x[2] * invE)};
+          Key brick{floor_div(bk[0], kBrick), floor_div(bk[1], kBrick), floor_div(bk[2], kBrick)};
+          const bool brick_empty = bricks.find(brick) == bricks.end();
+          const Block<R, Sto>* blk = brick_empty ? nullptr : find(Key{bk[0], bk[1], bk[2]});
+          if (!blk) {
+            // leave the empty brick (or the empty block): smallest parameter at which the ray reaches a far face
+            const int64_t cell[3] = {brick_empty ? brick.x : bk[0], brick_empty ? brick.y : bk[1],
+                                     brick_empty ? brick.z : bk[2]};
+            const int64_t span = brick_empty ? kBrick : 1;
             R t_exit = t_far + (R)1;
             for (int a = 0; a < 3; ++a) {
               if (r[a] == (R)0) continue;
-              R bf = std::floor(x[a] * invE);
-              R face = (r[a] > (R)0 ? bf + (R)1 : bf) * E;
-              R ta = (face - o[a]) / r[a];
+              R face = (R)((r[a] > (R)0 ? cell[a] + 1 : cell[a]) * span) * E;
+              R ta = (face - o[a]) * inv_r[a];
               if (ta < t_exit) t_exit = ta;
             }
-            R step_min = t + (R)1e-4 * E;
-            R tn = t_exit + (R)1e-4 * E;
+            R step_min = t + eps;
+            R tn = t_exit + eps;
             t = tn > step_min ? tn : step_min;
             have_prev = false;
             continue;
           }
+          const int l = blk->level;
+          R F = 0;
+          const bool valid = field(x, l, &F);
           if (valid && have_prev && F_prev > (R)0 && !(F > (R)0)) {
             R ta = t_prev, Fa = F_prev, tb = t, Fb = F;
             R ts = ta + (tb - ta) * (Fa / (Fa - Fb));
@@ -769,6 +787,10 @@ struct Map : MapBase {
           have_prev = valid;
           if (valid) { t_prev = t; F_prev = F; }
           R s = v[l] < half_tau ? v[l] : half_tau;
+          if (valid && F > (R)0) {
+            R sF = (R)0.75 * F;
+            if (sF > s) s = sF;
+          }
           t = t + s;
         }
         out[(size_t)vv * K->width + u] = (float)hit;

@@ -109,7 +109,11 @@ __device__ inline void flush_set(const MapDev& m, unsigned long long* s_set, uin
   }
 }
 
-__global__ void __launch_bounds__(256) k_alloc_depth(MapDev m, CamArgs c, const float* __restrict__ depth) {
+// Besides allocating, writes the frame's range image (rho = z |q|, -1 for invalid depth) and its colour packed as
+// r | g << 8 | b << 16 (when rgb is given) for the fusion kernel.
+__global__ void __launch_bounds__(256) k_alloc_depth(MapDev m, CamArgs c, const float* __restrict__ depth,
+                                                     const uint8_t* __restrict__ rgb, float* __restrict__ rho_img,
+                                                     uint32_t* __restrict__ rgb_img) {
   __shared__ unsigned long long s_set[kSetCap];
   __shared__ uint32_t s_valid;
   for (int i = threadIdx.x; i < kSetCap; i += blockDim.x) s_set[i] = kEmptyKey;
@@ -121,12 +125,17 @@ __global__ void __launch_bounds__(256) k_alloc_depth(MapDev m, CamArgs c, const 
   const int u = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
   const int v = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
   if (u < c.width && v < c.height) {
-    float z = depth[(size_t)v * c.width + u];
+    const size_t pix = (size_t)v * c.width + u;
+    float z = depth[pix];
+    if (rgb_img)
+      rgb_img[pix] = (uint32_t)rgb[3 * pix] | ((uint32_t)rgb[3 * pix + 1] << 8) | ((uint32_t)rgb[3 * pix + 2] << 16);
+    if (!(z >= c.min_depth && z <= c.max_depth)) rho_img[pix] = -1.0f;
     if (z >= c.min_depth && z <= c.max_depth) {
       float qx = ((float)u - c.cx) / c.fx;
       float qy = ((float)v - c.cy) / c.fy;
       float nq = sqrtf(qx * qx + qy * qy + 1.0f);
       float rho = z * nq;
+      rho_img[pix] = rho;
       float rc0 = qx / nq, rc1 = qy / nq, rc2 = 1.0f / nq;
       float r[3];
 #pragma unroll
@@ -183,6 +192,24 @@ __global__ void __launch_bounds__(256) k_bin(MapDev m) {
     uint32_t s = m.touched_all[i];
     uint32_t val = m.slots[s].val;
     if (val == kValPending) {
+      // a new block: record its brick for the raycaster's empty-space skipping (idempotent)
+      {
+        int bx, by, bz;
+        unpack_key(m.slots[s].key, &bx, &by, &bz);
+        bx >>= kBrickShift;
+        by >>= kBrickShift;
+        bz >>= kBrickShift;
+        const unsigned long long bkey = pack_key(bx, by, bz);
+        const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
+        for (uint32_t p = 0; p <= m.brick_mask && p < (uint32_t)kMaxProbes; ++p) {
+          unsigned long long* slot = &m.brick_keys[(h + p) & m.brick_mask];
+          const unsigned long long cur = *(volatile unsigned long long*)slot;
+          if (cur == bkey) break;
+          if (cur != kEmptyKey) continue;
+          const unsigned long long old = atomicCAS(slot, kEmptyKey, bkey);
+          if (old == kEmptyKey || old == bkey) break;
+        }
+      }
       const int l = 0;
       int t = atomicSub(&m.st->free_top[l], 1);
       if (t <= 0) {
@@ -199,14 +226,20 @@ __global__ void __launch_bounds__(256) k_bin(MapDev m) {
     uint32_t j = atomicAdd(&m.st->touched_count[l], 1u);
     m.touched[l][j] = s;
     m.slot_pos[s] = (l << 28) | j;
+    BlockMeta bm;
+    bm.key = m.slots[s].key;
+    bm.val = val;
+    bm.slot = s;
+    m.meta[l][j] = bm;
   }
 }
 
 }  // namespace
 
-void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, cudaStream_t s) {
+void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, float* rho_img,
+                        uint32_t* rgb_img, cudaStream_t s) {
   dim3 grid((c.width + 31) / 32, (c.height + 7) / 8);
-  k_alloc_depth<<<grid, 256, 0, s>>>(m, c, depth);
+  k_alloc_depth<<<grid, 256, 0, s>>>(m, c, depth, rgb, rho_img, rgb ? rgb_img : nullptr);
 }
 
 void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s) {

@@ -12,17 +12,19 @@
 //           (Sec. 3.2.1); then the mean voxel variance of the block over observed voxels; then merge to the next
 //           coarser level below theta_l (Sec. 3.2.1, Fig. 4a) or split to the next finer level above h theta_{l-1}.
 //
-// Work decomposition: a CTA of 128 threads takes 512 voxels per step: one level-0 block (8^3), eight level-1
-// blocks (4^3) or sixty-four level-2 blocks (2^3). Each thread owns 4 consecutive voxels and moves each field of
-// them with one 16-byte (fp32) or 8-byte (fp16) access, so a block's fields stream fully coalesced. The updated state
-// is staged in shared memory, the block variance is reduced with warp shuffles, and a block that changes level is
-// resampled from shared memory straight into a block popped from the other level's heap (a merged block never
-// writes its fine payload back).
+// Work decomposition: one warp per work item, with no CTA-wide barrier anywhere. An item is one level-0 block
+// (8^3 voxels, 32 lanes), two level-1 blocks (4^3, 16 lanes each) or sixteen level-2 blocks (2^3, 2 lanes each).
+// A lane owns 4 consecutive voxels per chunk of 4 G voxels (G = lanes per block) and moves each field of them with
+// one 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced, and the next chunk's
+// loads are issued before the current chunk is computed. The block's mean variance is a butterfly shuffle reduction
+// that leaves the sum in every lane of the block's group, so every lane takes the same decision without
+// communication. Re-levelled blocks (a small fraction per frame) are resampled from their just-written payload into
+// a heap block popped from the other level's free stack.
 //
-// The block variance decides in float; a value within 4e-6 (relative) of a threshold is recomputed in double, in
+// The block variance decides in float; a value within 1e-5 (relative) of a threshold is recomputed in double, in
 // voxel order, exactly as the CPU oracle computes it, so level decisions match the oracle bit for bit. (The float
-// sum's relative error is below 13 ulp: <= 3 sequential + 5 shuffle + 3 cross-warp additions of non-negative terms,
-// the per-voxel division and the final division.)
+// sum's relative error is below 22 ulp = 1.3e-6: 15 sequential + 5 shuffle additions of non-negative terms, the
+// per-voxel division and the final division.)
 //
 // This file is compiled without multiply-add contraction: float expressions round in source order, like the oracle.
 #include <cuda_fp16.h>
@@ -32,34 +34,38 @@
 namespace mrh {
 namespace {
 
-constexpr int kThreads = 128;
-constexpr double kBand = 4e-6;
+constexpr double kBand = 1e-5;
 constexpr int kLocalSort = 16;
+constexpr uint32_t kInvalidPtr = 0xFFFFFFFFu;
 enum { kActNone = 0, kActMerge = 1, kActSplit = 2 };
 
 template <bool FP16>
 struct Field {
-  static __device__ inline void load4(const uint8_t* p, int li, float out[4]) {
+  static __device__ inline void load4(const uint8_t* p, int i4, float out[4]) {
     if constexpr (FP16) {
-      uint2 u = reinterpret_cast<const uint2*>(p)[li];
+      uint2 u = reinterpret_cast<const uint2*>(p)[i4];
       __half2 a = *reinterpret_cast<__half2*>(&u.x), b = *reinterpret_cast<__half2*>(&u.y);
       float2 fa = __half22float2(a), fb = __half22float2(b);
       out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
     } else {
-      float4 f = reinterpret_cast<const float4*>(p)[li];
+      float4 f = reinterpret_cast<const float4*>(p)[i4];
       out[0] = f.x; out[1] = f.y; out[2] = f.z; out[3] = f.w;
     }
   }
-  static __device__ inline void store4(uint8_t* p, int li, const float in[4]) {
+  static __device__ inline void store4(uint8_t* p, int i4, const float in[4]) {
     if constexpr (FP16) {
       __half2 a = __floats2half2_rn(in[0], in[1]), b = __floats2half2_rn(in[2], in[3]);
       uint2 u;
       u.x = *reinterpret_cast<uint32_t*>(&a);
       u.y = *reinterpret_cast<uint32_t*>(&b);
-      reinterpret_cast<uint2*>(p)[li] = u;
+      reinterpret_cast<uint2*>(p)[i4] = u;
     } else {
-      reinterpret_cast<float4*>(p)[li] = make_float4(in[0], in[1], in[2], in[3]);
+      reinterpret_cast<float4*>(p)[i4] = make_float4(in[0], in[1], in[2], in[3]);
     }
+  }
+  static __device__ inline float get1(const uint8_t* p, int i) {
+    if constexpr (FP16) return __half2float(reinterpret_cast<const __half*>(p)[i]);
+    else return reinterpret_cast<const float*>(p)[i];
   }
   static __device__ inline void store1(uint8_t* p, int i, float x) {
     if constexpr (FP16) reinterpret_cast<__half*>(p)[i] = __float2half_rn(x);
@@ -70,16 +76,6 @@ struct Field {
     if constexpr (FP16) return __half2float(__float2half_rn(x));
     else return x;
   }
-};
-
-// What one CTA step knows about the block its thread group works on.
-struct Ctx {
-  int l, nl, nv, G, g, li;
-  bool active;
-  uint32_t idx;         // position in touched[l]
-  uint32_t P;           // position in the level-concatenated list (LiDAR buffers)
-  uint32_t P_first;     // P of the CTA step's first group
-  int kx, ky, kz;       // block key
 };
 
 // One Welford step (Eq. 3 incremental form + S2 update of Sec. 3.2.1).
@@ -93,60 +89,84 @@ __device__ inline void welford(float d, float& D, float& W, float& S2, float& Wn
   W = Wn;
 }
 
+// 4 consecutive voxels of one lane
+struct Chunk {
+  float D[4], W[4], S2[4], C[3][4];
+};
+
+// What a lane knows about the block its group works on.
+struct Ctx {
+  int l, nl, nv, G, g, li;
+  bool active;
+  uint32_t P;        // position in the level-concatenated list (LiDAR buffers)
+  uint32_t P_first;  // P of the item's first group
+  int kx, ky, kz;    // block key
+};
+
 // -------------------------------------------------------------------------------------------- camera observer
 
+// Reads the frame's range image (rho = z |K^-1 [u v 1]|, written by the allocation kernel with the same float
+// expression, -1 where the depth is invalid) and its colour packed as one 32-bit word per pixel, so a voxel costs one
+// 4-byte gather per image instead of recomputing the pixel ray.
 template <bool FP16, bool COLOR>
 struct CameraObs {
   CamArgs c;
-  const float* depth;
-  const uint8_t* rgb;
+  const float* rho_img;
+  const uint32_t* rgb_img;  // null when the frame has no colour
 
-  __device__ inline void collect(const MapDev&, const Ctx&) {}
+  __device__ inline void collect(const MapDev&, const Ctx&, int) {}
 
-  __device__ inline int apply(const MapDev& m, const Ctx& x, float D[4], float W[4], float S2[4], float C[3][4]) {
-    if (!x.active) return 0;
+  // voxels vi0 .. vi0 + 3 of the block. Written without early exits: all four voxels are computed side by side and
+  // an update is kept only where the voxel is observed, so the four independent chains can overlap.
+  __device__ inline int apply(const MapDev& m, const Ctx& x, int vi0, Chunk& ch) const {
     const float vl = m.v[x.l];
     const float ob0 = (float)x.kx * m.E - c.t[0];
     const float ob1 = (float)x.ky * m.E - c.t[1];
     const float ob2 = (float)x.kz * m.E - c.t[2];
+    const int sh = 3 - x.l, msk = x.nl - 1;
+    const float fw = (float)c.width, fh = (float)c.height;
     int n_upd = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int vi = 4 * x.li + k;
-      const int xi = vi % x.nl, yi = (vi / x.nl) % x.nl, zi = vi / (x.nl * x.nl);
-      float w0 = ob0 + ((float)xi + 0.5f) * vl;
-      float w1 = ob1 + ((float)yi + 0.5f) * vl;
-      float w2 = ob2 + ((float)zi + 0.5f) * vl;
-      float xc = c.R[0] * w0 + c.R[3] * w1 + c.R[6] * w2;
-      float yc = c.R[1] * w0 + c.R[4] * w1 + c.R[7] * w2;
-      float zc = c.R[2] * w0 + c.R[5] * w1 + c.R[8] * w2;
-      if (!(zc > 0.0f)) continue;
-      float uf = c.fx * xc / zc + c.cx + 0.5f;
-      float vf = c.fy * yc / zc + c.cy + 0.5f;
-      if (!(uf >= 0.0f && uf < (float)c.width && vf >= 0.0f && vf < (float)c.height)) continue;
-      int u = (int)floorf(uf), v = (int)floorf(vf);
-      size_t pix = (size_t)v * c.width + u;
-      float zm = __ldg(depth + pix);
-      if (!(zm >= c.min_depth && zm <= c.max_depth)) continue;
-      float qx = ((float)u - c.cx) / c.fx, qy = ((float)v - c.cy) / c.fy;
-      float rho = zm * sqrtf(qx * qx + qy * qy + 1.0f);
-      float dist = sqrtf(xc * xc + yc * yc + zc * zc);
-      float eta = rho - dist;
-      if (eta < -m.tau) continue;  // occluded: more than tau behind the measured surface
-      float d = eta < m.tau ? eta : m.tau;
-      float Wn;
-      welford<FP16>(d, D[k], W[k], S2[k], Wn);
+      const int vi = vi0 + k;
+      const int xi = vi & msk, yi = (vi >> sh) & msk, zi = vi >> (2 * sh);
+      const float w0 = ob0 + ((float)xi + 0.5f) * vl;
+      const float w1 = ob1 + ((float)yi + 0.5f) * vl;
+      const float w2 = ob2 + ((float)zi + 0.5f) * vl;
+      const float xc = c.R[0] * w0 + c.R[3] * w1 + c.R[6] * w2;
+      const float yc = c.R[1] * w0 + c.R[4] * w1 + c.R[7] * w2;
+      const float zc = c.R[2] * w0 + c.R[5] * w1 + c.R[8] * w2;
+      const float uf = c.fx * xc / zc + c.cx + 0.5f;
+      const float vf = c.fy * yc / zc + c.cy + 0.5f;
+      bool ok = zc > 0.0f && uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh;
+      const int u = ok ? (int)floorf(uf) : 0, v = ok ? (int)floorf(vf) : 0;
+      const int pix = v * c.width + u;
+      const float rho = __ldg(rho_img + pix);
+      const float dist = sqrtf(xc * xc + yc * yc + zc * zc);
+      const float eta = rho - dist;
+      ok = ok && rho >= 0.0f && !(eta < -m.tau);  // valid depth; not occluded (more than tau behind the surface)
+      const float d = eta < m.tau ? eta : m.tau;
+      const float Wn = ch.W[k] + 1.0f;
+      const float e = d - ch.D[k];
+      const float Dn = ch.D[k] + e / Wn;
+      const float S2n = ch.S2[k] + e * (d - Dn);
+      if (ok) {
+        ch.D[k] = Field<FP16>::kept(Dn);
+        ch.W[k] = Wn;
+        ch.S2[k] = S2n;
+        ++n_upd;
+      }
       if constexpr (COLOR) {
-        if (rgb) {
+        if (rgb_img) {
+          const uint32_t packed = __ldg(rgb_img + pix);
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            float col = (float)__ldg(rgb + 3 * pix + q);
-            float ec = col - C[q][k];
-            C[q][k] = Field<FP16>::kept(C[q][k] + ec / Wn);
+            const float col = (float)((packed >> (8 * q)) & 255u);
+            const float Cn = ch.C[q][k] + (col - ch.C[q][k]) / Wn;
+            if (ok) ch.C[q][k] = Field<FP16>::kept(Cn);
           }
         }
       }
-      ++n_upd;
     }
     return n_upd;
   }
@@ -154,77 +174,75 @@ struct CameraObs {
 
 // -------------------------------------------------------------------------------------------- LiDAR observer
 
+// Per warp: 512 voxel bins (the item's voxels) in shared memory: counts, exclusive offsets, fill cursors.
+constexpr int kLidarWarps = 4;
+
 template <bool FP16>
 struct LidarObs {
-  uint32_t* s_cnt;
-  uint32_t* s_off;
+  uint32_t (*s_bins)[3][512];  // [warp][cnt | off | fill][bin]
   uint32_t item_base;
 
-  // CTA-collective: bin this step's observations per voxel (bins are the step's 512 voxels).
-  __device__ inline void collect(const MapDev& m, const Ctx& x) {
-    uint32_t* s_fill = s_off + 512;
-    for (int i = threadIdx.x; i < 512; i += kThreads) {
-      s_cnt[i] = 0;
-      s_fill[i] = 0;
+  // warp-collective: bin the item's observations per voxel (bin = group * nv + voxel)
+  __device__ inline void collect(const MapDev& m, const Ctx& x, int warp) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* cnt = s_bins[warp][0];
+    uint32_t* off = s_bins[warp][1];
+    uint32_t* fill = s_bins[warp][2];
+    for (int i = lane; i < 512; i += 32) {
+      cnt[i] = 0;
+      fill[i] = 0;
     }
-    __syncthreads();
+    __syncwarp();
     uint32_t r0 = 0, r1 = 0;
     if (x.active) {
       r0 = m.blk_off[x.P];
       r1 = m.blk_off[x.P + 1];
       if (r1 > m.max_obs) r0 = r1 = 0;  // observations were not stored (status already set)
     }
-    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&s_cnt[x.g * x.nv + (m.obs_key[r] & 511u)], 1u);
-    __syncthreads();
-    // exclusive scan of the 512 bin counts: 4 per thread, warp shuffle, then across the 4 warps
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t c4[4], sum = 0;
+    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&cnt[x.g * x.nv + (m.obs_key[r] & 511u)], 1u);
+    __syncwarp();
+    uint32_t local[16], sum = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      c4[k] = s_cnt[4 * tid + k];
-      sum += c4[k];
+    for (int k = 0; k < 16; ++k) {
+      local[k] = cnt[16 * lane + k];
+      sum += local[k];
     }
     uint32_t incl = sum;
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t t = __shfl_up_sync(~0u, incl, o);
       if (lane >= o) incl += t;
     }
-    __shared__ uint32_t s_w[4];
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint32_t base = 0;
-    for (int w = 0; w < warp; ++w) base += s_w[w];
-    uint32_t run = base + incl - sum;
+    uint32_t run = incl - sum;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      s_off[4 * tid + k] = run;
-      run += c4[k];
+    for (int k = 0; k < 16; ++k) {
+      off[16 * lane + k] = run;
+      run += local[k];
     }
     item_base = m.blk_off[x.P_first];
-    __syncthreads();
+    __syncwarp();
     for (uint32_t r = r0 + x.li; r < r1; r += x.G) {
-      uint32_t bin = x.g * x.nv + (m.obs_key[r] & 511u);
-      uint32_t pos = s_off[bin] + atomicAdd(&s_fill[bin], 1u);
+      const uint32_t bin = x.g * x.nv + (m.obs_key[r] & 511u);
+      const uint32_t pos = off[bin] + atomicAdd(&fill[bin], 1u);
       m.obs_idx[item_base + pos] = r;
     }
-    __syncthreads();
+    __syncwarp();
   }
 
-  __device__ inline int apply(const MapDev& m, const Ctx& x, float D[4], float W[4], float S2[4], float (*)[4]) {
-    if (!x.active) return 0;
+  __device__ inline int apply(const MapDev& m, const Ctx& x, int vi0, Chunk& ch) const {
+    const int warp = threadIdx.x >> 5;
     int n_upd = 0;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
-      const int bin = 4 * threadIdx.x + k;
-      const uint32_t cnt = s_cnt[bin];
+      const int bin = x.g * x.nv + vi0 + k;
+      const uint32_t cnt = s_bins[warp][0][bin];
       if (cnt == 0) continue;
-      uint32_t* idx = m.obs_idx + item_base + s_off[bin];
+      uint32_t* idx = m.obs_idx + item_base + s_bins[warp][1][bin];
       // order the voxel's observations by point index (each ray observes a voxel at most once)
       if (cnt <= kLocalSort) {
         unsigned long long e[kLocalSort];
         for (uint32_t i = 0; i < cnt; ++i) {
-          uint32_t r = idx[i];
-          unsigned long long key = ((unsigned long long)(m.obs_key[r] >> 9) << 32) | r;
+          const uint32_t r = idx[i];
+          const unsigned long long key = ((unsigned long long)(m.obs_key[r] >> 9) << 32) | r;
           uint32_t j = i;
           while (j > 0 && e[j - 1] > key) {
             e[j] = e[j - 1];
@@ -234,12 +252,12 @@ struct LidarObs {
         }
         for (uint32_t i = 0; i < cnt; ++i) {
           float Wn;
-          welford<FP16>(m.obs_d[(uint32_t)e[i]], D[k], W[k], S2[k], Wn);
+          welford<FP16>(m.obs_d[(uint32_t)e[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
         }
       } else {
         for (uint32_t i = 1; i < cnt; ++i) {
-          uint32_t r = idx[i];
-          uint32_t kr = m.obs_key[r] >> 9;
+          const uint32_t r = idx[i];
+          const uint32_t kr = m.obs_key[r] >> 9;
           uint32_t j = i;
           while (j > 0 && (m.obs_key[idx[j - 1]] >> 9) > kr) {
             idx[j] = idx[j - 1];
@@ -249,7 +267,7 @@ struct LidarObs {
         }
         for (uint32_t i = 0; i < cnt; ++i) {
           float Wn;
-          welford<FP16>(m.obs_d[idx[i]], D[k], W[k], S2[k], Wn);
+          welford<FP16>(m.obs_d[idx[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
         }
       }
       n_upd += (int)cnt;
@@ -258,295 +276,311 @@ struct LidarObs {
   }
 };
 
-// -------------------------------------------------------------------------------------------- generic fusion kernel
+// -------------------------------------------------------------------------------------------- warp fusion body
+
+template <bool FP16, bool COLOR>
+struct BlockIO {
+  uint8_t* blk;
+  int nv;
+  __device__ inline void load(int i4, Chunk& ch) const {
+    Field<FP16>::load4(blk, i4, ch.D);
+    Field<false>::load4(blk + off_W(nv, FP16, COLOR), i4, ch.W);
+    Field<false>::load4(blk + off_S2(nv, FP16, COLOR), i4, ch.S2);
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Field<FP16>::load4(blk + off_C(nv, FP16, q), i4, ch.C[q]);
+    }
+  }
+  __device__ inline void store(int i4, const Chunk& ch) const {
+    Field<FP16>::store4(blk, i4, ch.D);
+    Field<false>::store4(blk + off_W(nv, FP16, COLOR), i4, ch.W);
+    Field<false>::store4(blk + off_S2(nv, FP16, COLOR), i4, ch.S2);
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Field<FP16>::store4(blk + off_C(nv, FP16, q), i4, ch.C[q]);
+    }
+  }
+};
+
+__device__ inline void zero_chunk(Chunk& ch) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ch.D[k] = ch.W[k] = ch.S2[k] = 0.0f;
+    ch.C[0][k] = ch.C[1][k] = ch.C[2][k] = 0.0f;
+  }
+}
+
+// merge (Sec. 3.2.1, Fig. 4a): coarse voxel = W-weighted pool of its observed 2x2x2 children of block `src`;
+// W = max child weight; S2 = pooled variance times W. Lanes li, li + G, ... of the group write coarse voxels.
+template <bool FP16, bool COLOR>
+__device__ void merge_block(const uint8_t* src, int nl, uint8_t* dst, int li, int G) {
+  using F = Field<FP16>;
+  const int nv = nl * nl * nl, nc = nl / 2, nvc = nc * nc * nc;
+  const float* sW = reinterpret_cast<const float*>(src + off_W(nv, FP16, COLOR));
+  const float* sS = reinterpret_cast<const float*>(src + off_S2(nv, FP16, COLOR));
+  for (int ci = li; ci < nvc; ci += G) {
+    const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
+    float sw = 0.f, swd = 0.f, ss2 = 0.f, wmax = 0.f, swc[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 8; ++q) {
+      const int ch = (2 * cx + (q & 1)) + nl * ((2 * cy + ((q >> 1) & 1)) + nl * (2 * cz + (q >> 2)));
+      const float Wi = sW[ch];
+      if (!(Wi > 0.0f)) continue;
+      sw = sw + Wi;
+      swd = swd + Wi * F::get1(src, ch);
+      ss2 = ss2 + sS[ch];
+      if (Wi > wmax) wmax = Wi;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) swc[c] = swc[c] + Wi * F::get1(src + off_C(nv, FP16, c), ch);
+      }
+    }
+    float oD = 0.f, oW = 0.f, oS = 0.f, oC[3] = {0.f, 0.f, 0.f};
+    if (sw > 0.0f) {
+      const float var = ss2 / sw;
+      oD = swd / sw;
+      oW = wmax;
+      oS = var * wmax;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = swc[c] / sw;
+      }
+    }
+    F::store1(dst, ci, oD);
+    reinterpret_cast<float*>(dst + off_W(nvc, FP16, COLOR))[ci] = oW;
+    reinterpret_cast<float*>(dst + off_S2(nvc, FP16, COLOR))[ci] = oS;
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F::store1(dst + off_C(nvc, FP16, c), ci, oC[c]);
+    }
+  }
+}
+
+// split (extension): fine voxel = trilinear interpolation of the observed coarse voxels at its centre (clamped to
+// the block); W and S2 from the coarse voxel that contains it.
+template <bool FP16, bool COLOR>
+__device__ void split_block(const uint8_t* src, int nc, uint8_t* dst, int li, int G) {
+  using F = Field<FP16>;
+  const int nv = nc * nc * nc, nf = 2 * nc, nvf = nf * nf * nf;
+  const float* sW = reinterpret_cast<const float*>(src + off_W(nv, FP16, COLOR));
+  const float* sS = reinterpret_cast<const float*>(src + off_S2(nv, FP16, COLOR));
+  for (int fi = li; fi < nvf; fi += G) {
+    const int f[3] = {fi % nf, (fi / nf) % nf, fi / (nf * nf)};
+    int i0[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float p = (float)f[a] * 0.5f - 0.25f;
+      if (p < 0.0f) p = 0.0f;
+      if (p > (float)(nc - 1)) p = (float)(nc - 1);
+      int i = (int)floorf(p);
+      if (i > nc - 2) i = nc - 2;
+      i0[a] = i;
+      fr[a] = p - (float)i;
+    }
+    float sw = 0.f, sd = 0.f, sc[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 8; ++q) {
+      const int ax = q & 1, ay = (q >> 1) & 1, az = q >> 2;
+      const int cv = (i0[0] + ax) + nc * ((i0[1] + ay) + nc * (i0[2] + az));
+      if (!(sW[cv] > 0.0f)) continue;
+      const float wx = ax ? fr[0] : 1.0f - fr[0];
+      const float wy = ay ? fr[1] : 1.0f - fr[1];
+      const float wz = az ? fr[2] : 1.0f - fr[2];
+      const float w = wx * wy * wz;
+      sw = sw + w;
+      sd = sd + w * F::get1(src, cv);
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sc[c] = sc[c] + w * F::get1(src + off_C(nv, FP16, c), cv);
+      }
+    }
+    const int own = (f[0] >> 1) + nc * ((f[1] >> 1) + nc * (f[2] >> 1));
+    float oD, oC[3] = {0.f, 0.f, 0.f};
+    if (sw > 0.0f) {
+      oD = sd / sw;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = sc[c] / sw;
+      }
+    } else {
+      oD = F::get1(src, own);
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = F::get1(src + off_C(nv, FP16, c), own);
+      }
+    }
+    F::store1(dst, fi, oD);
+    reinterpret_cast<float*>(dst + off_W(nvf, FP16, COLOR))[fi] = sW[own];
+    reinterpret_cast<float*>(dst + off_S2(nvf, FP16, COLOR))[fi] = sS[own];
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F::store1(dst + off_C(nvf, FP16, c), fi, oC[c]);
+    }
+  }
+}
 
 template <bool FP16, bool COLOR, class Obs>
-__device__ inline void fuse_body(const MapDev& m, Obs& obs) {
-  using F = Field<FP16>;
-  __shared__ float sD[512], sW[512], sS2[512];
-  __shared__ float sC[COLOR ? 3 : 1][COLOR ? 512 : 1];
-  __shared__ int s_act[64];
-  __shared__ uint32_t s_ptr[64];
-  __shared__ float s_rv[4];
-  __shared__ int s_rn[4];
-  __shared__ long long s_rw[4];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ inline void fuse_warp_body(const MapDev& m, Obs& obs, int warp_in_cta, uint32_t warp_id, uint32_t nwarps) {
+  const int lane = threadIdx.x & 31;
   const uint32_t n0 = min(m.st->touched_count[0], m.max_touched);
   const uint32_t n1 = m.L > 1 ? min(m.st->touched_count[1], m.max_touched) : 0;
   const uint32_t n2 = m.L > 2 ? min(m.st->touched_count[2], m.max_touched) : 0;
-  const uint32_t it0 = n0, it1 = (n1 + 7) / 8, it2 = (n2 + 63) / 64;
+  const uint32_t it0 = n0, it1 = (n1 + 1) / 2, it2 = (n2 + 15) / 16;
   const uint32_t items = it0 + it1 + it2;
   unsigned long long my_obs = 0;
 
-  for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+  for (uint32_t item = warp_id; item < items; item += nwarps) {
     Ctx x;
     uint32_t first, count, pbase;
     if (item < it0) { x.l = 0; first = item; count = n0; pbase = 0; }
-    else if (item < it0 + it1) { x.l = 1; first = (item - it0) * 8; count = n1; pbase = n0; }
-    else { x.l = 2; first = (item - it0 - it1) * 64; count = n2; pbase = n0 + n1; }
+    else if (item < it0 + it1) { x.l = 1; first = (item - it0) * 2; count = n1; pbase = n0; }
+    else { x.l = 2; first = (item - it0 - it1) * 16; count = n2; pbase = n0 + n1; }
     x.nl = kFineDim >> x.l;
     x.nv = x.nl * x.nl * x.nl;
-    x.G = x.nv / 4;
-    x.g = tid / x.G;
-    x.li = tid % x.G;
-    x.idx = first + x.g;
-    x.active = x.idx < count;
-    x.P = pbase + x.idx;
+    x.G = x.nv < 128 ? x.nv / 4 : 32;  // lanes per block: 32, 16, 2
+    x.g = lane / x.G;
+    x.li = lane % x.G;
+    const uint32_t idx = first + x.g;
+    x.active = idx < count;
+    x.P = pbase + idx;
     x.P_first = pbase + first;
-    const int l = x.l, nl = x.nl, nv = x.nv, G = x.G, g = x.g, li = x.li;
-    const bool active = x.active;
+    const int l = x.l, nl = x.nl, nv = x.nv, G = x.G, li = x.li;
+    const int chunks = nv / (4 * G);  // 4, 1, 1
 
-    uint32_t slot = 0, val = 0, ptr = 0;
-    bool isnew = true;
-    x.kx = x.ky = x.kz = 0;
-    if (active) {
-      slot = m.touched[l][x.idx];
-      val = m.slots[slot].val;
-      ptr = val & kPtrMask;
-      isnew = (val & kValNew) != 0;
-      unpack_key(m.slots[slot].key, &x.kx, &x.ky, &x.kz);
-    }
-    uint8_t* blk = m.heap[l] + (size_t)ptr * m.block_bytes[l];
-    uint8_t* pW = blk + off_W(nv, FP16, COLOR);
-    uint8_t* pS = blk + off_S2(nv, FP16, COLOR);
+    BlockMeta bm;
+    bm.key = 0;
+    bm.val = 0;
+    bm.slot = 0;
+    if (x.active) bm = m.meta[l][idx];
+    const bool isnew = (bm.val & kValNew) != 0;
+    const uint32_t ptr = bm.val & kPtrMask;
+    unpack_key(bm.key, &x.kx, &x.ky, &x.kz);
+    const BlockIO<FP16, COLOR> io{m.heap[l] + (size_t)ptr * m.block_bytes[l], nv};
+    const bool load = x.active && !isnew;
 
-    float D[4] = {0, 0, 0, 0}, W[4] = {0, 0, 0, 0}, S2[4] = {0, 0, 0, 0};
-    float C[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    if (active && !isnew) {
-      F::load4(blk, li, D);
-      Field<false>::load4(pW, li, W);
-      Field<false>::load4(pS, li, S2);
-      if constexpr (COLOR) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) F::load4(blk + off_C(nv, FP16, q), li, C[q]);
-      }
-    }
+    obs.collect(m, x, warp_in_cta);
 
-    obs.collect(m, x);
-    my_obs += (unsigned long long)obs.apply(m, x, D, W, S2, C);
-
-    // ---- stage in shared memory, block statistics (Sec. 3.2.1: mean voxel variance of the block)
+    // ---- chunks: prefetch the next chunk, update the current one, write it back, accumulate block statistics
     float vsum = 0.f;
     int nobs = 0;
     long long sumw = 0;
+    Chunk cur, nxt;
+    if (load) io.load(li, cur);
+    else zero_chunk(cur);
+    for (int c = 0; c < chunks; ++c) {
+      if (c + 1 < chunks) {
+        if (load) io.load((c + 1) * G + li, nxt);
+        else zero_chunk(nxt);
+      }
+      if (x.active) {
+        my_obs += (unsigned long long)obs.apply(m, x, 4 * (c * G + li), cur);
+        io.store(c * G + li, cur);
+      }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int si = 4 * tid + k;  // == g * nv + 4 li + k
-      sD[si] = D[k];
-      sW[si] = W[k];
-      sS2[si] = S2[k];
-      if constexpr (COLOR) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) sC[q][si] = C[q][k];
-      }
-      if (W[k] > 0.0f) {
-        vsum = vsum + S2[k] / W[k];
-        nobs += 1;
-        sumw += (long long)W[k];
-      }
-    }
-    const int width = G < 32 ? G : 32;
-    for (int off = width / 2; off > 0; off >>= 1) {
-      vsum = vsum + __shfl_xor_sync(~0u, vsum, off);
-      nobs += __shfl_xor_sync(~0u, nobs, off);
-      sumw += __shfl_xor_sync(~0u, sumw, off);
-    }
-    if (G == 128 && lane == 0) {
-      s_rv[warp] = vsum;
-      s_rn[warp] = nobs;
-      s_rw[warp] = sumw;
-    }
-    __syncthreads();
-    if (li == 0) {
-      if (G == 128) {
-        vsum = s_rv[0] + s_rv[1] + s_rv[2] + s_rv[3];
-        nobs = s_rn[0] + s_rn[1] + s_rn[2] + s_rn[3];
-        sumw = s_rw[0] + s_rw[1] + s_rw[2] + s_rw[3];
-      }
-      int act = kActNone;
-      uint32_t newptr = 0;
-      // eligibility: observed, mean weight >= k_min over observed voxels
-      if (active && nobs > 0 && sumw >= (long long)m.min_obs * nobs) {
-        const double vb32 = (double)(vsum / (float)nobs);
-        bool have_exact = false;
-        double vexact = 0.0;
-        auto vbar_near = [&](double thr) -> double {
-          if (fabs(vb32 - thr) <= kBand * fabs(thr)) {
-            if (!have_exact) {
-              double acc = 0.0;
-              for (int i = 0; i < nv; ++i) {
-                float w = sW[g * nv + i];
-                if (w > 0.0f) acc = acc + (double)sS2[g * nv + i] / (double)w;
-              }
-              vexact = acc / (double)nobs;
-              have_exact = true;
-              atomicAdd(&m.st->rechecks, 1u);
-            }
-            return vexact;
-          }
-          return vb32;
-        };
-        if (l < m.L - 1 && vbar_near(m.theta[l]) < m.theta[l]) {
-          act = kActMerge;
-        } else if (m.split_h > 0.0 && l > 0) {
-          const double thr = m.split_h * m.theta[l - 1];
-          if (vbar_near(thr) > thr) act = kActSplit;
-        }
-        if (act != kActNone) {
-          const int lt = act == kActMerge ? l + 1 : l - 1;
-          int t = atomicSub(&m.st->free_top[lt], 1);
-          if (t <= 0) {
-            atomicAdd(&m.st->free_top[lt], 1);
-            set_status(m.st, kStPoolEmpty);
-            act = kActNone;
-          } else {
-            newptr = m.free_stack[lt][t - 1];
-          }
+      for (int q = 0; q < 4; ++q) {
+        if (cur.W[q] > 0.0f) {
+          vsum = vsum + cur.S2[q] / cur.W[q];
+          nobs += 1;
+          sumw += (long long)(uint32_t)cur.W[q];
         }
       }
-      s_act[g] = act;
-      s_ptr[g] = newptr;
+      if (c + 1 < chunks) cur = nxt;
     }
-    __syncthreads();
+    for (int o = G / 2; o > 0; o >>= 1) {
+      vsum = vsum + __shfl_xor_sync(~0u, vsum, o);
+      nobs += __shfl_xor_sync(~0u, nobs, o);
+      sumw += __shfl_xor_sync(~0u, sumw, o);
+    }
 
-    const int act = active ? s_act[g] : kActNone;
-    if (active && act == kActNone) {
-      F::store4(blk, li, D);
-      Field<false>::store4(pW, li, W);
-      Field<false>::store4(pS, li, S2);
-      if constexpr (COLOR) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) F::store4(blk + off_C(nv, FP16, q), li, C[q]);
-      }
-    } else if (act == kActMerge) {
-      // coarse voxel = W-weighted pool of its observed 2x2x2 children; W = max child weight; S2 = pooled
-      // variance times W
-      const int nc = nl / 2, nvc = nc * nc * nc;
-      uint8_t* nb = m.heap[l + 1] + (size_t)s_ptr[g] * m.block_bytes[l + 1];
-      for (int ci = li; ci < nvc; ci += G) {
-        const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
-        float sw = 0.f, swd = 0.f, ss2 = 0.f, wmax = 0.f, swc[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < 8; ++k) {
-          const int ch = g * nv + (2 * cx + (k & 1)) + nl * ((2 * cy + ((k >> 1) & 1)) + nl * (2 * cz + (k >> 2)));
-          const float Wi = sW[ch];
-          if (!(Wi > 0.0f)) continue;
-          sw = sw + Wi;
-          swd = swd + Wi * sD[ch];
-          ss2 = ss2 + sS2[ch];
-          if (Wi > wmax) wmax = Wi;
-          if constexpr (COLOR) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) swc[q] = swc[q] + Wi * sC[q][ch];
-          }
-        }
-        float oD = 0.f, oW = 0.f, oS = 0.f, oC[3] = {0.f, 0.f, 0.f};
-        if (sw > 0.0f) {
-          const float var = ss2 / sw;
-          oD = swd / sw;
-          oW = wmax;
-          oS = var * wmax;
-          if constexpr (COLOR) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) oC[q] = swc[q] / sw;
-          }
-        }
-        F::store1(nb, ci, oD);
-        reinterpret_cast<float*>(nb + off_W(nvc, FP16, COLOR))[ci] = oW;
-        reinterpret_cast<float*>(nb + off_S2(nvc, FP16, COLOR))[ci] = oS;
-        if constexpr (COLOR) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q) F::store1(nb + off_C(nvc, FP16, q), ci, oC[q]);
-        }
-      }
-    } else if (act == kActSplit) {
-      // fine voxel = trilinear interpolation of the observed coarse voxels at its centre (clamped to the block);
-      // W and S2 from the coarse voxel that contains it
-      const int nc = nl, nf = 2 * nl, nvf = nf * nf * nf;
-      uint8_t* nb = m.heap[l - 1] + (size_t)s_ptr[g] * m.block_bytes[l - 1];
-      for (int fi = li; fi < nvf; fi += G) {
-        const int f[3] = {fi % nf, (fi / nf) % nf, fi / (nf * nf)};
-        int i0[3];
-        float fr[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          float p = (float)f[a] * 0.5f - 0.25f;
-          if (p < 0.0f) p = 0.0f;
-          if (p > (float)(nc - 1)) p = (float)(nc - 1);
-          int i = (int)floorf(p);
-          if (i > nc - 2) i = nc - 2;
-          i0[a] = i;
-          fr[a] = p - (float)i;
-        }
-        float sw = 0.f, sd = 0.f, sc[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < 8; ++k) {
-          const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
-          const int cv = g * nv + (i0[0] + ax) + nc * ((i0[1] + ay) + nc * (i0[2] + az));
-          if (!(sW[cv] > 0.0f)) continue;
-          const float wx = ax ? fr[0] : 1.0f - fr[0];
-          const float wy = ay ? fr[1] : 1.0f - fr[1];
-          const float wz = az ? fr[2] : 1.0f - fr[2];
-          const float w = wx * wy * wz;
-          sw = sw + w;
-          sd = sd + w * sD[cv];
-          if constexpr (COLOR) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) sc[q] = sc[q] + w * sC[q][cv];
-          }
-        }
-        const int own = g * nv + (f[0] >> 1) + nc * ((f[1] >> 1) + nc * (f[2] >> 1));
-        float oD, oC[3] = {0.f, 0.f, 0.f};
-        if (sw > 0.0f) {
-          oD = sd / sw;
-          if constexpr (COLOR) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) oC[q] = sc[q] / sw;
-          }
-        } else {
-          oD = sD[own];
-          if constexpr (COLOR) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) oC[q] = sC[q][own];
-          }
-        }
-        F::store1(nb, fi, oD);
-        reinterpret_cast<float*>(nb + off_W(nvf, FP16, COLOR))[fi] = sW[own];
-        reinterpret_cast<float*>(nb + off_S2(nvf, FP16, COLOR))[fi] = sS2[own];
-        if constexpr (COLOR) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q) F::store1(nb + off_C(nvf, FP16, q), fi, oC[q]);
-        }
-      }
+    // ---- decision (every lane of the group computes the same one)
+    int act = kActNone;
+    bool recheck = false;
+    double thr_m = 0.0, thr_s = 0.0;
+    const double vb32 = nobs > 0 ? (double)(vsum / (float)nobs) : 0.0;
+    const bool eligible = x.active && nobs > 0 && sumw >= (long long)m.min_obs * nobs;
+    const bool can_merge = eligible && l < m.L - 1;
+    const bool can_split = eligible && m.split_h > 0.0 && l > 0;
+    if (can_merge) {
+      thr_m = m.theta[l];
+      recheck |= fabs(vb32 - thr_m) <= kBand * fabs(thr_m);
     }
-    if (active && li == 0) {
-      if (act != kActNone) {
+    if (can_split) {
+      thr_s = m.split_h * m.theta[l - 1];
+      recheck |= fabs(vb32 - thr_s) <= kBand * fabs(thr_s);
+    }
+    double vbar = vb32;
+    const int leader = lane - li;
+    if (__any_sync(~0u, recheck)) {
+      __syncwarp();  // the group's payload writes are visible to its leader
+      double exact = 0.0;
+      if (recheck && li == 0) {
+        const float* W = reinterpret_cast<const float*>(io.blk + off_W(nv, FP16, COLOR));
+        const float* S = reinterpret_cast<const float*>(io.blk + off_S2(nv, FP16, COLOR));
+        double acc = 0.0;
+        for (int i = 0; i < nv; ++i) {
+          const float w = W[i];
+          if (w > 0.0f) acc = acc + (double)S[i] / (double)w;
+        }
+        exact = acc / (double)nobs;
+        atomicAdd(&m.st->rechecks, 1u);
+      }
+      exact = __shfl_sync(~0u, exact, leader);
+      if (recheck) vbar = exact;
+    }
+    if (can_merge && vbar < thr_m) act = kActMerge;
+    else if (can_split && vbar > thr_s) act = kActSplit;
+
+    // ---- re-level (rare): pop a heap block of the target level, resample into it, retire the old block
+    if (__any_sync(~0u, act != kActNone)) {
+      uint32_t newptr = 0;
+      if (act != kActNone && li == 0) {
         const int lt = act == kActMerge ? l + 1 : l - 1;
-        m.slots[slot].val = s_ptr[g] | ((uint32_t)lt << 28);
-        uint32_t r = atomicAdd(&m.st->retire_count, 1u);
+        const int t = atomicSub(&m.st->free_top[lt], 1);
+        if (t <= 0) {
+          atomicAdd(&m.st->free_top[lt], 1);
+          set_status(m.st, kStPoolEmpty);
+          newptr = kInvalidPtr;
+        } else {
+          newptr = m.free_stack[lt][t - 1];
+        }
+      }
+      newptr = __shfl_sync(~0u, newptr, leader);
+      if (newptr == kInvalidPtr) act = kActNone;
+      __syncwarp();  // the group's payload writes are visible to every lane that resamples them
+      if (act == kActMerge) {
+        merge_block<FP16, COLOR>(io.blk, nl, m.heap[l + 1] + (size_t)newptr * m.block_bytes[l + 1], li, G);
+      } else if (act == kActSplit) {
+        split_block<FP16, COLOR>(io.blk, nl, m.heap[l - 1] + (size_t)newptr * m.block_bytes[l - 1], li, G);
+      }
+      if (act != kActNone && li == 0) {
+        const int lt = act == kActMerge ? l + 1 : l - 1;
+        m.slots[bm.slot].val = newptr | ((uint32_t)lt << 28);
+        const uint32_t r = atomicAdd(&m.st->retire_count, 1u);
         m.retire[r] = ptr | ((uint32_t)l << 28);
         atomicAdd(act == kActMerge ? &m.st->merged : &m.st->split, 1u);
-      } else if (isnew) {
-        m.slots[slot].val = val & ~kValNew;
       }
     }
-    __syncthreads();
+    if (act == kActNone && isnew && x.active && li == 0) m.slots[bm.slot].val = bm.val & ~kValNew;
   }
-  for (int off = 16; off > 0; off >>= 1) my_obs += __shfl_xor_sync(~0u, my_obs, off);
+  for (int o = 16; o > 0; o >>= 1) my_obs += __shfl_xor_sync(~0u, my_obs, o);
   if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
 }
 
+constexpr int kCamWarps = 8;
+
 template <bool FP16, bool COLOR>
-__global__ void __launch_bounds__(kThreads) k_fuse_depth(MapDev m, CamArgs c, const float* __restrict__ depth,
-                                                         const uint8_t* __restrict__ rgb) {
-  CameraObs<FP16, COLOR> obs{c, depth, rgb};
-  fuse_body<FP16, COLOR>(m, obs);
+__global__ void __launch_bounds__(32 * kCamWarps, 3) k_fuse_depth(MapDev m, CamArgs c, const float* __restrict__ rho,
+                                                                 const uint32_t* __restrict__ rgb) {
+  CameraObs<FP16, COLOR> obs{c, rho, rgb};
+  const int warp = threadIdx.x >> 5;
+  fuse_warp_body<FP16, COLOR>(m, obs, warp, blockIdx.x * kCamWarps + warp, gridDim.x * kCamWarps);
 }
 
 template <bool FP16, bool COLOR>
-__global__ void __launch_bounds__(kThreads) k_fuse_points(MapDev m) {
-  __shared__ uint32_t s_cnt[512], s_off[1024];
-  LidarObs<FP16> obs{s_cnt, s_off, 0};
-  fuse_body<FP16, COLOR>(m, obs);
+__global__ void __launch_bounds__(32 * kLidarWarps) k_fuse_points(MapDev m) {
+  __shared__ uint32_t s_bins[kLidarWarps][3][512];
+  LidarObs<FP16> obs{s_bins, 0};
+  const int warp = threadIdx.x >> 5;
+  fuse_warp_body<FP16, COLOR>(m, obs, warp, blockIdx.x * kLidarWarps + warp, gridDim.x * kLidarWarps);
 }
 
 // -------------------------------------------------------------------------------------------- LiDAR observation passes
@@ -703,15 +737,15 @@ __global__ void __launch_bounds__(1024) k_scan_obs(MapDev m) {
 
 }  // namespace
 
-void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, cudaStream_t s,
+void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* rho, const uint32_t* rgb, cudaStream_t s,
                        int sms) {
-  const int grid = sms * 16;
+  const int grid = sms * 8;
   if (m.fp16) {
-    if (m.color) k_fuse_depth<true, true><<<grid, kThreads, 0, s>>>(m, c, depth, rgb);
-    else k_fuse_depth<true, false><<<grid, kThreads, 0, s>>>(m, c, depth, rgb);
+    if (m.color) k_fuse_depth<true, true><<<grid, 32 * kCamWarps, 0, s>>>(m, c, rho, rgb);
+    else k_fuse_depth<true, false><<<grid, 32 * kCamWarps, 0, s>>>(m, c, rho, rgb);
   } else {
-    if (m.color) k_fuse_depth<false, true><<<grid, kThreads, 0, s>>>(m, c, depth, rgb);
-    else k_fuse_depth<false, false><<<grid, kThreads, 0, s>>>(m, c, depth, rgb);
+    if (m.color) k_fuse_depth<false, true><<<grid, 32 * kCamWarps, 0, s>>>(m, c, rho, rgb);
+    else k_fuse_depth<false, false><<<grid, 32 * kCamWarps, 0, s>>>(m, c, rho, rgb);
   }
 }
 
@@ -731,13 +765,13 @@ void launch_lidar_observations(const MapDev& m, const double* T, const float* xy
 }
 
 void launch_fuse_points(const MapDev& m, const double*, const float*, uint64_t, cudaStream_t s, int sms) {
-  const int grid = sms * 12;
+  const int grid = sms * 8;
   if (m.fp16) {
-    if (m.color) k_fuse_points<true, true><<<grid, kThreads, 0, s>>>(m);
-    else k_fuse_points<true, false><<<grid, kThreads, 0, s>>>(m);
+    if (m.color) k_fuse_points<true, true><<<grid, 32 * kLidarWarps, 0, s>>>(m);
+    else k_fuse_points<true, false><<<grid, 32 * kLidarWarps, 0, s>>>(m);
   } else {
-    if (m.color) k_fuse_points<false, true><<<grid, kThreads, 0, s>>>(m);
-    else k_fuse_points<false, false><<<grid, kThreads, 0, s>>>(m);
+    if (m.color) k_fuse_points<false, true><<<grid, 32 * kLidarWarps, 0, s>>>(m);
+    else k_fuse_points<false, false><<<grid, 32 * kLidarWarps, 0, s>>>(m);
   }
 }
 

@@ -34,6 +34,7 @@ constexpr int kMaxProbes = 2048;                  // single-thread probing
 constexpr int kMaxSegmentCells = 64;
 constexpr int kMaxVoxelCells = 256;
 constexpr int kRaycastMaxIter = 8192;
+constexpr int kBrickShift = 2;  // a brick is 4 x 4 x 4 blocks
 
 // status bits (sticky)
 constexpr uint32_t kStHashFull = 1u << 0;
@@ -41,11 +42,19 @@ constexpr uint32_t kStPoolEmpty = 1u << 1;
 constexpr uint32_t kStListFull = 1u << 2;
 constexpr uint32_t kStSegment = 1u << 3;
 constexpr uint32_t kStObsFull = 1u << 4;
+constexpr uint32_t kStTimeout = 1u << 5;  // a bounded wait on an async copy gave up
 
 struct __align__(16) Slot {
   unsigned long long key;
   uint32_t val;    // heap id (28 bits) | level << 28 | kValNew, or kValPending
   uint32_t stamp;  // frame number of the last frame that touched the block
+};
+
+// Per touched block, written by k_bin in binned order: everything a fusion warp needs in one 16-byte load.
+struct __align__(16) BlockMeta {
+  unsigned long long key;
+  uint32_t val;
+  uint32_t slot;
 };
 
 struct DevState {
@@ -73,6 +82,7 @@ struct MapDev {
   uint32_t block_bytes[kMaxLevels];
   uint32_t* touched_all;
   uint32_t* touched[kMaxLevels];
+  BlockMeta* meta[kMaxLevels];  // parallel to touched[l]
   uint32_t max_touched;
   uint32_t* retire;
   uint32_t* slot_pos;         // per slot: level << 28 | position in touched[level] (written by k_bin)
@@ -85,7 +95,10 @@ struct MapDev {
   uint32_t* obs_idx;          // per-voxel bins of observation indices
   uint32_t max_obs;
   DevState* st;
+  unsigned long long* brick_keys;  // insert-only set of 4x4x4-block bricks holding an allocated block (raycast)
+  uint32_t brick_mask;
   float v[kMaxLevels];  // voxel edge per level
+  float inv_v[kMaxLevels];  // 1 / v, as the float division computes it
   float E;              // block edge
   float tau;
   float fix_scale;      // 65536 / E (float), camera key quantisation
@@ -261,13 +274,59 @@ __device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* x
          key_ok(floor_div(B[0], kBlockUnit), floor_div(B[1], kBlockUnit), floor_div(B[2], kBlockUnit));
 }
 
+// ---------------------------------------------------------------------------------------------------- async copies
+// Bulk (non-tensor) asynchronous copies between global and shared memory, completed through an mbarrier (loads) or a
+// per-thread bulk group (stores). Addresses must be 16-byte aligned and sizes multiples of 16.
+
+__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// arrive once and add `bytes` to the transaction count of the current phase
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false when the phase did not complete within the iteration limit
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter = 1u << 22) {
+  for (uint32_t i = 0; i < max_iter; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ inline void bulk_load(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ inline void bulk_store(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem), "r"(smem_addr(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's generic-proxy shared-memory writes before later async-proxy accesses
+__device__ inline void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------------------------------- host side
 
 // launch helpers implemented in the .cu files
-void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, cudaStream_t s);
+void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, float* rho_img,
+                        uint32_t* rgb_img, cudaStream_t s);
 void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s);
 void launch_bin(const MapDev& m, cudaStream_t s, int sms);
-void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, cudaStream_t s,
+void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* rho, const uint32_t* rgb, cudaStream_t s,
                        int sms);
 void launch_fuse_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s, int sms);
 void launch_lidar_observations(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s,

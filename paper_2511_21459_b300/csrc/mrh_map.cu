@@ -38,6 +38,10 @@ struct mrh_map {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
+  // per-frame images for the camera path (range image, packed colour), grown to the largest frame seen
+  float* rho_img = nullptr;
+  uint32_t* rgb_img = nullptr;
+  size_t img_pixels = 0;
 };
 
 namespace {
@@ -318,6 +322,11 @@ mrh_status dev_alloc(mrh_map* m, T** out, size_t count) {
 void free_all(mrh_map* m) {
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
+  if (m->rho_img) cudaFree(m->rho_img);
+  if (m->rgb_img) cudaFree(m->rgb_img);
+  m->rho_img = nullptr;
+  m->rgb_img = nullptr;
+  m->img_pixels = 0;
   for (auto& p : m->pending) {
     m->event_pool.push_back(p.a);
     m->event_pool.push_back(p.b);
@@ -389,7 +398,10 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   d.color = params->has_color;
   d.min_obs = params->min_obs;
   float v0 = params->base_voxel_size / (float)(1 << (d.L - 1));
-  for (int l = 0; l < kMaxLevels; ++l) d.v[l] = v0 * (float)(1 << l);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    d.v[l] = v0 * (float)(1 << l);
+    d.inv_v[l] = 1.0f / d.v[l];
+  }
   d.E = v0 * (float)kFineDim;
   d.tau = params->truncation;
   d.fix_scale = 65536.0f / d.E;
@@ -416,6 +428,9 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   TRY(dev_alloc(m, &d.touched_all, params->max_touched));
   TRY(dev_alloc(m, &d.retire, params->max_touched));
   TRY(dev_alloc(m, &d.slot_pos, n_slots));
+  const uint32_t n_brick_slots = 1u << (params->hash_slots_log2 > 12 ? params->hash_slots_log2 - 2 : 10);
+  d.brick_mask = n_brick_slots - 1;
+  TRY(dev_alloc(m, &d.brick_keys, n_brick_slots));
   TRY(dev_alloc(m, &d.blk_count, 3ull * params->max_touched));
   TRY(dev_alloc(m, &d.blk_fill, 3ull * params->max_touched));
   TRY(dev_alloc(m, &d.blk_off, 3ull * params->max_touched + 1));
@@ -431,14 +446,17 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
       TRY(dev_alloc(m, &d.heap[l], (size_t)d.max_blocks[l] * d.block_bytes[l]));
       TRY(dev_alloc(m, &d.free_stack[l], d.max_blocks[l]));
       TRY(dev_alloc(m, &d.touched[l], params->max_touched));
+      TRY(dev_alloc(m, &d.meta[l], params->max_touched));
     } else {
       d.heap[l] = nullptr;
       d.free_stack[l] = nullptr;
       d.touched[l] = nullptr;
+      d.meta[l] = nullptr;
     }
   }
 #undef TRY
   cudaError_t e = cudaMemset(d.slots, 0xFF, (size_t)n_slots * sizeof(Slot));
+  if (e == cudaSuccess) e = cudaMemset(d.brick_keys, 0xFF, (size_t)n_brick_slots * sizeof(unsigned long long));
   DevState hs;
   std::memset(&hs, 0, sizeof(hs));
   for (int l = 0; l < kMaxLevels; ++l) hs.free_top[l] = (int)d.max_blocks[l];
@@ -474,10 +492,23 @@ mrh_status mrh_integrate_depth(mrh_map* m, const mrh_pinhole* K, const double* T
   DeviceGuard guard(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   CamArgs c = cam_args(K, T_wc);
+  const size_t pixels = (size_t)K->width * K->height;
+  if (pixels > m->img_pixels) {
+    // first frame (or a larger one): grow the per-frame images; stream-ordered, so earlier frames are unaffected
+    if (m->rho_img) cudaFreeAsync(m->rho_img, s);
+    if (m->rgb_img) cudaFreeAsync(m->rgb_img, s);
+    m->rho_img = nullptr;
+    m->rgb_img = nullptr;
+    m->img_pixels = 0;
+    MRH_CUDA(cudaMallocAsync(&m->rho_img, pixels * sizeof(float), s));
+    MRH_CUDA(cudaMallocAsync(&m->rgb_img, pixels * sizeof(uint32_t), s));
+    m->img_pixels = pixels;
+  }
+  const uint8_t* rgb_in = m->p.has_color ? rgb : nullptr;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
-  { KernelScope ks(m, MRH_K_ALLOC, s, 1); launch_alloc_depth(m->d, c, depth, s); }
+  { KernelScope ks(m, MRH_K_ALLOC, s, 1); launch_alloc_depth(m->d, c, depth, rgb_in, m->rho_img, m->rgb_img, s); }
   { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
-  { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_depth(m->d, c, depth, m->p.has_color ? rgb : nullptr, s, m->sms); }
+  { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_depth(m->d, c, m->rho_img, rgb_in ? m->rgb_img : nullptr, s, m->sms); }
   { KernelScope ks(m, MRH_K_RELEASE, s, 1); k_release<<<m->sms, 256, 0, s>>>(m->d); }
   MRH_CUDA(cudaGetLastError());
   return MRH_OK;
