@@ -64,9 +64,12 @@ def profile_case(kind: str) -> int:
         m = mrh.Map(mrh.params_from(wl))
         K = mrh.pinhole_from(wl)
         out = torch.empty((wl.height, wl.width), device="cuda")
-        for d, c, T in camera_frames(wl, 0, 6):
+        for k, (d, c, T) in enumerate(camera_frames(wl, 0, 6)):
             m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
             m.raycast(K, T, out)
+            st = m.stats()
+            print(json.dumps({"frame": k, "touched_level": st["touched_level"], "new_blocks": st["new_blocks"],
+                              "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
     else:
         wl = synth.lidar()
         wl.max_blocks = (1 << 18, 1 << 16, 1 << 16)
@@ -424,7 +427,9 @@ def main():
         import hashlib
         src = open(os.path.join(ROOT, "paper_2511_21459_b300", "csrc", "mrh_fuse.cu"), "rb").read()
         if tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = tr.get("dram_bytes_per_launch")
+            # one ncu capture of a full-size frame of the same sequence, scaled to this run's launches by the
+            # algorithmic bytes (units) they process
+            traffic = int(tr["dram_bytes_per_algorithmic_byte"] * res["fuse_bytes"] / args.steps)
     roofline = {"kernel": "k_fuse_depth (fusion + block variance + re-level)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "peak_kind": peak_kind, "traffic": traffic,

@@ -63,7 +63,7 @@ typedef struct {
   float min_depth, max_depth;
 } mrh_pinhole;
 
-/* Map parameters (Sec. 3.2 grid, Sec. 3.2.1 merging criterion, Sec. 5.1 implementation details). */
+/* Map parameters (Sec. 3.2 grid, Sec. 3.2.1 merging criterion, Sec. 4.1.4 implementation details). */
 typedef struct {
   float base_voxel_size;     /* voxel edge of the coarsest level v_{L-1} [m]; v_0 = base / 2^(L-1) */
   int32_t n_levels;          /* L, 1..3 */

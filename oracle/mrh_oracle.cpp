@@ -39,7 +39,7 @@ namespace {
 
 // ------------------------------------------------------------------------------------------------ constants
 
-constexpr int kFineDim = 8;           // voxels per block side at the finest level (512-voxel blocks, Sec. 5.1)
+constexpr int kFineDim = 8;           // voxels per block side at the finest level (512-voxel blocks, Sec. 4.1.4)
 constexpr int kFracBits = 16;         // fixed-point fraction bits per block edge for segment endpoints
 constexpr int64_t kBlockUnit = int64_t(1) << kFracBits;
 constexpr int64_t kVoxelUnit = kBlockUnit / kFineDim;  // one finest voxel

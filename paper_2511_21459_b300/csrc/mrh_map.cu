@@ -534,7 +534,10 @@ mrh_status mrh_raycast(mrh_map* m, const mrh_pinhole* K, const double* T_wc, flo
   if (st != MRH_OK) return st;
   DeviceGuard guard(m->device);
   CamArgs c = cam_args(K, T_wc);
-  { KernelScope ks(m, MRH_K_RAYCAST, (cudaStream_t)stream, 1); launch_raycast(m->d, c, depth_out, (cudaStream_t)stream); }
+  {
+    KernelScope ks(m, MRH_K_RAYCAST, (cudaStream_t)stream, 1);
+    launch_raycast(m->d, c, depth_out, (cudaStream_t)stream);
+  }
   MRH_CUDA(cudaGetLastError());
   return MRH_OK;
 }

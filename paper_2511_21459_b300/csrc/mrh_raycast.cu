@@ -35,26 +35,58 @@ __device__ inline int ifloor(float v) {
   return fabsf(f) < 1073741824.0f ? (int)f : 0x7FFFFFFF;
 }
 
-// Small per-thread cache of the last looked-up blocks: the 8 corners of a sample almost always fall in 1-2 blocks.
-// Kept in registers (static indices only; replacement shifts the entries), never in local memory.
+// heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage
+__device__ inline uint32_t find_block(const MapDev& m, int x, int y, int z) {
+  if (!key_ok32(x, y, z)) return kValPending;
+  const int s = lookup_slot(m.slots, m.slot_mask, pack_key(x, y, z));
+  return s >= 0 ? m.slots[s].val : kValPending;
+}
+
+// Two most recent block lookups, keyed by coordinates, in registers (static indices only).
 struct BlockCache {
-  unsigned long long k0 = kEmptyKey, k1 = kEmptyKey, k2 = kEmptyKey, k3 = kEmptyKey;
-  uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-  // heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage
+  int x0 = 0x7FFFFFFF, y0 = 0, z0 = 0, x1 = 0x7FFFFFFF, y1 = 0, z1 = 0;
+  uint32_t v0 = 0, v1 = 0;
   __device__ inline uint32_t get(const MapDev& m, int x, int y, int z) {
-    if (!key_ok32(x, y, z)) return kValPending;
-    const unsigned long long k = pack_key(x, y, z);
-    if (k == k0) return v0;
-    if (k == k1) return v1;
-    if (k == k2) return v2;
-    if (k == k3) return v3;
-    const int s = lookup_slot(m.slots, m.slot_mask, k);
-    const uint32_t v = s >= 0 ? m.slots[s].val : kValPending;
-    k3 = k2; v3 = v2;
-    k2 = k1; v2 = v1;
-    k1 = k0; v1 = v0;
-    k0 = k; v0 = v;
+    if (x == x0 && y == y0 && z == z0) return v0;
+    if (x == x1 && y == y1 && z == z1) {
+      // promote
+      const int tx = x0, ty = y0, tz = z0;
+      const uint32_t tv = v0;
+      x0 = x1; y0 = y1; z0 = z1; v0 = v1;
+      x1 = tx; y1 = ty; z1 = tz; v1 = tv;
+      return v0;
+    }
+    const uint32_t v = find_block(m, x, y, z);
+    x1 = x0; y1 = y0; z1 = z0; v1 = v0;
+    x0 = x; y0 = y; z0 = z; v0 = v;
     return v;
+  }
+};
+
+// Brick membership with a one-entry register cache.
+struct BrickCache {
+  int x = 0x7FFFFFFF, y = 0, z = 0;
+  bool present = false;
+  __device__ inline bool get(const MapDev& m, int bx, int by, int bz) {
+    if (bx == x && by == y && bz == z) return present;
+    bool found = false;
+    if (key_ok32(bx, by, bz)) {
+      const unsigned long long k = pack_key(bx, by, bz);
+      const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
+      for (int p = 0; p < kMaxProbes; ++p) {
+        const unsigned long long c = m.brick_keys[(h + (uint32_t)p) & m.brick_mask];
+        if (c == k) {
+          found = true;
+          break;
+        }
+        if (c == kEmptyKey) break;
+      }
+    }
+    x = bx;
+    y = by;
+    z = bz;
+    present = found;
+    return found;
   }
 };
 
@@ -70,31 +102,8 @@ __device__ inline float read_W(const MapDev& m, const uint8_t* blk, int nv, int 
   return reinterpret_cast<const float*>(blk + off_W(nv, m.fp16, m.color))[i];
 }
 
-// Brick membership with a one-entry register cache.
-struct BrickCache {
-  unsigned long long key = kEmptyKey;
-  bool present = false;
-  __device__ inline bool get(const MapDev& m, int bx, int by, int bz) {
-    if (!key_ok32(bx, by, bz)) return false;
-    const unsigned long long k = pack_key(bx, by, bz);
-    if (k == key) return present;
-    const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
-    bool found = false;
-    for (int p = 0; p < kMaxProbes; ++p) {
-      const unsigned long long c = m.brick_keys[(h + (uint32_t)p) & m.brick_mask];
-      if (c == k) {
-        found = true;
-        break;
-      }
-      if (c == kEmptyKey) break;
-    }
-    key = k;
-    present = found;
-    return found;
-  }
-};
-
-// trilinear field at x on the level-l grid; false when a corner is unallocated or unobserved
+// trilinear field at x on the level-l grid; false when a corner is unallocated or unobserved. Each distinct block
+// among the 8 corners is looked up once (usually there is only one); the corner sum runs in corner order 0..7.
 __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, float* out) {
   const float inv = m.inv_v[l];
   int j0[3];
@@ -107,49 +116,41 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
     fr[a] = g - fl;
   }
   const int sh = 3 - l, nl = 1 << sh, mask = nl - 1;
-  float acc = 0.0f;
   const int b0[3] = {j0[0] >> sh, j0[1] >> sh, j0[2] >> sh};
-  const int r0[3] = {j0[0] & mask, j0[1] & mask, j0[2] & mask};
-  if (r0[0] < mask && r0[1] < mask && r0[2] < mask) {
-    // all 8 corners inside one block
-    const uint32_t val = bc.get(m, b0[0], b0[1], b0[2]);
-    if (val == kValPending) return false;
-    const int lb = (int)((val >> 28) & 3u);
-    if (lb == l) {
-      const uint8_t* blk = block_ptr(m, val);
-      const int nv = nl * nl * nl;
-      const int base = r0[0] + nl * (r0[1] + nl * r0[2]);
-      for (int k = 0; k < 8; ++k) {
-        const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
-        const int idx = base + ax + nl * (ay + nl * az);
-        if (!(read_W(m, blk, nv, idx) > 0.0f)) return false;
-        const float wx = ax ? fr[0] : 1.0f - fr[0];
-        const float wy = ay ? fr[1] : 1.0f - fr[1];
-        const float wz = az ? fr[2] : 1.0f - fr[2];
-        acc = acc + wx * wy * wz * read_D(m, blk, idx);
-      }
-      *out = acc;
-      return true;
-    }
-  }
+  // corners with offset 1 along axis a fall in the next block iff j0 sits on the block's last voxel along a
+  const bool sx = (j0[0] & mask) == mask, sy = (j0[1] & mask) == mask, sz = (j0[2] & mask) == mask;
+  // distinct blocks of the corners, in registers: v<zyx> for the block offset (x, y, z) in {0, 1}^3
+  uint32_t v000, v100 = 0, v010 = 0, v110 = 0, v001 = 0, v101 = 0, v011 = 0, v111 = 0;
+  v000 = bc.get(m, b0[0], b0[1], b0[2]);
+  bool ok = v000 != kValPending;
+  if (ok && sx) { v100 = bc.get(m, b0[0] + 1, b0[1], b0[2]); ok = v100 != kValPending; }
+  if (ok && sy) { v010 = bc.get(m, b0[0], b0[1] + 1, b0[2]); ok = v010 != kValPending; }
+  if (ok && sx && sy) { v110 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2]); ok = v110 != kValPending; }
+  if (ok && sz) { v001 = bc.get(m, b0[0], b0[1], b0[2] + 1); ok = v001 != kValPending; }
+  if (ok && sx && sz) { v101 = bc.get(m, b0[0] + 1, b0[1], b0[2] + 1); ok = v101 != kValPending; }
+  if (ok && sy && sz) { v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1); ok = v011 != kValPending; }
+  if (ok && sx && sy && sz) { v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1); ok = v111 != kValPending; }
+  if (!ok) return false;
+  float acc = 0.0f;
+#pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
-    const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
-    const int bk[3] = {j[0] >> sh, j[1] >> sh, j[2] >> sh};
-    const uint32_t val = bc.get(m, bk[0], bk[1], bk[2]);
-    if (val == kValPending) return false;
+    const bool bx = ax && sx, by = ay && sy, bz = az && sz;
+    const uint32_t val = bz ? (by ? (bx ? v111 : v011) : (bx ? v101 : v001))
+                            : (by ? (bx ? v110 : v010) : (bx ? v100 : v000));
     const int lb = (int)((val >> 28) & 3u);
     const int nb = kFineDim >> lb;
     const uint8_t* blk = block_ptr(m, val);
+    const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
     int idx;
     if (lb == l) {
       idx = (j[0] & mask) + nl * ((j[1] & mask) + nl * (j[2] & mask));
     } else {
-      // the finest-level cell holding the corner centre, then block bk's voxel (at its own level) containing it
-      int c[3];
+      // the finest-level cell holding the corner centre, then the block's voxel (at its own level) containing it
+      int cc[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) c[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
-      idx = (c[0] & (nb - 1)) + nb * ((c[1] & (nb - 1)) + nb * (c[2] & (nb - 1)));
+      for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
+      idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
     }
     if (!(read_W(m, blk, nb * nb * nb, idx) > 0.0f)) return false;
     const float wx = ax ? fr[0] : 1.0f - fr[0];
@@ -172,11 +173,8 @@ __device__ inline bool sample(const MapDev& m, BlockCache& bc, const float o[3],
   return true;
 }
 
-__global__ void __launch_bounds__(128) k_raycast(MapDev m, CamArgs c, float* __restrict__ out) {
-  // 16 x 8 pixel tiles: neighbouring threads march through the same blocks
-  const int u = blockIdx.x * 16 + (threadIdx.x & 15);
-  const int v = blockIdx.y * 8 + (threadIdx.x >> 4);
-  if (u >= c.width || v >= c.height) return;
+// One ray: march, find the first zero crossing, write its z-depth (0 = none).
+__device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
   BlockCache bc;
   BrickCache brc;
   const float qx = ((float)u - c.cx) / c.fx, qy = ((float)v - c.cy) / c.fy;
@@ -247,6 +245,14 @@ __global__ void __launch_bounds__(128) k_raycast(MapDev m, CamArgs c, float* __r
     t = t + s;
   }
   out[(size_t)v * c.width + u] = hit;
+}
+
+// One thread per pixel; each warp covers an 8 x 4 pixel tile so that its rays march through the same blocks.
+__global__ void __launch_bounds__(128) k_raycast(MapDev m, CamArgs c, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+  const int v = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+  if (u < c.width && v < c.height) cast_ray(m, c, u, v, out);
 }
 
 }  // namespace

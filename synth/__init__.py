@@ -3,7 +3,7 @@
 This package renders analytic scenes (boxes, spheres, planes) into pinhole depth + RGB frames and spinning-LiDAR scans,
 with seeded noise, and holds the workload tables (sensor, scene and map parameters as plain numbers). It contains none
 of the fusion method's arithmetic: it only produces inputs. The paper evaluates on ScanNet, Replica, Newer College and
-Oxford-Spires (Sec. 5.1 "Datasets"); these seeded scenes stand in for them.
+Oxford-Spires (Sec. 4.1.1 "Datasets"); these seeded scenes stand in for them.
 
 The renderer is plain C (``synth.c``), compiled on first use into ``libsynth.so`` next to this file.
 """
