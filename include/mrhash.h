@@ -125,6 +125,41 @@ mrh_status mrh_integrate_depth(mrh_map* map, const mrh_pinhole* K, const double*
 mrh_status mrh_integrate_points(mrh_map* map, const double* T_ws_host, const float* xyz_dev, uint64_t n,
                                 void* stream);
 
+/* ---- batched multi-scene integration (not in the paper: many maps fused per step, one launch per phase) ---- */
+
+typedef struct mrh_batch mrh_batch; /* opaque; refers to maps it does not own */
+
+enum { MRH_BATCH_GRAPH = 1, MRH_BATCH_AUTOTUNE = 2 };
+
+/* One map's input for one batched step. */
+typedef struct {
+  mrh_pinhole K;            /* intrinsics; width/height must equal the camera given to mrh_batch_create */
+  double T_wc[16];          /* world <- camera, row-major */
+  const float* depth_dev;   /* height x width float32 z-depth */
+  const uint8_t* rgb_dev;   /* height x width x 3 uint8, or NULL */
+  float* raycast_dev;       /* height x width float32: raycast of the same view after integration, or NULL */
+} mrh_batch_frame;
+
+/* Group n (1..64) maps of one device and one storage layout (same storage and has_color) whose frames have the
+ * fixed sizes of cams[i]. flags: MRH_BATCH_AUTOTUNE runs the first steps after the first as timed trials of
+ * alternative launch shapes (allocation CTA tile and probe width, fusion warps per CTA and grid, raycast warp tile)
+ * and keeps the fastest (every shape computes the same result); MRH_BATCH_GRAPH captures the step into a CUDA graph
+ * once tuning is done and replays it (needs a non-default stream). The batch owns per-map image buffers; the maps
+ * must outlive it. */
+mrh_status mrh_batch_create(mrh_map* const* maps, const mrh_pinhole* cams, int n, int flags, mrh_batch** out);
+
+/* Integrate frames[i] into map i for every map of the batch (the per-map semantics of mrh_integrate_depth followed by
+ * mrh_raycast into raycast_dev when given), as one launch per phase over all maps. Asynchronous on `stream`; the
+ * frames array may be reused when the call returns. */
+mrh_status mrh_batch_integrate(mrh_batch* batch, const mrh_batch_frame* frames, void* stream);
+
+/* The launch shapes in use: {alloc tile width, alloc tile height, probe width, fusion warps per CTA, fusion CTAs per
+ * SM, raycast warp tile (0: 8x4, 1: 16x2), tuned (0/1), graph captured (0/1)}. */
+mrh_status mrh_batch_config(const mrh_batch* batch, int* config_out8);
+
+/* Release the batch (not its maps). NULL is accepted. */
+mrh_status mrh_batch_destroy(mrh_batch* batch);
+
 /* Raycast the map from a pinhole view (the rendering branch of Fig. 2): depth_out_dev receives height x width
  * float32 z-depth of the first observed zero crossing, 0 where none. Empty blocks are skipped whole.
  * Asynchronous on `stream`. */

@@ -60,11 +60,20 @@ class Stats(ctypes.Structure):
 
 KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast"]
 
+MRH_BATCH_GRAPH, MRH_BATCH_AUTOTUNE = 1, 2
+
+
+class BatchFrame(ctypes.Structure):
+    """mrh_batch_frame"""
+    _fields_ = [("K", Pinhole), ("T_wc", ctypes.c_double * 16), ("depth_dev", ctypes.c_void_p),
+                ("rgb_dev", ctypes.c_void_p), ("raycast_dev", ctypes.c_void_p)]
+
 
 EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points", "mrh_raycast",
            "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc", "mrh_get_stats", "mrh_sync",
-           "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_hash_slot", "mrh_status_string",
-           "mrh_last_cuda_error", "mrh_version"]
+           "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create", "mrh_batch_integrate",
+           "mrh_batch_config", "mrh_batch_destroy", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
+           "mrh_version"]
 
 
 def lib():
@@ -89,6 +98,10 @@ def lib():
         L.mrh_clear_status.argtypes = [vp, vp]
         L.mrh_set_profiling.argtypes = [vp, i32]
         L.mrh_get_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), i32, i32, vp]
+        L.mrh_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Pinhole), i32, i32, ctypes.POINTER(vp)]
+        L.mrh_batch_integrate.argtypes = [vp, ctypes.POINTER(BatchFrame), vp]
+        L.mrh_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.mrh_batch_destroy.argtypes = [vp]
         L.mrh_hash_slot.restype = ctypes.c_uint32
         L.mrh_hash_slot.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
         L.mrh_status_string.restype = ctypes.c_char_p
@@ -97,7 +110,8 @@ def lib():
         for name in ("mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points",
                      "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc",
                      "mrh_get_stats", "mrh_sync",
-                     "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile"):
+                     "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create",
+                     "mrh_batch_integrate", "mrh_batch_config", "mrh_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -263,3 +277,49 @@ class Map:
 
     def clear_status(self, stream=None):
         _check(self._lib.mrh_clear_status(self._h, _stream(stream)), "mrh_clear_status")
+
+
+class Batch:
+    """Several maps integrated together, one launch per phase (mrh_batch_*). ``maps`` must outlive the batch."""
+
+    def __init__(self, maps, cams, flags: int = MRH_BATCH_GRAPH | MRH_BATCH_AUTOTUNE):
+        self._lib = lib()
+        self.maps = list(maps)
+        self.cams = list(cams)
+        n = len(self.maps)
+        hs = (ctypes.c_void_p * n)(*[m._h.value for m in self.maps])
+        ks = (Pinhole * n)(*self.cams)
+        h = ctypes.c_void_p()
+        _check(self._lib.mrh_batch_create(hs, ks, n, flags, ctypes.byref(h)), "mrh_batch_create")
+        self._h = h
+
+    def integrate(self, frames, stream=None):
+        """frames: per map (T_wc 4x4, depth CUDA tensor, rgb CUDA tensor or None, raycast out CUDA tensor or None)."""
+        n = len(self.maps)
+        arr = (BatchFrame * n)()
+        for i, (T, depth, rgb, out) in enumerate(frames):
+            arr[i].K = self.cams[i]
+            Tf = _pose(T).ravel()
+            for k in range(16):
+                arr[i].T_wc[k] = float(Tf[k])
+            arr[i].depth_dev = depth.data_ptr()
+            arr[i].rgb_dev = rgb.data_ptr() if rgb is not None else None
+            arr[i].raycast_dev = out.data_ptr() if out is not None else None
+        _check(self._lib.mrh_batch_integrate(self._h, arr, _stream(stream)), "mrh_batch_integrate")
+
+    def config(self) -> dict:
+        c = (ctypes.c_int * 8)()
+        _check(self._lib.mrh_batch_config(self._h, c), "mrh_batch_config")
+        return dict(alloc_tile=(c[0], c[1]), probe_width=c[2], fuse_warps=c[3], fuse_ctas_per_sm=c[4],
+                    raycast_warp_tile="16x2" if c[5] else "8x4", tuned=bool(c[6]), graph=bool(c[7]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mrh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

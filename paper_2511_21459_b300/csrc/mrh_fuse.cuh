@@ -1,0 +1,594 @@
+// Fusion of one frame into the touched blocks, the block variance and re-levelling, in one pass.
+//
+//   camera  (Sec. 3.1 "Cameras", Eq. 2): every voxel of a touched block projects to its nearest pixel; the signed
+//           distance is the pixel's range minus the voxel's distance, occluded voxels (more than tau behind) are
+//           skipped, the rest clipped to tau.
+//   LiDAR   (Sec. 3.1 "3D Point Cloud", Eq. 1): each ray walks the voxels of its truncation band (a DDA over
+//           finest-level cells, one observation per voxel of the block's own level); d = clip((p - x) . n, tau).
+//           Observations are counted per block, prefix-summed and scattered; inside a block they are binned per
+//           voxel and each voxel applies its observations in ascending point index, so the result does not depend on
+//           scheduling.
+//   both    running mean (Eq. 3, w_k = 1) in Welford's incremental form and S2 += (d - D_old)(d - D_new)
+//           (Sec. 3.2.1); then the mean voxel variance of the block over observed voxels; then merge to the next
+//           coarser level below theta_l (Sec. 3.2.1, Fig. 4a) or split to the next finer level above h theta_{l-1}.
+//
+// Work decomposition: one warp per work item, with no CTA-wide barrier anywhere. An item is one level-0 block
+// (8^3 voxels, 32 lanes), two level-1 blocks (4^3, 16 lanes each) or sixteen level-2 blocks (2^3, 2 lanes each).
+// A lane owns 4 consecutive voxels per chunk of 4 G voxels (G = lanes per block) and moves each field of them with
+// one 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced, and the next chunk's
+// loads are issued before the current chunk is computed. The block's mean variance is a butterfly shuffle reduction
+// that leaves the sum in every lane of the block's group, so every lane takes the same decision without
+// communication. Re-levelled blocks (a small fraction per frame) are resampled from their just-written payload into
+// a heap block popped from the other level's free stack.
+//
+// The block variance decides in float; a value within 1e-5 (relative) of a threshold is recomputed in double, in
+// voxel order, exactly as the CPU oracle computes it, so level decisions match the oracle bit for bit. (The float
+// sum's relative error is below 22 ulp = 1.3e-6: 15 sequential + 5 shuffle additions of non-negative terms, the
+// per-voxel division and the final division.)
+//
+// This file is compiled without multiply-add contraction: float expressions round in source order, like the oracle.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "mrh_internal.cuh"
+
+namespace mrh {
+namespace {
+
+constexpr double kBand = 1e-5;
+constexpr int kLocalSort = 16;
+constexpr uint32_t kInvalidPtr = 0xFFFFFFFFu;
+enum { kActNone = 0, kActMerge = 1, kActSplit = 2 };
+
+template <bool FP16>
+struct Field {
+  static __device__ inline void load4(const uint8_t* p, int i4, float out[4]) {
+    if constexpr (FP16) {
+      uint2 u = reinterpret_cast<const uint2*>(p)[i4];
+      __half2 a = *reinterpret_cast<__half2*>(&u.x), b = *reinterpret_cast<__half2*>(&u.y);
+      float2 fa = __half22float2(a), fb = __half22float2(b);
+      out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
+    } else {
+      float4 f = reinterpret_cast<const float4*>(p)[i4];
+      out[0] = f.x; out[1] = f.y; out[2] = f.z; out[3] = f.w;
+    }
+  }
+  static __device__ inline void store4(uint8_t* p, int i4, const float in[4]) {
+    if constexpr (FP16) {
+      __half2 a = __floats2half2_rn(in[0], in[1]), b = __floats2half2_rn(in[2], in[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&a);
+      u.y = *reinterpret_cast<uint32_t*>(&b);
+      reinterpret_cast<uint2*>(p)[i4] = u;
+    } else {
+      reinterpret_cast<float4*>(p)[i4] = make_float4(in[0], in[1], in[2], in[3]);
+    }
+  }
+  static __device__ inline float get1(const uint8_t* p, int i) {
+    if constexpr (FP16) return __half2float(reinterpret_cast<const __half*>(p)[i]);
+    else return reinterpret_cast<const float*>(p)[i];
+  }
+  static __device__ inline void store1(uint8_t* p, int i, float x) {
+    if constexpr (FP16) reinterpret_cast<__half*>(p)[i] = __float2half_rn(x);
+    else reinterpret_cast<float*>(p)[i] = x;
+  }
+  // the value a later read of the stored field returns
+  static __device__ inline float kept(float x) {
+    if constexpr (FP16) return __half2float(__float2half_rn(x));
+    else return x;
+  }
+};
+
+// One Welford step (Eq. 3 incremental form + S2 update of Sec. 3.2.1).
+template <bool FP16>
+__device__ inline void welford(float d, float& D, float& W, float& S2, float& Wn) {
+  Wn = W + 1.0f;
+  float e = d - D;
+  float Dn = D + e / Wn;
+  S2 = S2 + e * (d - Dn);
+  D = Field<FP16>::kept(Dn);
+  W = Wn;
+}
+
+// 4 consecutive voxels of one lane
+struct Chunk {
+  float D[4], W[4], S2[4], C[3][4];
+};
+
+// What a lane knows about the block its group works on.
+struct Ctx {
+  int l, nl, nv, G, g, li;
+  bool active;
+  uint32_t P;        // position in the level-concatenated list (LiDAR buffers)
+  uint32_t P_first;  // P of the item's first group
+  int kx, ky, kz;    // block key
+};
+
+// -------------------------------------------------------------------------------------------- camera observer
+
+// Reads the frame's range image (rho = z |K^-1 [u v 1]|, written by the allocation kernel with the same float
+// expression, -1 where the depth is invalid) and its colour packed as one 32-bit word per pixel, so a voxel costs one
+// 4-byte gather per image instead of recomputing the pixel ray.
+template <bool FP16, bool COLOR>
+struct CameraObs {
+  CamArgs c;
+  const float* rho_img;
+  const uint32_t* rgb_img;  // null when the frame has no colour
+
+  __device__ inline void collect(const MapDev&, const Ctx&, int) {}
+
+  // voxels vi0 .. vi0 + 3 of the block. Written without early exits: all four voxels are computed side by side and
+  // an update is kept only where the voxel is observed, so the four independent chains can overlap.
+  __device__ inline int apply(const MapDev& m, const Ctx& x, int vi0, Chunk& ch) const {
+    const float vl = m.v[x.l];
+    const float ob0 = (float)x.kx * m.E - c.t[0];
+    const float ob1 = (float)x.ky * m.E - c.t[1];
+    const float ob2 = (float)x.kz * m.E - c.t[2];
+    const int sh = 3 - x.l, msk = x.nl - 1;
+    const float fw = (float)c.width, fh = (float)c.height;
+    int n_upd = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int vi = vi0 + k;
+      const int xi = vi & msk, yi = (vi >> sh) & msk, zi = vi >> (2 * sh);
+      const float w0 = ob0 + ((float)xi + 0.5f) * vl;
+      const float w1 = ob1 + ((float)yi + 0.5f) * vl;
+      const float w2 = ob2 + ((float)zi + 0.5f) * vl;
+      const float xc = c.R[0] * w0 + c.R[3] * w1 + c.R[6] * w2;
+      const float yc = c.R[1] * w0 + c.R[4] * w1 + c.R[7] * w2;
+      const float zc = c.R[2] * w0 + c.R[5] * w1 + c.R[8] * w2;
+      const float uf = c.fx * xc / zc + c.cx + 0.5f;
+      const float vf = c.fy * yc / zc + c.cy + 0.5f;
+      bool ok = zc > 0.0f && uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh;
+      const int u = ok ? (int)floorf(uf) : 0, v = ok ? (int)floorf(vf) : 0;
+      const int pix = v * c.width + u;
+      const float rho = __ldg(rho_img + pix);
+      const float dist = sqrtf(xc * xc + yc * yc + zc * zc);
+      const float eta = rho - dist;
+      ok = ok && rho >= 0.0f && !(eta < -m.tau);  // valid depth; not occluded (more than tau behind the surface)
+      const float d = eta < m.tau ? eta : m.tau;
+      const float Wn = ch.W[k] + 1.0f;
+      const float e = d - ch.D[k];
+      const float Dn = ch.D[k] + e / Wn;
+      const float S2n = ch.S2[k] + e * (d - Dn);
+      if (ok) {
+        ch.D[k] = Field<FP16>::kept(Dn);
+        ch.W[k] = Wn;
+        ch.S2[k] = S2n;
+        ++n_upd;
+      }
+      if constexpr (COLOR) {
+        if (rgb_img) {
+          const uint32_t packed = __ldg(rgb_img + pix);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float col = (float)((packed >> (8 * q)) & 255u);
+            const float Cn = ch.C[q][k] + (col - ch.C[q][k]) / Wn;
+            if (ok) ch.C[q][k] = Field<FP16>::kept(Cn);
+          }
+        }
+      }
+    }
+    return n_upd;
+  }
+};
+
+// -------------------------------------------------------------------------------------------- LiDAR observer
+
+// Per warp: 512 voxel bins (the item's voxels) in shared memory: counts, exclusive offsets, fill cursors.
+constexpr int kLidarWarps = 4;
+
+template <bool FP16>
+struct LidarObs {
+  uint32_t (*s_bins)[3][512];  // [warp][cnt | off | fill][bin]
+  uint32_t item_base;
+
+  // warp-collective: bin the item's observations per voxel (bin = group * nv + voxel)
+  __device__ inline void collect(const MapDev& m, const Ctx& x, int warp) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* cnt = s_bins[warp][0];
+    uint32_t* off = s_bins[warp][1];
+    uint32_t* fill = s_bins[warp][2];
+    for (int i = lane; i < 512; i += 32) {
+      cnt[i] = 0;
+      fill[i] = 0;
+    }
+    __syncwarp();
+    uint32_t r0 = 0, r1 = 0;
+    if (x.active) {
+      r0 = m.blk_off[x.P];
+      r1 = m.blk_off[x.P + 1];
+      if (r1 > m.max_obs) r0 = r1 = 0;  // observations were not stored (status already set)
+    }
+    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&cnt[x.g * x.nv + (m.obs_key[r] & 511u)], 1u);
+    __syncwarp();
+    uint32_t local[16], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      local[k] = cnt[16 * lane + k];
+      sum += local[k];
+    }
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(~0u, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      off[16 * lane + k] = run;
+      run += local[k];
+    }
+    item_base = m.blk_off[x.P_first];
+    __syncwarp();
+    for (uint32_t r = r0 + x.li; r < r1; r += x.G) {
+      const uint32_t bin = x.g * x.nv + (m.obs_key[r] & 511u);
+      const uint32_t pos = off[bin] + atomicAdd(&fill[bin], 1u);
+      m.obs_idx[item_base + pos] = r;
+    }
+    __syncwarp();
+  }
+
+  __device__ inline int apply(const MapDev& m, const Ctx& x, int vi0, Chunk& ch) const {
+    const int warp = threadIdx.x >> 5;
+    int n_upd = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const int bin = x.g * x.nv + vi0 + k;
+      const uint32_t cnt = s_bins[warp][0][bin];
+      if (cnt == 0) continue;
+      uint32_t* idx = m.obs_idx + item_base + s_bins[warp][1][bin];
+      // order the voxel's observations by point index (each ray observes a voxel at most once)
+      if (cnt <= kLocalSort) {
+        unsigned long long e[kLocalSort];
+        for (uint32_t i = 0; i < cnt; ++i) {
+          const uint32_t r = idx[i];
+          const unsigned long long key = ((unsigned long long)(m.obs_key[r] >> 9) << 32) | r;
+          uint32_t j = i;
+          while (j > 0 && e[j - 1] > key) {
+            e[j] = e[j - 1];
+            --j;
+          }
+          e[j] = key;
+        }
+        for (uint32_t i = 0; i < cnt; ++i) {
+          float Wn;
+          welford<FP16>(m.obs_d[(uint32_t)e[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
+        }
+      } else {
+        for (uint32_t i = 1; i < cnt; ++i) {
+          const uint32_t r = idx[i];
+          const uint32_t kr = m.obs_key[r] >> 9;
+          uint32_t j = i;
+          while (j > 0 && (m.obs_key[idx[j - 1]] >> 9) > kr) {
+            idx[j] = idx[j - 1];
+            --j;
+          }
+          idx[j] = r;
+        }
+        for (uint32_t i = 0; i < cnt; ++i) {
+          float Wn;
+          welford<FP16>(m.obs_d[idx[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
+        }
+      }
+      n_upd += (int)cnt;
+    }
+    return n_upd;
+  }
+};
+
+// -------------------------------------------------------------------------------------------- warp fusion body
+
+template <bool FP16, bool COLOR>
+struct BlockIO {
+  uint8_t* blk;
+  int nv;
+  __device__ inline void load(int i4, Chunk& ch) const {
+    Field<FP16>::load4(blk, i4, ch.D);
+    Field<false>::load4(blk + off_W(nv, FP16, COLOR), i4, ch.W);
+    Field<false>::load4(blk + off_S2(nv, FP16, COLOR), i4, ch.S2);
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Field<FP16>::load4(blk + off_C(nv, FP16, q), i4, ch.C[q]);
+    }
+  }
+  __device__ inline void store(int i4, const Chunk& ch) const {
+    Field<FP16>::store4(blk, i4, ch.D);
+    Field<false>::store4(blk + off_W(nv, FP16, COLOR), i4, ch.W);
+    Field<false>::store4(blk + off_S2(nv, FP16, COLOR), i4, ch.S2);
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Field<FP16>::store4(blk + off_C(nv, FP16, q), i4, ch.C[q]);
+    }
+  }
+};
+
+__device__ inline void zero_chunk(Chunk& ch) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ch.D[k] = ch.W[k] = ch.S2[k] = 0.0f;
+    ch.C[0][k] = ch.C[1][k] = ch.C[2][k] = 0.0f;
+  }
+}
+
+// merge (Sec. 3.2.1, Fig. 4a): coarse voxel = W-weighted pool of its observed 2x2x2 children of block `src`;
+// W = max child weight; S2 = pooled variance times W. Lanes li, li + G, ... of the group write coarse voxels.
+template <bool FP16, bool COLOR>
+__device__ void merge_block(const uint8_t* src, int nl, uint8_t* dst, int li, int G) {
+  using F = Field<FP16>;
+  const int nv = nl * nl * nl, nc = nl / 2, nvc = nc * nc * nc;
+  const float* sW = reinterpret_cast<const float*>(src + off_W(nv, FP16, COLOR));
+  const float* sS = reinterpret_cast<const float*>(src + off_S2(nv, FP16, COLOR));
+  for (int ci = li; ci < nvc; ci += G) {
+    const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
+    float sw = 0.f, swd = 0.f, ss2 = 0.f, wmax = 0.f, swc[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 8; ++q) {
+      const int ch = (2 * cx + (q & 1)) + nl * ((2 * cy + ((q >> 1) & 1)) + nl * (2 * cz + (q >> 2)));
+      const float Wi = sW[ch];
+      if (!(Wi > 0.0f)) continue;
+      sw = sw + Wi;
+      swd = swd + Wi * F::get1(src, ch);
+      ss2 = ss2 + sS[ch];
+      if (Wi > wmax) wmax = Wi;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) swc[c] = swc[c] + Wi * F::get1(src + off_C(nv, FP16, c), ch);
+      }
+    }
+    float oD = 0.f, oW = 0.f, oS = 0.f, oC[3] = {0.f, 0.f, 0.f};
+    if (sw > 0.0f) {
+      const float var = ss2 / sw;
+      oD = swd / sw;
+      oW = wmax;
+      oS = var * wmax;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = swc[c] / sw;
+      }
+    }
+    F::store1(dst, ci, oD);
+    reinterpret_cast<float*>(dst + off_W(nvc, FP16, COLOR))[ci] = oW;
+    reinterpret_cast<float*>(dst + off_S2(nvc, FP16, COLOR))[ci] = oS;
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F::store1(dst + off_C(nvc, FP16, c), ci, oC[c]);
+    }
+  }
+}
+
+// split (extension): fine voxel = trilinear interpolation of the observed coarse voxels at its centre (clamped to
+// the block); W and S2 from the coarse voxel that contains it.
+template <bool FP16, bool COLOR>
+__device__ void split_block(const uint8_t* src, int nc, uint8_t* dst, int li, int G) {
+  using F = Field<FP16>;
+  const int nv = nc * nc * nc, nf = 2 * nc, nvf = nf * nf * nf;
+  const float* sW = reinterpret_cast<const float*>(src + off_W(nv, FP16, COLOR));
+  const float* sS = reinterpret_cast<const float*>(src + off_S2(nv, FP16, COLOR));
+  for (int fi = li; fi < nvf; fi += G) {
+    const int f[3] = {fi % nf, (fi / nf) % nf, fi / (nf * nf)};
+    int i0[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float p = (float)f[a] * 0.5f - 0.25f;
+      if (p < 0.0f) p = 0.0f;
+      if (p > (float)(nc - 1)) p = (float)(nc - 1);
+      int i = (int)floorf(p);
+      if (i > nc - 2) i = nc - 2;
+      i0[a] = i;
+      fr[a] = p - (float)i;
+    }
+    float sw = 0.f, sd = 0.f, sc[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 8; ++q) {
+      const int ax = q & 1, ay = (q >> 1) & 1, az = q >> 2;
+      const int cv = (i0[0] + ax) + nc * ((i0[1] + ay) + nc * (i0[2] + az));
+      if (!(sW[cv] > 0.0f)) continue;
+      const float wx = ax ? fr[0] : 1.0f - fr[0];
+      const float wy = ay ? fr[1] : 1.0f - fr[1];
+      const float wz = az ? fr[2] : 1.0f - fr[2];
+      const float w = wx * wy * wz;
+      sw = sw + w;
+      sd = sd + w * F::get1(src, cv);
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sc[c] = sc[c] + w * F::get1(src + off_C(nv, FP16, c), cv);
+      }
+    }
+    const int own = (f[0] >> 1) + nc * ((f[1] >> 1) + nc * (f[2] >> 1));
+    float oD, oC[3] = {0.f, 0.f, 0.f};
+    if (sw > 0.0f) {
+      oD = sd / sw;
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = sc[c] / sw;
+      }
+    } else {
+      oD = F::get1(src, own);
+      if constexpr (COLOR) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) oC[c] = F::get1(src + off_C(nv, FP16, c), own);
+      }
+    }
+    F::store1(dst, fi, oD);
+    reinterpret_cast<float*>(dst + off_W(nvf, FP16, COLOR))[fi] = sW[own];
+    reinterpret_cast<float*>(dst + off_S2(nvf, FP16, COLOR))[fi] = sS[own];
+    if constexpr (COLOR) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F::store1(dst + off_C(nvf, FP16, c), fi, oC[c]);
+    }
+  }
+}
+
+// Work items of this frame: one per level-0 block, one per two level-1 blocks, one per sixteen level-2 blocks.
+struct ItemCounts {
+  uint32_t n0, n1, n2, it0, it1, it2;
+  __device__ inline uint32_t items() const { return it0 + it1 + it2; }
+};
+
+__device__ inline ItemCounts item_counts(const MapDev& m) {
+  ItemCounts c;
+  c.n0 = min(m.st->touched_count[0], m.max_touched);
+  c.n1 = m.L > 1 ? min(m.st->touched_count[1], m.max_touched) : 0;
+  c.n2 = m.L > 2 ? min(m.st->touched_count[2], m.max_touched) : 0;
+  c.it0 = c.n0;
+  c.it1 = (c.n1 + 1) / 2;
+  c.it2 = (c.n2 + 15) / 16;
+  return c;
+}
+
+// One work item, processed by the whole warp (warp-uniform control flow).
+template <bool FP16, bool COLOR, class Obs>
+__device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, const ItemCounts& ic, uint32_t item,
+                                 unsigned long long& my_obs) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t n0 = ic.n0, n1 = ic.n1, n2 = ic.n2, it0 = ic.it0, it1 = ic.it1;
+  {
+    Ctx x;
+    uint32_t first, count, pbase;
+    if (item < it0) { x.l = 0; first = item; count = n0; pbase = 0; }
+    else if (item < it0 + it1) { x.l = 1; first = (item - it0) * 2; count = n1; pbase = n0; }
+    else { x.l = 2; first = (item - it0 - it1) * 16; count = n2; pbase = n0 + n1; }
+    x.nl = kFineDim >> x.l;
+    x.nv = x.nl * x.nl * x.nl;
+    x.G = x.nv < 128 ? x.nv / 4 : 32;  // lanes per block: 32, 16, 2
+    x.g = lane / x.G;
+    x.li = lane % x.G;
+    const uint32_t idx = first + x.g;
+    x.active = idx < count;
+    x.P = pbase + idx;
+    x.P_first = pbase + first;
+    const int l = x.l, nl = x.nl, nv = x.nv, G = x.G, li = x.li;
+    const int chunks = nv / (4 * G);  // 4, 1, 1
+
+    BlockMeta bm;
+    bm.key = 0;
+    bm.val = 0;
+    bm.slot = 0;
+    if (x.active) bm = m.meta[l][idx];
+    const bool isnew = (bm.val & kValNew) != 0;
+    const uint32_t ptr = bm.val & kPtrMask;
+    unpack_key(bm.key, &x.kx, &x.ky, &x.kz);
+    const BlockIO<FP16, COLOR> io{m.heap[l] + (size_t)ptr * m.block_bytes[l], nv};
+    const bool load = x.active && !isnew;
+
+    obs.collect(m, x, warp_in_cta);
+
+    // ---- chunks: prefetch the next chunk, update the current one, write it back, accumulate block statistics
+    float vsum = 0.f;
+    int nobs = 0;
+    long long sumw = 0;
+    Chunk cur, nxt;
+    if (load) io.load(li, cur);
+    else zero_chunk(cur);
+    for (int c = 0; c < chunks; ++c) {
+      if (c + 1 < chunks) {
+        if (load) io.load((c + 1) * G + li, nxt);
+        else zero_chunk(nxt);
+      }
+      if (x.active) {
+        my_obs += (unsigned long long)obs.apply(m, x, 4 * (c * G + li), cur);
+        io.store(c * G + li, cur);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (cur.W[q] > 0.0f) {
+          vsum = vsum + cur.S2[q] / cur.W[q];
+          nobs += 1;
+          sumw += (long long)(uint32_t)cur.W[q];
+        }
+      }
+      if (c + 1 < chunks) cur = nxt;
+    }
+    for (int o = G / 2; o > 0; o >>= 1) {
+      vsum = vsum + __shfl_xor_sync(~0u, vsum, o);
+      nobs += __shfl_xor_sync(~0u, nobs, o);
+      sumw += __shfl_xor_sync(~0u, sumw, o);
+    }
+
+    // ---- decision (every lane of the group computes the same one)
+    int act = kActNone;
+    bool recheck = false;
+    double thr_m = 0.0, thr_s = 0.0;
+    const double vb32 = nobs > 0 ? (double)(vsum / (float)nobs) : 0.0;
+    const bool eligible = x.active && nobs > 0 && sumw >= (long long)m.min_obs * nobs;
+    const bool can_merge = eligible && l < m.L - 1;
+    const bool can_split = eligible && m.split_h > 0.0 && l > 0;
+    if (can_merge) {
+      thr_m = m.theta[l];
+      recheck |= fabs(vb32 - thr_m) <= kBand * fabs(thr_m);
+    }
+    if (can_split) {
+      thr_s = m.split_h * m.theta[l - 1];
+      recheck |= fabs(vb32 - thr_s) <= kBand * fabs(thr_s);
+    }
+    double vbar = vb32;
+    const int leader = lane - li;
+    if (__any_sync(~0u, recheck)) {
+      __syncwarp();  // the group's payload writes are visible to its leader
+      double exact = 0.0;
+      if (recheck && li == 0) {
+        const float* W = reinterpret_cast<const float*>(io.blk + off_W(nv, FP16, COLOR));
+        const float* S = reinterpret_cast<const float*>(io.blk + off_S2(nv, FP16, COLOR));
+        double acc = 0.0;
+        for (int i = 0; i < nv; ++i) {
+          const float w = W[i];
+          if (w > 0.0f) acc = acc + (double)S[i] / (double)w;
+        }
+        exact = acc / (double)nobs;
+        atomicAdd(&m.st->rechecks, 1u);
+      }
+      exact = __shfl_sync(~0u, exact, leader);
+      if (recheck) vbar = exact;
+    }
+    if (can_merge && vbar < thr_m) act = kActMerge;
+    else if (can_split && vbar > thr_s) act = kActSplit;
+
+    // ---- re-level (rare): pop a heap block of the target level, resample into it, retire the old block
+    if (__any_sync(~0u, act != kActNone)) {
+      uint32_t newptr = 0;
+      if (act != kActNone && li == 0) {
+        const int lt = act == kActMerge ? l + 1 : l - 1;
+        const int t = atomicSub(&m.st->free_top[lt], 1);
+        if (t <= 0) {
+          atomicAdd(&m.st->free_top[lt], 1);
+          set_status(m.st, kStPoolEmpty);
+          newptr = kInvalidPtr;
+        } else {
+          newptr = m.free_stack[lt][t - 1];
+        }
+      }
+      newptr = __shfl_sync(~0u, newptr, leader);
+      if (newptr == kInvalidPtr) act = kActNone;
+      __syncwarp();  // the group's payload writes are visible to every lane that resamples them
+      if (act == kActMerge) {
+        merge_block<FP16, COLOR>(io.blk, nl, m.heap[l + 1] + (size_t)newptr * m.block_bytes[l + 1], li, G);
+      } else if (act == kActSplit) {
+        split_block<FP16, COLOR>(io.blk, nl, m.heap[l - 1] + (size_t)newptr * m.block_bytes[l - 1], li, G);
+      }
+      if (act != kActNone && li == 0) {
+        const int lt = act == kActMerge ? l + 1 : l - 1;
+        m.slots[bm.slot].val = newptr | ((uint32_t)lt << 28);
+        const uint32_t r = atomicAdd(&m.st->retire_count, 1u);
+        m.retire[r] = ptr | ((uint32_t)l << 28);
+        atomicAdd(act == kActMerge ? &m.st->merged : &m.st->split, 1u);
+      }
+    }
+    if (act == kActNone && isnew && x.active && li == 0) m.slots[bm.slot].val = bm.val & ~kValNew;
+  }
+}
+
+// A warp's share of the items of one map (grid-strided), then the observation counter.
+template <bool FP16, bool COLOR, class Obs>
+__device__ inline void fuse_warp_body(const MapDev& m, Obs& obs, int warp_in_cta, uint32_t warp_id, uint32_t nwarps) {
+  const int lane = threadIdx.x & 31;
+  const ItemCounts ic = item_counts(m);
+  const uint32_t items = ic.items();
+  unsigned long long my_obs = 0;
+  for (uint32_t item = warp_id; item < items; item += nwarps)
+    fuse_item<FP16, COLOR>(m, obs, warp_in_cta, ic, item, my_obs);
+  for (int o = 16; o > 0; o >>= 1) my_obs += __shfl_xor_sync(~0u, my_obs, o);
+  if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
+}
+
+}  // namespace
+}  // namespace mrh

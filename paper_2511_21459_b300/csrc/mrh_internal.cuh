@@ -321,6 +321,9 @@ __device__ inline void fence_proxy_async_smem() { asm volatile("fence.proxy.asyn
 
 // ---------------------------------------------------------------------------------------------------- host side
 
+// the device-side view of a map (mrh_map.cu), for the batched path
+const MapDev* map_dev(const mrh_map* m, int* device, int* sms);
+
 // launch helpers implemented in the .cu files
 void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, const uint8_t* rgb, float* rho_img,
                         uint32_t* rgb_img, cudaStream_t s);

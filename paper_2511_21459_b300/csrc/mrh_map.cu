@@ -17,6 +17,7 @@
 #include <new>
 #include <vector>
 
+#include "mrh_alloc.cuh"
 #include "mrh_internal.cuh"
 
 using namespace mrh;
@@ -44,6 +45,7 @@ struct mrh_map {
   size_t img_pixels = 0;
 };
 
+namespace mrh {
 namespace {
 
 thread_local char g_cuda_err[256] = "";
@@ -137,23 +139,11 @@ __global__ void k_init_stack(uint32_t* stack, uint32_t cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) stack[i] = cap - 1 - i;
 }
 
-__global__ void k_begin(DevState* st) {
-  st->frame += 1;
-  st->touched_all = 0;
-  for (int l = 0; l < 4; ++l) st->touched_count[l] = 0;
-  st->retire_count = 0;
-  st->new_blocks = st->merged = st->split = st->rechecks = st->valid_rays = 0;
-  st->observations = 0;
-}
+__global__ void k_begin(DevState* st) { begin_frame(st); }
 
 __global__ void __launch_bounds__(256) k_release(MapDev m) {
   const uint32_t n = m.st->retire_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t r = m.retire[i];
-    uint32_t l = r >> 28, id = r & kPtrMask;
-    int t = atomicAdd(&m.st->free_top[l], 1);
-    m.free_stack[l][t] = id;
-  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) release_one(m, i);
 }
 
 // ---- read-out kernels
@@ -337,12 +327,22 @@ void free_all(mrh_map* m) {
 }
 
 }  // namespace
+}  // namespace mrh
+
+namespace mrh {
+const MapDev* map_dev(const mrh_map* m, int* device, int* sms) {
+  *device = m->device;
+  *sms = m->sms;
+  return &m->d;
+}
+}  // namespace mrh
 
 // ------------------------------------------------------------------------------------------------ static scratch
 //
 // mrh_extract_blocks_noalloc sorts and scans inside this one array instead of allocating. Host code must not use the
 // symbol as a pointer: its device address is looked up once per device (cudaGetSymbolAddress, with that device
 // current) and passed to the kernels.
+namespace mrh {
 namespace {
 
 constexpr uint32_t kNoallocMaxBlocks = MRH_NOALLOC_MAX_BLOCKS;
@@ -373,6 +373,7 @@ mrh_status noalloc_scratch(int device, uint8_t** out) {
 }
 
 }  // namespace
+}  // namespace mrh
 
 // ------------------------------------------------------------------------------------------------ C ABI
 

@@ -1,0 +1,252 @@
+// Raycast of the adaptive grid (the rendering branch of Fig. 2): one thread per pixel.
+//
+// The ray marches from min_depth to max_depth (as z-depth). A sample in an empty brick (4 x 4 x 4 blocks, looked up
+// in a small insert-only set filled when blocks are created) jumps to the brick's exit face; a sample in an
+// unallocated block of a non-empty brick jumps to the block's exit face; so empty space costs one probe per 32 cm
+// instead of one per voxel. Inside an allocated block of level l the field is the trilinear interpolation over the
+// 8 nearest voxel centres of that level's grid; a corner in a neighbouring block reads that block's voxel containing
+// the corner centre, whatever its level, so coarse and fine blocks blend across resolution boundaries. A sample is
+// valid only when all 8 corners are observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead
+// when the sample is valid and F is larger (F <= tau underestimates the distance to the surface, so the step stays
+// in front of it). At the first valid + -> - sign change the linear root is taken, evaluated once more, and one
+// secant step refines it. Output is z-depth, 0 where nothing was hit.
+//
+// Every step follows the oracle's float operation order (this file is compiled without multiply-add contraction),
+// so depths agree with the oracle to rounding and hit/miss decisions agree except at exact ties.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "mrh_internal.cuh"
+
+namespace mrh {
+namespace {
+
+// Block coordinates fit in 32 bits (|key| < 2^20, voxel indices < 2^23), so all index math here is 32-bit: divisions
+// by the power-of-two block side are arithmetic shifts (floor for negatives) and remainders are masks. (64-bit
+// integer division and float -> int64 conversion run on the B300's small FP64 path and dominated an earlier
+// version of this kernel.)
+__device__ inline bool key_ok32(int x, int y, int z) {
+  const int lim = (int)kKeyLimit;
+  return x >= -lim && x <= lim && y >= -lim && y <= lim && z >= -lim && z <= lim;
+}
+
+// float -> int floor, out-of-range values map to an invalid key
+__device__ inline int ifloor(float v) {
+  const float f = floorf(v);
+  return fabsf(f) < 1073741824.0f ? (int)f : 0x7FFFFFFF;
+}
+
+// heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage
+__device__ inline uint32_t find_block(const MapDev& m, int x, int y, int z) {
+  if (!key_ok32(x, y, z)) return kValPending;
+  const int s = lookup_slot(m.slots, m.slot_mask, pack_key(x, y, z));
+  return s >= 0 ? m.slots[s].val : kValPending;
+}
+
+// Two most recent block lookups, keyed by coordinates, in registers (static indices only).
+struct BlockCache {
+  int x0 = 0x7FFFFFFF, y0 = 0, z0 = 0, x1 = 0x7FFFFFFF, y1 = 0, z1 = 0;
+  uint32_t v0 = 0, v1 = 0;
+  __device__ inline uint32_t get(const MapDev& m, int x, int y, int z) {
+    if (x == x0 && y == y0 && z == z0) return v0;
+    if (x == x1 && y == y1 && z == z1) {
+      // promote
+      const int tx = x0, ty = y0, tz = z0;
+      const uint32_t tv = v0;
+      x0 = x1; y0 = y1; z0 = z1; v0 = v1;
+      x1 = tx; y1 = ty; z1 = tz; v1 = tv;
+      return v0;
+    }
+    const uint32_t v = find_block(m, x, y, z);
+    x1 = x0; y1 = y0; z1 = z0; v1 = v0;
+    x0 = x; y0 = y; z0 = z; v0 = v;
+    return v;
+  }
+};
+
+// Brick membership with a one-entry register cache.
+struct BrickCache {
+  int x = 0x7FFFFFFF, y = 0, z = 0;
+  bool present = false;
+  __device__ inline bool get(const MapDev& m, int bx, int by, int bz) {
+    if (bx == x && by == y && bz == z) return present;
+    bool found = false;
+    if (key_ok32(bx, by, bz)) {
+      const unsigned long long k = pack_key(bx, by, bz);
+      const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
+      for (int p = 0; p < kMaxProbes; ++p) {
+        const unsigned long long c = m.brick_keys[(h + (uint32_t)p) & m.brick_mask];
+        if (c == k) {
+          found = true;
+          break;
+        }
+        if (c == kEmptyKey) break;
+      }
+    }
+    x = bx;
+    y = by;
+    z = bz;
+    present = found;
+    return found;
+  }
+};
+
+__device__ inline const uint8_t* block_ptr(const MapDev& m, uint32_t val) {
+  const int lb = (int)((val >> 28) & 3u);
+  return m.heap[lb] + (size_t)(val & kPtrMask) * m.block_bytes[lb];
+}
+
+__device__ inline float read_D(const MapDev& m, const uint8_t* blk, int i) {
+  return m.fp16 ? __half2float(reinterpret_cast<const __half*>(blk)[i]) : reinterpret_cast<const float*>(blk)[i];
+}
+__device__ inline float read_W(const MapDev& m, const uint8_t* blk, int nv, int i) {
+  return reinterpret_cast<const float*>(blk + off_W(nv, m.fp16, m.color))[i];
+}
+
+// trilinear field at x on the level-l grid; false when a corner is unallocated or unobserved. Each distinct block
+// among the 8 corners is looked up once (usually there is only one); the corner sum runs in corner order 0..7.
+__device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, float* out) {
+  const float inv = m.inv_v[l];
+  int j0[3];
+  float fr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float g = x[a] * inv - 0.5f;
+    const float fl = floorf(g);
+    j0[a] = (int)fl;
+    fr[a] = g - fl;
+  }
+  const int sh = 3 - l, nl = 1 << sh, mask = nl - 1;
+  const int b0[3] = {j0[0] >> sh, j0[1] >> sh, j0[2] >> sh};
+  // corners with offset 1 along axis a fall in the next block iff j0 sits on the block's last voxel along a
+  const bool sx = (j0[0] & mask) == mask, sy = (j0[1] & mask) == mask, sz = (j0[2] & mask) == mask;
+  // distinct blocks of the corners, in registers: v<zyx> for the block offset (x, y, z) in {0, 1}^3
+  uint32_t v000, v100 = 0, v010 = 0, v110 = 0, v001 = 0, v101 = 0, v011 = 0, v111 = 0;
+  v000 = bc.get(m, b0[0], b0[1], b0[2]);
+  bool ok = v000 != kValPending;
+  if (ok && sx) { v100 = bc.get(m, b0[0] + 1, b0[1], b0[2]); ok = v100 != kValPending; }
+  if (ok && sy) { v010 = bc.get(m, b0[0], b0[1] + 1, b0[2]); ok = v010 != kValPending; }
+  if (ok && sx && sy) { v110 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2]); ok = v110 != kValPending; }
+  if (ok && sz) { v001 = bc.get(m, b0[0], b0[1], b0[2] + 1); ok = v001 != kValPending; }
+  if (ok && sx && sz) { v101 = bc.get(m, b0[0] + 1, b0[1], b0[2] + 1); ok = v101 != kValPending; }
+  if (ok && sy && sz) { v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1); ok = v011 != kValPending; }
+  if (ok && sx && sy && sz) { v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1); ok = v111 != kValPending; }
+  if (!ok) return false;
+  float acc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+    const bool bx = ax && sx, by = ay && sy, bz = az && sz;
+    const uint32_t val = bz ? (by ? (bx ? v111 : v011) : (bx ? v101 : v001))
+                            : (by ? (bx ? v110 : v010) : (bx ? v100 : v000));
+    const int lb = (int)((val >> 28) & 3u);
+    const int nb = kFineDim >> lb;
+    const uint8_t* blk = block_ptr(m, val);
+    const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
+    int idx;
+    if (lb == l) {
+      idx = (j[0] & mask) + nl * ((j[1] & mask) + nl * (j[2] & mask));
+    } else {
+      // the finest-level cell holding the corner centre, then the block's voxel (at its own level) containing it
+      int cc[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
+      idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
+    }
+    if (!(read_W(m, blk, nb * nb * nb, idx) > 0.0f)) return false;
+    const float wx = ax ? fr[0] : 1.0f - fr[0];
+    const float wy = ay ? fr[1] : 1.0f - fr[1];
+    const float wz = az ? fr[2] : 1.0f - fr[2];
+    acc = acc + wx * wy * wz * read_D(m, blk, idx);
+  }
+  *out = acc;
+  return true;
+}
+
+// sample at t: false when the sample's block is not allocated
+__device__ inline bool sample(const MapDev& m, BlockCache& bc, const float o[3], const float r[3], float t, float invE,
+                              int* level, bool* valid, float* F) {
+  const float x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+  const uint32_t val = bc.get(m, ifloor(x[0] * invE), ifloor(x[1] * invE), ifloor(x[2] * invE));
+  if (val == kValPending) return false;
+  *level = (int)((val >> 28) & 3u);
+  *valid = field(m, bc, x, *level, F);
+  return true;
+}
+
+// One ray: march, find the first zero crossing, write its z-depth (0 = none).
+__device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
+  BlockCache bc;
+  BrickCache brc;
+  const float qx = ((float)u - c.cx) / c.fx, qy = ((float)v - c.cy) / c.fy;
+  const float nq = sqrtf(qx * qx + qy * qy + 1.0f);
+  const float rc[3] = {qx / nq, qy / nq, 1.0f / nq};
+  float r[3], inv_r[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[a] = c.R[3 * a + 0] * rc[0] + c.R[3 * a + 1] * rc[1] + c.R[3 * a + 2] * rc[2];
+    inv_r[a] = r[a] != 0.0f ? 1.0f / r[a] : 0.0f;
+  }
+  const float o[3] = {c.t[0], c.t[1], c.t[2]};
+  const float E = m.E, invE = 1.0f / E, half_tau = m.tau * 0.5f, eps = 1e-4f * E;
+  float t = c.min_depth * nq;
+  const float t_far = c.max_depth * nq;
+  bool have_prev = false;
+  float t_prev = 0.0f, F_prev = 0.0f, hit = 0.0f;
+  for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
+    const float x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+    const int bk[3] = {ifloor(x[0] * invE), ifloor(x[1] * invE), ifloor(x[2] * invE)};
+    const int br[3] = {bk[0] >> kBrickShift, bk[1] >> kBrickShift, bk[2] >> kBrickShift};
+    const bool brick = brc.get(m, br[0], br[1], br[2]);
+    const uint32_t val = brick ? bc.get(m, bk[0], bk[1], bk[2]) : kValPending;
+    if (val == kValPending) {
+      // jump to the exit face of the empty brick, or of the empty block
+      const int span = brick ? 1 : (1 << kBrickShift);
+      float t_exit = t_far + 1.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (r[a] == 0.0f) continue;
+        const int cell = brick ? bk[a] : br[a];
+        const float face = (float)((r[a] > 0.0f ? cell + 1 : cell) * span) * E;
+        const float ta = (face - o[a]) * inv_r[a];
+        if (ta < t_exit) t_exit = ta;
+      }
+      const float step_min = t + eps;
+      const float tn = t_exit + eps;
+      t = tn > step_min ? tn : step_min;
+      have_prev = false;
+      continue;
+    }
+    const int l = (int)((val >> 28) & 3u);
+    float F = 0.0f;
+    const bool valid = field(m, bc, x, l, &F);
+    if (valid && have_prev && F_prev > 0.0f && !(F > 0.0f)) {
+      float ta = t_prev, Fa = F_prev, tb = t, Fb = F;
+      float ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+      int l2 = 0;
+      bool v2 = false;
+      float F2 = 0.0f;
+      if (sample(m, bc, o, r, ts, invE, &l2, &v2, &F2) && v2) {
+        if (F2 > 0.0f) { ta = ts; Fa = F2; } else { tb = ts; Fb = F2; }
+        if (Fa - Fb > 0.0f) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+      }
+      hit = ts * rc[2];
+      break;
+    }
+    have_prev = valid;
+    if (valid) {
+      t_prev = t;
+      F_prev = F;
+    }
+    float s = m.v[l] < half_tau ? m.v[l] : half_tau;
+    if (valid && F > 0.0f) {
+      const float sF = 0.75f * F;
+      if (sF > s) s = sF;
+    }
+    t = t + s;
+  }
+  out[(size_t)v * c.width + u] = hit;
+}
+
+}  // namespace
+}  // namespace mrh
