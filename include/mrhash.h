@@ -160,6 +160,81 @@ mrh_status mrh_batch_config(const mrh_batch* batch, int* config_out8);
 /* Release the batch (not its maps). NULL is accepted. */
 mrh_status mrh_batch_destroy(mrh_batch* batch);
 
+/* ---- Learned level predictor (an addition to the paper's method; the paper has no counterpart).
+ * A 16 -> 64 -> 64 -> 3 multilayer perceptron with GELU activations reads 16 features of a NEW block taken from the
+ * current depth frame and predicts the level the variance rule of Sec. 3.2.1 would give that block after fusing the
+ * sequence. With a predictor set, mrh_integrate_depth allocates each new block at the predicted level instead of the
+ * finest one (Sec. 3.2.1 starts every block fine), so a block predicted coarse is never fused at the fine level. The
+ * variance rule still runs on every touched block afterwards and re-levels any block the network got wrong. LiDAR
+ * frames and batched integration always use the plain rule.
+ *
+ * Features (float32, in this order; computed on the device from the frame's range image rho = z |(q_x, q_y, 1)|,
+ * q = ((u - cx)/fx, (v - cy)/fy), and rounded to BF16): with c the block centre in camera coordinates, r = |c|,
+ * (u0, v0) its projection rounded to the nearest pixel, s = clamp(floor(fx E / (4 c_z)), 1, 16) pixels and a 5 x 5
+ * grid of range samples p_ij at (u0 + (i-2) s, v0 + (j-2) s) (invalid or outside = missing):
+ *   f0 r;  f1 S((mean p - r) / tau);  f2 S(std p / tau);  f3 S((max p - min p) / E);  f4 fraction of the 25
+ *   samples present;  f5 E / r;  f6, f7 S(|central difference of p| along u and v per metre of lateral offset, r s /
+ *   fx metres per step);  f8 S(mean |second difference of p along u| / E);  f9, f10 |2 (u / width - 1/2)|,
+ *   |2 (v / height - 1/2)|;  f11 c_z / r;  f12 1 / r;  f13 0 (camera);  f14 tau / E;  f15 1;
+ *   with S(x) = x / (1 + |x|).
+ * A block whose centre projects outside the image (or behind the camera) gets the finest level and no record.
+ *
+ * Network: x = BF16(f); h1 = BF16(GELU(W1^T x + b1)); h2 = BF16(GELU(W2^T h1 + b2)); logits = W3^T h2 + b3; the
+ * level is the first argmax, clamped to n_levels - 1. Sums are float32 in index order; GELU(x) = x (1 + erf(x /
+ * sqrt 2)) / 2 with erf from Abramowitz & Stegun 7.1.26 and exp by Cody-Waite reduction and a degree-6 Taylor
+ * polynomial, so every decision is reproducible on a CPU. Parameters are packed as W1 [16][64] (input-major), b1
+ * [64], W2 [64][64], b2 [64], W3 [64][3], b3 [3]: MRH_MLP_PARAMS values. */
+#define MRH_MLP_IN 16
+#define MRH_MLP_HIDDEN 64
+#define MRH_MLP_LEVELS 3
+#define MRH_MLP_PARAMS (MRH_MLP_IN * MRH_MLP_HIDDEN + MRH_MLP_HIDDEN + MRH_MLP_HIDDEN * MRH_MLP_HIDDEN + \
+                        MRH_MLP_HIDDEN + MRH_MLP_HIDDEN * MRH_MLP_LEVELS + MRH_MLP_LEVELS)
+
+/* Set the map's predictor from MRH_MLP_PARAMS BF16 bit patterns (host; copied, so the caller keeps ownership), or
+ * turn it off with NULL. n_params must equal MRH_MLP_PARAMS; an inf or NaN weight is rejected. Waits for all work on
+ * the map's device first (frames in flight read the previous weights). */
+mrh_status mrh_set_predictor(mrh_map* map, const uint16_t* bf16_weights_host, uint64_t n_params);
+
+/* Record the features of every new block of later depth frames (training data for the predictor): up to `capacity`
+ * records of (key x, y, z; 16 features), in no particular order; later ones are counted but dropped. 0 turns
+ * recording off and frees its buffers. Waits for all work on the map's device first. */
+mrh_status mrh_set_feature_capture(mrh_map* map, uint32_t capacity);
+
+/* Copy the recorded features out: keys_dev n x 3 int32, features_dev n x 16 float32 (device), n_out = n records
+ * stored, n_seen_out (nullable) = records offered since the last reset (> n when some were dropped). MRH_ERR_CAPACITY
+ * (nothing copied) if capacity < n. With `reset` non-zero the record is emptied afterwards. Synchronises `stream`.
+ * MRH_ERR_INVALID_ARG if recording is off. */
+mrh_status mrh_get_features(mrh_map* map, int32_t* keys_dev, float* features_dev, uint32_t capacity, uint32_t* n_out,
+                            uint64_t* n_seen_out, int reset, void* stream);
+
+/* Trainer of the predictor on the GPU: FP32 master weights, a BF16 copy used by the forward and backward passes (the
+ * same network as above, with the derivative of each BF16 rounding taken as 1), softmax cross-entropy loss averaged
+ * over the batch, and Adam (beta1 0.9, beta2 0.999, epsilon 1e-8, bias-corrected). */
+typedef struct mrh_mlp mrh_mlp; /* opaque, owned by the library */
+
+/* Create a trainer on `device` from MRH_MLP_PARAMS float32 initial weights (host, packed as above, finite). */
+mrh_status mrh_mlp_create(const float* init_host, int device, mrh_mlp** out);
+
+/* Release the trainer. NULL is accepted. */
+mrh_status mrh_mlp_destroy(mrh_mlp* mlp);
+
+/* One Adam step on a batch: x_dev n x 16 float32 features, labels_dev n int32 levels in [0, 3), lr > 0; loss_dev
+ * (one float32, device) receives the batch's mean loss before the step. Asynchronous on `stream`. */
+mrh_status mrh_mlp_train_step(mrh_mlp* mlp, const float* x_dev, const int32_t* labels_dev, uint32_t n, float lr,
+                              float* loss_dev, void* stream);
+
+/* Mean loss and its gradient with respect to the BF16 weights (grad_dev MRH_MLP_PARAMS float32, device), without
+ * updating anything. Asynchronous on `stream`. */
+mrh_status mrh_mlp_loss_grad(const mrh_mlp* mlp, const float* x_dev, const int32_t* labels_dev, uint32_t n,
+                             float* loss_dev, float* grad_dev, void* stream);
+
+/* Logits of n samples (logits_dev n x 3 float32, device) with the BF16 weights. Asynchronous on `stream`. */
+mrh_status mrh_mlp_predict(const mrh_mlp* mlp, const float* x_dev, uint32_t n, float* logits_dev, void* stream);
+
+/* Copy the FP32 master weights and/or the BF16 weights (bit patterns) to the host; either may be NULL, not both.
+ * Synchronises `stream`. */
+mrh_status mrh_mlp_get_weights(const mrh_mlp* mlp, float* master_host, uint16_t* bf16_host, void* stream);
+
 /* Raycast the map from a pinhole view (the rendering branch of Fig. 2): depth_out_dev receives height x width
  * float32 z-depth of the first observed zero crossing, 0 where none. Empty blocks are skipped whole.
  * Asynchronous on `stream`. */

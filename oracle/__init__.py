@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrh_oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "level_predictor.cpp")]
 _SO = os.path.join(_HERE, "libmrh_oracle.so")
 _lib = None
 
@@ -30,9 +31,9 @@ CFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "
 
 def build(force: bool = False) -> str:
     """Compile libmrh_oracle.so if it is missing or older than its source."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(s) for s in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", *CFLAGS, "-o", tmp, _SRC])
+        subprocess.check_call(["g++", *CFLAGS, "-o", tmp, *_SRCS])
         os.replace(tmp, _SO)
     return _SO
 
@@ -78,6 +79,17 @@ def _load():
         lib.orc_resample_block.argtypes = [vp, ctypes.c_int, ctypes.c_int] + [vp] * 8
         lib.orc_half_round.restype = ctypes.c_float
         lib.orc_half_round.argtypes = [ctypes.c_float]
+        for name in ("orc_bf16_round", "orc_exp_cw", "orc_erf_as", "orc_gelu"):
+            getattr(lib, name).restype = ctypes.c_float
+            getattr(lib, name).argtypes = [ctypes.c_float]
+        lib.orc_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
+        lib.orc_block_features.restype = ctypes.c_int
+        lib.orc_block_features.argtypes = [ctypes.POINTER(Pinhole), vp, vp, vp, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int, vp, vp]
+        lib.orc_set_predictor.argtypes = [vp, vp, ctypes.c_int64]
+        lib.orc_set_capture.argtypes = [vp, ctypes.c_int]
+        lib.orc_get_features.restype = ctypes.c_int64
+        lib.orc_get_features.argtypes = [vp, vp, vp, ctypes.c_int64]
         _lib = lib
     return _lib
 
@@ -182,6 +194,29 @@ class OracleMap:
             raise ValueError("invalid level/direction")
         return out
 
+    def set_predictor(self, w_bf16: np.ndarray | None):
+        """Learned level predictor for later depth frames: MLP_PARAMS BF16 bit patterns (uint16), or None."""
+        if w_bf16 is None:
+            self._lib.orc_set_predictor(self._h, None, 0)
+            return
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        if w.size != MLP_PARAMS:
+            raise ValueError("predictor needs %d weights" % MLP_PARAMS)
+        self._lib.orc_set_predictor(self._h, _p(w), w.size)
+
+    def set_capture(self, on: bool):
+        """Record (key, 16 features) of every new block of later depth frames; clears earlier records."""
+        self._lib.orc_set_capture(self._h, int(bool(on)))
+
+    def features(self):
+        """Captured records sorted by key: keys (n, 3) int32, features (n, 16) float32."""
+        n = self._lib.orc_get_features(self._h, None, None, 0)
+        keys = np.zeros((n, 3), np.int32)
+        feats = np.zeros((n, MLP_IN), np.float32)
+        self._lib.orc_get_features(self._h, _p(keys), _p(feats), n)
+        order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+        return keys[order], feats[order]
+
     def block_stats(self) -> dict:
         """Per block (sorted by key): level, mean variance over observed voxels (double), observed count, weight sum."""
         nb, _ = self.count()
@@ -209,3 +244,51 @@ def half_round(x: float) -> float:
 
 BLOCK_UNIT = 1 << 16      # fixed-point units per block edge
 VOXEL_UNIT = BLOCK_UNIT // 8
+
+
+# ---- learned level predictor (level_predictor.cpp): float restatement used for bit-exact level parity
+MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
+MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
+    MLP_LEVELS
+
+
+def bf16_round(x: float) -> float:
+    return _load().orc_bf16_round(x)
+
+
+def exp_cw(x: float) -> float:
+    return _load().orc_exp_cw(x)
+
+
+def erf_as(x: float) -> float:
+    return _load().orc_erf_as(x)
+
+
+def gelu(x: float) -> float:
+    return _load().orc_gelu(x)
+
+
+def mlp_forward(w_bf16: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Logits (n, 3) float32 of the network with BF16 weights (bit patterns) on features x (n, 16)."""
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    xs = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_IN)
+    out = np.zeros((xs.shape[0], MLP_LEVELS), np.float32)
+    _load().orc_mlp_forward(_p(w), _p(xs), xs.shape[0], _p(out))
+    return out
+
+
+def block_features(K: Pinhole, R: np.ndarray, t: np.ndarray, rho: np.ndarray, E: float, tau: float, key,
+                   w_bf16: np.ndarray | None = None, n_levels: int = 3):
+    """Features (16,) float32 of block ``key`` from a range image (h, w) (< 0 invalid), with float pose R (3x3,
+    world <- camera) and t; and the predicted level when weights are given. None when the block is not visible."""
+    Rf = np.ascontiguousarray(R, dtype=np.float32).reshape(9)
+    tf = np.ascontiguousarray(t, dtype=np.float32).reshape(3)
+    r = np.ascontiguousarray(rho, dtype=np.float32)
+    f = np.zeros(MLP_IN, np.float32)
+    lvl = ctypes.c_int(-1)
+    w = None if w_bf16 is None else np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    ok = _load().orc_block_features(ctypes.byref(K), _p(Rf), _p(tf), _p(r), E, tau, int(key[0]), int(key[1]),
+                                    int(key[2]), _p(w), n_levels, _p(f), ctypes.byref(lvl))
+    if not ok:
+        return None
+    return (f, lvl.value) if w is not None else f

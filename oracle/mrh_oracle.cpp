@@ -254,6 +254,10 @@ struct orc_frame_stats {
   int64_t valid_rays, touched, new_blocks, merged, split, fp64_rechecks, observations;
 };
 
+// learned level predictor (level_predictor.cpp)
+int orc_block_features(const orc_pinhole* K, const float* R, const float* t, const float* rho, float E, float tau,
+                       int64_t bx, int64_t by, int64_t bz, const uint16_t* w, int n_levels, float* f, int* level);
+
 }  // extern "C"
 
 namespace {
@@ -285,6 +289,12 @@ struct MapBase {
   virtual int block_stats(int32_t*, uint8_t*, double*, int64_t*, int64_t*) = 0;
   virtual int resample(int, int, const double*, const double*, const double*, const double*, double*, double*,
                        double*, double*) = 0;
+  // learned level predictor (camera frames): BF16 weights, or empty for the plain rule
+  std::vector<uint16_t> pred_w;
+  // feature records of new blocks (training data), when capture is on
+  bool capture = false;
+  std::vector<Key> cap_keys;
+  std::vector<float> cap_feat;
 };
 
 template <class R, class Sto>
@@ -311,13 +321,15 @@ struct Map : MapBase {
   static size_t vox(int n, int x, int y, int z) { return (size_t)x + (size_t)n * ((size_t)y + (size_t)n * z); }
 
   // ---- allocation (Sec. 3.2): insert the blocks of a segment; new blocks start at the finest level (Sec. 3.2.1)
-  void allocate(const std::vector<Key>& cells, std::set<Key>& touched, orc_frame_stats* st) {
+  void allocate(const std::vector<Key>& cells, std::set<Key>& touched, orc_frame_stats* st,
+                std::vector<Key>* fresh = nullptr) {
     for (const Key& k : cells) {
       touched.insert(k);
       if (blocks.find(k) == blocks.end()) {
         Block<R, Sto>& b = blocks[k];
         b.level = 0;
         b.resize(n[0], P.has_color != 0);
+        if (fresh) fresh->push_back(k);
         st->new_blocks++;
         bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
       }
@@ -497,6 +509,7 @@ struct Map : MapBase {
     const float tauf = P.truncation;
     const float Sfix = 65536.0f / E_f;
     std::set<Key> touched;
+    std::vector<Key> fresh;  // blocks created by this frame
     for (int v_ = 0; v_ < K->height; ++v_) {
       for (int u = 0; u < K->width; ++u) {
         float z = depth[(size_t)v_ * K->width + u];
@@ -522,10 +535,39 @@ struct Map : MapBase {
         Key kb{floor_div(B[0], kBlockUnit), floor_div(B[1], kBlockUnit), floor_div(B[2], kBlockUnit)};
         if (!key_in_range(ka) || !key_in_range(kb)) continue;
         st->valid_rays++;
-        allocate(cells_bruteforce(A, B, kBlockUnit), touched, st);
+        allocate(cells_bruteforce(A, B, kBlockUnit), touched, st, &fresh);
       }
     }
     st->touched = (int64_t)touched.size();
+    // (1b) learned level predictor (not in the paper): a new block starts at the level predicted from its features
+    // in this frame's range image instead of the finest level; capture records the features as training data.
+    if (!pred_w.empty() || capture) {
+      std::vector<float> rho_img((size_t)K->width * K->height, -1.0f);
+      for (int v_ = 0; v_ < K->height; ++v_)
+        for (int u = 0; u < K->width; ++u) {
+          float z = depth[(size_t)v_ * K->width + u];
+          if (!(z >= K->min_depth && z <= K->max_depth)) continue;
+          float qx = ((float)u - K->cx) / K->fx;
+          float qy = ((float)v_ - K->cy) / K->fy;
+          rho_img[(size_t)v_ * K->width + u] = z * std::sqrt(qx * qx + qy * qy + 1.0f);
+        }
+      for (const Key& k : fresh) {
+        float f[16];
+        int lvl = -1;
+        if (!orc_block_features(K, Rf, tf, rho_img.data(), E_f, P.truncation, k.x, k.y, k.z,
+                                pred_w.empty() ? nullptr : pred_w.data(), L, f, &lvl))
+          continue;
+        if (lvl > 0) {
+          Block<R, Sto>& b = blocks[k];
+          b.level = lvl;
+          b.resize(n[lvl], P.has_color != 0);
+        }
+        if (capture) {
+          cap_keys.push_back(k);
+          cap_feat.insert(cap_feat.end(), f, f + 16);
+        }
+      }
+    }
     // (2) projective fusion of every voxel of every touched block.
     R Rm[9], t[3];
     pose(T, Rm, t);
@@ -932,6 +974,33 @@ int64_t orc_segment_cells(const int64_t* A, const int64_t* B, int64_t U, int mod
 }
 
 float orc_half_round(float x) { return half_round(x); }
+
+// Learned level predictor: weights (MRH-packed BF16 bits, 5443 values) or null to turn it off.
+void orc_set_predictor(void* h, const uint16_t* w, int64_t n) {
+  MapBase* m = (MapBase*)h;
+  if (w) m->pred_w.assign(w, w + n);
+  else m->pred_w.clear();
+}
+
+void orc_set_capture(void* h, int on) {
+  MapBase* m = (MapBase*)h;
+  m->capture = on != 0;
+  m->cap_keys.clear();
+  m->cap_feat.clear();
+}
+
+// Captured records in capture order; returns the count (records written up to cap).
+int64_t orc_get_features(void* h, int32_t* keys, float* feats, int64_t cap) {
+  MapBase* m = (MapBase*)h;
+  const int64_t n = (int64_t)m->cap_keys.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    keys[3 * i] = (int32_t)m->cap_keys[i].x;
+    keys[3 * i + 1] = (int32_t)m->cap_keys[i].y;
+    keys[3 * i + 2] = (int32_t)m->cap_keys[i].z;
+    for (int q = 0; q < 16; ++q) feats[16 * i + q] = m->cap_feat[16 * i + q];
+  }
+  return n;
+}
 
 // Test hook: the merge (dir = +1) or split (dir = -1) payload rule applied to one block of the given level.
 int orc_resample_block(void* h, int level, int dir, const double* D, const double* W, const double* S2,

@@ -72,8 +72,14 @@ class BatchFrame(ctypes.Structure):
 EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points", "mrh_raycast",
            "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc", "mrh_get_stats", "mrh_sync",
            "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create", "mrh_batch_integrate",
-           "mrh_batch_config", "mrh_batch_destroy", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
+           "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
+           "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
+           "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
            "mrh_version"]
+
+MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
+MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
+    MLP_LEVELS
 
 
 def lib():
@@ -102,6 +108,16 @@ def lib():
         L.mrh_batch_integrate.argtypes = [vp, ctypes.POINTER(BatchFrame), vp]
         L.mrh_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.mrh_batch_destroy.argtypes = [vp]
+        L.mrh_set_predictor.argtypes = [vp, vp, u64]
+        L.mrh_set_feature_capture.argtypes = [vp, ctypes.c_uint32]
+        L.mrh_get_features.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(u64), i32, vp]
+        L.mrh_mlp_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.mrh_mlp_destroy.argtypes = [vp]
+        L.mrh_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, vp, vp]
+        L.mrh_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, vp]
+        L.mrh_mlp_predict.argtypes = [vp, vp, ctypes.c_uint32, vp, vp]
+        L.mrh_mlp_get_weights.argtypes = [vp, vp, vp, vp]
         L.mrh_hash_slot.restype = ctypes.c_uint32
         L.mrh_hash_slot.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
         L.mrh_status_string.restype = ctypes.c_char_p
@@ -111,7 +127,9 @@ def lib():
                      "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc",
                      "mrh_get_stats", "mrh_sync",
                      "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create",
-                     "mrh_batch_integrate", "mrh_batch_config", "mrh_batch_destroy"):
+                     "mrh_batch_integrate", "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor",
+                     "mrh_set_feature_capture", "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy",
+                     "mrh_mlp_train_step", "mrh_mlp_loss_grad", "mrh_mlp_predict", "mrh_mlp_get_weights"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -277,6 +295,88 @@ class Map:
 
     def clear_status(self, stream=None):
         _check(self._lib.mrh_clear_status(self._h, _stream(stream)), "mrh_clear_status")
+
+    def set_predictor(self, w_bf16):
+        """Learned level predictor for later depth frames: MLP_PARAMS BF16 bit patterns (numpy uint16), or None."""
+        if w_bf16 is None:
+            _check(self._lib.mrh_set_predictor(self._h, None, 0), "mrh_set_predictor")
+            return
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        _check(self._lib.mrh_set_predictor(self._h, ctypes.c_void_p(w.ctypes.data), w.size), "mrh_set_predictor")
+
+    def set_feature_capture(self, capacity: int):
+        """Record (key, features) of up to ``capacity`` new blocks of later depth frames; 0 turns it off."""
+        _check(self._lib.mrh_set_feature_capture(self._h, int(capacity)), "mrh_set_feature_capture")
+
+    def features(self, reset: bool = False, stream=None):
+        """Recorded new-block features: (keys (n,3) int32, features (n,16) float32) CUDA tensors in record order,
+        and the number of records offered (more than n when the capacity was exceeded)."""
+        import torch
+        n, seen = ctypes.c_uint32(), ctypes.c_uint64()
+        _check(self._lib.mrh_get_features(self._h, None, None, 0, ctypes.byref(n), ctypes.byref(seen), 0,
+                                          _stream(stream)), "mrh_get_features", allow=(7,))
+        dev = f"cuda:{self.device}"
+        keys = torch.empty((max(n.value, 1), 3), dtype=torch.int32, device=dev)
+        feats = torch.empty((max(n.value, 1), MLP_IN), dtype=torch.float32, device=dev)
+        _check(self._lib.mrh_get_features(self._h, _ptr(keys), _ptr(feats), max(n.value, 1), ctypes.byref(n),
+                                          ctypes.byref(seen), int(reset), _stream(stream)), "mrh_get_features")
+        return keys[:n.value], feats[:n.value], seen.value
+
+
+class Mlp:
+    """GPU trainer of the level predictor (mrh_mlp_*): FP32 master weights, BF16 forward / backward, Adam."""
+
+    def __init__(self, init_weights, device: int = 0):
+        self._lib = lib()
+        self.device = device
+        w = np.ascontiguousarray(init_weights, dtype=np.float32)
+        if w.size != MLP_PARAMS:
+            raise ValueError(f"need {MLP_PARAMS} weights")
+        h = ctypes.c_void_p()
+        _check(self._lib.mrh_mlp_create(ctypes.c_void_p(w.ctypes.data), device, ctypes.byref(h)), "mrh_mlp_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mrh_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train_step(self, x, labels, lr: float, loss_out, stream=None):
+        """One Adam step on (x (n,16) float32, labels (n,) int32) CUDA tensors; loss_out: 1-element CUDA tensor."""
+        _check(self._lib.mrh_mlp_train_step(self._h, _ptr(x), _ptr(labels), x.shape[0], float(lr), _ptr(loss_out),
+                                            _stream(stream)), "mrh_mlp_train_step")
+
+    def loss_grad(self, x, labels, stream=None):
+        """(loss (1,), grad (MLP_PARAMS,)) CUDA tensors for the current BF16 weights."""
+        import torch
+        dev = f"cuda:{self.device}"
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=dev)
+        _check(self._lib.mrh_mlp_loss_grad(self._h, _ptr(x), _ptr(labels), x.shape[0], _ptr(loss), _ptr(grad),
+                                           _stream(stream)), "mrh_mlp_loss_grad")
+        return loss, grad
+
+    def predict(self, x, stream=None):
+        import torch
+        out = torch.empty((x.shape[0], MLP_LEVELS), dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(self._lib.mrh_mlp_predict(self._h, _ptr(x), x.shape[0], _ptr(out), _stream(stream)),
+               "mrh_mlp_predict")
+        return out
+
+    def weights(self, stream=None):
+        """(FP32 master weights, BF16 bit patterns) as numpy arrays."""
+        master = np.zeros(MLP_PARAMS, np.float32)
+        bf = np.zeros(MLP_PARAMS, np.uint16)
+        _check(self._lib.mrh_mlp_get_weights(self._h, ctypes.c_void_p(master.ctypes.data),
+                                             ctypes.c_void_p(bf.ctypes.data), _stream(stream)),
+               "mrh_mlp_get_weights")
+        return master, bf
 
 
 class Batch:

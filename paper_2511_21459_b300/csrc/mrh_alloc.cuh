@@ -209,12 +209,14 @@ __device__ inline void alloc_points_cta(const MapDev& m, const PoseD& P, const f
 }
 
 // Touched entry i of this frame: new blocks get a heap block of the finest level (Sec. 3.2.1: "we initialize the
-// voxel blocks to the finest resolution") and their brick is recorded for the raycaster; the slot is binned by
-// level. A block whose heap is empty keeps no storage, is not fused, and is retried in later frames.
-__device__ inline void bin_one(const MapDev& m, uint32_t i) {
+// voxel blocks to the finest resolution"), or of new_level when the learned predictor gave one, and their brick is
+// recorded for the raycaster; the slot is binned by level. A block whose heap is empty keeps no storage, is not
+// fused, and is retried in later frames.
+__device__ inline void bin_one(const MapDev& m, uint32_t i, int new_level = 0) {
   const uint32_t s = m.touched_all[i];
   uint32_t val = m.slots[s].val;
   if (val == kValPending) {
+    const int l = new_level;
     {
       int bx, by, bz;
       unpack_key(m.slots[s].key, &bx, &by, &bz);
@@ -232,7 +234,6 @@ __device__ inline void bin_one(const MapDev& m, uint32_t i) {
         if (old == kEmptyKey || old == bkey) break;
       }
     }
-    const int l = 0;
     int t = atomicSub(&m.st->free_top[l], 1);
     if (t <= 0) {
       atomicAdd(&m.st->free_top[l], 1);

@@ -205,17 +205,10 @@ struct mrh_batch {
 
 namespace {
 
-thread_local char g_batch_err[256] = "";
-
-mrh_status batch_cuda_fail(cudaError_t e, const char* what) {
-  std::snprintf(g_batch_err, sizeof(g_batch_err), "%s: %s", what, cudaGetErrorString(e));
-  return MRH_ERR_CUDA;
-}
-
 #define MRH_BCUDA(call)                                        \
   do {                                                         \
     cudaError_t e_ = (call);                                   \
-    if (e_ != cudaSuccess) return batch_cuda_fail(e_, #call);  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
   } while (0)
 
 struct BatchDeviceGuard {
@@ -335,7 +328,7 @@ mrh_status mrh_batch_create(mrh_map* const* maps, const mrh_pinhole* cams, int n
   }
   auto fail = [&](cudaError_t e, const char* what) {
     mrh_batch_destroy(b);
-    return e == cudaErrorMemoryAllocation ? MRH_ERR_OUT_OF_MEMORY : batch_cuda_fail(e, what);
+    return e == cudaErrorMemoryAllocation ? MRH_ERR_OUT_OF_MEMORY : cuda_fail(e, what);
   };
   cudaError_t e = cudaMalloc(&b->maps_dev, sizeof(MapDev) * n);
   if (e != cudaSuccess) return fail(e, "cudaMalloc");
@@ -479,12 +472,12 @@ mrh_status mrh_batch_integrate(mrh_batch* b, const mrh_batch_frame* frames, void
       launch_step(b, b->alloc_shape, b->fuse_shape, b->ray_shape, s, nullptr);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(s, &g);
-      if (e != cudaSuccess) return batch_cuda_fail(e, "cudaStreamEndCapture");
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
       b->graph = g;
       e = cudaGraphInstantiate(&b->exec, g, 0);
       if (e != cudaSuccess) {
         destroy_graph(b);
-        return batch_cuda_fail(e, "cudaGraphInstantiate");
+        return cuda_fail(e, "cudaGraphInstantiate");
       }
       b->graph_stream = s;
     }

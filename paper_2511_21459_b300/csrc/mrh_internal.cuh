@@ -96,6 +96,11 @@ struct MapDev {
   uint32_t max_obs;
   DevState* st;
   unsigned long long* brick_keys;  // insert-only set of 4x4x4-block bricks holding an allocated block (raycast)
+  const uint16_t* pred_w;          // learned level predictor: BF16 weights, or null (variance rule only)
+  int* cap_keys;                   // feature capture of new blocks (3 ints per record), or null
+  float* cap_feat;                 // 16 floats per record
+  uint32_t* cap_count;
+  uint32_t cap_max;
   uint32_t brick_mask;
   float v[kMaxLevels];  // voxel edge per level
   float inv_v[kMaxLevels];  // 1 / v, as the float division computes it
@@ -329,6 +334,9 @@ void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, c
                         uint32_t* rgb_img, cudaStream_t s);
 void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s);
 void launch_bin(const MapDev& m, cudaStream_t s, int sms);
+// Record the failing call's text for mrh_last_cuda_error (calling thread) and return MRH_ERR_CUDA.
+mrh_status cuda_fail(cudaError_t e, const char* what);
+void launch_bin_camera(const MapDev& m, const CamArgs& c, const float* rho_img, cudaStream_t s, int sms);
 void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* rho, const uint32_t* rgb, cudaStream_t s,
                        int sms);
 void launch_fuse_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s, int sms);

@@ -43,17 +43,22 @@ struct mrh_map {
   float* rho_img = nullptr;
   uint32_t* rgb_img = nullptr;
   size_t img_pixels = 0;
+  // learned level predictor weights (BF16), owned; d.pred_w points here while the predictor is on
+  uint16_t* pred_buf = nullptr;
 };
 
 namespace mrh {
-namespace {
 
+namespace {
 thread_local char g_cuda_err[256] = "";
+}  // namespace
 
 mrh_status cuda_fail(cudaError_t e, const char* what) {
   std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
   return MRH_ERR_CUDA;
 }
+
+namespace {
 
 #define MRH_CUDA(call)                                   \
   do {                                                   \
@@ -309,11 +314,25 @@ mrh_status dev_alloc(mrh_map* m, T** out, size_t count) {
   return MRH_OK;
 }
 
+void free_capture(mrh_map* m) {
+  if (m->d.cap_keys) cudaFree(m->d.cap_keys);
+  if (m->d.cap_feat) cudaFree(m->d.cap_feat);
+  if (m->d.cap_count) cudaFree(m->d.cap_count);
+  m->d.cap_keys = nullptr;
+  m->d.cap_feat = nullptr;
+  m->d.cap_count = nullptr;
+  m->d.cap_max = 0;
+}
+
 void free_all(mrh_map* m) {
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
   if (m->rho_img) cudaFree(m->rho_img);
   if (m->rgb_img) cudaFree(m->rgb_img);
+  if (m->pred_buf) cudaFree(m->pred_buf);
+  free_capture(m);
+  m->pred_buf = nullptr;
+  m->d.pred_w = nullptr;
   m->rho_img = nullptr;
   m->rgb_img = nullptr;
   m->img_pixels = 0;
@@ -485,6 +504,66 @@ mrh_status mrh_map_destroy(mrh_map* m) {
   return MRH_OK;
 }
 
+mrh_status mrh_set_predictor(mrh_map* m, const uint16_t* bf16_weights_host, uint64_t n_params) {
+  if (!m) return MRH_ERR_INVALID_ARG;
+  if (!bf16_weights_host) {
+    m->d.pred_w = nullptr;
+    return MRH_OK;
+  }
+  if (n_params != (uint64_t)MRH_MLP_PARAMS) return MRH_ERR_INVALID_ARG;
+  for (uint64_t i = 0; i < n_params; ++i)
+    if ((bf16_weights_host[i] & 0x7F80u) == 0x7F80u) return MRH_ERR_INVALID_ARG;  // inf or nan
+  DeviceGuard guard(m->device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  MRH_CUDA(cudaDeviceSynchronize());  // frames in flight may still read the old weights
+  if (!m->pred_buf) MRH_CUDA(cudaMalloc(&m->pred_buf, sizeof(uint16_t) * MRH_MLP_PARAMS));
+  MRH_CUDA(cudaMemcpy(m->pred_buf, bf16_weights_host, sizeof(uint16_t) * MRH_MLP_PARAMS, cudaMemcpyHostToDevice));
+  m->d.pred_w = m->pred_buf;
+  return MRH_OK;
+}
+
+mrh_status mrh_set_feature_capture(mrh_map* m, uint32_t capacity) {
+  if (!m) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  MRH_CUDA(cudaDeviceSynchronize());
+  free_capture(m);
+  if (capacity == 0) return MRH_OK;
+  cudaError_t e = cudaMalloc(&m->d.cap_keys, sizeof(int) * 3 * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.cap_feat, sizeof(float) * MRH_MLP_IN * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.cap_count, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(m->d.cap_count, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    free_capture(m);
+    return e == cudaErrorMemoryAllocation ? MRH_ERR_OUT_OF_MEMORY : cuda_fail(e, "mrh_set_feature_capture");
+  }
+  m->d.cap_max = capacity;
+  return MRH_OK;
+}
+
+mrh_status mrh_get_features(mrh_map* m, int32_t* keys_dev, float* features_dev, uint32_t capacity, uint32_t* n_out,
+                            uint64_t* n_seen_out, int reset, void* stream) {
+  if (!m || !n_out || !m->d.cap_count) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t seen = 0;
+  MRH_CUDA(cudaMemcpyAsync(&seen, m->d.cap_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  MRH_CUDA(cudaStreamSynchronize(s));
+  const uint32_t stored = std::min(seen, m->d.cap_max);
+  *n_out = stored;
+  if (n_seen_out) *n_seen_out = seen;
+  if (stored > 0 && (!keys_dev || !features_dev || capacity < stored)) return MRH_ERR_CAPACITY;
+  if (stored > 0) {
+    MRH_CUDA(cudaMemcpyAsync(keys_dev, m->d.cap_keys, sizeof(int32_t) * 3 * (size_t)stored,
+                             cudaMemcpyDeviceToDevice, s));
+    MRH_CUDA(cudaMemcpyAsync(features_dev, m->d.cap_feat, sizeof(float) * MRH_MLP_IN * (size_t)stored,
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  if (reset) MRH_CUDA(cudaMemsetAsync(m->d.cap_count, 0, sizeof(uint32_t), s));
+  MRH_CUDA(cudaStreamSynchronize(s));
+  return MRH_OK;
+}
+
 mrh_status mrh_integrate_depth(mrh_map* m, const mrh_pinhole* K, const double* T_wc, const float* depth,
                                const uint8_t* rgb, void* stream) {
   if (!m || !depth || !finite_pose(T_wc)) return MRH_ERR_INVALID_ARG;
@@ -508,8 +587,11 @@ mrh_status mrh_integrate_depth(mrh_map* m, const mrh_pinhole* K, const double* T
   const uint8_t* rgb_in = m->p.has_color ? rgb : nullptr;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
   { KernelScope ks(m, MRH_K_ALLOC, s, 1); launch_alloc_depth(m->d, c, depth, rgb_in, m->rho_img, m->rgb_img, s); }
-  { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
-  { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_depth(m->d, c, m->rho_img, rgb_in ? m->rgb_img : nullptr, s, m->sms); }
+  { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin_camera(m->d, c, m->rho_img, s, m->sms); }
+  {
+    KernelScope ks(m, MRH_K_FUSE, s, 1);
+    launch_fuse_depth(m->d, c, m->rho_img, rgb_in ? m->rgb_img : nullptr, s, m->sms);
+  }
   { KernelScope ks(m, MRH_K_RELEASE, s, 1); k_release<<<m->sms, 256, 0, s>>>(m->d); }
   MRH_CUDA(cudaGetLastError());
   return MRH_OK;
