@@ -220,19 +220,11 @@ __device__ inline void bin_one(const MapDev& m, uint32_t i, int new_level = 0) {
     {
       int bx, by, bz;
       unpack_key(m.slots[s].key, &bx, &by, &bz);
-      bx >>= kBrickShift;
-      by >>= kBrickShift;
-      bz >>= kBrickShift;
-      const unsigned long long bkey = pack_key(bx, by, bz);
-      const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
-      for (uint32_t p = 0; p <= m.brick_mask && p < (uint32_t)kMaxProbes; ++p) {
-        unsigned long long* slot = &m.brick_keys[(h + p) & m.brick_mask];
-        const unsigned long long cur = *(volatile unsigned long long*)slot;
-        if (cur == bkey) break;
-        if (cur != kEmptyKey) continue;
-        const unsigned long long old = atomicCAS(slot, kEmptyKey, bkey);
-        if (old == kEmptyKey || old == bkey) break;
-      }
+      const int rx = bx >> kBrickShift, ry = by >> kBrickShift, rz = bz >> kBrickShift;
+      bool ok = occupancy_insert(m.brick_keys, m.brick_bits, m.brick_mask, rx, ry, rz, cell_bit(bx, by, bz));
+      ok = ok && occupancy_insert(m.super_keys, m.super_bits, m.super_mask, rx >> kSuperShift, ry >> kSuperShift,
+                                  rz >> kSuperShift, cell_bit(rx, ry, rz));
+      if (!ok) set_status(m.st, kStHashFull);
     }
     int t = atomicSub(&m.st->free_top[l], 1);
     if (t <= 0) {

@@ -15,7 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/mrhash.h"
+#include "mrhash.h"
 
 namespace mrh {
 
@@ -35,6 +35,7 @@ constexpr int kMaxSegmentCells = 64;
 constexpr int kMaxVoxelCells = 256;
 constexpr int kRaycastMaxIter = 8192;
 constexpr int kBrickShift = 2;  // a brick is 4 x 4 x 4 blocks
+constexpr int kSuperShift = 2;  // a super-brick is 4 x 4 x 4 bricks
 
 // status bits (sticky)
 constexpr uint32_t kStHashFull = 1u << 0;
@@ -95,7 +96,14 @@ struct MapDev {
   uint32_t* obs_idx;          // per-voxel bins of observation indices
   uint32_t max_obs;
   DevState* st;
-  unsigned long long* brick_keys;  // insert-only set of 4x4x4-block bricks holding an allocated block (raycast)
+  // Raycast occupancy (insert-only open-addressing sets, filled when blocks are created): bricks of 4 x 4 x 4 blocks
+  // with a 64-bit mask of their created blocks, and super-bricks of 4 x 4 x 4 bricks with a mask of their non-empty
+  // bricks. Bit of cell (x, y, z) inside its parent: x + 4 y + 16 z.
+  unsigned long long* brick_keys;
+  unsigned long long* brick_bits;
+  unsigned long long* super_keys;
+  unsigned long long* super_bits;
+  uint32_t super_mask;
   const uint16_t* pred_w;          // learned level predictor: BF16 weights, or null (variance rule only)
   int* cap_keys;                   // feature capture of new blocks (3 ints per record), or null
   float* cap_feat;                 // 16 floats per record
@@ -183,6 +191,45 @@ __device__ inline bool to_fixed_d(double v, double S, long long* out) {
 }
 
 __device__ inline void set_status(DevState* st, uint32_t bit) { atomicOr(&st->status, bit); }
+
+// bit of a cell inside its 4 x 4 x 4 parent
+__host__ __device__ inline unsigned long long cell_bit(int x, int y, int z) {
+  return 1ull << ((x & 3) + 4 * (y & 3) + 16 * (z & 3));
+}
+
+// Insert key (x, y, z) into an insert-only set (keys[], bits[], linear probing from Eq. 4's hash) and OR `bit` into
+// its mask. Returns false when no slot was found within the probe limit.
+__device__ inline bool occupancy_insert(unsigned long long* keys, unsigned long long* bits, uint32_t mask, int x,
+                                        int y, int z, unsigned long long bit) {
+  const unsigned long long key = pack_key(x, y, z);
+  const uint32_t h = hash_xyz(x, y, z, mask);
+  for (uint32_t p = 0; p <= mask && p < (uint32_t)kMaxProbes; ++p) {
+    const uint32_t s = (h + p) & mask;
+    const unsigned long long cur = *(volatile unsigned long long*)&keys[s];
+    if (cur != key) {
+      if (cur != kEmptyKey) continue;
+      const unsigned long long old = atomicCAS(&keys[s], kEmptyKey, key);
+      if (old != kEmptyKey && old != key) continue;
+    }
+    if ((*(volatile unsigned long long*)&bits[s] & bit) == 0) atomicOr(&bits[s], bit);
+    return true;
+  }
+  return false;
+}
+
+// Mask of key (x, y, z) in an occupancy set, 0 when absent.
+__device__ inline unsigned long long occupancy_bits(const unsigned long long* keys, const unsigned long long* bits,
+                                                    uint32_t mask, int x, int y, int z) {
+  const unsigned long long key = pack_key(x, y, z);
+  const uint32_t h = hash_xyz(x, y, z, mask);
+  for (int p = 0; p < kMaxProbes; ++p) {
+    const uint32_t s = (h + (uint32_t)p) & mask;
+    const unsigned long long c = keys[s];
+    if (c == key) return bits[s];
+    if (c == kEmptyKey) return 0;
+  }
+  return 0;
+}
 
 // Single-thread lookup (linear probing from H). Returns the slot index or -1.
 __device__ inline int lookup_slot(const Slot* slots, uint32_t mask, unsigned long long key) {

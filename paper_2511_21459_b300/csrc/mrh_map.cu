@@ -451,6 +451,11 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   const uint32_t n_brick_slots = 1u << (params->hash_slots_log2 > 12 ? params->hash_slots_log2 - 2 : 10);
   d.brick_mask = n_brick_slots - 1;
   TRY(dev_alloc(m, &d.brick_keys, n_brick_slots));
+  TRY(dev_alloc(m, &d.brick_bits, n_brick_slots));
+  const uint32_t n_super_slots = std::max(n_brick_slots >> 3, 1024u);
+  d.super_mask = n_super_slots - 1;
+  TRY(dev_alloc(m, &d.super_keys, n_super_slots));
+  TRY(dev_alloc(m, &d.super_bits, n_super_slots));
   TRY(dev_alloc(m, &d.blk_count, 3ull * params->max_touched));
   TRY(dev_alloc(m, &d.blk_fill, 3ull * params->max_touched));
   TRY(dev_alloc(m, &d.blk_off, 3ull * params->max_touched + 1));
@@ -477,6 +482,9 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
 #undef TRY
   cudaError_t e = cudaMemset(d.slots, 0xFF, (size_t)n_slots * sizeof(Slot));
   if (e == cudaSuccess) e = cudaMemset(d.brick_keys, 0xFF, (size_t)n_brick_slots * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d.brick_bits, 0, (size_t)n_brick_slots * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d.super_keys, 0xFF, (size_t)n_super_slots * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d.super_bits, 0, (size_t)n_super_slots * sizeof(unsigned long long));
   DevState hs;
   std::memset(&hs, 0, sizeof(hs));
   for (int l = 0; l < kMaxLevels; ++l) hs.free_top[l] = (int)d.max_blocks[l];

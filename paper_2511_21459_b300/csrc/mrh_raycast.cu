@@ -4,19 +4,27 @@
 namespace mrh {
 namespace {
 
-// One thread per pixel; each warp covers an 8 x 4 pixel tile so that its rays march through the same blocks.
-__global__ void __launch_bounds__(128) k_raycast(MapDev m, CamArgs c, float* __restrict__ out) {
+// One thread per pixel; each warp covers an 8 x 4 pixel tile so that its rays march through the same blocks. Six
+// CTAs per SM (at most 80 registers) measured best among 4 to 8 CTAs of 128 threads and 32- or 256-thread CTAs.
+template <bool FP16, bool COLOR>
+__global__ void __launch_bounds__(128, 6) k_raycast(MapDev m, CamArgs c, float* __restrict__ out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int v = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-  if (u < c.width && v < c.height) cast_ray(m, c, u, v, out);
+  if (u < c.width && v < c.height) cast_ray<FP16, COLOR>(m, c, u, v, out);
 }
 
 }  // namespace
 
 void launch_raycast(const MapDev& m, const CamArgs& c, float* out, cudaStream_t s) {
   dim3 grid((c.width + 15) / 16, (c.height + 7) / 8);
-  k_raycast<<<grid, 128, 0, s>>>(m, c, out);
+  if (m.fp16) {
+    if (m.color) k_raycast<true, true><<<grid, 128, 0, s>>>(m, c, out);
+    else k_raycast<true, false><<<grid, 128, 0, s>>>(m, c, out);
+  } else {
+    if (m.color) k_raycast<false, true><<<grid, 128, 0, s>>>(m, c, out);
+    else k_raycast<false, false><<<grid, 128, 0, s>>>(m, c, out);
+  }
 }
 
 }  // namespace mrh

@@ -1,9 +1,10 @@
 // Raycast of the adaptive grid (the rendering branch of Fig. 2): one thread per pixel.
 //
-// The ray marches from min_depth to max_depth (as z-depth). A sample in an empty brick (4 x 4 x 4 blocks, looked up
-// in a small insert-only set filled when blocks are created) jumps to the brick's exit face; a sample in an
-// unallocated block of a non-empty brick jumps to the block's exit face; so empty space costs one probe per 32 cm
-// instead of one per voxel. Inside an allocated block of level l the field is the trilinear interpolation over the
+// The ray marches from min_depth to max_depth (as z-depth). A sample in an empty brick (4 x 4 x 4 blocks) jumps to
+// the brick's exit face; a sample in an unallocated block of a non-empty brick jumps to the block's exit face. Brick
+// and block occupancy come from two small insert-only sets filled when blocks are created (super-bricks of 4 x 4 x 4
+// bricks with a 64-bit mask of non-empty bricks; bricks with a 64-bit mask of created blocks), cached in registers,
+// so an empty-space step costs a memory probe only when the ray enters a new super-brick or non-empty brick. Inside an allocated block of level l the field is the trilinear interpolation over the
 // 8 nearest voxel centres of that level's grid; a corner in a neighbouring block reads that block's voxel containing
 // the corner centre, whatever its level, so coarse and fine blocks blend across resolution boundaries. A sample is
 // valid only when all 8 corners are observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead
@@ -36,11 +37,18 @@ __device__ inline int ifloor(float v) {
   return fabsf(f) < 1073741824.0f ? (int)f : 0x7FFFFFFF;
 }
 
-// heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage
-__device__ inline uint32_t find_block(const MapDev& m, int x, int y, int z) {
+// heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage. Not inlined:
+// the probe loop is the cache-miss path of several call sites, and one copy keeps the kernel's code small.
+__device__ __noinline__ uint32_t find_block(const Slot* __restrict__ slots, uint32_t slot_mask, int x, int y, int z) {
   if (!key_ok32(x, y, z)) return kValPending;
-  const int s = lookup_slot(m.slots, m.slot_mask, pack_key(x, y, z));
-  return s >= 0 ? m.slots[s].val : kValPending;
+  const int s = lookup_slot(slots, slot_mask, pack_key(x, y, z));
+  return s >= 0 ? slots[s].val : kValPending;
+}
+
+__device__ __noinline__ unsigned long long find_bits(const unsigned long long* __restrict__ keys,
+                                                     const unsigned long long* __restrict__ vals, uint32_t mask,
+                                                     int x, int y, int z) {
+  return key_ok32(x, y, z) ? occupancy_bits(keys, vals, mask, x, y, z) : 0ull;
 }
 
 // Two most recent block lookups, keyed by coordinates, in registers (static indices only).
@@ -57,37 +65,25 @@ struct BlockCache {
       x1 = tx; y1 = ty; z1 = tz; v1 = tv;
       return v0;
     }
-    const uint32_t v = find_block(m, x, y, z);
+    const uint32_t v = find_block(m.slots, m.slot_mask, x, y, z);
     x1 = x0; y1 = y0; z1 = z0; v1 = v0;
     x0 = x; y0 = y; z0 = z; v0 = v;
     return v;
   }
 };
 
-// Brick membership with a one-entry register cache.
-struct BrickCache {
+// Occupancy mask of one set (bricks or super-bricks) with a one-entry register cache.
+struct OccCache {
   int x = 0x7FFFFFFF, y = 0, z = 0;
-  bool present = false;
-  __device__ inline bool get(const MapDev& m, int bx, int by, int bz) {
-    if (bx == x && by == y && bz == z) return present;
-    bool found = false;
-    if (key_ok32(bx, by, bz)) {
-      const unsigned long long k = pack_key(bx, by, bz);
-      const uint32_t h = hash_xyz(bx, by, bz, m.brick_mask);
-      for (int p = 0; p < kMaxProbes; ++p) {
-        const unsigned long long c = m.brick_keys[(h + (uint32_t)p) & m.brick_mask];
-        if (c == k) {
-          found = true;
-          break;
-        }
-        if (c == kEmptyKey) break;
-      }
-    }
-    x = bx;
-    y = by;
-    z = bz;
-    present = found;
-    return found;
+  unsigned long long bits = 0;
+  __device__ inline unsigned long long get(const unsigned long long* keys, const unsigned long long* vals,
+                                           uint32_t mask, int cx, int cy, int cz) {
+    if (cx == x && cy == y && cz == z) return bits;
+    x = cx;
+    y = cy;
+    z = cz;
+    bits = find_bits(keys, vals, mask, cx, cy, cz);
+    return bits;
   }
 };
 
@@ -96,15 +92,20 @@ __device__ inline const uint8_t* block_ptr(const MapDev& m, uint32_t val) {
   return m.heap[lb] + (size_t)(val & kPtrMask) * m.block_bytes[lb];
 }
 
-__device__ inline float read_D(const MapDev& m, const uint8_t* blk, int i) {
-  return m.fp16 ? __half2float(reinterpret_cast<const __half*>(blk)[i]) : reinterpret_cast<const float*>(blk)[i];
+// Storage format (FP16 / colour) is a template parameter of the raycaster, so field reads carry no format branches.
+template <bool FP16>
+__device__ inline float read_D(const uint8_t* blk, int i) {
+  if (FP16) return __half2float(reinterpret_cast<const __half*>(blk)[i]);
+  return reinterpret_cast<const float*>(blk)[i];
 }
-__device__ inline float read_W(const MapDev& m, const uint8_t* blk, int nv, int i) {
-  return reinterpret_cast<const float*>(blk + off_W(nv, m.fp16, m.color))[i];
+template <bool FP16, bool COLOR>
+__device__ inline float read_W(const uint8_t* blk, int nv, int i) {
+  return reinterpret_cast<const float*>(blk + off_W(nv, FP16, COLOR))[i];
 }
 
 // trilinear field at x on the level-l grid; false when a corner is unallocated or unobserved. Each distinct block
 // among the 8 corners is looked up once (usually there is only one); the corner sum runs in corner order 0..7.
+template <bool FP16, bool COLOR>
 __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, float* out) {
   const float inv = m.inv_v[l];
   int j0[3];
@@ -132,6 +133,33 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
   if (ok && sy && sz) { v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1); ok = v011 != kValPending; }
   if (ok && sx && sy && sz) { v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1); ok = v111 != kValPending; }
   if (!ok) return false;
+  if (!(sx || sy || sz) && (int)((v000 >> 28) & 3u) == l) {
+    // all 8 corners in one block of level l: issue the 16 loads together, then test and sum in corner order
+    const uint8_t* blk = block_ptr(m, v000);
+    const int i0 = (j0[0] & mask) + nl * ((j0[1] & mask) + nl * (j0[2] & mask));
+    const int nv = nl * nl * nl;
+    float w[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int idx = i0 + (k & 1) + nl * ((k >> 1) & 1) + nl * nl * (k >> 2);
+      w[k] = read_W<FP16, COLOR>(blk, nv, idx);
+      d[k] = read_D<FP16>(blk, idx);
+    }
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) all = all && w[k] > 0.0f;
+    if (!all) return false;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float wx = (k & 1) ? fr[0] : 1.0f - fr[0];
+      const float wy = ((k >> 1) & 1) ? fr[1] : 1.0f - fr[1];
+      const float wz = (k >> 2) ? fr[2] : 1.0f - fr[2];
+      acc = acc + wx * wy * wz * d[k];
+    }
+    *out = acc;
+    return true;
+  }
   float acc = 0.0f;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -153,31 +181,21 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
       for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
       idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
     }
-    if (!(read_W(m, blk, nb * nb * nb, idx) > 0.0f)) return false;
+    if (!(read_W<FP16, COLOR>(blk, nb * nb * nb, idx) > 0.0f)) return false;
     const float wx = ax ? fr[0] : 1.0f - fr[0];
     const float wy = ay ? fr[1] : 1.0f - fr[1];
     const float wz = az ? fr[2] : 1.0f - fr[2];
-    acc = acc + wx * wy * wz * read_D(m, blk, idx);
+    acc = acc + wx * wy * wz * read_D<FP16>(blk, idx);
   }
   *out = acc;
   return true;
 }
 
-// sample at t: false when the sample's block is not allocated
-__device__ inline bool sample(const MapDev& m, BlockCache& bc, const float o[3], const float r[3], float t, float invE,
-                              int* level, bool* valid, float* F) {
-  const float x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
-  const uint32_t val = bc.get(m, ifloor(x[0] * invE), ifloor(x[1] * invE), ifloor(x[2] * invE));
-  if (val == kValPending) return false;
-  *level = (int)((val >> 28) & 3u);
-  *valid = field(m, bc, x, *level, F);
-  return true;
-}
-
 // One ray: march, find the first zero crossing, write its z-depth (0 = none).
+template <bool FP16, bool COLOR>
 __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
   BlockCache bc;
-  BrickCache brc;
+  OccCache super_c, brick_c;
   const float qx = ((float)u - c.cx) / c.fx, qy = ((float)v - c.cy) / c.fy;
   const float nq = sqrtf(qx * qx + qy * qy + 1.0f);
   const float rc[3] = {qx / nq, qy / nq, 1.0f / nq};
@@ -193,13 +211,30 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
   const float t_far = c.max_depth * nq;
   bool have_prev = false;
   float t_prev = 0.0f, F_prev = 0.0f, hit = 0.0f;
-  for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
+  // After a sign change the loop runs once more in refine mode: one extra sample at the linear root ts (the same
+  // code path as every other sample, so the field evaluation exists once in the kernel), then the secant step.
+  bool refine = false;
+  float ta = 0.0f, Fa = 0.0f, tb = 0.0f, Fb = 0.0f, ts = 0.0f;
+  for (int it = 0; refine || (it < kRaycastMaxIter && t <= t_far); ++it) {
     const float x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
     const int bk[3] = {ifloor(x[0] * invE), ifloor(x[1] * invE), ifloor(x[2] * invE)};
     const int br[3] = {bk[0] >> kBrickShift, bk[1] >> kBrickShift, bk[2] >> kBrickShift};
-    const bool brick = brc.get(m, br[0], br[1], br[2]);
-    const uint32_t val = brick ? bc.get(m, bk[0], bk[1], bk[2]) : kValPending;
+    // occupancy: super-brick mask (probed when the super-brick changes) -> brick non-empty? -> brick mask (probed
+    // when the brick changes) -> block created? -> block lookup. Empty cells cost register work only.
+    const unsigned long long sbits = super_c.get(m.super_keys, m.super_bits, m.super_mask, br[0] >> kSuperShift,
+                                                 br[1] >> kSuperShift, br[2] >> kSuperShift);
+    const bool brick = (sbits & cell_bit(br[0], br[1], br[2])) != 0;
+    bool block = false;
+    if (brick) {
+      const unsigned long long bbits = brick_c.get(m.brick_keys, m.brick_bits, m.brick_mask, br[0], br[1], br[2]);
+      block = (bbits & cell_bit(bk[0], bk[1], bk[2])) != 0;
+    }
+    const uint32_t val = block ? bc.get(m, bk[0], bk[1], bk[2]) : kValPending;
     if (val == kValPending) {
+      if (refine) {  // the root's block is not allocated: keep the linear root
+        hit = ts * rc[2];
+        break;
+      }
       // jump to the exit face of the empty brick, or of the empty block
       const int span = brick ? 1 : (1 << kBrickShift);
       float t_exit = t_far + 1.0f;
@@ -219,19 +254,30 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     }
     const int l = (int)((val >> 28) & 3u);
     float F = 0.0f;
-    const bool valid = field(m, bc, x, l, &F);
-    if (valid && have_prev && F_prev > 0.0f && !(F > 0.0f)) {
-      float ta = t_prev, Fa = F_prev, tb = t, Fb = F;
-      float ts = ta + (tb - ta) * (Fa / (Fa - Fb));
-      int l2 = 0;
-      bool v2 = false;
-      float F2 = 0.0f;
-      if (sample(m, bc, o, r, ts, invE, &l2, &v2, &F2) && v2) {
-        if (F2 > 0.0f) { ta = ts; Fa = F2; } else { tb = ts; Fb = F2; }
+    const bool valid = field<FP16, COLOR>(m, bc, x, l, &F);
+    if (refine) {
+      if (valid) {
+        if (F > 0.0f) {
+          ta = ts;
+          Fa = F;
+        } else {
+          tb = ts;
+          Fb = F;
+        }
         if (Fa - Fb > 0.0f) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
       }
       hit = ts * rc[2];
       break;
+    }
+    if (valid && have_prev && F_prev > 0.0f && !(F > 0.0f)) {
+      ta = t_prev;
+      Fa = F_prev;
+      tb = t;
+      Fb = F;
+      ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+      refine = true;
+      t = ts;
+      continue;
     }
     have_prev = valid;
     if (valid) {
@@ -246,6 +292,17 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     t = t + s;
   }
   out[(size_t)v * c.width + u] = hit;
+}
+
+// cast_ray with the storage format chosen at run time (one branch per ray)
+__device__ inline void cast_ray_any(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
+  if (m.fp16) {
+    if (m.color) cast_ray<true, true>(m, c, u, v, out);
+    else cast_ray<true, false>(m, c, u, v, out);
+  } else {
+    if (m.color) cast_ray<false, true>(m, c, u, v, out);
+    else cast_ray<false, false>(m, c, u, v, out);
+  }
 }
 
 }  // namespace
