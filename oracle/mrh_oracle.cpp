@@ -338,13 +338,16 @@ struct Map : MapBase {
 
   // ---- Eq. 3 with w_k = 1 in Welford's incremental form, and the Welford S2 update (Sec. 3.2.1).
   // The running mean D + (d - D)/(W + 1) equals (W D + d)/(W + 1) of Eq. 3 in exact arithmetic; this form keeps a
-  // voxel that sees the same d again at exactly D, so its S2 stays exactly 0.
+  // voxel that sees the same d again at exactly D, so its S2 stays exactly 0. Reading of the arithmetic: the division
+  // by W + 1 is a multiplication by the correctly rounded reciprocal 1/(W + 1), shared by the distance and the colour
+  // channels (the same quantity in exact arithmetic; one reciprocal per observation instead of four quotients).
   void update(Block<R, Sto>& b, size_t i, R d, const R* col) {
     R W = b.W[i];
     R D = (R)Store<Sto>::get(b.D[i]);
     R Wn = W + (R)1;
+    R inv = (R)1 / Wn;
     R e = d - D;
-    R Dn = D + e / Wn;
+    R Dn = D + e * inv;
     b.S2[i] = b.S2[i] + e * (d - Dn);
     b.D[i] = Store<Sto>::put(Dn);
     b.W[i] = Wn;
@@ -352,7 +355,7 @@ struct Map : MapBase {
       for (int c = 0; c < 3; ++c) {
         R C = (R)Store<Sto>::get(b.C[c][i]);
         R ec = col[c] - C;
-        b.C[c][i] = Store<Sto>::put(C + ec / Wn);
+        b.C[c][i] = Store<Sto>::put(C + ec * inv);
       }
     }
   }
@@ -586,8 +589,10 @@ struct Map : MapBase {
             R yc = Rm[1] * w[0] + Rm[4] * w[1] + Rm[7] * w[2];
             R zc = Rm[2] * w[0] + Rm[5] * w[1] + Rm[8] * w[2];
             if (!(zc > (R)0)) continue;
-            R uf = fx * xc / zc + cx + (R)0.5;
-            R vf = fy * yc / zc + cy + (R)0.5;
+            // Eq. 2's projection pi(x), nearest pixel; the two quotients by z use its correctly rounded reciprocal
+            R iz = (R)1 / zc;
+            R uf = fx * xc * iz + cx + (R)0.5;
+            R vf = fy * yc * iz + cy + (R)0.5;
             if (!(uf >= (R)0 && uf < (R)K->width && vf >= (R)0 && vf < (R)K->height)) continue;
             int u = (int)std::floor(uf), vv = (int)std::floor(vf);
             size_t pix = (size_t)vv * K->width + u;

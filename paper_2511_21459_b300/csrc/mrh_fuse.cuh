@@ -23,8 +23,8 @@
 //
 // The block variance decides in float; a value within 1e-5 (relative) of a threshold is recomputed in double, in
 // voxel order, exactly as the CPU oracle computes it, so level decisions match the oracle bit for bit. (The float
-// sum's relative error is below 22 ulp = 1.3e-6: 15 sequential + 5 shuffle additions of non-negative terms, the
-// per-voxel division and the final division.)
+// estimate's relative error is below 24 ulp = 1.5e-6: 15 sequential + 5 shuffle additions of non-negative terms, the
+// per-voxel approximate quotient S2 / W (__fdividef, within 2 ulp) and the final division.)
 //
 // This file is compiled without multiply-add contraction: float expressions round in source order, like the oracle.
 #pragma once
@@ -79,12 +79,14 @@ struct Field {
   }
 };
 
-// One Welford step (Eq. 3 incremental form + S2 update of Sec. 3.2.1).
+// One Welford step (Eq. 3 incremental form + S2 update of Sec. 3.2.1); the division by W + 1 is a multiplication by
+// its correctly rounded reciprocal (the oracle's reading of the arithmetic).
 template <bool FP16>
 __device__ inline void welford(float d, float& D, float& W, float& S2, float& Wn) {
   Wn = W + 1.0f;
+  const float inv = __frcp_rn(Wn);
   float e = d - D;
-  float Dn = D + e / Wn;
+  float Dn = D + e * inv;
   S2 = S2 + e * (d - Dn);
   D = Field<FP16>::kept(Dn);
   W = Wn;
@@ -137,8 +139,9 @@ struct CameraObs {
       const float xc = c.R[0] * w0 + c.R[3] * w1 + c.R[6] * w2;
       const float yc = c.R[1] * w0 + c.R[4] * w1 + c.R[7] * w2;
       const float zc = c.R[2] * w0 + c.R[5] * w1 + c.R[8] * w2;
-      const float uf = c.fx * xc / zc + c.cx + 0.5f;
-      const float vf = c.fy * yc / zc + c.cy + 0.5f;
+      const float iz = __frcp_rn(zc);  // both quotients by z use its correctly rounded reciprocal
+      const float uf = c.fx * xc * iz + c.cx + 0.5f;
+      const float vf = c.fy * yc * iz + c.cy + 0.5f;
       bool ok = zc > 0.0f && uf >= 0.0f && uf < fw && vf >= 0.0f && vf < fh;
       const int u = ok ? (int)floorf(uf) : 0, v = ok ? (int)floorf(vf) : 0;
       const int pix = v * c.width + u;
@@ -148,8 +151,9 @@ struct CameraObs {
       ok = ok && rho >= 0.0f && !(eta < -m.tau);  // valid depth; not occluded (more than tau behind the surface)
       const float d = eta < m.tau ? eta : m.tau;
       const float Wn = ch.W[k] + 1.0f;
+      const float inv = __frcp_rn(Wn);  // 1 / (W + 1), shared by D and the colour channels
       const float e = d - ch.D[k];
-      const float Dn = ch.D[k] + e / Wn;
+      const float Dn = ch.D[k] + e * inv;
       const float S2n = ch.S2[k] + e * (d - Dn);
       if (ok) {
         ch.D[k] = Field<FP16>::kept(Dn);
@@ -163,7 +167,7 @@ struct CameraObs {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const float col = (float)((packed >> (8 * q)) & 255u);
-            const float Cn = ch.C[q][k] + (col - ch.C[q][k]) / Wn;
+            const float Cn = ch.C[q][k] + (col - ch.C[q][k]) * inv;
             if (ok) ch.C[q][k] = Field<FP16>::kept(Cn);
           }
         }
@@ -476,7 +480,7 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
     // ---- chunks: prefetch the next chunk, update the current one, write it back, accumulate block statistics
     float vsum = 0.f;
     int nobs = 0;
-    long long sumw = 0;
+    uint32_t sumw32 = 0;  // at most 16 voxels per lane, each W < 2^24
     Chunk cur, nxt;
     if (load) io.load(li, cur);
     else zero_chunk(cur);
@@ -492,13 +496,14 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (cur.W[q] > 0.0f) {
-          vsum = vsum + cur.S2[q] / cur.W[q];
+          vsum = vsum + __fdividef(cur.S2[q], cur.W[q]);  // estimate only (see the error bound above)
           nobs += 1;
-          sumw += (long long)(uint32_t)cur.W[q];
+          sumw32 += (uint32_t)cur.W[q];
         }
       }
       if (c + 1 < chunks) cur = nxt;
     }
+    long long sumw = sumw32;
     for (int o = G / 2; o > 0; o >>= 1) {
       vsum = vsum + __shfl_xor_sync(~0u, vsum, o);
       nobs += __shfl_xor_sync(~0u, nobs, o);
