@@ -22,40 +22,39 @@ __global__ void __launch_bounds__(256) k_alloc_points(MapDev m, PoseD P, const f
   alloc_points_cta<kProbeW>(m, P, xyz, n, (uint64_t)blockIdx.x * blockDim.x, s_set, &s_valid);
 }
 
-__global__ void __launch_bounds__(256) k_bin(MapDev m) {
-  const uint32_t n = min(m.st->touched_all, m.max_touched);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) bin_one(m, i);
+__global__ void __launch_bounds__(256) k_bin(MapDev m, const uint8_t* __restrict__ pred_level) {
+  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x, pred_level);
 }
 
-// Camera frames with the learned predictor or feature capture on: one warp per touched entry (grid-strided), so
-// that the new blocks of a frame, which sit next to each other in the touched list, spread over the whole grid. For
-// a new block the warp computes its features and, with a predictor, its level (warp_block_features,
-// warp_mlp_level); lane 0 then bins the entry as k_bin does. With capture on, lane 0 appends (key, features).
-__global__ void __launch_bounds__(256) k_bin_camera(MapDev m, CamArgs c, const float* __restrict__ rho_img) {
+// Camera frames with the learned predictor or feature capture on, before k_bin: one warp per touched entry
+// (grid-strided), so that the new blocks of a frame, which sit next to each other in the touched list, spread over
+// the whole grid. For a new block the warp computes its features and, with a predictor, its level
+// (warp_block_features, warp_mlp_level) and stores the level for k_bin; with capture on, lane 0 appends (key,
+// features).
+__global__ void __launch_bounds__(256) k_predict(MapDev m, CamArgs c, const float* __restrict__ rho_img) {
   const uint32_t n = min(m.st->touched_all, m.max_touched);
   const int lane = threadIdx.x & 31;
   const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += n_warps) {  // warp-uniform
     const uint32_t s = m.touched_all[i];
+    if (m.slots[s].val != kValPending) continue;
+    int bx, by, bz;
+    unpack_key(m.slots[s].key, &bx, &by, &bz);
+    float f[kMlpIn];
     int level = 0;
-    if (m.slots[s].val == kValPending) {
-      int bx, by, bz;
-      unpack_key(m.slots[s].key, &bx, &by, &bz);
-      float f[kMlpIn];
-      if (warp_block_features(m, c, rho_img, bx, by, bz, f)) {  // same answer on every lane
-        if (m.pred_w) level = warp_mlp_level(m.pred_w, f, m.L);
-        if (m.cap_feat && lane == 0) {
-          const uint32_t r = atomicAdd(m.cap_count, 1u);
-          if (r < m.cap_max) {
-            m.cap_keys[3 * r] = bx;
-            m.cap_keys[3 * r + 1] = by;
-            m.cap_keys[3 * r + 2] = bz;
-            for (int k = 0; k < kMlpIn; ++k) m.cap_feat[(size_t)kMlpIn * r + k] = f[k];
-          }
+    if (warp_block_features(m, c, rho_img, bx, by, bz, f)) {  // same answer on every lane
+      if (m.pred_w) level = warp_mlp_level(m.pred_w, f, m.L);
+      if (m.cap_feat && lane == 0) {
+        const uint32_t r = atomicAdd(m.cap_count, 1u);
+        if (r < m.cap_max) {
+          m.cap_keys[3 * r] = bx;
+          m.cap_keys[3 * r + 1] = by;
+          m.cap_keys[3 * r + 2] = bz;
+          for (int k = 0; k < kMlpIn; ++k) m.cap_feat[(size_t)kMlpIn * r + k] = f[k];
         }
       }
     }
-    if (lane == 0) bin_one(m, i, level);
+    if (lane == 0) m.pred_level[i] = (uint8_t)level;
   }
 }
 
@@ -75,11 +74,15 @@ void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uin
   k_alloc_points<<<blocks, 256, 0, s>>>(m, P, xyz, n);
 }
 
-void launch_bin(const MapDev& m, cudaStream_t s, int sms) { k_bin<<<sms * 2, 256, 0, s>>>(m); }
+void launch_bin(const MapDev& m, cudaStream_t s, int sms) { k_bin<<<sms * 2, 256, 0, s>>>(m, nullptr); }
 
 void launch_bin_camera(const MapDev& m, const CamArgs& c, const float* rho_img, cudaStream_t s, int sms) {
-  if (m.pred_w || m.cap_feat) k_bin_camera<<<sms * 8, 256, 0, s>>>(m, c, rho_img);
-  else k_bin<<<sms * 2, 256, 0, s>>>(m);
+  if (m.pred_w || m.cap_feat) {
+    k_predict<<<sms * 8, 256, 0, s>>>(m, c, rho_img);
+    k_bin<<<sms * 2, 256, 0, s>>>(m, m.pred_level);
+  } else {
+    k_bin<<<sms * 2, 256, 0, s>>>(m, nullptr);
+  }
 }
 
 }  // namespace mrh

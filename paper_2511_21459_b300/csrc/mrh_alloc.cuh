@@ -208,12 +208,11 @@ __device__ inline void alloc_points_cta(const MapDev& m, const PoseD& P, const f
   if (threadIdx.x == 0 && *s_valid) atomicAdd(&m.st->valid_rays, *s_valid);
 }
 
-// Touched entry i of this frame: new blocks get a heap block of the finest level (Sec. 3.2.1: "we initialize the
-// voxel blocks to the finest resolution"), or of new_level when the learned predictor gave one, and their brick is
-// recorded for the raycaster; the slot is binned by level. A block whose heap is empty keeps no storage, is not
-// fused, and is retried in later frames.
-__device__ inline void bin_one(const MapDev& m, uint32_t i, int new_level = 0) {
-  const uint32_t s = m.touched_all[i];
+// Touched entry i of this frame, first half: a new block gets a heap block of the finest level (Sec. 3.2.1: "we
+// initialize the voxel blocks to the finest resolution"), or of new_level when the learned predictor gave one, and
+// its brick is recorded for the raycaster. Returns the block's level and heap value, or -1 when the block has no
+// storage (its level's heap is empty: it is not fused and is retried in later frames).
+__device__ inline int bin_entry(const MapDev& m, uint32_t s, int new_level, uint32_t* val_out) {
   uint32_t val = m.slots[s].val;
   if (val == kValPending) {
     const int l = new_level;
@@ -230,22 +229,50 @@ __device__ inline void bin_one(const MapDev& m, uint32_t i, int new_level = 0) {
     if (t <= 0) {
       atomicAdd(&m.st->free_top[l], 1);
       set_status(m.st, kStPoolEmpty);
-      return;
+      return -1;
     }
     uint32_t id = m.free_stack[l][t - 1];
     val = id | ((uint32_t)l << 28) | kValNew;
     m.slots[s].val = val;
     atomicAdd(&m.st->new_blocks, 1u);
   }
-  const uint32_t l = (val >> 28) & 3u;
-  const uint32_t j = atomicAdd(&m.st->touched_count[l], 1u);
-  m.touched[l][j] = s;
-  m.slot_pos[s] = (l << 28) | j;
-  BlockMeta bm;
-  bm.key = m.slots[s].key;
-  bm.val = val;
-  bm.slot = s;
-  m.meta[l][j] = bm;
+  *val_out = val;
+  return (int)((val >> 28) & 3u);
+}
+
+// Bins the touched entries first_warp_thread + lane, + stride, ... (a warp-uniform loop: first_warp_thread and
+// stride are multiples of 32): each entry is appended to its level's list (Sec. 3.2: the per-level work lists of
+// the fusion pass) with one atomic per level per warp. pred_level (or null): the predicted level of new entries.
+__device__ inline void bin_entries(const MapDev& m, uint32_t first_warp_thread, uint32_t stride,
+                                   const uint8_t* __restrict__ pred_level) {
+  const uint32_t n = min(m.st->touched_all, m.max_touched);
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = first_warp_thread; base < n; base += stride) {
+    const uint32_t i = base + lane;
+    int l = -1;
+    uint32_t s = 0, val = 0;
+    if (i < n) {
+      s = m.touched_all[i];
+      l = bin_entry(m, s, pred_level ? (int)pred_level[i] : 0, &val);
+    }
+    for (int L = 0; L < m.L; ++L) {
+      const unsigned mask = __ballot_sync(0xffffffffu, l == L);
+      if (!mask) continue;
+      const int leader = __ffs(mask) - 1;
+      uint32_t j = 0;
+      if (lane == leader) j = atomicAdd(&m.st->touched_count[L], (uint32_t)__popc(mask));
+      j = __shfl_sync(0xffffffffu, j, leader) + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+      if (l == L) {
+        m.touched[L][j] = s;
+        m.slot_pos[s] = ((uint32_t)L << 28) | j;
+        BlockMeta bm;
+        bm.key = m.slots[s].key;
+        bm.val = val;
+        bm.slot = s;
+        m.meta[L][j] = bm;
+      }
+    }
+  }
 }
 
 // Heap blocks freed by re-levelling go back to their free stacks.

@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(256) k_batch_alloc(BatchDev b) {
 
 __global__ void __launch_bounds__(256) k_batch_bin(BatchDev b) {
   const MapDev& m = b.maps[blockIdx.y];
-  const uint32_t n = min(m.st->touched_all, m.max_touched);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) bin_one(m, i);
+  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_batch_release(BatchDev b) {
