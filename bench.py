@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-lidar", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--profile-case", choices=["rgbd", "lidar"], default=None,
                     help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
@@ -207,11 +208,13 @@ def voxel_bytes(wl):
 
 # ----------------------------------------------------------------------------------------------------- GPU arm
 
-def run_camera_gpu(wl, frames, warmup, steps, flush):
+def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False):
     import torch
     import paper_2511_21459_b300 as mrh
     K = mrh.pinhole_from(wl)
     m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
+    if predictor is not None:
+        m.set_predictor(predictor)
     dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
     out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -222,7 +225,8 @@ def run_camera_gpu(wl, frames, warmup, steps, flush):
     torch.cuda.synchronize()
     m.set_profiling(True)
     m.profile(reset=True)
-    times, rays, fbytes = [], 0, 0
+    times, rays, fbytes, obs = [], 0, 0, 0
+    touched = [0, 0, 0]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
         flush.zero_()
@@ -235,13 +239,97 @@ def run_camera_gpu(wl, frames, warmup, steps, flush):
         if st["status_code"] != 0:
             raise RuntimeError(f"map status {st['status_code']} at step {k}")
         rays += st["valid_rays"]
+        obs += st["observations"]
+        touched = [a + b for a, b in zip(touched, st["touched_level"])]
         fbytes += fuse_bytes_camera(st, wl, voxel_bytes(wl))
     torch.cuda.synchronize()
     times = [a.elapsed_time(b) for a, b in ev]
     prof = m.profile()
     final = m.stats()
-    m.close()
-    return dict(ms=sum(times), ms_steps=times, rays=rays, fuse_bytes=fbytes, prof=prof, final=final)
+    out = dict(ms=sum(times), ms_steps=times, rays=rays, fuse_bytes=fbytes, prof=prof, final=final, observations=obs,
+               touched_level=touched)
+    if keep:
+        out["map"] = m
+    else:
+        m.close()
+    return out
+
+
+def chamfer_vs_truth(m, wl, views):
+    """Chamfer-L1 (Sec. 4.1.2) of the map's raycast depth at the given frames against noise-free renders of the same
+    views, both back-projected (every 2nd pixel)."""
+    import dataclasses
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import metrics
+    K = mrh.pinhole_from(wl)
+    clean = dataclasses.replace(wl, noise_coef=0.0, dropout=0.0)
+    scene = wl.scene()
+    rec, gt = [], []
+    for k in views:
+        T = wl.pose(k)
+        d = m.raycast(K, T).cpu().numpy()
+        rec.append(metrics.backproject(d, wl.fx, wl.fy, wl.cx, wl.cy, T, stride=2))
+        g, _, _ = synth.render_depth(clean, k, scene=scene)
+        g = np.where((g >= wl.min_depth) & (g <= wl.max_depth), g, 0.0)
+        gt.append(metrics.backproject(g, wl.fx, wl.fy, wl.cx, wl.cy, T, stride=2))
+    return metrics.chamfer(np.concatenate(rec), np.concatenate(gt))
+
+
+def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epochs=30):
+    """The learned level predictor against the plain rule on the same frames: train on the plain rule's levels of a
+    different seeded scene (features recorded by the library, labels = final levels), then time the same sequence
+    with the predictor set, and compare fused work, misclassification and Chamfer error."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import predictor
+    t0 = time.perf_counter()
+    K = mrh.pinhole_from(wl)
+
+    def captured_run(w, frs):
+        m = mrh.Map(mrh.params_from(w))
+        m.set_feature_capture(1 << 21)
+        for d, c, T in frs:
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        keys, feats, _ = m.features()
+        ex = m.extract()
+        y = predictor.level_labels(keys.cpu().numpy(), ex["keys"].cpu().numpy(), ex["levels"].cpu().numpy())
+        ok = torch.from_numpy(y >= 0).cuda()
+        m.close()
+        return feats[ok].contiguous(), torch.from_numpy(y[y >= 0]).cuda()
+
+    train_wl = dataclasses.replace(wl, seed=wl.seed + 10)
+    x, y = captured_run(train_wl, camera_frames(train_wl, 0, train_frames))
+    net, hist = predictor.train(x, y, epochs=epochs, batch=4096, lr=2e-3, seed=0)
+    train_err = float((predictor.predicted_levels(net, x) != y).float().mean().item())
+    _, w_bf16 = net.weights()
+    # misclassification on the evaluation sequence: the features of its new blocks do not depend on levels
+    xe, ye = captured_run(wl, frames[:warmup + steps])
+    misclass = float((predictor.predicted_levels(net, xe) != ye).float().mean().item())
+    learned = run_camera_gpu(wl, frames, warmup, steps, flush, predictor=w_bf16, keep=True)
+    plain_map = run_camera_gpu(wl, frames, warmup, steps, flush, keep=True)
+    views = list(range(warmup, warmup + steps, max(1, steps // 10)))
+    ch_l = chamfer_vs_truth(learned["map"], wl, views)
+    ch_p = chamfer_vs_truth(plain_map["map"], wl, views)
+    learned["map"].close()
+    plain_map["map"].close()
+    return {"value": learned["rays"] / (learned["ms"] / 1000.0), "unit": "points/s",
+            "plain_value": plain["rays"] / (plain["ms"] / 1000.0),
+            "speedup_vs_plain": plain["ms"] / learned["ms"],
+            "ms_per_step": learned["ms"] / steps, "plain_ms_per_step": plain["ms"] / steps,
+            "misclassification": round(misclass, 4), "train": {"scene_seed": train_wl.seed, "frames": train_frames,
+                                                               "samples": int(x.shape[0]), "epochs": epochs,
+                                                               "loss": [round(hist[0], 4), round(hist[-1], 4)],
+                                                               "error": round(train_err, 4)},
+            "label_histogram": np.bincount(ye.cpu().numpy(), minlength=3).tolist(),
+            "fused_observations": {"plain": plain["observations"], "learned": learned["observations"]},
+            "touched_blocks_per_level": {"plain": plain["touched_level"], "learned": learned["touched_level"]},
+            "chamfer_mm": {"plain": round(1000 * ch_p["chamfer"], 4), "learned": round(1000 * ch_l["chamfer"], 4),
+                           "added": round(1000 * (ch_l["chamfer"] - ch_p["chamfer"]), 4)},
+            "fscore_10cm": {"plain": round(ch_p["fscore"], 5), "learned": round(ch_l["fscore"], 5)},
+            "kernels_ms": {"plain": {g: round(v[0], 3) for g, v in plain["prof"].items() if v[1] > 0},
+                           "learned": {g: round(v[0], 3) for g, v in learned["prof"].items() if v[1] > 0}},
+            "wall_s": round(time.perf_counter() - t0, 1)}
 
 
 def run_camera_e2e(wl, frames, warmup, steps):
@@ -540,6 +628,10 @@ def main():
                                " (1/2/4 cm, FP16 storage, colour) + raycast per map per step",
                    "tuned_config": bres["config"]}
 
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(wl, frames, args.warmup, args.steps, flush, res)
+
     if rank == 0:
         final = res["final"]
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -554,7 +646,7 @@ def main():
                 "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
-                "lidar": lidar, "batched": batched}
+                "lidar": lidar, "batched": batched, "learned": learned}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
