@@ -200,6 +200,17 @@ def fuse_bytes_camera(stats, wl, s_v):
     return img + payload + 16 * stats["touched"] + 16 * stats["new_blocks"]
 
 
+def fusion_source_sha256() -> str:
+    """Hash of the sources the camera fusion kernel is compiled from (a stored ncu capture is used only while it
+    matches)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("mrh_fuse.cu", "mrh_fuse.cuh", "mrh_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2511_21459_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def voxel_bytes(wl):
     if wl.fp16:
         return 2 + (6 if wl.has_color else 0) + 8
@@ -581,9 +592,7 @@ def main():
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_2511_21459_b300", "csrc", "mrh_fuse.cu"), "rb").read()
-        if tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
+        if tr.get("source_sha256") == fusion_source_sha256():
             # one ncu capture of a full-size frame of the same sequence, scaled to this run's launches by the
             # algorithmic bytes (units) they process
             traffic = int(tr["dram_bytes_per_algorithmic_byte"] * res["fuse_bytes"] / args.steps)
