@@ -89,7 +89,7 @@ __device__ inline void touch(const MapDev& m, int slot, uint32_t frame) {
 
 __device__ inline void add_cells(const MapDev& m, unsigned long long* s_set, const long long A[3],
                                  const long long B[3], uint32_t frame) {
-  bool ok = walk_cells(A, B, kBlockUnit, kMaxSegmentCells, [&](const long long* c) {
+  bool ok = walk_cells(A, B, kBlockShift, kMaxSegmentCells, [&](const int* c) {
     unsigned long long key = pack_key(c[0], c[1], c[2]);
     if (!set_insert(s_set, key)) {
       int s = thread_find_or_insert(m, key);

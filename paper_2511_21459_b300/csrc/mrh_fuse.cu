@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
   const float rh[3] = {(float)rhat[0], (float)rhat[1], (float)rhat[2]};
   const float o_f[3] = {(float)P.T[3], (float)P.T[7], (float)P.T[11]};
 
-  long long cb[3] = {0, 0, 0}, lg[3] = {0, 0, 0};
+  int cb[3] = {0, 0, 0}, lg[3] = {0, 0, 0};
   bool have_block = false, cur_ok = false, have_last = false;
   int cl = 0;
   uint32_t cur_P = 0, run = 0;
@@ -55,10 +55,7 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
     } else {
       uint32_t base = m.blk_off[cur_P] + atomicAdd(&m.blk_fill[cur_P], run);
       if (base + run <= m.max_obs) {
-        for (uint32_t i = 0; i < run; ++i) {
-          m.obs_key[base + i] = rk[i];
-          m.obs_d[base + i] = rd[i];
-        }
+        for (uint32_t i = 0; i < run; ++i) m.obs_rec[base + i] = make_uint2(rk[i], __float_as_uint(rd[i]));
       } else {
         set_status(m.st, kStObsFull);
       }
@@ -66,8 +63,8 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
     run = 0;
   };
 
-  bool ok = walk_cells(A, B, kVoxelUnit, kMaxVoxelCells, [&](const long long* f) {
-    long long bk[3] = {floor_div(f[0], kFineDim), floor_div(f[1], kFineDim), floor_div(f[2], kFineDim)};
+  bool ok = walk_cells(A, B, kVoxelShift, kMaxVoxelCells, [&](const int* f) {
+    const int bk[3] = {f[0] >> 3, f[1] >> 3, f[2] >> 3};  // finest cell -> block (floor division by 8)
     if (!have_block || bk[0] != cb[0] || bk[1] != cb[1] || bk[2] != cb[2]) {
       flush();
       have_block = true;
@@ -94,12 +91,12 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
       }
     }
     if (!cur_ok) return;
-    long long g[3] = {floor_div(f[0], 1LL << cl), floor_div(f[1], 1LL << cl), floor_div(f[2], 1LL << cl)};
+    const int g[3] = {f[0] >> cl, f[1] >> cl, f[2] >> cl};  // voxel of the block's level containing the cell
     if (have_last && g[0] == lg[0] && g[1] == lg[1] && g[2] == lg[2]) return;
     have_last = true;
     lg[0] = g[0]; lg[1] = g[1]; lg[2] = g[2];
     const int nl = kFineDim >> cl;
-    const int li[3] = {(int)(g[0] - cb[0] * nl), (int)(g[1] - cb[1] * nl), (int)(g[2] - cb[2] * nl)};
+    const int li[3] = {g[0] - cb[0] * nl, g[1] - cb[1] * nl, g[2] - cb[2] * nl};
     if constexpr (FILL) {
       if (run == kRunCap) flush();  // cannot happen at level 0 (<= 22 voxels of one block per ray), kept as a guard
       const float vl = m.v[cl];

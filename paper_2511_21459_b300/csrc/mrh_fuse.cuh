@@ -204,7 +204,7 @@ struct LidarObs {
       r1 = m.blk_off[x.P + 1];
       if (r1 > m.max_obs) r0 = r1 = 0;  // observations were not stored (status already set)
     }
-    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&cnt[x.g * x.nv + (m.obs_key[r] & 511u)], 1u);
+    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&cnt[x.g * x.nv + (m.obs_rec[r].x & 511u)], 1u);
     __syncwarp();
     uint32_t local[16], sum = 0;
 #pragma unroll
@@ -226,9 +226,10 @@ struct LidarObs {
     item_base = m.blk_off[x.P_first];
     __syncwarp();
     for (uint32_t r = r0 + x.li; r < r1; r += x.G) {
-      const uint32_t bin = x.g * x.nv + (m.obs_key[r] & 511u);
+      const uint2 rec = m.obs_rec[r];
+      const uint32_t bin = x.g * x.nv + (rec.x & 511u);
       const uint32_t pos = off[bin] + atomicAdd(&fill[bin], 1u);
-      m.obs_idx[item_base + pos] = r;
+      m.obs_bin[item_base + pos] = rec;
     }
     __syncwarp();
   }
@@ -241,13 +242,18 @@ struct LidarObs {
       const int bin = x.g * x.nv + vi0 + k;
       const uint32_t cnt = s_bins[warp][0][bin];
       if (cnt == 0) continue;
-      uint32_t* idx = m.obs_idx + item_base + s_bins[warp][1][bin];
-      // order the voxel's observations by point index (each ray observes a voxel at most once)
-      if (cnt <= kLocalSort) {
+      uint2* rec = m.obs_bin + item_base + s_bins[warp][1][bin];
+      // order the voxel's observations by point index (each ray observes a voxel at most once, so the keys of one
+      // voxel are distinct): a single record is applied directly; up to kLocalSort records are insertion-sorted in
+      // a per-thread array; longer lists (rare) are sorted in place in the binned array
+      if (cnt == 1) {
+        float Wn;
+        welford<FP16>(__uint_as_float(rec[0].y), ch.D[k], ch.W[k], ch.S2[k], Wn);
+      } else if (cnt <= kLocalSort) {
         unsigned long long e[kLocalSort];
         for (uint32_t i = 0; i < cnt; ++i) {
-          const uint32_t r = idx[i];
-          const unsigned long long key = ((unsigned long long)(m.obs_key[r] >> 9) << 32) | r;
+          const uint2 q = rec[i];
+          const unsigned long long key = ((unsigned long long)q.x << 32) | q.y;
           uint32_t j = i;
           while (j > 0 && e[j - 1] > key) {
             e[j] = e[j - 1];
@@ -257,22 +263,21 @@ struct LidarObs {
         }
         for (uint32_t i = 0; i < cnt; ++i) {
           float Wn;
-          welford<FP16>(m.obs_d[(uint32_t)e[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
+          welford<FP16>(__uint_as_float((uint32_t)e[i]), ch.D[k], ch.W[k], ch.S2[k], Wn);
         }
       } else {
         for (uint32_t i = 1; i < cnt; ++i) {
-          const uint32_t r = idx[i];
-          const uint32_t kr = m.obs_key[r] >> 9;
+          const uint2 r = rec[i];
           uint32_t j = i;
-          while (j > 0 && (m.obs_key[idx[j - 1]] >> 9) > kr) {
-            idx[j] = idx[j - 1];
+          while (j > 0 && rec[j - 1].x > r.x) {
+            rec[j] = rec[j - 1];
             --j;
           }
-          idx[j] = r;
+          rec[j] = r;
         }
         for (uint32_t i = 0; i < cnt; ++i) {
           float Wn;
-          welford<FP16>(m.obs_d[idx[i]], ch.D[k], ch.W[k], ch.S2[k], Wn);
+          welford<FP16>(__uint_as_float(rec[i].y), ch.D[k], ch.W[k], ch.S2[k], Wn);
         }
       }
       n_upd += (int)cnt;

@@ -24,6 +24,8 @@ constexpr int kMaxLevels = 3;
 constexpr int kFracBits = 16;                     // fixed-point fraction bits per block edge
 constexpr long long kBlockUnit = 1LL << kFracBits;
 constexpr long long kVoxelUnit = kBlockUnit / kFineDim;
+constexpr int kBlockShift = kFracBits;      // log2 of kBlockUnit
+constexpr int kVoxelShift = kFracBits - 3;  // log2 of kVoxelUnit
 constexpr long long kKeyLimit = (1LL << 20) - 2;  // |block coordinate| bound of the 21-bit packed key
 constexpr unsigned long long kEmptyKey = ~0ULL;
 constexpr uint32_t kValPending = 0xFFFFFFFFu;     // key present, no heap block yet
@@ -91,9 +93,8 @@ struct MapDev {
   uint32_t* blk_count;        // per touched block (levels concatenated): observations
   uint32_t* blk_off;          // exclusive prefix of blk_count, one extra entry = total
   uint32_t* blk_fill;
-  uint32_t* obs_key;          // ray << 9 | voxel index within the block
-  float* obs_d;
-  uint32_t* obs_idx;          // per-voxel bins of observation indices
+  uint2* obs_rec;             // LiDAR observations grouped by block: {ray << 9 | voxel index in the block, d bits}
+  uint2* obs_bin;             // the same records regrouped per voxel inside each block (fusion pass)
   uint32_t max_obs;
   DevState* st;
   // Raycast occupancy (insert-only open-addressing sets, filled when blocks are created): bricks of 4 x 4 x 4 blocks
@@ -244,18 +245,28 @@ __device__ inline int lookup_slot(const Slot* slots, uint32_t mask, unsigned lon
   return -1;
 }
 
-// Exact cell walk over cells of edge U from A to B (fixed point). visit(cell) is called for every cell in order.
-// Returns false if more than max_cells cells would be visited.
+// Exact cell walk over cells of edge U = 2^ush from A to B (fixed point). visit(cell) is called for every cell in
+// order (ties: upward crossings first, then downward). Returns false if more than max_cells cells would be visited;
+// a segment longer than max_cells + 1 cells along some axis is refused before any visit. Cell coordinates are below
+// 2^23 in magnitude and, after that check, the segment and the distances to the next boundaries below 2^23, so the
+// walk runs in 32-bit integers with 64-bit products for the exact crossing order.
 template <class F>
-__device__ inline bool walk_cells(const long long A[3], const long long B[3], long long U, int max_cells, F&& visit) {
-  long long cell[3], end[3], D[3], aD[3], N[3];
+__device__ inline bool walk_cells(const long long A[3], const long long B[3], int ush, int max_cells, F&& visit) {
+  const int U = 1 << ush;
+  const long long lim = (long long)(max_cells + 1) << ush;
+  int cell[3], end[3], aD[3], N[3];
+  bool pos[3], neg[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    cell[i] = floor_div(A[i], U);
-    end[i] = floor_div(B[i], U);
-    D[i] = B[i] - A[i];
-    aD[i] = D[i] < 0 ? -D[i] : D[i];
-    N[i] = D[i] > 0 ? (cell[i] + 1) * U - A[i] : (D[i] < 0 ? A[i] - cell[i] * U : 0);
+    const long long d = B[i] - A[i];
+    if (d > lim || d < -lim) return false;
+    cell[i] = (int)(A[i] >> ush);  // arithmetic shift: floor division by 2^ush
+    end[i] = (int)(B[i] >> ush);
+    pos[i] = d > 0;
+    neg[i] = d < 0;
+    aD[i] = (int)(d < 0 ? -d : d);
+    const int frac = (int)(A[i] & (long long)(U - 1));  // A - cell * U
+    N[i] = pos[i] ? U - frac : (neg[i] ? frac : 0);
   }
   visit(cell);
   for (int n = 1; n < max_cells; ++n) {
@@ -263,27 +274,27 @@ __device__ inline bool walk_cells(const long long A[3], const long long B[3], lo
     int best = -1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      if (D[i] == 0) continue;
-      if (best < 0 || N[i] * aD[best] < N[best] * aD[i]) best = i;
+      if (aD[i] == 0) continue;
+      if (best < 0 || (long long)N[i] * aD[best] < (long long)N[best] * aD[i]) best = i;
     }
     bool tie[3], up = false, down = false;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      tie[i] = D[i] != 0 && N[i] * aD[best] == N[best] * aD[i];
-      up |= tie[i] && D[i] > 0;
-      down |= tie[i] && D[i] < 0;
+      tie[i] = aD[i] != 0 && (long long)N[i] * aD[best] == (long long)N[best] * aD[i];
+      up |= tie[i] && pos[i];
+      down |= tie[i] && neg[i];
     }
     if (up) {
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        if (tie[i] && D[i] > 0) { cell[i] += 1; N[i] += U; }
+        if (tie[i] && pos[i]) { cell[i] += 1; N[i] += U; }
       visit(cell);
     }
     if (down) {
       if (cell[0] == end[0] && cell[1] == end[1] && cell[2] == end[2]) return true;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        if (tie[i] && D[i] < 0) { cell[i] -= 1; N[i] += U; }
+        if (tie[i] && neg[i]) { cell[i] -= 1; N[i] += U; }
       visit(cell);
     }
   }

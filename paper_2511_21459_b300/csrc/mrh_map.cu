@@ -461,9 +461,8 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   TRY(dev_alloc(m, &d.blk_fill, 3ull * params->max_touched));
   TRY(dev_alloc(m, &d.blk_off, 3ull * params->max_touched + 1));
   d.max_obs = params->max_observations;
-  TRY(dev_alloc(m, &d.obs_key, d.max_obs));
-  TRY(dev_alloc(m, &d.obs_d, d.max_obs));
-  TRY(dev_alloc(m, &d.obs_idx, d.max_obs));
+  TRY(dev_alloc(m, &d.obs_rec, d.max_obs));
+  TRY(dev_alloc(m, &d.obs_bin, d.max_obs));
   for (int l = 0; l < kMaxLevels; ++l) {
     int nl = kFineDim >> l;
     d.block_bytes[l] = block_bytes_for(nl * nl * nl, d.fp16, d.color);
