@@ -200,6 +200,12 @@ def fuse_bytes_camera(stats, wl, s_v):
     return img + payload + 16 * stats["touched"] + 16 * stats["new_blocks"]
 
 
+def fuse_bytes_lidar(stats, n_points, s_v):
+    """Algorithmic bytes of one LiDAR fusion launch: the scan's points once, every voxel the rays cross read and
+    written once, and the touched blocks' 16-byte hash entries."""
+    return 12 * n_points + 2 * s_v * stats["updated_voxels"] + 16 * stats["touched"]
+
+
 def fusion_source_sha256() -> str:
     """Hash of the sources the camera fusion kernel is compiled from (a stored ncu capture is used only while it
     matches)."""
@@ -406,11 +412,7 @@ def run_lidar_gpu(wl, warmup, steps, flush):
             raise RuntimeError(f"LiDAR map status {st['status_code']} at step {k}")
         ms += a.elapsed_time(b)
         rays += st["valid_rays"]
-        # algorithmic bytes of the fusion kernel (distinct observed voxels are bounded by the touched blocks):
-        # every touched block's payload read + written, its hash entry, and the scan's points once
-        s_v = voxel_bytes(wl)
-        fbytes += (12 * wl.n_beams * wl.n_azimuth + 16 * st["touched"] +
-                   sum(2 * ((8 >> l) ** 3) * s_v * n for l, n in enumerate(st["touched_level"])))
+        fbytes += fuse_bytes_lidar(st, wl.n_beams * wl.n_azimuth, voxel_bytes(wl))
     prof = m.profile()
     m.close()
     return dict(ms=ms, rays=rays, steps=steps, prof=prof, fuse_bytes=fbytes)

@@ -53,7 +53,8 @@ class Pinhole(ctypes.Structure):
 
 class FrameStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
-                ("valid_rays", "touched", "new_blocks", "merged", "split", "fp64_rechecks", "observations")]
+                ("valid_rays", "touched", "new_blocks", "merged", "split", "fp64_rechecks", "observations",
+                 "updated_voxels")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

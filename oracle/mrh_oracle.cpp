@@ -252,6 +252,7 @@ struct orc_pinhole {
 
 struct orc_frame_stats {
   int64_t valid_rays, touched, new_blocks, merged, split, fp64_rechecks, observations;
+  int64_t updated_voxels;  // distinct voxels updated by the frame
 };
 
 // learned level predictor (level_predictor.cpp)
@@ -613,7 +614,8 @@ struct Map : MapBase {
             st->observations++;
           }
     }
-    // (3) block variance and re-levelling
+    // (3) block variance and re-levelling (a camera frame observes a voxel at most once)
+    st->updated_voxels = st->observations;
     relevel(touched, st);
     return 0;
   }
@@ -668,6 +670,7 @@ struct Map : MapBase {
     pose(T, Rm, t);
     (void)Rm;
     const R E = (R)E_f;
+    std::unordered_set<uint64_t> updated;  // (block, voxel) pairs updated by this scan
     for (size_t q = 0; q < rays.size(); ++q) {
       const RayRec& rr = rays[q];
       std::vector<Key> fine = cells_dda(rr.A, rr.B, kVoxelUnit);
@@ -698,9 +701,11 @@ struct Map : MapBase {
         if (d < -tau) d = -tau;
         if (d > tau) d = tau;
         update(b, vox(nl, li[0], li[1], li[2]), d, nullptr);
+        updated.insert((uint64_t)(uintptr_t)&b * 1024u + (uint64_t)vox(nl, li[0], li[1], li[2]));
         st->observations++;
       }
     }
+    st->updated_voxels = (int64_t)updated.size();
     relevel(touched, st);
     return 0;
   }

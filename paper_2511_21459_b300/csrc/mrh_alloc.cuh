@@ -196,11 +196,16 @@ __device__ inline void alloc_points_cta(const MapDev& m, const PoseD& P, const f
   const uint32_t frame = m.st->frame;
   const uint64_t j = first + threadIdx.x;
   if (j < n) {
-    long long A[3], B[3];
+    LidarRay ray;
     double rho, rhat[3];
-    if (lidar_ray(m, P, xyz, j, A, B, &rho, rhat)) {
+    const bool ok = lidar_ray(m, P, xyz, j, ray.A, ray.B, &rho, rhat);
+    ray.rho = ok ? (float)rho : -1.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ray.rh[a] = (float)rhat[a];
+    m.rays[j] = ray;  // reused by the observation passes
+    if (ok) {
       atomicAdd(s_valid, 1u);
-      add_cells(m, s_set, A, B, frame);
+      add_cells(m, s_set, ray.A, ray.B, frame);
     }
   }
   __syncthreads();
@@ -291,6 +296,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->retire_count = 0;
   st->new_blocks = st->merged = st->split = st->rechecks = st->valid_rays = 0;
   st->observations = 0;
+  st->updated_voxels = 0;
 }
 
 }  // namespace

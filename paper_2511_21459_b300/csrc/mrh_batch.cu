@@ -130,10 +130,14 @@ __global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_batch_fuse(BatchDev 
     const MapDev& m = b.maps[mi];
     const BatchFrame& f = b.frames[mi];
     CameraObs<FP16, COLOR> obs{f.cam, f.rho_img, f.rgb ? f.rgb_img : nullptr};
-    unsigned long long my_obs = 0;
-    fuse_item<FP16, COLOR>(m, obs, warp, s_ic[mi], local, my_obs);
-    for (int o = 16; o > 0; o >>= 1) my_obs += __shfl_xor_sync(~0u, my_obs, o);
+    unsigned long long my_obs = 0, my_vox = 0;
+    fuse_item<FP16, COLOR>(m, obs, warp, s_ic[mi], local, my_obs, my_vox);
+    for (int o = 16; o > 0; o >>= 1) {
+      my_obs += __shfl_xor_sync(~0u, my_obs, o);
+      my_vox += __shfl_xor_sync(~0u, my_vox, o);
+    }
     if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
+    if (lane == 0 && my_vox) atomicAdd(&m.st->updated_voxels, my_vox);
   }
 }
 

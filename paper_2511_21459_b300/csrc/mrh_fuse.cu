@@ -16,8 +16,8 @@ __global__ void __launch_bounds__(32 * kCamWarps, 3) k_fuse_depth(MapDev m, CamA
 
 template <bool FP16, bool COLOR>
 __global__ void __launch_bounds__(32 * kLidarWarps) k_fuse_points(MapDev m) {
-  __shared__ uint32_t s_bins[kLidarWarps][3][512];
-  LidarObs<FP16> obs{s_bins, 0};
+  __shared__ LidarSmem s_lidar;
+  LidarObs<FP16> obs{&s_lidar, nullptr};
   const int warp = threadIdx.x >> 5;
   fuse_warp_body<FP16, COLOR>(m, obs, warp, blockIdx.x * kLidarWarps + warp, gridDim.x * kLidarWarps);
 }
@@ -29,14 +29,18 @@ template <bool FILL>
 __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const float* __restrict__ xyz, uint64_t n) {
   const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
+  const LidarRay& ray = m.rays[j];  // computed by the allocation pass
+  const float rho_f = ray.rho;
+  if (!(rho_f >= 0.0f)) return;
   long long A[3], B[3];
-  double rho;
-  double rhat[3];
-  if (!lidar_ray(m, P, xyz, j, A, B, &rho, rhat)) return;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    A[a] = ray.A[a];
+    B[a] = ray.B[a];
+  }
   const uint32_t n0 = min(m.st->touched_count[0], m.max_touched);
   const uint32_t n1 = min(m.st->touched_count[1], m.max_touched);
-  const float rho_f = (float)rho;
-  const float rh[3] = {(float)rhat[0], (float)rhat[1], (float)rhat[2]};
+  const float rh[3] = {ray.rh[0], ray.rh[1], ray.rh[2]};
   const float o_f[3] = {(float)P.T[3], (float)P.T[7], (float)P.T[11]};
 
   int cb[3] = {0, 0, 0}, lg[3] = {0, 0, 0};
@@ -122,53 +126,47 @@ __global__ void k_zero_obs_counts(MapDev m) {
     m.blk_count[i] = 0;
     m.blk_fill[i] = 0;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) m.st->obs_total = 0;
 }
 
-// exclusive prefix sum of the per-block observation counts (one CTA, 16 consecutive entries per thread)
-__global__ void __launch_bounds__(1024) k_scan_obs(MapDev m) {
-  __shared__ uint32_t s_w[32];
-  __shared__ uint32_t s_carry;
-  const uint32_t total = min(m.st->touched_count[0], m.max_touched) + min(m.st->touched_count[1], m.max_touched) +
-                         min(m.st->touched_count[2], m.max_touched);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_carry = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < total; base += 1024u * 16u) {
-    uint32_t v[16], sum = 0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      uint32_t i = base + (uint32_t)tid * 16u + k;
-      v[k] = i < total ? m.blk_count[i] : 0u;
-      sum += v[k];
+// One thread per fusion work item (the grouping of k_fuse_points: one level-0 block, two level-1 blocks or sixteen
+// level-2 blocks): the item's blocks get consecutive ranges of one segment of the observation buffer, the segment
+// taken from a running total with one atomic per warp. Segments of different items may lie in any order.
+__global__ void __launch_bounds__(256) k_obs_segments(MapDev m) {
+  const ItemCounts ic = item_counts(m);
+  const uint32_t items = ic.items();
+  const int lane = threadIdx.x & 31;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < items; base += stride) {
+    const uint32_t item = base + lane;
+    uint32_t first = 0, nb = 0;
+    if (item < ic.it0) {
+      first = item;
+      nb = 1;
+    } else if (item < ic.it0 + ic.it1) {
+      const uint32_t idx = (item - ic.it0) * 2;
+      first = ic.n0 + idx;
+      nb = min(2u, ic.n1 - idx);
+    } else if (item < items) {
+      const uint32_t idx = (item - ic.it0 - ic.it1) * 16;
+      first = ic.n0 + ic.n1 + idx;
+      nb = min(16u, ic.n2 - idx);
     }
+    uint32_t sum = 0;
+    for (uint32_t g = 0; g < nb; ++g) sum += m.blk_count[first + g];
     uint32_t incl = sum;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(~0u, incl, o);
+      const uint32_t t = __shfl_up_sync(~0u, incl, o);
       if (lane >= o) incl += t;
     }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = s_w[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(~0u, w, o);
-        if (lane >= o) w += t;
-      }
-      s_w[lane] = w;
+    uint32_t seg = 0;
+    if (lane == 31) seg = atomicAdd(&m.st->obs_total, incl);
+    uint32_t start = __shfl_sync(~0u, seg, 31) + incl - sum;
+    for (uint32_t g = 0; g < nb; ++g) {
+      m.blk_off[first + g] = start;
+      start += m.blk_count[first + g];
     }
-    __syncthreads();
-    uint32_t run = s_carry + (warp > 0 ? s_w[warp - 1] : 0u) + incl - sum;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      uint32_t i = base + (uint32_t)tid * 16u + k;
-      if (i < total) m.blk_off[i] = run;
-      run += v[k];
-    }
-    __syncthreads();
-    if (tid == 0) s_carry += s_w[31];
-    __syncthreads();
   }
-  if (tid == 0) m.blk_off[total] = s_carry;
 }
 
 }  // namespace
@@ -191,17 +189,17 @@ void launch_lidar_observations(const MapDev& m, const double* T, const float* xy
   for (int i = 0; i < 16; ++i) P.T[i] = T[i];
   k_zero_obs_counts<<<sms * 2, 256, 0, s>>>(m);
   if (n == 0) {
-    k_scan_obs<<<1, 1024, 0, s>>>(m);
+    k_obs_segments<<<sms * 2, 256, 0, s>>>(m);
     return;
   }
   const unsigned blocks = (unsigned)((n + 127) / 128);
   k_lidar_walk<false><<<blocks, 128, 0, s>>>(m, P, xyz, n);
-  k_scan_obs<<<1, 1024, 0, s>>>(m);
+  k_obs_segments<<<sms * 2, 256, 0, s>>>(m);
   k_lidar_walk<true><<<blocks, 128, 0, s>>>(m, P, xyz, n);
 }
 
 void launch_fuse_points(const MapDev& m, const double*, const float*, uint64_t, cudaStream_t s, int sms) {
-  const int grid = sms * 8;
+  const int grid = sms * 16;  // 16 CTAs of 4 warps per SM over the items (measured best of 8 / 16 per SM)
   if (m.fp16) {
     if (m.color) k_fuse_points<true, true><<<grid, 32 * kLidarWarps, 0, s>>>(m);
     else k_fuse_points<true, false><<<grid, 32 * kLidarWarps, 0, s>>>(m);

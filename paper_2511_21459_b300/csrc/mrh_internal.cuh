@@ -70,6 +70,8 @@ struct DevState {
   uint32_t new_blocks, merged, split, rechecks, valid_rays;
   uint32_t pad;
   unsigned long long observations;
+  unsigned long long updated_voxels;
+  uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
 };
 
 // Everything a kernel needs, passed by value.
@@ -91,8 +93,9 @@ struct MapDev {
   uint32_t* slot_pos;         // per slot: level << 28 | position in touched[level] (written by k_bin)
   // LiDAR observation buffers (per frame)
   uint32_t* blk_count;        // per touched block (levels concatenated): observations
-  uint32_t* blk_off;          // exclusive prefix of blk_count, one extra entry = total
+  uint32_t* blk_off;          // start of the block's observation records (its fusion item's segment, in order)
   uint32_t* blk_fill;
+  struct LidarRay* rays;      // per point of the current scan: its ray, computed once by the allocation pass
   uint2* obs_rec;             // LiDAR observations grouped by block: {ray << 9 | voxel index in the block, d bits}
   uint2* obs_bin;             // the same records regrouped per voxel inside each block (fusion pass)
   uint32_t max_obs;
@@ -303,6 +306,13 @@ __device__ inline bool walk_cells(const long long A[3], const long long B[3], in
 
 struct PoseD {
   double T[16];  // world <- sensor, row-major
+};
+
+// One LiDAR ray as the allocation pass computes it (in double) and the observation passes reuse it.
+struct __align__(16) LidarRay {
+  long long A[3], B[3];  // band end points, fixed point
+  float rho;             // range, float of the double value; negative: the point gives no ray
+  float rh[3];           // unit direction, float of the double value
 };
 
 // LiDAR ray of point j in double (Sec. 3.1 "3D Point Cloud"): origin o = sensor position, p = T x_s,

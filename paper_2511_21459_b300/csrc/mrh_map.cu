@@ -43,6 +43,9 @@ struct mrh_map {
   float* rho_img = nullptr;
   uint32_t* rgb_img = nullptr;
   size_t img_pixels = 0;
+  // per-point rays of the LiDAR path, grown to the largest scan seen
+  LidarRay* rays = nullptr;
+  size_t ray_cap = 0;
   // learned level predictor weights (BF16), owned; d.pred_w points here while the predictor is on
   uint16_t* pred_buf = nullptr;
 };
@@ -336,6 +339,9 @@ void free_all(mrh_map* m) {
   m->rho_img = nullptr;
   m->rgb_img = nullptr;
   m->img_pixels = 0;
+  if (m->rays) cudaFree(m->rays);
+  m->rays = nullptr;
+  m->ray_cap = 0;
   for (auto& p : m->pending) {
     m->event_pool.push_back(p.a);
     m->event_pool.push_back(p.b);
@@ -609,6 +615,14 @@ mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz
   if (!m || (!xyz && n) || !finite_pose(T_ws) || n > (1ull << 23)) return MRH_ERR_INVALID_ARG;
   DeviceGuard guard(m->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (n > m->ray_cap) {
+    if (m->rays) cudaFreeAsync(m->rays, s);
+    m->rays = nullptr;
+    m->ray_cap = 0;
+    MRH_CUDA(cudaMallocAsync(&m->rays, n * sizeof(LidarRay), s));
+    m->ray_cap = n;
+  }
+  m->d.rays = m->rays;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
   { KernelScope ks(m, MRH_K_ALLOC, s, n ? 1 : 0); launch_alloc_points(m->d, T_ws, xyz, n, s); }
   { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
@@ -761,6 +775,7 @@ mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
     out->touched_level[l] = std::min<uint32_t>(hs.touched_count[l], m->d.max_touched);
   }
   out->observations = hs.observations;
+  out->updated_voxels = hs.updated_voxels;
   out->status = hs.status;
   return status_from_bits(hs.status);
 }

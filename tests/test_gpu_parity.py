@@ -49,7 +49,7 @@ def run_camera(wl, frames, gmap, omap, check_each=False, theta0=None, raycast_fr
         st_o = omap.integrate_depth(K_o, T, depth, rgb)
         st_g = gmap.stats()
         assert st_g["status_code"] == 0, st_g
-        for k in ("valid_rays", "touched", "new_blocks", "merged", "split"):
+        for k in ("valid_rays", "touched", "new_blocks", "merged", "split", "observations", "updated_voxels"):
             assert st_g[k] == st_o[k], (f, k, st_g[k], st_o[k])
         if check_each or f == len(frames) - 1:
             reports.append(compare_extracts(gmap.extract(), omap.extract(), wl.truncation, theta0,
@@ -179,7 +179,7 @@ def run_lidar(wl, n_frames, check_each=True, scene=None):
         st_o = o.integrate_points(T, xyz)
         st_g = g.stats()
         assert st_g["status_code"] == 0, st_g
-        for k in ("valid_rays", "touched", "new_blocks", "merged", "split"):
+        for k in ("valid_rays", "touched", "new_blocks", "merged", "split", "observations", "updated_voxels"):
             assert st_g[k] == st_o[k], (f, k, st_g[k], st_o[k])
         if check_each or f == n_frames - 1:
             compare_extracts(g.extract(), o.extract(), wl.truncation, wl.var_threshold[0], check_color=False)
