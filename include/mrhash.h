@@ -91,6 +91,8 @@ typedef struct {
   uint64_t live_blocks[3];   /* blocks currently held per level */
   uint64_t touched_level[3]; /* blocks fused in the last frame, per level */
   uint64_t observations;     /* voxel updates applied in the last frame */
+  uint64_t updated_voxels;   /* distinct voxels updated in the last frame (a voxel with several observations counts
+                                once) */
   uint32_t status;           /* sticky device status bits (see mrh_status) */
 } mrh_stats;
 
@@ -120,7 +122,8 @@ mrh_status mrh_integrate_depth(mrh_map* map, const mrh_pinhole* K, const double*
                                const uint8_t* rgb_dev, void* stream);
 
 /* Integrate one LiDAR scan (Sec. 3.1 "3D Point Cloud", Eq. 1): xyz_dev holds n points (n x 3 float32, sensor
- * frame; NaN = no return). Observations of one voxel are applied in ascending point index. T_ws_host: world <- sensor.
+ * frame; NaN = no return; n <= 2^23). Observations of one voxel are applied in ascending point index. T_ws_host:
+ * world <- sensor. The map keeps a per-point ray buffer grown to the largest n seen (64 bytes per point).
  * Asynchronous on `stream`. */
 mrh_status mrh_integrate_points(mrh_map* map, const double* T_ws_host, const float* xyz_dev, uint64_t n,
                                 void* stream);
