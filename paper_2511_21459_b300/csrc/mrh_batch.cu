@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_batch_release(BatchDev b) {
 }
 
 template <bool FP16, bool COLOR, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 24 / WARPS) k_batch_fuse(BatchDev b) {
+__global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch_fuse(BatchDev b) {
   __shared__ uint32_t s_end[kBatchMaxMaps];  // inclusive prefix of work items over maps
   __shared__ ItemCounts s_ic[kBatchMaxMaps];
   if (threadIdx.x < 32) {

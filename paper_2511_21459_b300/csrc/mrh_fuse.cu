@@ -7,7 +7,7 @@ namespace {
 constexpr int kCamWarps = 8;
 
 template <bool FP16, bool COLOR>
-__global__ void __launch_bounds__(32 * kCamWarps, 3) k_fuse_depth(MapDev m, CamArgs c, const float* __restrict__ rho,
+__global__ void __launch_bounds__(32 * kCamWarps, 4) k_fuse_depth(MapDev m, CamArgs c, const float* __restrict__ rho,
                                                                  const uint32_t* __restrict__ rgb) {
   CameraObs<FP16, COLOR> obs{c, rho, rgb};
   const int warp = threadIdx.x >> 5;

@@ -15,8 +15,7 @@
 // Work decomposition: one warp per work item, with no CTA-wide barrier anywhere. An item is one level-0 block
 // (8^3 voxels, 32 lanes), two level-1 blocks (4^3, 16 lanes each) or sixteen level-2 blocks (2^3, 2 lanes each).
 // A lane owns 4 consecutive voxels per chunk of 4 G voxels (G = lanes per block) and moves each field of them with
-// one 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced, and the next chunk's
-// loads are issued before the current chunk is computed. The block's mean variance is a butterfly shuffle reduction
+// one 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced. The block's mean variance is a butterfly shuffle reduction
 // that leaves the sum in every lane of the block's group, so every lane takes the same decision without
 // communication. Re-levelled blocks (a small fraction per frame) are resampled from their just-written payload into
 // a heap block popped from the other level's free stack.
@@ -511,18 +510,16 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
 
     obs.collect(m, x, warp_in_cta);
 
-    // ---- chunks: prefetch the next chunk, update the current one, write it back, accumulate block statistics
+    // ---- chunks: load, update, write back (when changed), accumulate block statistics
     float vsum = 0.f;
     int nobs = 0;
     uint32_t sumw32 = 0;  // at most 16 voxels per lane, each W < 2^24
-    Chunk cur, nxt;
-    if (load) io.load(li, cur);
-    else zero_chunk(cur);
+    // one chunk in registers at a time: at 64 registers a thread, 4 CTAs of 8 warps share an SM and their
+    // interleaving hides the load latency better than a register double buffer at 3 CTAs (measured)
+    Chunk cur;
     for (int c = 0; c < chunks; ++c) {
-      if (c + 1 < chunks) {
-        if (load) io.load((c + 1) * G + li, nxt);
-        else zero_chunk(nxt);
-      }
+      if (load) io.load(c * G + li, cur);
+      else zero_chunk(cur);
       if (x.active) {
         int n_vox = 0;
         my_obs += (unsigned long long)obs.apply(m, x, 4 * (c * G + li), cur, n_vox);
@@ -538,7 +535,6 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
           sumw32 += (uint32_t)cur.W[q];
         }
       }
-      if (c + 1 < chunks) cur = nxt;
     }
     long long sumw = sumw32;
     for (int o = G / 2; o > 0; o >>= 1) {
