@@ -93,6 +93,8 @@ typedef struct {
   uint64_t observations;     /* voxel updates applied in the last frame */
   uint64_t updated_voxels;   /* distinct voxels updated in the last frame (a voxel with several observations counts
                                 once) */
+  uint64_t lidar_restaged;   /* LiDAR: points of the last scan whose observations exceeded the per-point stage and
+                                were written by a second walk (correct either way; a cost diagnostic) */
   uint32_t status;           /* sticky device status bits (see mrh_status) */
 } mrh_stats;
 
@@ -123,7 +125,8 @@ mrh_status mrh_integrate_depth(mrh_map* map, const mrh_pinhole* K, const double*
 
 /* Integrate one LiDAR scan (Sec. 3.1 "3D Point Cloud", Eq. 1): xyz_dev holds n points (n x 3 float32, sensor
  * frame; NaN = no return; n <= 2^23). Observations of one voxel are applied in ascending point index. T_ws_host:
- * world <- sensor. The map keeps a per-point ray buffer grown to the largest n seen (64 bytes per point).
+ * world <- sensor. The map keeps per-point buffers (the ray and its staged observations, 840 bytes per point) grown to
+ * the largest n seen.
  * Asynchronous on `stream`. */
 mrh_status mrh_integrate_points(mrh_map* map, const double* T_ws_host, const float* xyz_dev, uint64_t n,
                                 void* stream);

@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("new_blocks", ctypes.c_uint64), ("merged", ctypes.c_uint64), ("split", ctypes.c_uint64),
                 ("fp64_rechecks", ctypes.c_uint64), ("live_blocks", ctypes.c_uint64 * 3),
                 ("touched_level", ctypes.c_uint64 * 3), ("observations", ctypes.c_uint64),
-                ("updated_voxels", ctypes.c_uint64), ("status", ctypes.c_uint32)]
+                ("updated_voxels", ctypes.c_uint64), ("lidar_restaged", ctypes.c_uint64), ("status", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("live_blocks", "touched_level")}

@@ -297,6 +297,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->new_blocks = st->merged = st->split = st->rechecks = st->valid_rays = 0;
   st->observations = 0;
   st->updated_voxels = 0;
+  st->n_over = 0;
 }
 
 }  // namespace

@@ -24,14 +24,20 @@ __global__ void __launch_bounds__(32 * kLidarWarps) k_fuse_points(MapDev m) {
 
 // -------------------------------------------------------------------------------------------- LiDAR observation passes
 
-// FILL = false: count each block's observations; FILL = true: write them (point index, voxel, d).
+// One point: the walk over the finest cells of its ray's band (Sec. 3.1, Eq. 1), one observation (point index << 9 |
+// voxel, d) per voxel of the crossed block's own level.
+//   STAGE: count each block's observations and stage the point's runs (a header {kStageHeader | block, length}
+//          followed by the run's records) in its kStageCap entries; a point whose runs do not fit is listed in
+//          stage_over and only counted.
+//   FILL:  for the listed points: write the records straight into the blocks' segments.
 template <bool FILL>
-__global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const float* __restrict__ xyz, uint64_t n) {
-  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__device__ inline void lidar_point(const MapDev& m, const PoseD& P, uint64_t j) {
   const LidarRay& ray = m.rays[j];  // computed by the allocation pass
   const float rho_f = ray.rho;
-  if (!(rho_f >= 0.0f)) return;
+  if (!(rho_f >= 0.0f)) {
+    if constexpr (!FILL) m.stage_len[j] = 0;
+    return;
+  }
   long long A[3], B[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -48,21 +54,16 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
   int cl = 0;
   uint32_t cur_P = 0, run = 0;
   float ob[3] = {0.f, 0.f, 0.f};
-  constexpr int kRunCap = 32;
-  uint32_t rk[FILL ? kRunCap : 1];
-  float rd[FILL ? kRunCap : 1];
+  // STAGE: the point's entries; FILL: the current run's reserved range
+  uint2* const stage = m.stage + (size_t)j * kStageCap;
+  uint32_t pos = 0, hpos = 0;
+  bool fits = true;
 
-  auto flush = [&]() {
+  auto close_run = [&]() {
     if (!cur_ok || run == 0) return;
     if constexpr (!FILL) {
       atomicAdd(&m.blk_count[cur_P], run);
-    } else {
-      uint32_t base = m.blk_off[cur_P] + atomicAdd(&m.blk_fill[cur_P], run);
-      if (base + run <= m.max_obs) {
-        for (uint32_t i = 0; i < run; ++i) m.obs_rec[base + i] = make_uint2(rk[i], __float_as_uint(rd[i]));
-      } else {
-        set_status(m.st, kStObsFull);
-      }
+      if (fits) stage[hpos] = make_uint2(kStageHeader | cur_P, run);
     }
     run = 0;
   };
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
   bool ok = walk_cells(A, B, kVoxelShift, kMaxVoxelCells, [&](const int* f) {
     const int bk[3] = {f[0] >> 3, f[1] >> 3, f[2] >> 3};  // finest cell -> block (floor division by 8)
     if (!have_block || bk[0] != cb[0] || bk[1] != cb[1] || bk[2] != cb[2]) {
-      flush();
+      close_run();
       have_block = true;
       cb[0] = bk[0]; cb[1] = bk[1]; cb[2] = bk[2];
       have_last = false;
@@ -90,6 +91,11 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
             ob[0] = (float)bk[0] * m.E - o_f[0];
             ob[1] = (float)bk[1] * m.E - o_f[1];
             ob[2] = (float)bk[2] * m.E - o_f[2];
+            if constexpr (!FILL) {
+              hpos = pos;  // the run's header slot, written when the run closes
+              if (fits && pos + 1 > (uint32_t)kStageCap) fits = false;
+              pos += 1;
+            }
           }
         }
       }
@@ -101,22 +107,94 @@ __global__ void __launch_bounds__(128) k_lidar_walk(MapDev m, PoseD P, const flo
     lg[0] = g[0]; lg[1] = g[1]; lg[2] = g[2];
     const int nl = kFineDim >> cl;
     const int li[3] = {g[0] - cb[0] * nl, g[1] - cb[1] * nl, g[2] - cb[2] * nl};
+    const float vl = m.v[cl];
+    const float xr0 = ob[0] + ((float)li[0] + 0.5f) * vl;
+    const float xr1 = ob[1] + ((float)li[1] + 0.5f) * vl;
+    const float xr2 = ob[2] + ((float)li[2] + 0.5f) * vl;
+    float d = rho_f - (xr0 * rh[0] + xr1 * rh[1] + xr2 * rh[2]);
+    if (d < -m.tau) d = -m.tau;
+    if (d > m.tau) d = m.tau;
+    const uint2 rec = make_uint2(((uint32_t)j << 9) | (uint32_t)(li[0] + nl * (li[1] + nl * li[2])), __float_as_uint(d));
     if constexpr (FILL) {
-      if (run == kRunCap) flush();  // cannot happen at level 0 (<= 22 voxels of one block per ray), kept as a guard
-      const float vl = m.v[cl];
-      float xr0 = ob[0] + ((float)li[0] + 0.5f) * vl;
-      float xr1 = ob[1] + ((float)li[1] + 0.5f) * vl;
-      float xr2 = ob[2] + ((float)li[2] + 0.5f) * vl;
-      float d = rho_f - (xr0 * rh[0] + xr1 * rh[1] + xr2 * rh[2]);
-      if (d < -m.tau) d = -m.tau;
-      if (d > m.tau) d = m.tau;
-      rk[run] = ((uint32_t)j << 9) | (uint32_t)(li[0] + nl * (li[1] + nl * li[2]));
-      rd[run] = d;
+      // one record at a time into the block's segment (the overflow path is rare)
+      const uint32_t at = m.blk_off[cur_P] + atomicAdd(&m.blk_fill[cur_P], 1u);
+      if (at < m.max_obs) m.obs_rec[at] = rec;
+      else set_status(m.st, kStObsFull);
+    } else {
+      if (fits && pos + 1 > (uint32_t)kStageCap) fits = false;
+      if (fits) stage[pos] = rec;
+      pos += 1;
     }
     ++run;
   });
-  flush();
-  if (!ok) set_status(m.st, kStSegment);
+  close_run();
+  if constexpr (!FILL) {
+    if (fits) {
+      m.stage_len[j] = pos;
+    } else {
+      m.stage_len[j] = kStageOverflow;
+      const uint32_t t = atomicAdd(&m.st->n_over, 1u);
+      m.stage_over[t] = (uint32_t)j;
+    }
+  }
+  if (!ok && !FILL) set_status(m.st, kStSegment);
+}
+
+__global__ void __launch_bounds__(128) k_lidar_stage(MapDev m, PoseD P, uint64_t n) {
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) lidar_point<false>(m, P, j);
+}
+
+__global__ void __launch_bounds__(128) k_lidar_fill_over(MapDev m, PoseD P) {
+  const uint32_t n_over = m.st->n_over;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_over; t += gridDim.x * blockDim.x)
+    lidar_point<true>(m, P, m.stage_over[t]);
+}
+
+// One warp per point: copy the point's staged runs into the blocks' segments. Lane i takes entry i of each group of
+// 32; a header lane reserves its run's range with one atomic, and the record lanes after it (or, before the first
+// header of the group, the run carried over from the previous group) write at consecutive positions.
+__global__ void __launch_bounds__(256) k_lidar_scatter(MapDev m, uint64_t n) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += n_warps) {  // warp-uniform
+    const uint32_t len = m.stage_len[j];
+    if (len == 0 || len == kStageOverflow) continue;
+    const uint2* e = m.stage + (size_t)j * kStageCap;
+    uint32_t run_base = 0, run_pos = 0;
+    bool run_ok = false;
+    for (uint32_t c0 = 0; c0 < len; c0 += 32) {
+      const uint32_t i = c0 + (uint32_t)lane;
+      const uint2 v = i < len ? e[i] : make_uint2(0u, 0u);
+      const bool hdr = i < len && (v.x & kStageHeader) != 0;
+      uint32_t base = 0;
+      bool ok = false;
+      if (hdr) {
+        const uint32_t P = v.x & ~kStageHeader, rl = v.y;
+        base = m.blk_off[P] + atomicAdd(&m.blk_fill[P], rl);
+        ok = base + rl <= m.max_obs;
+        if (!ok) set_status(m.st, kStObsFull);
+      }
+      const unsigned hmask = __ballot_sync(~0u, hdr);
+      const unsigned okmask = __ballot_sync(~0u, ok);
+      const unsigned upto = hmask & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
+      const int h = upto ? 31 - __clz(upto) : -1;
+      const uint32_t hb = __shfl_sync(~0u, base, h < 0 ? 0 : h);
+      if (i < len && !hdr) {
+        const bool good = h >= 0 ? ((okmask >> h) & 1u) != 0 : run_ok;
+        const uint32_t dst = h >= 0 ? hb + (uint32_t)(lane - h - 1) : run_base + run_pos + (uint32_t)lane;
+        if (good) m.obs_rec[dst] = v;
+      }
+      const int last_h = hmask ? 31 - __clz(hmask) : -1;
+      if (last_h >= 0) {
+        run_base = __shfl_sync(~0u, base, last_h);
+        run_ok = ((okmask >> last_h) & 1u) != 0;
+        run_pos = (uint32_t)(31 - last_h);
+      } else {
+        run_pos += 32;
+      }
+    }
+  }
 }
 
 __global__ void k_zero_obs_counts(MapDev m) {
@@ -126,7 +204,10 @@ __global__ void k_zero_obs_counts(MapDev m) {
     m.blk_count[i] = 0;
     m.blk_fill[i] = 0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) m.st->obs_total = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    m.st->obs_total = 0;
+    m.st->n_over = 0;
+  }
 }
 
 // One thread per fusion work item (the grouping of k_fuse_points: one level-0 block, two level-1 blocks or sixteen
@@ -193,9 +274,10 @@ void launch_lidar_observations(const MapDev& m, const double* T, const float* xy
     return;
   }
   const unsigned blocks = (unsigned)((n + 127) / 128);
-  k_lidar_walk<false><<<blocks, 128, 0, s>>>(m, P, xyz, n);
+  k_lidar_stage<<<blocks, 128, 0, s>>>(m, P, n);
   k_obs_segments<<<sms * 2, 256, 0, s>>>(m);
-  k_lidar_walk<true><<<blocks, 128, 0, s>>>(m, P, xyz, n);
+  k_lidar_scatter<<<sms * 8, 256, 0, s>>>(m, n);
+  k_lidar_fill_over<<<sms * 4, 128, 0, s>>>(m, P);  // points whose runs did not fit the stage (usually none)
 }
 
 void launch_fuse_points(const MapDev& m, const double*, const float*, uint64_t, cudaStream_t s, int sms) {

@@ -38,6 +38,9 @@ constexpr int kMaxVoxelCells = 256;
 constexpr int kRaycastMaxIter = 8192;
 constexpr int kBrickShift = 2;  // a brick is 4 x 4 x 4 blocks
 constexpr int kSuperShift = 2;  // a super-brick is 4 x 4 x 4 bricks
+constexpr int kStageCap = 96;   // LiDAR: staged entries per point (a run header per block + one record per voxel)
+constexpr uint32_t kStageOverflow = 0xFFFFFFFFu;
+constexpr uint32_t kStageHeader = 0x80000000u;
 
 // status bits (sticky)
 constexpr uint32_t kStHashFull = 1u << 0;
@@ -72,6 +75,7 @@ struct DevState {
   unsigned long long observations;
   unsigned long long updated_voxels;
   uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
+  uint32_t n_over;     // LiDAR: points in stage_over
 };
 
 // Everything a kernel needs, passed by value.
@@ -96,6 +100,9 @@ struct MapDev {
   uint32_t* blk_off;          // start of the block's observation records (its fusion item's segment, in order)
   uint32_t* blk_fill;
   struct LidarRay* rays;      // per point of the current scan: its ray, computed once by the allocation pass
+  uint2* stage;               // per point: kStageCap entries, its observation runs ({flag | block, length} + records)
+  uint32_t* stage_len;        // per point: entries staged, or kStageOverflow
+  uint32_t* stage_over;       // points whose runs did not fit (filled by a second walk)
   uint2* obs_rec;             // LiDAR observations grouped by block: {ray << 9 | voxel index in the block, d bits}
   uint2* obs_bin;             // the same records regrouped per voxel inside each block (fusion pass)
   uint32_t max_obs;

@@ -43,8 +43,11 @@ struct mrh_map {
   float* rho_img = nullptr;
   uint32_t* rgb_img = nullptr;
   size_t img_pixels = 0;
-  // per-point rays of the LiDAR path, grown to the largest scan seen
+  // per-point buffers of the LiDAR path (rays, staged observation runs), grown to the largest scan seen
   LidarRay* rays = nullptr;
+  uint2* stage = nullptr;
+  uint32_t* stage_len = nullptr;
+  uint32_t* stage_over = nullptr;
   size_t ray_cap = 0;
   // learned level predictor weights (BF16), owned; d.pred_w points here while the predictor is on
   uint16_t* pred_buf = nullptr;
@@ -339,8 +342,12 @@ void free_all(mrh_map* m) {
   m->rho_img = nullptr;
   m->rgb_img = nullptr;
   m->img_pixels = 0;
-  if (m->rays) cudaFree(m->rays);
+  for (void* p : {(void*)m->rays, (void*)m->stage, (void*)m->stage_len, (void*)m->stage_over})
+    if (p) cudaFree(p);
   m->rays = nullptr;
+  m->stage = nullptr;
+  m->stage_len = nullptr;
+  m->stage_over = nullptr;
   m->ray_cap = 0;
   for (auto& p : m->pending) {
     m->event_pool.push_back(p.a);
@@ -616,13 +623,23 @@ mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz
   DeviceGuard guard(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (n > m->ray_cap) {
-    if (m->rays) cudaFreeAsync(m->rays, s);
+    for (void* p : {(void*)m->rays, (void*)m->stage, (void*)m->stage_len, (void*)m->stage_over})
+      if (p) cudaFreeAsync(p, s);
     m->rays = nullptr;
+    m->stage = nullptr;
+    m->stage_len = nullptr;
+    m->stage_over = nullptr;
     m->ray_cap = 0;
     MRH_CUDA(cudaMallocAsync(&m->rays, n * sizeof(LidarRay), s));
+    MRH_CUDA(cudaMallocAsync(&m->stage, n * kStageCap * sizeof(uint2), s));
+    MRH_CUDA(cudaMallocAsync(&m->stage_len, n * sizeof(uint32_t), s));
+    MRH_CUDA(cudaMallocAsync(&m->stage_over, n * sizeof(uint32_t), s));
     m->ray_cap = n;
   }
   m->d.rays = m->rays;
+  m->d.stage = m->stage;
+  m->d.stage_len = m->stage_len;
+  m->d.stage_over = m->stage_over;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
   { KernelScope ks(m, MRH_K_ALLOC, s, n ? 1 : 0); launch_alloc_points(m->d, T_ws, xyz, n, s); }
   { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
@@ -776,6 +793,7 @@ mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
   }
   out->observations = hs.observations;
   out->updated_voxels = hs.updated_voxels;
+  out->lidar_restaged = hs.n_over;
   out->status = hs.status;
   return status_from_bits(hs.status);
 }

@@ -204,6 +204,17 @@ def test_lidar_small_scans_fp32_with_relevel():
     assert (o.block_stats()["levels"] > 0).sum() > 10
 
 
+def test_lidar_long_bands_take_the_restage_path():
+    """A truncation band of 3.2 m at 5 cm voxels gives oblique points more observation entries than the per-point
+    stage holds: those points are written by the second walk, with the same result."""
+    wl = synth.lidar()
+    wl.n_beams, wl.n_azimuth = 32, 256
+    wl.truncation = 1.6  # the largest band allowed: 2 tau = 8 blocks
+    wl.min_obs = 2
+    g, o = run_lidar(wl, 3)
+    assert g.stats()["lidar_restaged"] > 0
+
+
 def test_lidar_full_scan():
     """Full 128 x 2048 scans of the benchmark's LiDAR configuration (FP16 storage)."""
     wl = synth.lidar()
