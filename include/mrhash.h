@@ -68,7 +68,8 @@ typedef struct {
   float base_voxel_size;     /* voxel edge of the coarsest level v_{L-1} [m]; v_0 = base / 2^(L-1) */
   int32_t n_levels;          /* L, 1..3 */
   float truncation;          /* tau [m] (Sec. 3.1); 2 tau must not exceed 8 block edges */
-  double var_threshold[2];   /* theta_l [m^2]: a block at level l merges to l+1 when its mean voxel variance < theta_l */
+  double var_threshold[2];   /* theta_l [m^2]: a block at level l merges to l + 1 when its mean voxel variance is
+                                below theta_l */
   double split_hysteresis;   /* h >= 1: a block at level l > 0 splits when its mean variance > h theta_{l-1}; 0 = off */
   int32_t min_obs;           /* k_min: re-levelling needs mean weight >= k_min over the block's observed voxels */
   uint32_t hash_slots_log2;  /* hash table size 2^k slots of 16 bytes, k in [10, 28] */

@@ -72,7 +72,7 @@ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
   return q;
 }
 
-// ------------------------------------------------------------------------------------------------ exact segment geometry
+// ---------------------------------------------------------------------------------------- exact segment geometry
 //
 // Allocation (Sec. 3.2, "leverage DDA ... to allocate all intersected voxel blocks") needs the set of cells a segment
 // meets. Cells are half-open [c U, (c+1) U)^3. Endpoints are fixed-point integers, so "the closed segment meets the

@@ -114,7 +114,8 @@ __device__ inline void lidar_point(const MapDev& m, const PoseD& P, uint64_t j) 
     float d = rho_f - (xr0 * rh[0] + xr1 * rh[1] + xr2 * rh[2]);
     if (d < -m.tau) d = -m.tau;
     if (d > m.tau) d = m.tau;
-    const uint2 rec = make_uint2(((uint32_t)j << 9) | (uint32_t)(li[0] + nl * (li[1] + nl * li[2])), __float_as_uint(d));
+    const uint32_t key = ((uint32_t)j << 9) | (uint32_t)(li[0] + nl * (li[1] + nl * li[2]));
+    const uint2 rec = make_uint2(key, __float_as_uint(d));
     if constexpr (FILL) {
       // one record at a time into the block's segment (the overflow path is rare)
       const uint32_t at = m.blk_off[cur_P] + atomicAdd(&m.blk_fill[cur_P], 1u);

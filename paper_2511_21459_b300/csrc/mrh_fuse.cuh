@@ -5,20 +5,21 @@
 //           skipped, the rest clipped to tau.
 //   LiDAR   (Sec. 3.1 "3D Point Cloud", Eq. 1): each ray walks the voxels of its truncation band (a DDA over
 //           finest-level cells, one observation per voxel of the block's own level); d = clip((p - x) . n, tau).
-//           Observations are counted per block, prefix-summed and scattered; inside a block they are binned per
-//           voxel and each voxel applies its observations in ascending point index, so the result does not depend on
-//           scheduling.
+//           One walk per point stages its observations and counts them per block; each fusion item gets one
+//           segment of the observation buffer and the staged runs are scattered into it; inside a block they are
+//           binned per voxel and each voxel applies its observations in ascending point index, so the result does
+//           not depend on scheduling.
 //   both    running mean (Eq. 3, w_k = 1) in Welford's incremental form and S2 += (d - D_old)(d - D_new)
 //           (Sec. 3.2.1); then the mean voxel variance of the block over observed voxels; then merge to the next
 //           coarser level below theta_l (Sec. 3.2.1, Fig. 4a) or split to the next finer level above h theta_{l-1}.
 //
-// Work decomposition: one warp per work item, with no CTA-wide barrier anywhere. An item is one level-0 block
-// (8^3 voxels, 32 lanes), two level-1 blocks (4^3, 16 lanes each) or sixteen level-2 blocks (2^3, 2 lanes each).
-// A lane owns 4 consecutive voxels per chunk of 4 G voxels (G = lanes per block) and moves each field of them with
-// one 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced. The block's mean variance is a butterfly shuffle reduction
-// that leaves the sum in every lane of the block's group, so every lane takes the same decision without
-// communication. Re-levelled blocks (a small fraction per frame) are resampled from their just-written payload into
-// a heap block popped from the other level's free stack.
+// Work decomposition: one warp per work item, with no CTA-wide barrier anywhere. An item is one level-0 block (8^3
+// voxels, 32 lanes), two level-1 blocks (4^3, 16 lanes each) or sixteen level-2 blocks (2^3, 2 lanes each). A lane
+// owns 4 consecutive voxels per chunk of 4 G voxels (G = lanes per block) and moves each field of them with one
+// 16-byte (fp32) or 8-byte (fp16) access: the fields of a block stream fully coalesced. The block's mean variance is
+// a butterfly shuffle reduction that leaves the sum in every lane of the block's group, so every lane takes the same
+// decision without communication. Re-levelled blocks (a small fraction per frame) are resampled from their just-
+// written payload into a heap block popped from the other level's free stack.
 //
 // The block variance decides in float; a value within 1e-5 (relative) of a threshold is recomputed in double, in
 // voxel order, exactly as the CPU oracle computes it, so level decisions match the oracle bit for bit. (The float

@@ -245,7 +245,8 @@ __global__ void k_extract(MapDev m, const uint32_t* slots, uint32_t n, const uns
       if (b == n - 1) off_out[n] = off[n];
     }
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-      float dv = m.fp16 ? __half2float(reinterpret_cast<const __half*>(blk)[i]) : reinterpret_cast<const float*>(blk)[i];
+      float dv = m.fp16 ? __half2float(reinterpret_cast<const __half*>(blk)[i])
+                        : reinterpret_cast<const float*>(blk)[i];
       D[o + i] = dv;
       W[o + i] = reinterpret_cast<const float*>(blk + off_W(nv, m.fp16, m.color))[i];
       S2[o + i] = reinterpret_cast<const float*>(blk + off_S2(nv, m.fp16, m.color))[i];

@@ -4,16 +4,17 @@
 // the brick's exit face; a sample in an unallocated block of a non-empty brick jumps to the block's exit face. Brick
 // and block occupancy come from two small insert-only sets filled when blocks are created (super-bricks of 4 x 4 x 4
 // bricks with a 64-bit mask of non-empty bricks; bricks with a 64-bit mask of created blocks), cached in registers,
-// so an empty-space step costs a memory probe only when the ray enters a new super-brick or non-empty brick. Inside an allocated block of level l the field is the trilinear interpolation over the
-// 8 nearest voxel centres of that level's grid; a corner in a neighbouring block reads that block's voxel containing
-// the corner centre, whatever its level, so coarse and fine blocks blend across resolution boundaries. A sample is
-// valid only when all 8 corners are observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead
-// when the sample is valid and F is larger (F <= tau underestimates the distance to the surface, so the step stays
-// in front of it). At the first valid + -> - sign change the linear root is taken, evaluated once more, and one
-// secant step refines it. Output is z-depth, 0 where nothing was hit.
+// so an empty-space step costs a memory probe only when the ray enters a new super-brick or non-empty brick. Inside
+// an allocated block of level l the field is the trilinear interpolation over the 8 nearest voxel centres of that
+// level's grid; a corner in a neighbouring block reads that block's voxel containing the corner centre, whatever its
+// level, so coarse and fine blocks blend across resolution boundaries. A sample is valid only when all 8 corners are
+// observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead when the sample is valid and F is
+// larger (F <= tau underestimates the distance to the surface, so the step stays in front of it). At the first valid
+// + -> - sign change the linear root is taken, evaluated once more, and one secant step refines it. Output is
+// z-depth, 0 where nothing was hit.
 //
-// Every step follows the oracle's float operation order (this file is compiled without multiply-add contraction),
-// so depths agree with the oracle to rounding and hit/miss decisions agree except at exact ties.
+// Every step follows the oracle's float operation order (this file is compiled without multiply-add contraction), so
+// depths agree with the oracle to rounding and hit/miss decisions agree except at exact ties.
 #pragma once
 #include <cuda_fp16.h>
 

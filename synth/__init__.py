@@ -87,7 +87,8 @@ def rgbd_scene(seed: int, n_boxes: int = 20, n_spheres: int = 10) -> np.ndarray:
     trajectory stays in free space. Every primitive carries a 10 cm checker of two seeded colours.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    prims = [_prim(PRIM_ROOM, [-4.0, -4.0, 0.0, 4.0, 4.0, 3.0], rng.integers(40, 256, 3), rng.integers(40, 256, 3), 0.1)]
+    prims = [_prim(PRIM_ROOM, [-4.0, -4.0, 0.0, 4.0, 4.0, 3.0], rng.integers(40, 256, 3), rng.integers(40, 256, 3),
+                   0.1)]
     made = 0
     while made < n_boxes:
         e = rng.uniform(0.2, 1.0, 3)
