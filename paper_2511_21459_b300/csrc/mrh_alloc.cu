@@ -22,28 +22,45 @@ __global__ void __launch_bounds__(256) k_alloc_points(MapDev m, PoseD P, const f
   alloc_points_cta<kProbeW>(m, P, xyz, n, (uint64_t)blockIdx.x * blockDim.x, s_set, &s_valid);
 }
 
-__global__ void __launch_bounds__(256) k_bin(MapDev m, const uint8_t* __restrict__ pred_level) {
-  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x, pred_level);
+__global__ void __launch_bounds__(256) k_bin(MapDev m) {
+  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x);
 }
 
-// Camera frames with the learned predictor or feature capture on, before k_bin: one warp per touched entry
-// (grid-strided), so that the new blocks of a frame, which sit next to each other in the touched list, spread over
-// the whole grid. For a new block the warp computes its features and, with a predictor, its level
-// (warp_block_features, warp_mlp_level) and stores the level for k_bin; with capture on, lane 0 appends (key,
-// features).
-__global__ void __launch_bounds__(256) k_predict(MapDev m, CamArgs c, const float* __restrict__ rho_img) {
+// Camera frames with the learned predictor or feature capture on: binning with the prediction folded in. Lane k of
+// warp w takes entry w + k W (W = warps in the grid), so that the new blocks of a frame, which sit next to each other
+// in the touched list, fall into different warps. For each new block of its 32 entries the warp computes the features
+// and, with a predictor, the level (warp_block_features, warp_mlp_level, the weights staged in shared memory); with
+// capture on, lane 0 appends (key, features). Then the entries are binned as in k_bin.
+__global__ void __launch_bounds__(256) k_bin_predict(MapDev m, CamArgs c, const float* __restrict__ rho_img) {
+  __shared__ __align__(16) uint16_t s_w[(kMlpParams + 7) & ~7];
+  if (m.pred_w) {
+    for (int t = threadIdx.x; t < kMlpParams; t += blockDim.x) s_w[t] = m.pred_w[t];
+  }
+  __syncthreads();
   const uint32_t n = min(m.st->touched_all, m.max_touched);
   const int lane = threadIdx.x & 31;
   const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += n_warps) {  // warp-uniform
-    const uint32_t s = m.touched_all[i];
-    if (m.slots[s].val != kValPending) continue;
-    int bx, by, bz;
-    unpack_key(m.slots[s].key, &bx, &by, &bz);
-    float f[kMlpIn];
-    int level = 0;
-    if (warp_block_features(m, c, rho_img, bx, by, bz, f)) {  // same answer on every lane
-      if (m.pred_w) level = warp_mlp_level(m.pred_w, f, m.L);
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (uint32_t base = warp; base < n; base += n_warps * 32u) {  // warp-uniform
+    const uint32_t i = base + (uint32_t)lane * n_warps;
+    uint32_t s = 0;
+    bool fresh = false;
+    if (i < n) {
+      s = m.touched_all[i];
+      fresh = m.slots[s].val == kValPending;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, fresh);
+    int my_level = 0;
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t ss = __shfl_sync(0xffffffffu, s, src);
+      int bx, by, bz;
+      unpack_key(m.slots[ss].key, &bx, &by, &bz);
+      float f[kMlpIn];
+      if (!warp_block_features(m, c, rho_img, bx, by, bz, f)) continue;  // same answer on every lane
+      const int l = m.pred_w ? warp_mlp_level(s_w, f, m.L) : 0;
+      if (lane == src) my_level = l;
       if (m.cap_feat && lane == 0) {
         const uint32_t r = atomicAdd(m.cap_count, 1u);
         if (r < m.cap_max) {
@@ -54,7 +71,10 @@ __global__ void __launch_bounds__(256) k_predict(MapDev m, CamArgs c, const floa
         }
       }
     }
-    if (lane == 0) m.pred_level[i] = (uint8_t)level;
+    int l = -1;
+    uint32_t val = 0;
+    if (i < n) l = bin_entry(m, s, my_level, &val);
+    append_binned(m, l, s, val);
   }
 }
 
@@ -74,15 +94,11 @@ void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uin
   k_alloc_points<<<blocks, 256, 0, s>>>(m, P, xyz, n);
 }
 
-void launch_bin(const MapDev& m, cudaStream_t s, int sms) { k_bin<<<sms * 2, 256, 0, s>>>(m, nullptr); }
+void launch_bin(const MapDev& m, cudaStream_t s, int sms) { k_bin<<<sms * 2, 256, 0, s>>>(m); }
 
 void launch_bin_camera(const MapDev& m, const CamArgs& c, const float* rho_img, cudaStream_t s, int sms) {
-  if (m.pred_w || m.cap_feat) {
-    k_predict<<<sms * 8, 256, 0, s>>>(m, c, rho_img);
-    k_bin<<<sms * 2, 256, 0, s>>>(m, m.pred_level);
-  } else {
-    k_bin<<<sms * 2, 256, 0, s>>>(m, nullptr);
-  }
+  if (m.pred_w || m.cap_feat) k_bin_predict<<<sms * 2, 256, 0, s>>>(m, c, rho_img);
+  else k_bin<<<sms * 2, 256, 0, s>>>(m);
 }
 
 }  // namespace mrh

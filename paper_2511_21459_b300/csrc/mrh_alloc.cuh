@@ -245,11 +245,32 @@ __device__ inline int bin_entry(const MapDev& m, uint32_t s, int new_level, uint
   return (int)((val >> 28) & 3u);
 }
 
+// Warp-collective: append each lane's binned entry (level l >= 0; -1 = nothing) to its level's list (Sec. 3.2: the
+// per-level work lists of the fusion pass) with one atomic per level per warp. All 32 lanes must call it.
+__device__ inline void append_binned(const MapDev& m, int l, uint32_t s, uint32_t val) {
+  const int lane = threadIdx.x & 31;
+  for (int L = 0; L < m.L; ++L) {
+    const unsigned mask = __ballot_sync(0xffffffffu, l == L);
+    if (!mask) continue;
+    const int leader = __ffs(mask) - 1;
+    uint32_t j = 0;
+    if (lane == leader) j = atomicAdd(&m.st->touched_count[L], (uint32_t)__popc(mask));
+    j = __shfl_sync(0xffffffffu, j, leader) + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+    if (l == L) {
+      m.touched[L][j] = s;
+      m.slot_pos[s] = ((uint32_t)L << 28) | j;
+      BlockMeta bm;
+      bm.key = m.slots[s].key;
+      bm.val = val;
+      bm.slot = s;
+      m.meta[L][j] = bm;
+    }
+  }
+}
+
 // Bins the touched entries first_warp_thread + lane, + stride, ... (a warp-uniform loop: first_warp_thread and
-// stride are multiples of 32): each entry is appended to its level's list (Sec. 3.2: the per-level work lists of
-// the fusion pass) with one atomic per level per warp. pred_level (or null): the predicted level of new entries.
-__device__ inline void bin_entries(const MapDev& m, uint32_t first_warp_thread, uint32_t stride,
-                                   const uint8_t* __restrict__ pred_level) {
+// stride are multiples of 32).
+__device__ inline void bin_entries(const MapDev& m, uint32_t first_warp_thread, uint32_t stride) {
   const uint32_t n = min(m.st->touched_all, m.max_touched);
   const int lane = threadIdx.x & 31;
   for (uint32_t base = first_warp_thread; base < n; base += stride) {
@@ -258,25 +279,9 @@ __device__ inline void bin_entries(const MapDev& m, uint32_t first_warp_thread, 
     uint32_t s = 0, val = 0;
     if (i < n) {
       s = m.touched_all[i];
-      l = bin_entry(m, s, pred_level ? (int)pred_level[i] : 0, &val);
+      l = bin_entry(m, s, 0, &val);
     }
-    for (int L = 0; L < m.L; ++L) {
-      const unsigned mask = __ballot_sync(0xffffffffu, l == L);
-      if (!mask) continue;
-      const int leader = __ffs(mask) - 1;
-      uint32_t j = 0;
-      if (lane == leader) j = atomicAdd(&m.st->touched_count[L], (uint32_t)__popc(mask));
-      j = __shfl_sync(0xffffffffu, j, leader) + (uint32_t)__popc(mask & ((1u << lane) - 1u));
-      if (l == L) {
-        m.touched[L][j] = s;
-        m.slot_pos[s] = ((uint32_t)L << 28) | j;
-        BlockMeta bm;
-        bm.key = m.slots[s].key;
-        bm.val = val;
-        bm.slot = s;
-        m.meta[L][j] = bm;
-      }
-    }
+    append_binned(m, l, s, val);
   }
 }
 

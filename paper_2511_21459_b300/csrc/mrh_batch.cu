@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_batch_alloc(BatchDev b) {
 
 __global__ void __launch_bounds__(256) k_batch_bin(BatchDev b) {
   const MapDev& m = b.maps[blockIdx.y];
-  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x, nullptr);
+  bin_entries(m, blockIdx.x * blockDim.x + (threadIdx.x & ~31u), gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_batch_release(BatchDev b) {

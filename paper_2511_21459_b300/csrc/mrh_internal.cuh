@@ -120,7 +120,6 @@ struct MapDev {
   float* cap_feat;                 // 16 floats per record
   uint32_t* cap_count;
   uint32_t cap_max;
-  uint8_t* pred_level;             // per touched entry: level predicted for a new block (written by k_predict)
   uint32_t brick_mask;
   float v[kMaxLevels];  // voxel edge per level
   float inv_v[kMaxLevels];  // 1 / v, as the float division computes it

@@ -461,7 +461,6 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   TRY(dev_alloc(m, &d.st, 1));
   TRY(dev_alloc(m, &d.touched_all, params->max_touched));
   TRY(dev_alloc(m, &d.retire, params->max_touched));
-  TRY(dev_alloc(m, &d.pred_level, params->max_touched));
   TRY(dev_alloc(m, &d.slot_pos, n_slots));
   const uint32_t n_brick_slots = 1u << (params->hash_slots_log2 > 12 ? params->hash_slots_log2 - 2 : 10);
   d.brick_mask = n_brick_slots - 1;
