@@ -161,6 +161,56 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
     *out = acc;
     return true;
   }
+  const uint32_t lvl = (uint32_t)l;
+  const bool same = ((v000 >> 28) & 3u) == lvl && (!sx || ((v100 >> 28) & 3u) == lvl) &&
+                    (!sy || ((v010 >> 28) & 3u) == lvl) && (!(sx && sy) || ((v110 >> 28) & 3u) == lvl) &&
+                    (!sz || ((v001 >> 28) & 3u) == lvl) && (!(sx && sz) || ((v101 >> 28) & 3u) == lvl) &&
+                    (!(sy && sz) || ((v011 >> 28) & 3u) == lvl) && (!(sx && sy && sz) || ((v111 >> 28) & 3u) == lvl);
+  if (same) {
+    // the corners span 2 to 8 blocks, all of level l: one pointer per block offset (a missing offset reuses the
+    // block the corner falls in), the index formula of the level's grid, the 16 loads issued together
+    const uint8_t* hl = m.heap[l];
+    const size_t bb = m.block_bytes[l];
+    const uint8_t* p[8];
+    p[0] = hl + (size_t)(v000 & kPtrMask) * bb;
+    p[1] = sx ? hl + (size_t)(v100 & kPtrMask) * bb : p[0];
+    p[2] = sy ? hl + (size_t)(v010 & kPtrMask) * bb : p[0];
+    p[3] = sx && sy ? hl + (size_t)(v110 & kPtrMask) * bb : (sx ? p[1] : p[2]);
+    p[4] = sz ? hl + (size_t)(v001 & kPtrMask) * bb : p[0];
+    p[5] = sx && sz ? hl + (size_t)(v101 & kPtrMask) * bb : (sx ? p[1] : p[4]);
+    p[6] = sy && sz ? hl + (size_t)(v011 & kPtrMask) * bb : (sy ? p[2] : p[4]);
+    p[7] = sx && sy && sz ? hl + (size_t)(v111 & kPtrMask) * bb
+           : sx && sy ? p[3]
+           : sx && sz ? p[5]
+           : sy && sz ? p[6]
+           : sx       ? p[1]
+           : sy       ? p[2]
+                      : p[4];
+    const int nv = nl * nl * nl;
+    float w[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int ix = (j0[0] + (k & 1)) & mask, iy = (j0[1] + ((k >> 1) & 1)) & mask, iz = (j0[2] + (k >> 2)) & mask;
+      const int idx = ix + nl * (iy + nl * iz);
+      w[k] = read_W<FP16, COLOR>(p[k], nv, idx);
+      d[k] = read_D<FP16>(p[k], idx);
+    }
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) all = all && w[k] > 0.0f;
+    if (!all) return false;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float wx = (k & 1) ? fr[0] : 1.0f - fr[0];
+      const float wy = ((k >> 1) & 1) ? fr[1] : 1.0f - fr[1];
+      const float wz = (k >> 2) ? fr[2] : 1.0f - fr[2];
+      acc = acc + wx * wy * wz * d[k];
+    }
+    *out = acc;
+    return true;
+  }
+  // corners in blocks of different levels
   float acc = 0.0f;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
