@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(128) k_batch_raycast(BatchDev b) {
 struct AllocShape {
   int tw, th, pw;
 };
-constexpr AllocShape kAllocShapes[] = {{32, 8, 32}, {16, 16, 32}, {32, 8, 8}, {16, 16, 8}};
+constexpr AllocShape kAllocShapes[] = {{32, 8, 8}, {16, 16, 8}, {32, 8, 4}, {16, 16, 4}};
 struct FuseShape {
   int warps, per_sm;
 };
@@ -234,10 +234,10 @@ void launch_alloc_shape(const mrh_batch* b, cudaStream_t s, uint32_t tiles) {
 void launch_alloc(const mrh_batch* b, int shape, cudaStream_t s) {
   const uint32_t tiles = b->alloc_tiles[shape];
   switch (shape) {
-    case 0: launch_alloc_shape<32, 8, 32>(b, s, tiles); break;
-    case 1: launch_alloc_shape<16, 16, 32>(b, s, tiles); break;
-    case 2: launch_alloc_shape<32, 8, 8>(b, s, tiles); break;
-    default: launch_alloc_shape<16, 16, 8>(b, s, tiles); break;
+    case 0: launch_alloc_shape<32, 8, 8>(b, s, tiles); break;
+    case 1: launch_alloc_shape<16, 16, 8>(b, s, tiles); break;
+    case 2: launch_alloc_shape<32, 8, 4>(b, s, tiles); break;
+    default: launch_alloc_shape<16, 16, 4>(b, s, tiles); break;
   }
 }
 
