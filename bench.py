@@ -350,37 +350,68 @@ def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epoch
 
 
 def run_camera_e2e(wl, frames, warmup, steps):
-    """Same workload through the public API with host buffers: pinned host frame -> device, integrate, raycast,
-    raycast depth -> pinned host, every step inside the timed events."""
+    """Same workload through the public API with host buffers: every step copies its depth + colour frame from pinned
+    host memory to the device, integrates it, raycasts it and copies the raycast depth back to pinned host memory, all
+    inside the timed events. Copies run on a second stream with two device buffers each way, so frame k + 1 is
+    uploaded and frame k - 1's depth read back while frame k is computed (stream order: the upload of a buffer waits
+    for the integration that last read it; the integration waits for its upload; the read-back waits for the
+    raycast)."""
     import torch
     import paper_2511_21459_b300 as mrh
     K = mrh.pinhole_from(wl)
     m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
     host = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(c).pin_memory(), T) for d, c, T in frames]
-    d_dev = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
-    c_dev = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
-    out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
-    out_host = torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory()
-    stream = torch.cuda.current_stream()
+    d_dev = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
+    c_dev = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    out = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
+    out_host = [torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory() for _ in range(2)]
+    compute = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    read = [torch.cuda.Event() for _ in range(2)]
+    for b in range(2):
+        consumed[b].record(compute)
+        read[b].record(copy)
 
-    def step(k):
-        d, c, T = host[k]
-        d_dev.copy_(d, non_blocking=True)
-        c_dev.copy_(c, non_blocking=True)
-        m.integrate_depth(K, T, d_dev, c_dev)
-        m.raycast(K, T, out)
-        out_host.copy_(out, non_blocking=True)
+    def upload(k):
+        b = k % 2
+        d, c, _ = host[k]
+        with torch.cuda.stream(copy):
+            copy.wait_event(consumed[b])
+            d_dev[b].copy_(d, non_blocking=True)
+            c_dev[b].copy_(c, non_blocking=True)
+            uploaded[b].record(copy)
 
+    def step(k, last):
+        b = k % 2
+        compute.wait_event(uploaded[b])
+        compute.wait_event(read[b])  # out[b] free again
+        m.integrate_depth(K, host[k][2], d_dev[b], c_dev[b], stream=compute)
+        consumed[b].record(compute)
+        if k + 1 <= last:
+            upload(k + 1)
+        m.raycast(K, host[k][2], out[b], stream=compute)
+        rendered[b].record(compute)
+        with torch.cuda.stream(copy):
+            copy.wait_event(rendered[b])
+            out_host[b].copy_(out[b], non_blocking=True)
+            read[b].record(copy)
+
+    upload(0)
     for k in range(warmup):
-        step(k)
+        step(k, warmup - 1)
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for k in range(steps):
-        step(warmup + k)
-    b.record(stream)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(compute)
+    upload(warmup)
+    for k in range(warmup, warmup + steps):
+        step(k, warmup + steps - 1)
+    compute.wait_stream(copy)
+    z.record(compute)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
+    ms = a.elapsed_time(z)
     m.close()
     h2d = wl.width * wl.height * (4 + 3)
     d2h = wl.width * wl.height * 4
@@ -609,7 +640,9 @@ def main():
         e_ms, h2d, d2h = run_camera_e2e(wl, frames, args.warmup, args.steps)
         e_ms = max_over_ranks(e_ms, world)
         e2e = {"value": rays_all / (e_ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps,
+               "note": "pinned host frames uploaded and raycast depth read back every step on a second stream, "
+                       "overlapping the neighbouring frames' kernels; no L2 flush between steps"}
 
     lidar = None
     if not args.no_lidar:
