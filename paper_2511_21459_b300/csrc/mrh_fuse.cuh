@@ -35,7 +35,7 @@
 namespace mrh {
 namespace {
 
-constexpr double kBand = 1e-5;
+constexpr float kBandF = 1e-5f;
 constexpr uint32_t kInvalidPtr = 0xFFFFFFFFu;
 enum { kActNone = 0, kActMerge = 1, kActSplit = 2 };
 
@@ -644,26 +644,21 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
     }
 
     // ---- decision (every lane of the group computes the same one)
+    // Outside the band the float estimate and the float threshold are on the same side as the exact values (the
+    // estimate is within 1.5e-6 and the float threshold within 6e-8, relative), so the float comparison decides.
     int act = kActNone;
     bool recheck = false;
-    double thr_m = 0.0, thr_s = 0.0;
-    const double vb32 = nobs > 0 ? (double)(vsum / (float)nobs) : 0.0;
+    const float vb = nobs > 0 ? vsum / (float)nobs : 0.0f;
     const bool eligible = x.active && nobs > 0 && sumw >= (long long)m.min_obs * nobs;
     const bool can_merge = eligible && l < m.L - 1;
     const bool can_split = eligible && m.split_h > 0.0 && l > 0;
-    if (can_merge) {
-      thr_m = m.theta[l];
-      recheck |= fabs(vb32 - thr_m) <= kBand * fabs(thr_m);
-    }
-    if (can_split) {
-      thr_s = m.split_h * m.theta[l - 1];
-      recheck |= fabs(vb32 - thr_s) <= kBand * fabs(thr_s);
-    }
-    double vbar = vb32;
+    const float thr_mf = m.thr_merge_f[l], thr_sf = m.thr_split_f[l];
+    if (can_merge) recheck |= fabsf(vb - thr_mf) <= kBandF * fabsf(thr_mf);
+    if (can_split) recheck |= fabsf(vb - thr_sf) <= kBandF * fabsf(thr_sf);
+    double exact = 0.0;
     const int leader = lane - li;
     if (__any_sync(~0u, recheck)) {
       __syncwarp();  // the group's payload writes are visible to its leader
-      double exact = 0.0;
       if (recheck && li == 0) {
         const float* W = reinterpret_cast<const float*>(io.blk + off_W(nv, FP16, COLOR));
         const float* S = reinterpret_cast<const float*>(io.blk + off_S2(nv, FP16, COLOR));
@@ -676,10 +671,9 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
         atomicAdd(&m.st->rechecks, 1u);
       }
       exact = __shfl_sync(~0u, exact, leader);
-      if (recheck) vbar = exact;
     }
-    if (can_merge && vbar < thr_m) act = kActMerge;
-    else if (can_split && vbar > thr_s) act = kActSplit;
+    if (can_merge && (recheck ? exact < m.thr_merge[l] : vb < thr_mf)) act = kActMerge;
+    else if (can_split && (recheck ? exact > m.thr_split[l] : vb > thr_sf)) act = kActSplit;
 
     // ---- re-level (rare): pop a heap block of the target level, resample into it, retire the old block
     if (__any_sync(~0u, act != kActNone)) {

@@ -129,6 +129,10 @@ struct MapDev {
   double fix_scale64;   // 65536 / E (double), LiDAR key quantisation
   double theta[2];
   double split_h;
+  // per level: merge threshold theta_l and split threshold h theta_{l-1} (in double, as the oracle compares), and
+  // their nearest floats for the float-side decision
+  double thr_merge[3], thr_split[3];
+  float thr_merge_f[3], thr_split_f[3];
   float min_range, max_range;
 };
 

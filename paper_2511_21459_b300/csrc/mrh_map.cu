@@ -443,6 +443,12 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   d.theta[0] = params->var_threshold[0];
   d.theta[1] = params->var_threshold[1];
   d.split_h = params->split_hysteresis;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    d.thr_merge[l] = l < 2 ? d.theta[l] : 0.0;
+    d.thr_split[l] = l > 0 ? d.split_h * d.theta[l - 1] : 0.0;
+    d.thr_merge_f[l] = (float)d.thr_merge[l];
+    d.thr_split_f[l] = (float)d.thr_split[l];
+  }
   d.min_range = params->min_range;
   d.max_range = params->max_range;
   d.max_touched = params->max_touched;
