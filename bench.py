@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
-    ap.add_argument("--profile-case", choices=["rgbd", "lidar"], default=None,
+    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned"], default=None,
                     help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
     return ap.parse_args()
 
@@ -74,7 +74,7 @@ def profile_case(kind: str) -> int:
             st = m.stats()
             print(json.dumps({"frame": k, "touched_level": st["touched_level"], "new_blocks": st["new_blocks"],
                               "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
-    else:
+    elif kind == "lidar":
         wl = synth.lidar()
         wl.max_blocks = (1 << 18, 1 << 16, 1 << 16)
         m = mrh.Map(mrh.params_from(wl, max_observations=1 << 24))
@@ -82,6 +82,45 @@ def profile_case(kind: str) -> int:
         for k in range(4):
             xyz, T = synth.render_lidar(wl, k, scene=scene)
             m.integrate_points(T, torch.from_numpy(xyz).cuda())
+    elif kind == "batched":
+        # the first 8 of the 16 batched maps, 4 steps, reduced heaps (about 2 GB on the device)
+        wls = synth.batched()[:8]
+        for w in wls:
+            w.max_blocks = (1 << 15, 1 << 13, 1 << 13)
+        maps = [mrh.Map(mrh.params_from(w)) for w in wls]
+        batch = mrh.Batch(maps, [mrh.pinhole_from(w) for w in wls])
+        outs = [torch.empty((w.height, w.width), device="cuda") for w in wls]
+        scenes = [w.scene() for w in wls]
+        for k in range(4):
+            fr = [synth.render_depth(w, k, scene=sc) for w, sc in zip(wls, scenes)]
+            batch.integrate([(T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), o)
+                             for (d, c, T), o in zip(fr, outs)])
+        torch.cuda.synchronize()
+        batch.close()
+        m = maps[0]
+    else:
+        # the learned level predictor: a short GPU training run on the features of 3 plain frames, then 3 frames with
+        # the predictor set (reduced heaps)
+        from paper_2511_21459_b300 import predictor
+        wl = synth.rgbd()
+        wl.max_blocks = (1 << 15, 1 << 14, 1 << 14)
+        K = mrh.pinhole_from(wl)
+        frames = camera_frames(wl, 0, 6)
+        m0 = mrh.Map(mrh.params_from(wl))
+        m0.set_feature_capture(1 << 16)
+        for d, c, T in frames[:3]:
+            m0.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        keys, feats, _ = m0.features()
+        ex = m0.extract()
+        y = predictor.level_labels(keys.cpu().numpy(), ex["keys"].cpu().numpy(), ex["levels"].cpu().numpy())
+        ok = y >= 0
+        net, _ = predictor.train(feats[torch.from_numpy(ok).cuda()].contiguous(), torch.from_numpy(y[ok]).cuda(),
+                                 epochs=4, batch=4096)
+        m0.close()
+        m = mrh.Map(mrh.params_from(wl))
+        m.set_predictor(net.weights()[1])
+        for d, c, T in frames[3:]:
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
     torch.cuda.synchronize()
     st = m.stats()
     print(json.dumps({"profile_case": kind, "status": st["status_code"], "touched_last": st["touched"]}))
