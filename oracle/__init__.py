@@ -11,6 +11,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   merge / split payloads       pinned on linear fields (exact); the rule itself is a reading: parity unpinned
   thresholds                   chosen values: parity unpinned
   raycast                      pinned: analytic plane / sphere depth; step constants are a reading
+  raycast normal / colour      pinned: a linear TSDF and colour field set block by block gives the plane's unit
+                               normal and the colour field at the hit (trilinear is exact on linear fields);
+                               analytic walls of a fused noise-free frame; constant-colour frames
 """
 from __future__ import annotations
 
@@ -70,7 +73,8 @@ def _load():
         lib.orc_destroy.argtypes = [vp]
         lib.orc_integrate_depth.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, ctypes.POINTER(FrameStats)]
         lib.orc_integrate_points.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(FrameStats)]
-        lib.orc_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp]
+        lib.orc_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp]
+        lib.orc_set_block.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
         lib.orc_count_blocks.restype = ctypes.c_int64
         lib.orc_count_blocks.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         lib.orc_extract.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -161,11 +165,27 @@ class OracleMap:
         self._lib.orc_integrate_points(self._h, _p(T), _p(x), x.shape[0], ctypes.byref(st))
         return st.as_dict()
 
-    def raycast(self, K: Pinhole, T_wc: np.ndarray) -> np.ndarray:
+    def raycast(self, K: Pinhole, T_wc: np.ndarray, normals: bool = False, rgb: bool = False):
+        """z-depth (h, w) float32; with normals / rgb also the unit normal (h, w, 3) float32 (world frame, towards
+        positive TSDF) and the colour (h, w, 3) uint8 at the hit, zero where there is none."""
         T = np.ascontiguousarray(T_wc, dtype=np.float64)
         out = np.zeros((K.height, K.width), dtype=np.float32)
-        self._lib.orc_raycast(self._h, ctypes.byref(K), _p(T), _p(out))
-        return out
+        nrm = np.zeros((K.height, K.width, 3), dtype=np.float32) if normals else None
+        col = np.zeros((K.height, K.width, 3), dtype=np.uint8) if rgb else None
+        self._lib.orc_raycast(self._h, ctypes.byref(K), _p(T), _p(out), _p(nrm), _p(col))
+        if not (normals or rgb):
+            return out
+        return (out,) + ((nrm,) if normals else ()) + ((col,) if rgb else ())
+
+    def set_block(self, key, level: int, D, W, S2=None, C=None):
+        """Test hook: create or overwrite block ``key`` at ``level`` with the given voxel payload (x fastest)."""
+        nv = (8 >> level) ** 3
+        a = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (nv,)))
+             for x in (D, W, np.zeros(nv) if S2 is None else S2)]
+        c = None if C is None else np.ascontiguousarray(np.broadcast_to(np.asarray(C, np.float64), (nv, 3)))
+        k = np.ascontiguousarray(key, dtype=np.int32)
+        if self._lib.orc_set_block(self._h, _p(k), int(level), *[_p(x) for x in a], _p(c)) != 0:
+            raise ValueError("invalid level")
 
     def count(self):
         nv = ctypes.c_int64()

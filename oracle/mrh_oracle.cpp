@@ -284,7 +284,8 @@ struct MapBase {
   virtual ~MapBase() {}
   virtual int integrate_depth(const orc_pinhole*, const double*, const float*, const uint8_t*, orc_frame_stats*) = 0;
   virtual int integrate_points(const double*, const float*, int64_t, orc_frame_stats*) = 0;
-  virtual int raycast(const orc_pinhole*, const double*, float*) = 0;
+  virtual int raycast(const orc_pinhole*, const double*, float*, float*, uint8_t*) = 0;
+  virtual int set_block(const int32_t*, int, const double*, const double*, const double*, const double*) = 0;
   virtual int64_t count_blocks(int64_t* n_voxels) = 0;
   virtual int extract(int32_t*, uint8_t*, int64_t*, double*, double*, double*, double*) = 0;
   virtual int block_stats(int32_t*, uint8_t*, double*, int64_t*, int64_t*) = 0;
@@ -764,6 +765,56 @@ struct Map : MapBase {
     return true;
   }
 
+  // Surface attributes at a hit point x inside a block of level l, over the same 8 corners as field(): g is the
+  // gradient of the trilinear interpolant up to the positive factor 1 / v_l (d/dx of the x weight is +1 for the
+  // upper corner, -1 for the lower), summed in corner order; c is the trilinear mean of the stored colour. False when
+  // a corner's block is unallocated or a corner is unobserved.
+  bool shade(const R x[3], int l, R g[3], R c[3]) const {
+    R inv = (R)1 / v[l];
+    int64_t j0[3];
+    R fr[3];
+    for (int a = 0; a < 3; ++a) {
+      R gg = x[a] * inv - (R)0.5;
+      R fl = std::floor(gg);
+      j0[a] = (int64_t)fl;
+      fr[a] = gg - fl;
+    }
+    for (int a = 0; a < 3; ++a) g[a] = c[a] = 0;
+    for (int k = 0; k < 8; ++k) {
+      int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+      int64_t j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
+      int nl = n[l];
+      Key bk{floor_div(j[0], nl), floor_div(j[1], nl), floor_div(j[2], nl)};
+      const Block<R, Sto>* b = find(bk);
+      if (!b) return false;
+      size_t idx;
+      if (b->level == l) {
+        idx = vox(nl, (int)(j[0] - bk.x * nl), (int)(j[1] - bk.y * nl), (int)(j[2] - bk.z * nl));
+      } else {
+        int lb = b->level, nb = n[lb];
+        int64_t cf[3];
+        for (int a = 0; a < 3; ++a) cf[a] = l == 0 ? j[a] : j[a] * ((int64_t)1 << l) + ((int64_t)1 << (l - 1));
+        idx = vox(nb, (int)(floor_div(cf[0], (int64_t)1 << lb) - bk.x * nb),
+                  (int)(floor_div(cf[1], (int64_t)1 << lb) - bk.y * nb),
+                  (int)(floor_div(cf[2], (int64_t)1 << lb) - bk.z * nb));
+      }
+      if (!(b->W[idx] > (R)0)) return false;
+      R wx = ax ? fr[0] : (R)1 - fr[0];
+      R wy = ay ? fr[1] : (R)1 - fr[1];
+      R wz = az ? fr[2] : (R)1 - fr[2];
+      R d = (R)Store<Sto>::get(b->D[idx]);
+      R tx = (wy * wz) * d, ty = (wx * wz) * d, tz = (wx * wy) * d;
+      g[0] = ax ? g[0] + tx : g[0] - tx;
+      g[1] = ay ? g[1] + ty : g[1] - ty;
+      g[2] = az ? g[2] + tz : g[2] - tz;
+      if (P.has_color) {
+        R w = (wx * wy) * wz;
+        for (int q = 0; q < 3; ++q) c[q] = c[q] + w * (R)Store<Sto>::get(b->C[q][idx]);
+      }
+    }
+    return true;
+  }
+
   // sample at parameter t: returns false when the block is unallocated; *valid tells whether the field exists
   bool sample(const R o[3], const R r[3], R t, R invE, int* level, bool* valid, R* F) const {
     R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
@@ -775,7 +826,7 @@ struct Map : MapBase {
     return true;
   }
 
-  int raycast(const orc_pinhole* K, const double* T, float* out) override {
+  int raycast(const orc_pinhole* K, const double* T, float* out, float* normal, uint8_t* rgb) override {
     R Rm[9], o[3];
     pose(T, Rm, o);
     const R fx = (R)K->fx, fy = (R)K->fy, cx = (R)K->cx, cy = (R)K->cy;
@@ -794,7 +845,7 @@ struct Map : MapBase {
         }
         R t = (R)K->min_depth * nq, t_far = (R)K->max_depth * nq;
         bool have_prev = false;
-        R t_prev = 0, F_prev = 0, hit = 0;
+        R t_prev = 0, F_prev = 0, hit = 0, t_hit = 0;
         for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
           R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
           int64_t bk[3] = {(int64_t)std::floor(x[0] * invE), (int64_t)std::floor(x[1] * invE),
@@ -834,6 +885,7 @@ struct Map : MapBase {
               if (Fa - Fb > (R)0) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
             }
             hit = ts * rc[2];
+            t_hit = ts;
             break;
           }
           have_prev = valid;
@@ -845,8 +897,48 @@ struct Map : MapBase {
           }
           t = t + s;
         }
-        out[(size_t)vv * K->width + u] = (float)hit;
+        const size_t px = (size_t)vv * K->width + u;
+        out[px] = (float)hit;
+        if (normal || rgb) {
+          // surface normal and colour at the hit point, from the block holding it (zero when none)
+          R g[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+          bool ok = false;
+          if (hit != (R)0) {
+            const R xh[3] = {o[0] + t_hit * r[0], o[1] + t_hit * r[1], o[2] + t_hit * r[2]};
+            const Block<R, Sto>* bh = find(Key{(int64_t)std::floor(xh[0] * invE), (int64_t)std::floor(xh[1] * invE),
+                                               (int64_t)std::floor(xh[2] * invE)});
+            ok = bh && shade(xh, bh->level, g, c);
+          }
+          if (normal) {
+            R nn = ok ? std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : (R)0;
+            for (int a = 0; a < 3; ++a) normal[3 * px + a] = nn > (R)0 ? (float)(g[a] / nn) : 0.0f;
+          }
+          if (rgb)
+            for (int q = 0; q < 3; ++q) {
+              R cv = ok ? c[q] + (R)0.5 : (R)0;
+              rgb[3 * px + q] = (uint8_t)(cv <= (R)0 ? 0 : cv >= (R)255 ? 255 : (int)cv);
+            }
+        }
       }
+    return 0;
+  }
+
+  // ---- test hook: write one block (created at `level` if missing) with the given payload
+  int set_block(const int32_t* key, int level, const double* D, const double* W, const double* S2,
+                const double* C) override {
+    if (level < 0 || level >= L) return -1;
+    Key k{key[0], key[1], key[2]};
+    Block<R, Sto>& b = blocks[k];
+    b.level = level;
+    b.resize(n[level], P.has_color != 0);
+    for (size_t i = 0; i < b.W.size(); ++i) {
+      b.D[i] = Store<Sto>::put((R)D[i]);
+      b.W[i] = (R)W[i];
+      b.S2[i] = (R)S2[i];
+      if (P.has_color && C)
+        for (int q = 0; q < 3; ++q) b.C[q][i] = Store<Sto>::put((R)C[3 * i + q]);
+    }
+    bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
     return 0;
   }
 
@@ -956,8 +1048,14 @@ int orc_integrate_points(void* h, const double* T_ws, const float* xyz, int64_t 
   return ((MapBase*)h)->integrate_points(T_ws, xyz, n, st);
 }
 
-int orc_raycast(void* h, const orc_pinhole* K, const double* T_wc, float* depth_out) {
-  return ((MapBase*)h)->raycast(K, T_wc, depth_out);
+int orc_raycast(void* h, const orc_pinhole* K, const double* T_wc, float* depth_out, float* normal_out,
+                uint8_t* rgb_out) {
+  return ((MapBase*)h)->raycast(K, T_wc, depth_out, normal_out, rgb_out);
+}
+
+int orc_set_block(void* h, const int32_t* key, int level, const double* D, const double* W, const double* S2,
+                  const double* C) {
+  return ((MapBase*)h)->set_block(key, level, D, W, S2, C);
 }
 
 int64_t orc_count_blocks(void* h, int64_t* n_voxels) { return ((MapBase*)h)->count_blocks(n_voxels); }
