@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """Benchmark of the per-frame hot path: integrated points/s and frames/s on the RGB-D sequence (640x480, 3 levels
-1/2/4 cm, tau 12 cm, 2^20-slot hash, colour, FP32 storage; a 640x480 raycast every frame), with a LiDAR line
+1/2/4 cm, tau 12 cm, 2^20-slot hash, colour, FP32 storage; a 640x480 raycast of depth, normal and colour every
+frame), with a LiDAR line
 (128 x 2048 = 262,144 points per scan, FP16 storage) and the HBM roofline of the fusion kernel.
 
-A step is one frame: allocation, fusion + block variance + re-levelling, heap release, and the raycast of that frame's
-view. Inputs are seeded synthetic frames (the paper's RGB-D and LiDAR datasets are not available), generated before
+A step is one frame: allocation, fusion + block variance + re-levelling, heap release, and the raycast (depth, normal
+and colour) of that frame's view. Inputs are seeded synthetic frames (the paper's RGB-D and LiDAR datasets are not available), generated before
 timing and resident in HBM. Every step is timed with CUDA events on the launching stream; L2 is flushed (a 256 MiB
 write) between steps, outside the timed events.
 
@@ -68,9 +69,11 @@ def profile_case(kind: str) -> int:
         m = mrh.Map(mrh.params_from(wl))
         K = mrh.pinhole_from(wl)
         out = torch.empty((wl.height, wl.width), device="cuda")
+        nrm = torch.empty((wl.height, wl.width, 3), device="cuda")
+        col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
         for k, (d, c, T) in enumerate(camera_frames(wl, 0, 6)):
             m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
-            m.raycast(K, T, out)
+            m.raycast(K, T, out, normals=nrm, rgb=col)
             st = m.stats()
             print(json.dumps({"frame": k, "touched_level": st["touched_level"], "new_blocks": st["new_blocks"],
                               "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
@@ -274,11 +277,13 @@ def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False)
         m.set_predictor(predictor)
     dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
     out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    nrm = torch.empty((wl.height, wl.width, 3), dtype=torch.float32, device="cuda")
+    col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     for k in range(warmup):
         d, c, T = dev[k]
         m.integrate_depth(K, T, d, c)
-        m.raycast(K, T, out)
+        m.raycast(K, T, out, normals=nrm, rgb=col)
     torch.cuda.synchronize()
     m.set_profiling(True)
     m.profile(reset=True)
@@ -290,7 +295,7 @@ def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False)
         d, c, T = dev[warmup + k]
         ev[k][0].record(stream)
         m.integrate_depth(K, T, d, c)
-        m.raycast(K, T, out)
+        m.raycast(K, T, out, normals=nrm, rgb=col)
         ev[k][1].record(stream)
         st = m.stats()  # synchronises (outside the timed events)
         if st["status_code"] != 0:
@@ -391,8 +396,8 @@ def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epoch
 
 def run_camera_e2e(wl, frames, warmup, steps):
     """Same workload through the public API with host buffers: every step copies its depth + colour frame from pinned
-    host memory to the device, integrates it, raycasts it and copies the raycast depth back to pinned host memory, all
-    inside the timed events. Copies run on a second stream with two device buffers each way, so frame k + 1 is
+    host memory to the device, integrates it, raycasts it and copies the raycast depth, normals and colours back to
+    pinned host memory, all inside the timed events. Copies run on a second stream with two device buffers each way, so frame k + 1 is
     uploaded and frame k - 1's depth read back while frame k is computed (stream order: the upload of a buffer waits
     for the integration that last read it; the integration waits for its upload; the read-back waits for the
     raycast)."""
@@ -404,7 +409,11 @@ def run_camera_e2e(wl, frames, warmup, steps):
     d_dev = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
     c_dev = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
     out = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
+    nrm = [torch.empty((wl.height, wl.width, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    col = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
     out_host = [torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory() for _ in range(2)]
+    nrm_host = [torch.empty((wl.height, wl.width, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    col_host = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8).pin_memory() for _ in range(2)]
     compute = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
     uploaded = [torch.cuda.Event() for _ in range(2)]
@@ -432,11 +441,13 @@ def run_camera_e2e(wl, frames, warmup, steps):
         consumed[b].record(compute)
         if k + 1 <= last:
             upload(k + 1)
-        m.raycast(K, host[k][2], out[b], stream=compute)
+        m.raycast(K, host[k][2], out[b], stream=compute, normals=nrm[b], rgb=col[b])
         rendered[b].record(compute)
         with torch.cuda.stream(copy):
             copy.wait_event(rendered[b])
             out_host[b].copy_(out[b], non_blocking=True)
+            nrm_host[b].copy_(nrm[b], non_blocking=True)
+            col_host[b].copy_(col[b], non_blocking=True)
             read[b].record(copy)
 
     upload(0)
@@ -454,7 +465,7 @@ def run_camera_e2e(wl, frames, warmup, steps):
     ms = a.elapsed_time(z)
     m.close()
     h2d = wl.width * wl.height * (4 + 3)
-    d2h = wl.width * wl.height * 4
+    d2h = wl.width * wl.height * (4 + 12 + 3)
     return ms, h2d, d2h
 
 
@@ -567,7 +578,7 @@ def oracle_camera_sample(wl, frames, budget_s, max_frames):
     for depth, rgb, T in frames[:max_frames]:
         t0 = time.perf_counter()
         st = om.integrate_depth(K, T, depth, rgb)
-        om.raycast(K, T)
+        om.raycast(K, T, normals=True, rgb=True)
         t_total += time.perf_counter() - t0
         rays += st["valid_rays"]
         n += 1
@@ -590,7 +601,7 @@ def _oracle_replica(seed_frames, budget_s, barrier, queue):
     for depth, rgb, T in frames:
         t0 = time.perf_counter()
         st = om.integrate_depth(K, T, depth, rgb)
-        om.raycast(K, T)
+        om.raycast(K, T, normals=True, rgb=True)
         t_total += time.perf_counter() - t0
         rays += st["valid_rays"]
         n += 1
@@ -633,13 +644,13 @@ def main():
         K = oracle.pinhole_from(wl)
         for depth, rgb, T in frames[:warm]:
             om.integrate_depth(K, T, depth, rgb)
-            om.raycast(K, T)
+            om.raycast(K, T, normals=True, rgb=True)
         rays, t_total, n = 0, 0.0, 0
         budget = 150.0
         for depth, rgb, T in frames[warm:]:
             t0 = time.perf_counter()
             st = om.integrate_depth(K, T, depth, rgb)
-            om.raycast(K, T)
+            om.raycast(K, T, normals=True, rgb=True)
             t_total += time.perf_counter() - t0
             rays += st["valid_rays"]
             n += 1
@@ -647,11 +658,13 @@ def main():
                 break
         value = rays / t_total
         sample = (f"frames {warm}..{warm + n - 1} of the RGB-D sequence after {warm} untimed, integrate + full "
-                  f"640x480 raycast per frame, oracle f32s mode, 1 thread (time-boxed at {budget:.0f} s)")
+                  f"640x480 raycast (depth, normal, colour) per frame, oracle f32s mode, 1 thread (time-boxed at "
+                  f"{budget:.0f} s)")
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
                 "steps": n, "warmup": warm, "ms_per_step": 1000.0 * t_total / n, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm) + 640x480 raycast"},
+                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm) + 640x480 raycast "
+                                       "(depth, normal, colour)"},
                 "frames_per_s": n / t_total,
                 "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -673,8 +686,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rays_c, t_c, n_c = oracle_camera_sample(wl, frames, args.cpu_budget_s, 8)
         cpu = {"value": rays_c / t_c, "unit": "points/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_c} frames of the RGB-D sequence, integrate + full 640x480 raycast each, f32s "
-                         f"mode, single thread ({t_c:.1f} s)"}
+               "sample": f"first {n_c} frames of the RGB-D sequence, integrate + full 640x480 raycast (depth, "
+                         f"normal, colour) each, f32s mode, single thread ({t_c:.1f} s)"}
         n_procs = max(1, min(args.cpu_replicas, os.cpu_count() or 1))
         if n_procs > 1:
             rays_r, t_r, n_r = oracle_camera_replicas(n_procs, 4, args.cpu_budget_s)
@@ -725,8 +738,8 @@ def main():
         e_ms = max_over_ranks(e_ms, world)
         e2e = {"value": rays_all / (e_ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps,
-               "note": "pinned host frames uploaded and raycast depth read back every step on a second stream, "
-                       "overlapping the neighbouring frames' kernels; no L2 flush between steps"}
+               "note": "pinned host frames uploaded and raycast depth, normals and colours read back every step on a "
+                       "second stream, overlapping the neighbouring frames' kernels; no L2 flush between steps"}
 
     lidar = None
     if not args.no_lidar:
@@ -767,7 +780,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded procedural RGB-D room sequence; stands in for ScanNet/Replica)",
                 "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm, 2^20 hash, colour, FP32 "
-                                       "storage) + 640x480 raycast per frame",
+                                       "storage) + 640x480 raycast (depth, normal, colour) per frame",
                            "frames": f"{args.warmup}..{args.warmup + args.steps - 1} timed after {args.warmup} warm-up",
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

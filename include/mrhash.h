@@ -242,11 +242,18 @@ mrh_status mrh_mlp_predict(const mrh_mlp* mlp, const float* x_dev, uint32_t n, f
  * Synchronises `stream`. */
 mrh_status mrh_mlp_get_weights(const mrh_mlp* mlp, float* master_host, uint16_t* bf16_host, void* stream);
 
-/* Raycast the map from a pinhole view (the rendering branch of Fig. 2): depth_out_dev receives height x width
- * float32 z-depth of the first observed zero crossing, 0 where none. Empty blocks are skipped whole.
+/* Raycast the map from a pinhole view (the rendering branch of Fig. 2; the paper renders through splats and gives no
+ * raycaster, so the march is this library's reading): depth_out_dev receives height x width float32 z-depth of the
+ * first observed + -> - zero crossing of the trilinear TSDF, 0 where none. Empty bricks and blocks are skipped whole.
+ * Optional outputs (device, NULL to skip), at the hit point and from the same 8 trilinear corners:
+ *   normal_out_dev  height x width x 3 float32, world frame: the normalised gradient of the trilinear interpolant
+ *                   (pointing towards positive distance, i.e. out of the surface);
+ *   rgb_out_dev     height x width x 3 uint8: the trilinear mean of the stored colour, rounded half up and clamped
+ *                   (maps created with has_color only, else MRH_ERR_INVALID_ARG).
+ * Both are 0 where there is no hit, or where the hit's block or one of the corners is unallocated or unobserved.
  * Asynchronous on `stream`. */
 mrh_status mrh_raycast(mrh_map* map, const mrh_pinhole* K, const double* T_wc_host, float* depth_out_dev,
-                       void* stream);
+                       float* normal_out_dev, uint8_t* rgb_out_dev, void* stream);
 
 /* Number of allocated blocks and voxels (synchronises `stream`). */
 mrh_status mrh_count_blocks(mrh_map* map, uint64_t* n_blocks, uint64_t* n_voxels, void* stream);

@@ -95,7 +95,7 @@ def lib():
         L.mrh_map_destroy.argtypes = [vp]
         L.mrh_integrate_depth.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp]
         L.mrh_integrate_points.argtypes = [vp, vp, vp, u64, vp]
-        L.mrh_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp]
+        L.mrh_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp, vp]
         L.mrh_count_blocks.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
                                          ctypes.POINTER(u64), vp]
@@ -235,14 +235,26 @@ class Map:
         _check(self._lib.mrh_integrate_points(self._h, ctypes.c_void_p(T.ctypes.data), _ptr(xyz), xyz.shape[0],
                                               _stream(stream)), "mrh_integrate_points")
 
-    def raycast(self, K: Pinhole, T_wc, out=None, stream=None):
+    def raycast(self, K: Pinhole, T_wc, out=None, stream=None, normals=None, rgb=None):
+        """z-depth (h, w) float32 CUDA tensor (written into ``out`` when given). ``normals`` / ``rgb``: True (allocate)
+        or a CUDA tensor (h, w, 3) float32 / uint8 to receive the unit normal / colour at the hit as well; then the
+        result is a tuple (depth, [normals], [rgb])."""
         import torch
         T = _pose(T_wc)
+        dev = f"cuda:{self.device}"
         if out is None:
-            out = torch.empty((K.height, K.width), dtype=torch.float32, device=f"cuda:{self.device}")
-        _check(self._lib.mrh_raycast(self._h, ctypes.byref(K), ctypes.c_void_p(T.ctypes.data), _ptr(out),
-                                     _stream(stream)), "mrh_raycast")
-        return out
+            out = torch.empty((K.height, K.width), dtype=torch.float32, device=dev)
+        if normals is True:
+            normals = torch.empty((K.height, K.width, 3), dtype=torch.float32, device=dev)
+        if rgb is True:
+            rgb = torch.empty((K.height, K.width, 3), dtype=torch.uint8, device=dev)
+        nrm = normals if normals is not None and normals is not False else None
+        col = rgb if rgb is not None and rgb is not False else None
+        _check(self._lib.mrh_raycast(self._h, ctypes.byref(K), ctypes.c_void_p(T.ctypes.data), _ptr(out), _ptr(nrm),
+                                     _ptr(col), _stream(stream)), "mrh_raycast")
+        if nrm is None and col is None:
+            return out
+        return (out,) + ((nrm,) if nrm is not None else ()) + ((col,) if col is not None else ())
 
     def count(self, stream=None):
         nb, nv = ctypes.c_uint64(), ctypes.c_uint64()

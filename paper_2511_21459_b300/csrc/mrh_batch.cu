@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) k_batch_raycast(BatchDev b) {
     v = ty * 8 + (warp >> 1) * 4 + (lane >> 3);
   }
   const CamArgs c = f.cam;
-  if (u < c.width && v < c.height) cast_ray_any(b.maps[mi], c, u, v, f.raycast_out);
+  if (u < c.width && v < c.height) cast_ray_any(b.maps[mi], c, u, v, RayOut{f.raycast_out, nullptr, nullptr});
 }
 
 // ---- launch shapes (the autotuner's search space)

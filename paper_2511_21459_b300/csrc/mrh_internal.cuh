@@ -421,6 +421,7 @@ void launch_fuse_depth(const MapDev& m, const CamArgs& c, const float* rho, cons
 void launch_fuse_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s, int sms);
 void launch_lidar_observations(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s,
                                int sms);
-void launch_raycast(const MapDev& m, const CamArgs& c, float* out, cudaStream_t s);
+void launch_raycast(const MapDev& m, const CamArgs& c, float* depth, float* normal, uint8_t* rgb,
+                   cudaStream_t s);
 
 }  // namespace mrh

@@ -656,15 +656,16 @@ mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz
   return MRH_OK;
 }
 
-mrh_status mrh_raycast(mrh_map* m, const mrh_pinhole* K, const double* T_wc, float* depth_out, void* stream) {
-  if (!m || !depth_out || !finite_pose(T_wc)) return MRH_ERR_INVALID_ARG;
+mrh_status mrh_raycast(mrh_map* m, const mrh_pinhole* K, const double* T_wc, float* depth_out, float* normal_out,
+                       uint8_t* rgb_out, void* stream) {
+  if (!m || !depth_out || !finite_pose(T_wc) || (rgb_out && !m->d.color)) return MRH_ERR_INVALID_ARG;
   mrh_status st = validate_pinhole(K);
   if (st != MRH_OK) return st;
   DeviceGuard guard(m->device);
   CamArgs c = cam_args(K, T_wc);
   {
     KernelScope ks(m, MRH_K_RAYCAST, (cudaStream_t)stream, 1);
-    launch_raycast(m->d, c, depth_out, (cudaStream_t)stream);
+    launch_raycast(m->d, c, depth_out, normal_out, rgb_out, (cudaStream_t)stream);
   }
   MRH_CUDA(cudaGetLastError());
   return MRH_OK;

@@ -7,7 +7,7 @@ namespace {
 // One thread per pixel; each warp covers an 8 x 4 pixel tile so that its rays march through the same blocks. Six
 // CTAs per SM (at most 80 registers) measured best among 4 to 8 CTAs of 128 threads and 32- or 256-thread CTAs.
 template <bool FP16, bool COLOR>
-__global__ void __launch_bounds__(128, 6) k_raycast(MapDev m, CamArgs c, float* __restrict__ out) {
+__global__ void __launch_bounds__(128, 6) k_raycast(MapDev m, CamArgs c, RayOut out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int v = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(128, 6) k_raycast(MapDev m, CamArgs c, float* 
 
 }  // namespace
 
-void launch_raycast(const MapDev& m, const CamArgs& c, float* out, cudaStream_t s) {
+void launch_raycast(const MapDev& m, const CamArgs& c, float* depth, float* normal, uint8_t* rgb, cudaStream_t s) {
+  const RayOut out{depth, normal, rgb};
   dim3 grid((c.width + 15) / 16, (c.height + 7) / 8);
   if (m.fp16) {
     if (m.color) k_raycast<true, true><<<grid, 128, 0, s>>>(m, c, out);

@@ -11,7 +11,9 @@
 // observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead when the sample is valid and F is
 // larger (F <= tau underestimates the distance to the surface, so the step stays in front of it). At the first valid
 // + -> - sign change the linear root is taken, evaluated once more, and one secant step refines it. Output is
-// z-depth, 0 where nothing was hit.
+// z-depth, 0 where nothing was hit; optionally the unit normal (the normalised gradient of the same trilinear
+// interpolant at the hit) and the colour (its trilinear mean of the stored colour, rounded to u8), zero where the
+// hit's block or one of its 8 corners is missing or unobserved.
 //
 // Every step follows the oracle's float operation order (this file is compiled without multiply-add contraction), so
 // depths agree with the oracle to rounding and hit/miss decisions agree except at exact ties.
@@ -103,6 +105,18 @@ template <bool FP16, bool COLOR>
 __device__ inline float read_W(const uint8_t* blk, int nv, int i) {
   return reinterpret_cast<const float*>(blk + off_W(nv, FP16, COLOR))[i];
 }
+template <bool FP16>
+__device__ inline float read_C(const uint8_t* blk, int nv, int i, int q) {
+  if (FP16) return __half2float(reinterpret_cast<const __half*>(blk + off_C(nv, 1, q))[i]);
+  return reinterpret_cast<const float*>(blk + off_C(nv, 0, q))[i];
+}
+
+// Destination of one raycast: z-depth, and optionally normals (3 floats per pixel) and colours (3 bytes per pixel).
+struct RayOut {
+  float* depth;
+  float* normal;
+  uint8_t* rgb;
+};
 
 // trilinear field at x on the level-l grid; false when a corner is unallocated or unobserved. Each distinct block
 // among the 8 corners is looked up once (usually there is only one); the corner sum runs in corner order 0..7.
@@ -134,66 +148,43 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
   if (ok && sy && sz) { v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1); ok = v011 != kValPending; }
   if (ok && sx && sy && sz) { v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1); ok = v111 != kValPending; }
   if (!ok) return false;
-  if (!(sx || sy || sz) && (int)((v000 >> 28) & 3u) == l) {
-    // all 8 corners in one block of level l: issue the 16 loads together, then test and sum in corner order
-    const uint8_t* blk = block_ptr(m, v000);
-    const int i0 = (j0[0] & mask) + nl * ((j0[1] & mask) + nl * (j0[2] & mask));
-    const int nv = nl * nl * nl;
-    float w[8], d[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int idx = i0 + (k & 1) + nl * ((k >> 1) & 1) + nl * nl * (k >> 2);
-      w[k] = read_W<FP16, COLOR>(blk, nv, idx);
-      d[k] = read_D<FP16>(blk, idx);
-    }
-    bool all = true;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) all = all && w[k] > 0.0f;
-    if (!all) return false;
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float wx = (k & 1) ? fr[0] : 1.0f - fr[0];
-      const float wy = ((k >> 1) & 1) ? fr[1] : 1.0f - fr[1];
-      const float wz = (k >> 2) ? fr[2] : 1.0f - fr[2];
-      acc = acc + wx * wy * wz * d[k];
-    }
-    *out = acc;
-    return true;
-  }
   const uint32_t lvl = (uint32_t)l;
   const bool same = ((v000 >> 28) & 3u) == lvl && (!sx || ((v100 >> 28) & 3u) == lvl) &&
                     (!sy || ((v010 >> 28) & 3u) == lvl) && (!(sx && sy) || ((v110 >> 28) & 3u) == lvl) &&
                     (!sz || ((v001 >> 28) & 3u) == lvl) && (!(sx && sz) || ((v101 >> 28) & 3u) == lvl) &&
                     (!(sy && sz) || ((v011 >> 28) & 3u) == lvl) && (!(sx && sy && sz) || ((v111 >> 28) & 3u) == lvl);
   if (same) {
-    // the corners span 2 to 8 blocks, all of level l: one pointer per block offset (a missing offset reuses the
-    // block the corner falls in), the index formula of the level's grid, the 16 loads issued together
+    // the corners span 1 to 8 blocks (one in most samples), all of level l: a 32-bit word offset per block offset (a missing offset reuses
+    // the block the corner falls in), the index of each corner from per-axis terms, the 16 loads issued together
     const uint8_t* hl = m.heap[l];
-    const size_t bb = m.block_bytes[l];
-    const uint8_t* p[8];
-    p[0] = hl + (size_t)(v000 & kPtrMask) * bb;
-    p[1] = sx ? hl + (size_t)(v100 & kPtrMask) * bb : p[0];
-    p[2] = sy ? hl + (size_t)(v010 & kPtrMask) * bb : p[0];
-    p[3] = sx && sy ? hl + (size_t)(v110 & kPtrMask) * bb : (sx ? p[1] : p[2]);
-    p[4] = sz ? hl + (size_t)(v001 & kPtrMask) * bb : p[0];
-    p[5] = sx && sz ? hl + (size_t)(v101 & kPtrMask) * bb : (sx ? p[1] : p[4]);
-    p[6] = sy && sz ? hl + (size_t)(v011 & kPtrMask) * bb : (sy ? p[2] : p[4]);
-    p[7] = sx && sy && sz ? hl + (size_t)(v111 & kPtrMask) * bb
-           : sx && sy ? p[3]
-           : sx && sz ? p[5]
-           : sy && sz ? p[6]
-           : sx       ? p[1]
-           : sy       ? p[2]
-                      : p[4];
+    const uint32_t bw = m.block_bytes[l] >> 2;
+    uint32_t q[8];
+    q[0] = (v000 & kPtrMask) * bw;
+    q[1] = sx ? (v100 & kPtrMask) * bw : q[0];
+    q[2] = sy ? (v010 & kPtrMask) * bw : q[0];
+    q[3] = sx && sy ? (v110 & kPtrMask) * bw : (sx ? q[1] : q[2]);
+    q[4] = sz ? (v001 & kPtrMask) * bw : q[0];
+    q[5] = sx && sz ? (v101 & kPtrMask) * bw : (sx ? q[1] : q[4]);
+    q[6] = sy && sz ? (v011 & kPtrMask) * bw : (sy ? q[2] : q[4]);
+    q[7] = sx && sy && sz ? (v111 & kPtrMask) * bw
+           : sx && sy ? q[3]
+           : sx && sz ? q[5]
+           : sy && sz ? q[6]
+           : sx       ? q[1]
+           : sy       ? q[2]
+                      : q[4];
     const int nv = nl * nl * nl;
+    const uint32_t wo = off_W(nv, FP16, COLOR) >> 2;
+    const int ix0 = j0[0] & mask, ix1 = (j0[0] + 1) & mask;
+    const int iy0 = (j0[1] & mask) * nl, iy1 = ((j0[1] + 1) & mask) * nl;
+    const int iz0 = (j0[2] & mask) * nl * nl, iz1 = ((j0[2] + 1) & mask) * nl * nl;
     float w[8], d[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int ix = (j0[0] + (k & 1)) & mask, iy = (j0[1] + ((k >> 1) & 1)) & mask, iz = (j0[2] + (k >> 2)) & mask;
-      const int idx = ix + nl * (iy + nl * iz);
-      w[k] = read_W<FP16, COLOR>(p[k], nv, idx);
-      d[k] = read_D<FP16>(p[k], idx);
+      const uint32_t idx = (uint32_t)((k & 1 ? ix1 : ix0) + ((k >> 1) & 1 ? iy1 : iy0) + (k >> 2 ? iz1 : iz0));
+      w[k] = reinterpret_cast<const float*>(hl)[q[k] + wo + idx];
+      if (FP16) d[k] = __half2float(reinterpret_cast<const __half*>(hl)[2 * q[k] + idx]);
+      else d[k] = reinterpret_cast<const float*>(hl)[q[k] + idx];
     }
     bool all = true;
 #pragma unroll
@@ -242,9 +233,64 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
   return true;
 }
 
-// One ray: march, find the first zero crossing, write its z-depth (0 = none).
+// Surface attributes at a hit x in a block of level l, over the 8 corners field() uses (each corner's block and voxel
+// found the same way): g = the interpolant's gradient times v_l (the x weight's derivative is +1 for the upper
+// corner, -1 for the lower), col = the trilinear mean of the stored colour, both summed in corner order. False when a
+// corner's block is unallocated or a corner is unobserved. Runs once per hit pixel, so it takes the generic corner
+// path only.
 template <bool FP16, bool COLOR>
-__device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
+__device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, float g[3], float col[3]) {
+  const float inv = m.inv_v[l];
+  int j0[3];
+  float fr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float gg = x[a] * inv - 0.5f;
+    const float fl = floorf(gg);
+    j0[a] = (int)fl;
+    fr[a] = gg - fl;
+    g[a] = 0.0f;
+    col[a] = 0.0f;
+  }
+  const int sh = 3 - l, nl = 1 << sh, mask = nl - 1;
+  for (int k = 0; k < 8; ++k) {
+    const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+    const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
+    const uint32_t val = find_block(m.slots, m.slot_mask, j[0] >> sh, j[1] >> sh, j[2] >> sh);
+    if (val == kValPending) return false;
+    const int lb = (int)((val >> 28) & 3u);
+    const int nb = kFineDim >> lb, nv = nb * nb * nb;
+    const uint8_t* blk = block_ptr(m, val);
+    int idx;
+    if (lb == l) {
+      idx = (j[0] & mask) + nl * ((j[1] & mask) + nl * (j[2] & mask));
+    } else {
+      int cc[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
+      idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
+    }
+    if (!(read_W<FP16, COLOR>(blk, nv, idx) > 0.0f)) return false;
+    const float wx = ax ? fr[0] : 1.0f - fr[0];
+    const float wy = ay ? fr[1] : 1.0f - fr[1];
+    const float wz = az ? fr[2] : 1.0f - fr[2];
+    const float d = read_D<FP16>(blk, idx);
+    const float tx = (wy * wz) * d, ty = (wx * wz) * d, tz = (wx * wy) * d;
+    g[0] = ax ? g[0] + tx : g[0] - tx;
+    g[1] = ay ? g[1] + ty : g[1] - ty;
+    g[2] = az ? g[2] + tz : g[2] - tz;
+    if (COLOR) {
+      const float w = (wx * wy) * wz;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) col[q] = col[q] + w * read_C<FP16>(blk, nv, idx, q);
+    }
+  }
+  return true;
+}
+
+// One ray: march, find the first zero crossing, write its z-depth (0 = none) and the requested surface attributes.
+template <bool FP16, bool COLOR>
+__device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, const RayOut& out) {
   BlockCache bc;
   OccCache super_c, brick_c;
   const float qx = ((float)u - c.cx) / c.fx, qy = ((float)v - c.cy) / c.fy;
@@ -342,11 +388,34 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     }
     t = t + s;
   }
-  out[(size_t)v * c.width + u] = hit;
+  const size_t px = (size_t)v * c.width + u;
+  out.depth[px] = hit;
+  if (out.normal || out.rgb) {
+    float g[3], col[3];
+    bool ok = false;
+    if (hit != 0.0f) {
+      const float xh[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+      const uint32_t val = find_block(m.slots, m.slot_mask, ifloor(xh[0] * invE), ifloor(xh[1] * invE),
+                                      ifloor(xh[2] * invE));
+      ok = val != kValPending && shade<FP16, COLOR>(m, xh, (int)((val >> 28) & 3u), g, col);
+    }
+    if (out.normal) {
+      const float nn = ok ? sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) out.normal[3 * px + a] = nn > 0.0f ? g[a] / nn : 0.0f;
+    }
+    if (out.rgb) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float cv = ok && COLOR ? col[q] + 0.5f : 0.0f;
+        out.rgb[3 * px + q] = (uint8_t)(cv <= 0.0f ? 0 : cv >= 255.0f ? 255 : (int)cv);
+      }
+    }
+  }
 }
 
 // cast_ray with the storage format chosen at run time (one branch per ray)
-__device__ inline void cast_ray_any(const MapDev& m, const CamArgs& c, int u, int v, float* __restrict__ out) {
+__device__ inline void cast_ray_any(const MapDev& m, const CamArgs& c, int u, int v, const RayOut& out) {
   if (m.fp16) {
     if (m.color) cast_ray<true, true>(m, c, u, v, out);
     else cast_ray<true, false>(m, c, u, v, out);

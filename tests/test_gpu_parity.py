@@ -1,7 +1,8 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle on the same seeded inputs.
 
 Keys, levels and weights bit-exact; D, sigma^2 and colour within 1e-4 relative (tests/parity.py); raycast depth within
-1e-4 relative with at most 0.1 % hit/miss disagreement. Sizes span many CTA tiles with ragged tails; the RGB-D and
+1e-4 relative with at most 0.1 % hit/miss disagreement; raycast normals within 1e-5 and colours within 1 (u8) where
+the two depths are identical. Sizes span many CTA tiles with ragged tails; the RGB-D and
 LiDAR cases run the full-size frames of the benchmark configuration.
 """
 import numpy as np
@@ -55,10 +56,29 @@ def run_camera(wl, frames, gmap, omap, check_each=False, theta0=None, raycast_fr
             reports.append(compare_extracts(gmap.extract(), omap.extract(), wl.truncation, theta0,
                                             check_color=wl.has_color))
         if f in raycast_frames:
-            rc_g = gmap.raycast(K_g, T).cpu().numpy()
-            rc_o = omap.raycast(K_o, T)
-            check_raycast(rc_g, rc_o)
+            color = bool(wl.has_color)
+            out_g = [x.cpu().numpy() for x in gmap.raycast(K_g, T, normals=True, rgb=color)]
+            out_o = omap.raycast(K_o, T, normals=True, rgb=color)
+            check_raycast(out_g[0], out_o[0])
+            check_shading(out_g, out_o)
     return reports
+
+
+def check_shading(out_g, out_o):
+    """Normal (and colour) where the GPU and oracle depths are identical: same shaded / unshaded decision, normals
+    within 1e-5 (the same float operations in the same order), colours within 1 after rounding."""
+    same = (out_g[0] == out_o[0]) & (out_o[0] > 0)
+    assert same.mean() > 0.5 * (out_o[0] > 0).mean()
+    ng, no = out_g[1][same], out_o[1][same]
+    assert np.array_equal(np.any(ng != 0, -1), np.any(no != 0, -1))
+    assert np.abs(ng - no).max() <= 1e-5
+    shaded = np.any(no != 0, -1)
+    assert shaded.mean() > 0.9
+    np.testing.assert_allclose(np.linalg.norm(ng[shaded], axis=-1), 1.0, atol=1e-6)
+    if len(out_o) > 2:
+        cg, co = out_g[2][same].astype(np.int32), out_o[2][same].astype(np.int32)
+        assert np.abs(cg - co).max() <= 1
+        assert np.mean(cg == co) > 0.999
 
 
 def check_raycast(rc_g, rc_o, rel=1e-4, max_mismatch=1e-3):
@@ -102,7 +122,7 @@ def test_fp16_storage_matches_oracle_half_mode():
     wl = synth.tiny()
     wl.fp16 = True
     frames = [synth.render_depth(wl, 0, seed=s) for s in range(8)]
-    run_camera(wl, frames, gpu_map(wl), orc_map(wl), check_each=True)
+    run_camera(wl, frames, gpu_map(wl), orc_map(wl), check_each=True, raycast_frames=(7,))
 
 
 def test_rgbd_full_size_prefix():
@@ -213,6 +233,31 @@ def test_lidar_long_bands_take_the_restage_path():
     wl.min_obs = 2
     g, o = run_lidar(wl, 3)
     assert g.stats()["lidar_restaged"] > 0
+
+
+def test_lidar_map_raycast_normals_fp16():
+    """Raycast of a LiDAR-fused map (FP16 storage, no colour) from a pinhole looking along the sensor's heading:
+    depth and normals match the oracle; asking for colour from a map without colour is an argument error."""
+    wl = synth.lidar()
+    wl.n_beams, wl.n_azimuth = 128, 1024
+    wl.min_obs = 2
+    g, o = run_lidar(wl, 3, check_each=False)
+    c, s = np.cos(0.3), np.sin(0.3)          # optical axis along the heading, pitched 0.3 rad down
+    cam_from_sensor = np.eye(4)
+    cam_from_sensor[:3, :3] = [[0.0, -s, c], [-1.0, 0.0, 0.0], [0.0, -c, -s]]
+    T = synth.lidar_pose(2) @ cam_from_sensor
+    K_g, K_o = mrh().Pinhole(), oracle.Pinhole()
+    for K in (K_g, K_o):
+        K.fx = K.fy = 160.0
+        K.cx, K.cy, K.width, K.height = 160.0, 60.0, 320, 120
+        K.min_depth, K.max_depth = 0.5, 40.0
+    out_g = [x.cpu().numpy() for x in g.raycast(K_g, T, normals=True)]
+    out_o = o.raycast(K_o, T, normals=True)
+    check_raycast(out_g[0], out_o[0])
+    assert (out_o[0] > 0).mean() > 0.5
+    check_shading(out_g, out_o)
+    with pytest.raises(mrh().MrhError):
+        g.raycast(K_g, T, rgb=True)
 
 
 def test_lidar_full_scan():
