@@ -303,6 +303,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->observations = 0;
   st->updated_voxels = 0;
   st->n_over = 0;
+  st->item_next = 0;
 }
 
 }  // namespace

@@ -14,12 +14,29 @@ __global__ void __launch_bounds__(32 * kCamWarps, 4) k_fuse_depth(MapDev m, CamA
   fuse_warp_body<FP16, COLOR>(m, obs, warp, blockIdx.x * kCamWarps + warp, gridDim.x * kCamWarps);
 }
 
+// Items are handed out one per warp from a counter (zeroed when the frame begins), the level-1 and level-2 items
+// first: they hold the most observations per voxel and are the longest, so they must not start last.
 template <bool FP16, bool COLOR>
 __global__ void __launch_bounds__(32 * kLidarWarps) k_fuse_points(MapDev m) {
   __shared__ LidarSmem s_lidar;
   LidarObs<FP16> obs{&s_lidar, nullptr};
-  const int warp = threadIdx.x >> 5;
-  fuse_warp_body<FP16, COLOR>(m, obs, warp, blockIdx.x * kLidarWarps + warp, gridDim.x * kLidarWarps);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const ItemCounts ic = item_counts(m);
+  const uint32_t items = ic.items(), coarse = items - ic.it0;
+  unsigned long long my_obs = 0, my_vox = 0;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&m.st->item_next, 1u);
+    t = __shfl_sync(~0u, t, 0);
+    if (t >= items) break;
+    fuse_item<FP16, COLOR>(m, obs, warp, ic, t < coarse ? ic.it0 + t : t - coarse, my_obs, my_vox);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    my_obs += __shfl_xor_sync(~0u, my_obs, o);
+    my_vox += __shfl_xor_sync(~0u, my_vox, o);
+  }
+  if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
+  if (lane == 0 && my_vox) atomicAdd(&m.st->updated_voxels, my_vox);
 }
 
 // -------------------------------------------------------------------------------------------- LiDAR observation passes
@@ -282,7 +299,7 @@ void launch_lidar_observations(const MapDev& m, const double* T, const float* xy
 }
 
 void launch_fuse_points(const MapDev& m, const double*, const float*, uint64_t, cudaStream_t s, int sms) {
-  const int grid = sms * 16;  // 16 CTAs of 4 warps per SM over the items (measured best of 8 / 16 per SM)
+  const int grid = sms * 8;  // more CTAs than fit (5 per SM at 96 registers); the warps take items from a counter
   if (m.fp16) {
     if (m.color) k_fuse_points<true, true><<<grid, 32 * kLidarWarps, 0, s>>>(m);
     else k_fuse_points<true, false><<<grid, 32 * kLidarWarps, 0, s>>>(m);

@@ -214,7 +214,19 @@ struct LidarObs {
       r1 = r0 + m.blk_count[x.P];
       if (r1 > m.max_obs) r0 = r1 = 0;  // observations were not stored (status already set)
     }
-    for (uint32_t r = r0 + x.li; r < r1; r += x.G) atomicAdd(&off[x.g * x.nv + (m.obs_rec[r].x & 511u)], 1u);
+    {
+      // four independent record loads in flight before their shared-memory counts
+      const uint32_t base = (uint32_t)(x.g * x.nv);
+      uint32_t r = r0 + x.li;
+      for (; r + 3u * x.G < r1; r += 4u * x.G) {
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = m.obs_rec[r + k * x.G].x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(&off[base + (v[k] & 511u)], 1u);
+      }
+      for (; r < r1; r += x.G) atomicAdd(&off[base + (m.obs_rec[r].x & 511u)], 1u);
+    }
     __syncwarp();
     // counts -> exclusive offsets (16 consecutive bins per lane)
     uint32_t local[16], sum = 0;
@@ -237,10 +249,24 @@ struct LidarObs {
     if (lane == 31) off[512] = incl;
     recs = m.obs_bin + m.blk_off[x.P_first];
     __syncwarp();
-    for (uint32_t r = r0 + x.li; r < r1; r += x.G) {
-      const uint2 rec = m.obs_rec[r];
-      const uint32_t bin = x.g * x.nv + (rec.x & 511u);
-      recs[off[bin] + atomicAdd(&fill[bin], 1u)] = rec;
+    {
+      const uint32_t base = (uint32_t)(x.g * x.nv);
+      uint32_t r = r0 + x.li;
+      for (; r + 3u * x.G < r1; r += 4u * x.G) {
+        uint2 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = m.obs_rec[r + k * x.G];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t bin = base + (q[k].x & 511u);
+          recs[off[bin] + atomicAdd(&fill[bin], 1u)] = q[k];
+        }
+      }
+      for (; r < r1; r += x.G) {
+        const uint2 rec = m.obs_rec[r];
+        const uint32_t bin = base + (rec.x & 511u);
+        recs[off[bin] + atomicAdd(&fill[bin], 1u)] = rec;
+      }
     }
     if (lane == 0) sm->n_deferred[warp] = 0;
     __syncwarp();

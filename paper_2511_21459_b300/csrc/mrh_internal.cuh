@@ -76,6 +76,7 @@ struct DevState {
   unsigned long long updated_voxels;
   uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
   uint32_t n_over;     // LiDAR: points in stage_over
+  uint32_t item_next;  // LiDAR point fusion: next work item to hand out
 };
 
 // Everything a kernel needs, passed by value.
