@@ -11,6 +11,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   merge / split payloads       pinned on linear fields (exact); the rule itself is a reading: parity unpinned
   thresholds                   chosen values: parity unpinned
   raycast                      pinned: analytic plane / sphere depth; step constants are a reading
+  mesh (Marching Cubes)        pinned: case table against brute-force checks (triangle count of the plane cases,
+                               every inside corner cut off, orientation towards the outside); linear fields give
+                               vertices on the plane at every level; closed single-level surfaces are watertight
+                               with Euler characteristic 2; the resolution-boundary rule is a reading
   raycast normal / colour      pinned: a linear TSDF and colour field set block by block gives the plane's unit
                                normal and the colour field at the hit (trilinear is exact on linear fields);
                                analytic walls of a fused noise-free frame; constant-colour frames
@@ -75,6 +79,9 @@ def _load():
         lib.orc_integrate_points.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(FrameStats)]
         lib.orc_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp]
         lib.orc_set_block.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+        lib.orc_extract_mesh.restype = ctypes.c_int64
+        lib.orc_extract_mesh.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64]
+        lib.orc_mc_table.argtypes = [vp, vp, vp]
         lib.orc_count_blocks.restype = ctypes.c_int64
         lib.orc_count_blocks.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         lib.orc_extract.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -177,6 +184,14 @@ class OracleMap:
             return out
         return (out,) + ((nrm,) if normals else ()) + ((col,) if rgb else ())
 
+    def extract_mesh(self) -> np.ndarray:
+        """Multi-resolution Marching Cubes triangle soup (n, 3, 3) float32: blocks in key order, voxels in index
+        order, triangles facing increasing distance."""
+        n = self._lib.orc_extract_mesh(self._h, 1, None, 0)
+        out = np.zeros((n, 3, 3), np.float32)
+        self._lib.orc_extract_mesh(self._h, 0, _p(out), n)
+        return out
+
     def set_block(self, key, level: int, D, W, S2=None, C=None):
         """Test hook: create or overwrite block ``key`` at ``level`` with the given voxel payload (x fastest)."""
         nv = (8 >> level) ** 3
@@ -246,6 +261,20 @@ class OracleMap:
         self._lib.orc_block_stats(self._h, _p(out["keys"]), _p(out["levels"]), _p(out["vbar"]), _p(out["n_obs"]),
                                   _p(out["sum_w"]))
         return out
+
+
+def mc_table():
+    """The oracle's Marching Cubes case table: triangles per case (256,), edge triples (256, 12, 3) (-1 unused),
+    edge end corners (12, 2)."""
+    lib = _load()
+    nt = np.zeros(256, np.int32)
+    ed = np.zeros((256, 36), np.int8)
+    ec = np.zeros((12, 2), np.int8)
+    lib.orc_mc_table(_p(nt), _p(ed), _p(ec))
+    tri = ed.reshape(256, 12, 3).astype(np.int32)
+    for c in range(256):
+        tri[c, nt[c]:] = -1
+    return nt, tri, ec.astype(np.int32)
 
 
 def segment_cells(A, B, unit: int, mode: str = "bruteforce") -> np.ndarray:

@@ -286,6 +286,8 @@ struct MapBase {
   virtual int integrate_points(const double*, const float*, int64_t, orc_frame_stats*) = 0;
   virtual int raycast(const orc_pinhole*, const double*, float*, float*, uint8_t*) = 0;
   virtual int set_block(const int32_t*, int, const double*, const double*, const double*, const double*) = 0;
+  virtual void extract_mesh(std::vector<float>& tris) const = 0;
+  std::vector<float> mesh;  // last extracted triangle soup
   virtual int64_t count_blocks(int64_t* n_voxels) = 0;
   virtual int extract(int32_t*, uint8_t*, int64_t*, double*, double*, double*, double*) = 0;
   virtual int block_stats(int32_t*, uint8_t*, double*, int64_t*, int64_t*) = 0;
@@ -297,6 +299,80 @@ struct MapBase {
   bool capture = false;
   std::vector<Key> cap_keys;
   std::vector<float> cap_feat;
+};
+
+// ---- Marching Cubes case table (Lorensen and Cline's cube cases), built here from its definition rather than copied.
+// Corner c of a cell has offset (c & 1, (c >> 1) & 1, (c >> 2) & 1); a corner is inside when its value is below zero.
+// Edge 4a + r joins corner c0 and c0 | 1 << a, where c0 is the r-th corner (ascending) whose bit a is clear. On each
+// face the corners are walked counter-clockwise as seen from outside the cell; the surface crosses an edge where the
+// walk passes between an inside and an outside corner, and every crossing entering the inside is joined to the next
+// crossing (in walk order) leaving it, so that two diagonal inside corners of a face stay separated. Joined across the
+// six faces the segments close into loops, each fanned into triangles from its lowest edge; the triangles then face
+// the outside (increasing value).
+struct McTable {
+  int n_tris[256];
+  int8_t edges[256][36];
+  int8_t edge_corner[12][2];
+  McTable() {
+    int e = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int c0 = 0; c0 < 8; ++c0)
+        if (!((c0 >> a) & 1)) {
+          edge_corner[e][0] = (int8_t)c0;
+          edge_corner[e][1] = (int8_t)(c0 | (1 << a));
+          ++e;
+        }
+    auto edge_of = [&](int c0, int c1) {
+      for (int k = 0; k < 12; ++k)
+        if ((edge_corner[k][0] == c0 && edge_corner[k][1] == c1) || (edge_corner[k][0] == c1 && edge_corner[k][1] == c0))
+          return k;
+      return -1;
+    };
+    for (int cs = 0; cs < 256; ++cs) {
+      int next[12];
+      for (int k = 0; k < 12; ++k) next[k] = -1;
+      for (int a = 0; a < 3; ++a)
+        for (int side = 0; side < 2; ++side) {
+          const int u = (a + 1) % 3, w = (a + 2) % 3;
+          static const int ccw[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+          int q[4];
+          for (int i = 0; i < 4; ++i) {
+            const int* uw = side ? ccw[i] : ccw[(4 - i) % 4];
+            q[i] = (side << a) | (uw[0] << u) | (uw[1] << w);
+          }
+          int cross[4], enters[4], nc = 0;
+          for (int i = 0; i < 4; ++i) {
+            const int c0 = q[i], c1 = q[(i + 1) % 4];
+            const int in0 = (cs >> c0) & 1, in1 = (cs >> c1) & 1;
+            if (in0 != in1) {
+              cross[nc] = edge_of(c0, c1);
+              enters[nc] = in1;
+              ++nc;
+            }
+          }
+          for (int i = 0; i < nc; ++i)
+            if (enters[i]) next[cross[i]] = cross[(i + 1) % nc];
+        }
+      int nt = 0;
+      bool seen[12] = {false};
+      for (int k = 0; k < 12; ++k) {
+        if (next[k] < 0 || seen[k]) continue;
+        int loop[12], len = 0, f = k;
+        do {
+          seen[f] = true;
+          loop[len++] = f;
+          f = next[f];
+        } while (f != k);
+        for (int i = 1; i + 1 < len; ++i) {
+          edges[cs][3 * nt] = (int8_t)loop[0];
+          edges[cs][3 * nt + 1] = (int8_t)loop[i];
+          edges[cs][3 * nt + 2] = (int8_t)loop[i + 1];
+          ++nt;
+        }
+      }
+      n_tris[cs] = nt;
+    }
+  }
 };
 
 template <class R, class Sto>
@@ -942,6 +1018,107 @@ struct Map : MapBase {
     return 0;
   }
 
+  // ---- multi-resolution Marching Cubes (Sec. 3.4, Figs. 5 and 6). Reading: positions are
+  // integers in units of half a finest voxel (a block edge is 2 n_0 units; a level-l voxel centre lies at an odd
+  // multiple of 2^l). Every voxel of every block is the low corner of one cell, which runs along each axis to the next
+  // voxel centre: inside the block one voxel further; from the block's last voxel, to the first centre of the
+  // neighbouring block (half a voxel of each level), so a coarse cell next to a finer block is cut short and the two
+  // blocks' cells tile space without overlap (the "truncated" coarse voxels); no cell where that neighbour is
+  // missing. A cell corner's value is the trilinear field at the corner on the grid of the block that contains it,
+  // each of the 8 nearest centres read from the voxel that contains it, whatever its block's level (coarse and fine
+  // values blend across resolution boundaries); corners of zero weight are not read. A cell with an unallocated or
+  // unobserved corner read emits nothing. The surface crossing on an edge is linear between its two corner values.
+  bool mc_value(const int64_t P[3], R* out) const {
+    const int64_t bu = 2 * kFineDim;
+    const Block<R, Sto>* b = find(Key{floor_div(P[0], bu), floor_div(P[1], bu), floor_div(P[2], bu)});
+    if (!b) return false;
+    const int64_t s = (int64_t)1 << b->level, s2 = 2 * s;
+    int64_t j0[3];
+    R fr[3];
+    for (int a = 0; a < 3; ++a) {
+      const int64_t g = P[a] - s;
+      j0[a] = floor_div(g, s2);
+      fr[a] = (R)(g - j0[a] * s2) / (R)s2;
+    }
+    R acc = 0;
+    for (int k = 0; k < 8; ++k) {
+      const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+      const R wx = ax ? fr[0] : (R)1 - fr[0];
+      const R wy = ay ? fr[1] : (R)1 - fr[1];
+      const R wz = az ? fr[2] : (R)1 - fr[2];
+      const R w = (wx * wy) * wz;
+      if (w == (R)0) continue;
+      const int bit[3] = {ax, ay, az};
+      int64_t C[3];
+      for (int a = 0; a < 3; ++a) C[a] = (2 * (j0[a] + bit[a]) + 1) * s;
+      const Key kc{floor_div(C[0], bu), floor_div(C[1], bu), floor_div(C[2], bu)};
+      const Block<R, Sto>* bc = find(kc);
+      if (!bc) return false;
+      const int64_t vu = (int64_t)2 << bc->level;
+      const int nb = n[bc->level];
+      const size_t idx = vox(nb, (int)((C[0] - kc.x * bu) / vu), (int)((C[1] - kc.y * bu) / vu),
+                             (int)((C[2] - kc.z * bu) / vu));
+      if (!(bc->W[idx] > (R)0)) return false;
+      acc = acc + w * (R)Store<Sto>::get(bc->D[idx]);
+    }
+    *out = acc;
+    return true;
+  }
+
+  // triangle soup, 9 coordinates per triangle, blocks in key order and voxels in index order
+  void extract_mesh(std::vector<float>& tris) const {
+    static const McTable tab;
+    const int64_t bu = 2 * kFineDim;
+    const R unit = (R)(E_f / (float)bu);
+    for (const Key& k : sorted_keys()) {
+      const Block<R, Sto>& b = blocks.at(k);
+      const int l = b.level, nl = n[l];
+      const int64_t s = (int64_t)1 << l;
+      const int64_t K[3] = {k.x, k.y, k.z};
+      int64_t h_last[3];
+      bool ok_last[3];
+      for (int a = 0; a < 3; ++a) {
+        Key nk = k;
+        if (a == 0) nk.x += 1; else if (a == 1) nk.y += 1; else nk.z += 1;
+        const Block<R, Sto>* nb = find(nk);
+        ok_last[a] = nb != nullptr;
+        h_last[a] = nb ? s + ((int64_t)1 << nb->level) : 0;
+      }
+      for (int iz = 0; iz < nl; ++iz)
+        for (int iy = 0; iy < nl; ++iy)
+          for (int ix = 0; ix < nl; ++ix) {
+            const int i[3] = {ix, iy, iz};
+            int64_t c[3], h[3];
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+              c[a] = K[a] * bu + (2 * i[a] + 1) * s;
+              if (i[a] < nl - 1) h[a] = 2 * s;
+              else { h[a] = h_last[a]; ok = ok && ok_last[a]; }
+            }
+            if (!ok) continue;
+            R F[8];
+            int64_t P[8][3];
+            int cs = 0;
+            for (int o = 0; o < 8 && ok; ++o) {
+              for (int a = 0; a < 3; ++a) P[o][a] = c[a] + ((o >> a) & 1) * h[a];
+              ok = mc_value(P[o], &F[o]);
+              if (ok && F[o] < (R)0) cs |= 1 << o;
+            }
+            if (!ok) continue;
+            for (int t = 0; t < tab.n_tris[cs]; ++t)
+              for (int q = 0; q < 3; ++q) {
+                const int e = tab.edges[cs][3 * t + q];
+                const int c0 = tab.edge_corner[e][0], c1 = tab.edge_corner[e][1];
+                const R f = F[c0] / (F[c0] - F[c1]);
+                for (int a = 0; a < 3; ++a) {
+                  const R pa = (R)P[c0][a] * unit, pb = (R)P[c1][a] * unit;
+                  tris.push_back((float)(pa + f * (pb - pa)));
+                }
+              }
+          }
+    }
+  }
+
   // ---- read-out, sorted by key (x, then y, then z)
   std::vector<Key> sorted_keys() const {
     std::vector<Key> ks;
@@ -1056,6 +1233,33 @@ int orc_raycast(void* h, const orc_pinhole* K, const double* T_wc, float* depth_
 int orc_set_block(void* h, const int32_t* key, int level, const double* D, const double* W, const double* S2,
                   const double* C) {
   return ((MapBase*)h)->set_block(key, level, D, W, S2, C);
+}
+
+// Extract the mesh; returns the triangle count. out (9 floats per triangle) may be NULL or smaller (cap triangles):
+// the extraction is kept and later calls with out != NULL and extract == 0 copy it.
+int64_t orc_extract_mesh(void* h, int extract, float* out, int64_t cap) {
+  MapBase* m = (MapBase*)h;
+  if (extract) {
+    m->mesh.clear();
+    m->extract_mesh(m->mesh);
+  }
+  const int64_t nt = (int64_t)(m->mesh.size() / 9);
+  if (out)
+    for (int64_t i = 0; i < 9 * std::min(nt, cap); ++i) out[i] = m->mesh[(size_t)i];
+  return nt;
+}
+
+// the case table (test hook): n_tris[256], edges[256 * 36], edge corners[24]
+void orc_mc_table(int* n_tris, int8_t* edges, int8_t* edge_corner) {
+  static const McTable t;
+  for (int c = 0; c < 256; ++c) {
+    n_tris[c] = t.n_tris[c];
+    for (int i = 0; i < 36; ++i) edges[36 * c + i] = t.edges[c][i];
+  }
+  for (int e = 0; e < 12; ++e) {
+    edge_corner[2 * e] = t.edge_corner[e][0];
+    edge_corner[2 * e + 1] = t.edge_corner[e][1];
+  }
 }
 
 int64_t orc_count_blocks(void* h, int64_t* n_voxels) { return ((MapBase*)h)->count_blocks(n_voxels); }
