@@ -108,7 +108,8 @@ enum {
   MRH_K_FUSE = 4,      /* fusion + block variance + re-levelling */
   MRH_K_RELEASE = 5,   /* freed heap blocks back to their free stacks */
   MRH_K_RAYCAST = 6,   /* raycast */
-  MRH_K_COUNT = 7
+  MRH_K_MESH = 7,      /* Marching Cubes mesh extraction */
+  MRH_K_COUNT = 8
 };
 
 /* Create a map on CUDA device `device`. Allocates the hash table, one block heap per level and per-frame lists.
@@ -254,6 +255,23 @@ mrh_status mrh_mlp_get_weights(const mrh_mlp* mlp, float* master_host, uint16_t*
  * Asynchronous on `stream`. */
 mrh_status mrh_raycast(mrh_map* map, const mrh_pinhole* K, const double* T_wc_host, float* depth_out_dev,
                        float* normal_out_dev, uint8_t* rgb_out_dev, void* stream);
+
+/* Multi-resolution Marching Cubes over every allocated block (Sec. 3.4, Figs. 5 and 6). Output: triangles as 9
+ * float32 each (three vertices x, y, z in metres, counter-clockwise seen from the side of positive distance), in no
+ * particular order, written to tris_dev (device; NULL with capacity 0 only counts); n_tris_out receives the number of
+ * triangles. MRH_ERR_CAPACITY when that number exceeds capacity (the first `capacity` triangles written are then
+ * some subset). Cells: every voxel is the low corner of one cell reaching the next voxel centres along +x, +y, +z; the
+ * cells of a block's last voxels reach the first centre of the neighbouring block (so coarse cells next to finer
+ * blocks are shortened and the levels tile space), and there is none where that neighbour is missing. Cell corners take
+ * the trilinear field on the grid of the block containing them (reading voxels of any level); cells with an
+ * unallocated or unobserved corner read emit nothing. The case table is Marching Cubes' (inside = value below zero),
+ * with the two inside corners of an ambiguous face kept apart. Synchronises `stream`. */
+mrh_status mrh_extract_mesh(mrh_map* map, float* tris_dev, uint64_t capacity, uint64_t* n_tris_out, void* stream);
+
+/* The case table used by mrh_extract_mesh (host, no device work): ntri[256] triangles per case, tri[256 * 15] edge
+ * triples (-1 unused), edge_end[12 * 2] corner pairs. Corner c lies at (c & 1, c >> 1 & 1, c >> 2 & 1) of the cell;
+ * edge 4a + r joins the r-th corner (ascending) with bit a clear to its neighbour along axis a. */
+void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
 
 /* Number of allocated blocks and voxels (synchronises `stream`). */
 mrh_status mrh_count_blocks(mrh_map* map, uint64_t* n_blocks, uint64_t* n_voxels, void* stream);

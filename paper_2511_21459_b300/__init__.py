@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
         return d
 
 
-KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast"]
+KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast", "mesh"]
 
 MRH_BATCH_GRAPH, MRH_BATCH_AUTOTUNE = 1, 2
 
@@ -76,7 +76,7 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
-           "mrh_version"]
+           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -97,6 +97,9 @@ def lib():
         L.mrh_integrate_points.argtypes = [vp, vp, vp, u64, vp]
         L.mrh_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp, vp]
         L.mrh_count_blocks.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
+        L.mrh_extract_mesh.argtypes = [vp, vp, u64, ctypes.POINTER(u64), vp]
+        L.mrh_mesh_case_table.argtypes = [vp, vp, vp]
+        L.mrh_mesh_case_table.restype = None
         L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
                                          ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks_noalloc.argtypes = L.mrh_extract_blocks.argtypes
@@ -143,6 +146,18 @@ def _check(code: int, what: str, allow=()):
     if code != 0 and code not in allow:
         err = lib().mrh_last_cuda_error().decode()
         raise MrhError(code, what + (f" [{err}]" if code == 6 and err else ""))
+
+
+def mesh_case_table():
+    """The library's Marching Cubes case table (host, no GPU needed): triangles per case (256,), edge triples
+    (256, 5, 3) (-1 unused), edge end corners (12, 2)."""
+    import numpy as np
+    nt = np.zeros(256, np.uint8)
+    tri = np.zeros((256, 15), np.int8)
+    ec = np.zeros((12, 2), np.int8)
+    lib().mrh_mesh_case_table(ctypes.c_void_p(nt.ctypes.data), ctypes.c_void_p(tri.ctypes.data),
+                              ctypes.c_void_p(ec.ctypes.data))
+    return nt.astype(np.int32), tri.reshape(256, 5, 3).astype(np.int32), ec.astype(np.int32)
 
 
 def _ptr(t):
@@ -255,6 +270,21 @@ class Map:
         if nrm is None and col is None:
             return out
         return (out,) + ((nrm,) if nrm is not None else ()) + ((col,) if col is not None else ())
+
+    def extract_mesh(self, capacity=None, stream=None):
+        """Multi-resolution Marching Cubes triangles (n, 3, 3) float32 CUDA tensor (vertices in metres, counter-clockwise
+        seen from positive distance, in no particular order). With capacity None the call counts first, then
+        allocates exactly; otherwise MrhError (capacity) when the mesh has more triangles."""
+        import torch
+        n = ctypes.c_uint64()
+        if capacity is None:
+            _check(self._lib.mrh_extract_mesh(self._h, None, 0, ctypes.byref(n), _stream(stream)), "mrh_extract_mesh",
+                   allow=(7,))
+            capacity = n.value
+        out = torch.empty((max(int(capacity), 1), 3, 3), dtype=torch.float32, device=f"cuda:{self.device}")
+        _check(self._lib.mrh_extract_mesh(self._h, ctypes.c_void_p(out.data_ptr()), int(capacity), ctypes.byref(n),
+                                          _stream(stream)), "mrh_extract_mesh")
+        return out[:n.value]
 
     def count(self, stream=None):
         nb, nv = ctypes.c_uint64(), ctypes.c_uint64()

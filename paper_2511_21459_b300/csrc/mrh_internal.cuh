@@ -77,6 +77,7 @@ struct DevState {
   uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
   uint32_t n_over;     // LiDAR: points in stage_over
   uint32_t item_next;  // LiDAR point fusion: next work item to hand out
+  unsigned long long mesh_tris;  // triangles counted by the last mesh extraction
 };
 
 // Everything a kernel needs, passed by value.
@@ -424,5 +425,9 @@ void launch_lidar_observations(const MapDev& m, const double* T, const float* xy
                                int sms);
 void launch_raycast(const MapDev& m, const CamArgs& c, float* depth, float* normal, uint8_t* rgb,
                    cudaStream_t s);
+// multi-resolution Marching Cubes (mrh_mesh.cu): the case table is uploaded once per device
+cudaError_t mesh_table_ready(int device);
+void host_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
+void launch_mesh(const MapDev& m, float* tris, uint64_t cap, unsigned long long* count, cudaStream_t s, int sms);
 
 }  // namespace mrh

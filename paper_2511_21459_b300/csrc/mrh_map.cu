@@ -671,6 +671,30 @@ mrh_status mrh_raycast(mrh_map* m, const mrh_pinhole* K, const double* T_wc, flo
   return MRH_OK;
 }
 
+mrh_status mrh_extract_mesh(mrh_map* m, float* tris, uint64_t capacity, uint64_t* n_tris_out, void* stream) {
+  if (!m || !n_tris_out || (capacity > 0 && !tris)) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  const cudaError_t te = mesh_table_ready(m->device);
+  if (te != cudaSuccess) return cuda_fail(te, "mesh case table");
+  const cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* count = &m->d.st->mesh_tris;
+  MRH_CUDA(cudaMemsetAsync(count, 0, sizeof(*count), s));
+  {
+    KernelScope ks(m, MRH_K_MESH, s, 1);
+    launch_mesh(m->d, tris, capacity, count, s, m->sms);
+  }
+  MRH_CUDA(cudaGetLastError());
+  unsigned long long n = 0;
+  MRH_CUDA(cudaMemcpyAsync(&n, count, sizeof(n), cudaMemcpyDeviceToHost, s));
+  MRH_CUDA(cudaStreamSynchronize(s));
+  *n_tris_out = n;
+  return n > capacity ? MRH_ERR_CAPACITY : MRH_OK;
+}
+
+void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {
+  if (ntri && tri && edge_end) host_case_table(ntri, tri, edge_end);
+}
+
 mrh_status mrh_count_blocks(mrh_map* m, uint64_t* n_blocks, uint64_t* n_voxels, void* stream) {
   if (!m) return MRH_ERR_INVALID_ARG;
   DeviceGuard guard(m->device);

@@ -1,0 +1,315 @@
+// Multi-resolution Marching Cubes over every allocated block of a map (Sec. 3.4, Figs. 5 and 6).
+//
+// Positions are integers in units of half a finest voxel: a block edge is 16 units and a level-l voxel centre lies at
+// an odd multiple of 2^l. Every voxel is the low corner of one cell that runs, along each axis, to the next voxel
+// centre: one voxel further inside its block; from the block's last voxel, to the first centre of the neighbouring
+// block, half a voxel of each level away. A coarse cell next to a finer block is therefore cut short (the truncated
+// coarse voxels of Fig. 6) and the cells of neighbouring blocks tile space without overlap; there is no cell where
+// that neighbour is missing. A cell corner takes the trilinear field of the block that contains it, on that block's
+// grid, each of the 8 nearest centres read from the voxel that contains it whatever its block's level (coarse and fine
+// values blend across the boundary, Fig. 5); corners of zero weight are not read, and a cell with an unallocated or
+// unobserved read emits nothing. The surface crosses a cell edge where it is linear between the corner values.
+//
+// One warp per allocated block: lanes take the block's cells in index order; a cell whose corners all lie in its own
+// block (the interior) reads them straight from the payload, the others evaluate the field with hash lookups. Each
+// warp reserves its triangles with one atomic per pass over 32 cells. Compiled without multiply-add contraction, so
+// every vertex is the float result of the same operations the oracle performs.
+#include <cuda_fp16.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "mrh_internal.cuh"
+
+namespace mrh {
+namespace {
+
+// ---- case table: triangles per case (at most 5) as edge triples; corner c sits at (c & 1, c >> 1 & 1, c >> 2 & 1)
+// and is inside when its value is below zero; edge 4a + r joins the r-th corner (ascending) with bit a clear to its
+// neighbour along a.
+__constant__ uint8_t c_ntri[256];
+__constant__ int8_t c_tri[256][15];
+__constant__ int8_t c_edge_end[12][2];
+
+struct CaseTable {
+  uint8_t ntri[256];
+  int8_t tri[256][15];
+  int8_t edge_end[12][2];
+  bool ok = true;
+};
+
+// Built on the host from the definition: each face's corners are walked counter-clockwise as seen from outside the
+// cell; a crossing where the walk enters the inside is joined to the next crossing where it leaves (so two diagonal
+// inside corners of a face are cut off separately); the joined segments of the six faces close into loops, taken in
+// order of their lowest edge and fanned into triangles from it.
+CaseTable make_case_table() {
+  CaseTable t;
+  int edge_id[8][8];
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) edge_id[i][j] = -1;
+  int ne = 0;
+  for (int axis = 0; axis < 3; ++axis)
+    for (int lo = 0; lo < 8; ++lo) {
+      if (lo & (1 << axis)) continue;
+      const int hi = lo | (1 << axis);
+      t.edge_end[ne][0] = (int8_t)lo;
+      t.edge_end[ne][1] = (int8_t)hi;
+      edge_id[lo][hi] = edge_id[hi][lo] = ne;
+      ++ne;
+    }
+  // the 6 faces as corner cycles, counter-clockwise seen from outside: for the face at coordinate `side` of axis a,
+  // with p = a + 1 and q = a + 2 (mod 3), the cycle (0,0) (1,0) (1,1) (0,1) in (p, q) faces +a, its reverse -a
+  int face[6][4];
+  for (int a = 0; a < 3; ++a) {
+    const int p = (a + 1) % 3, q = (a + 2) % 3;
+    const int pq[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+    for (int side = 0; side < 2; ++side)
+      for (int k = 0; k < 4; ++k) {
+        const int* c = pq[side ? k : (4 - k) & 3];
+        face[2 * a + side][k] = (side << a) | (c[0] << p) | (c[1] << q);
+      }
+  }
+  for (int cs = 0; cs < 256; ++cs) {
+    int link[12];
+    for (int e = 0; e < 12; ++e) link[e] = -1;
+    for (int f = 0; f < 6; ++f) {
+      int at[4], into[4], n = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int c0 = face[f][k], c1 = face[f][(k + 1) & 3];
+        const bool in0 = (cs >> c0) & 1, in1 = (cs >> c1) & 1;
+        if (in0 == in1) continue;
+        at[n] = edge_id[c0][c1];
+        into[n] = in1 ? 1 : 0;
+        ++n;
+      }
+      for (int k = 0; k < n; ++k)
+        if (into[k]) link[at[k]] = at[(k + 1) % n];
+    }
+    int nt = 0;
+    bool used[12] = {};
+    for (int e0 = 0; e0 < 12; ++e0) {
+      if (link[e0] < 0 || used[e0]) continue;
+      int ring[12], len = 0;
+      for (int e = e0; !used[e]; e = link[e]) {
+        used[e] = true;
+        ring[len++] = e;
+        if (link[e] < 0) {
+          t.ok = false;
+          break;
+        }
+      }
+      for (int k = 1; k + 1 < len; ++k) {
+        if (nt >= 5) {
+          t.ok = false;
+          break;
+        }
+        t.tri[cs][3 * nt] = (int8_t)ring[0];
+        t.tri[cs][3 * nt + 1] = (int8_t)ring[k];
+        t.tri[cs][3 * nt + 2] = (int8_t)ring[k + 1];
+        ++nt;
+      }
+    }
+    for (int k = 3 * nt; k < 15; ++k) t.tri[cs][k] = -1;
+    t.ntri[cs] = (uint8_t)nt;
+  }
+  return t;
+}
+
+// ---- device side
+
+__device__ inline uint32_t block_val(const MapDev& m, int x, int y, int z) {
+  const int lim = (int)kKeyLimit;
+  if (x < -lim || x > lim || y < -lim || y > lim || z < -lim || z > lim) return kValPending;
+  const int s = lookup_slot(m.slots, m.slot_mask, pack_key(x, y, z));
+  return s >= 0 ? m.slots[s].val : kValPending;
+}
+
+__device__ inline const uint8_t* payload(const MapDev& m, uint32_t val) {
+  const int l = (int)((val >> 28) & 3u);
+  return m.heap[l] + (size_t)(val & kPtrMask) * m.block_bytes[l];
+}
+
+template <bool FP16>
+__device__ inline float voxel_D(const uint8_t* blk, int i) {
+  if (FP16) return __half2float(reinterpret_cast<const __half*>(blk)[i]);
+  return reinterpret_cast<const float*>(blk)[i];
+}
+
+// trilinear field at the unit point P on the grid of the block containing it (see the file comment)
+template <bool FP16, bool COLOR>
+__device__ bool corner_value(const MapDev& m, const int P[3], float* out) {
+  const uint32_t v = block_val(m, P[0] >> 4, P[1] >> 4, P[2] >> 4);
+  if (v == kValPending) return false;
+  const int lp = (int)((v >> 28) & 3u);
+  const int s = 1 << lp, s2 = 2 * s;
+  int j0[3];
+  float fr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int g = P[a] - s;
+    j0[a] = g >> (lp + 1);
+    fr[a] = (float)(g - j0[a] * s2) / (float)s2;
+  }
+  float acc = 0.0f;
+  int cx = 0x7FFFFFFF, cy = 0, cz = 0;  // last block looked up, and its value
+  uint32_t cv = kValPending;
+  for (int k = 0; k < 8; ++k) {
+    const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+    const float wx = ax ? fr[0] : 1.0f - fr[0];
+    const float wy = ay ? fr[1] : 1.0f - fr[1];
+    const float wz = az ? fr[2] : 1.0f - fr[2];
+    const float w = (wx * wy) * wz;
+    if (w == 0.0f) continue;
+    const int C[3] = {(2 * (j0[0] + ax) + 1) * s, (2 * (j0[1] + ay) + 1) * s, (2 * (j0[2] + az) + 1) * s};
+    const int kx = C[0] >> 4, ky = C[1] >> 4, kz = C[2] >> 4;
+    if (kx != cx || ky != cy || kz != cz) {
+      cx = kx;
+      cy = ky;
+      cz = kz;
+      cv = block_val(m, kx, ky, kz);
+    }
+    if (cv == kValPending) return false;
+    const int lb = (int)((cv >> 28) & 3u), nb = kFineDim >> lb, sh = lb + 1;
+    const int idx = ((C[0] - kx * 16) >> sh) + nb * (((C[1] - ky * 16) >> sh) + nb * ((C[2] - kz * 16) >> sh));
+    const uint8_t* blk = payload(m, cv);
+    if (!(reinterpret_cast<const float*>(blk + off_W(nb * nb * nb, FP16, COLOR))[idx] > 0.0f)) return false;
+    acc = acc + w * voxel_D<FP16>(blk, idx);
+  }
+  *out = acc;
+  return true;
+}
+
+struct MeshOut {
+  float* tris;
+  unsigned long long cap;
+  unsigned long long* count;
+};
+
+template <bool FP16, bool COLOR>
+__global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nslots = m.slot_mask + 1;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const float unit = m.E / 16.0f;
+  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; base < nslots; base += nw * 32u) {
+    const uint32_t sl = base + lane;
+    const unsigned long long key_l = sl < nslots ? m.slots[sl].key : kEmptyKey;
+    const uint32_t val_l = sl < nslots ? m.slots[sl].val : kValPending;
+    unsigned live = __ballot_sync(~0u, key_l != kEmptyKey && val_l != kValPending);
+    while (live) {
+      const int src = __ffs(live) - 1;
+      live &= live - 1;
+      const unsigned long long key = __shfl_sync(~0u, key_l, src);
+      const uint32_t val = __shfl_sync(~0u, val_l, src);
+      int K[3];
+      unpack_key(key, &K[0], &K[1], &K[2]);
+      const int l = (int)((val >> 28) & 3u), nl = kFineDim >> l, nv = nl * nl * nl, s = 1 << l;
+      const uint8_t* blk = payload(m, val);
+      const float* Wb = reinterpret_cast<const float*>(blk + off_W(nv, FP16, COLOR));
+      // extent of the cells of the last voxel along each axis: to the first centre of the neighbouring block
+      int h_last = 0;
+      if (lane < 3) {
+        const uint32_t nvl = block_val(m, K[0] + (lane == 0), K[1] + (lane == 1), K[2] + (lane == 2));
+        h_last = nvl == kValPending ? 0 : s + (1 << ((nvl >> 28) & 3u));
+      }
+      const int hl[3] = {__shfl_sync(~0u, h_last, 0), __shfl_sync(~0u, h_last, 1), __shfl_sync(~0u, h_last, 2)};
+      for (int c0 = 0; c0 < nv; c0 += 32) {
+        const int cell = c0 + lane;
+        int i[3] = {cell % nl, (cell / nl) % nl, cell / (nl * nl)};
+        int c[3], h[3];
+        bool ok = cell < nv;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          c[a] = K[a] * 16 + (2 * i[a] + 1) * s;
+          h[a] = i[a] < nl - 1 ? 2 * s : hl[a];
+          ok = ok && h[a] > 0;
+        }
+        float F[8];
+        int cs = 0;
+        if (ok) {
+          const bool interior = i[0] < nl - 1 && i[1] < nl - 1 && i[2] < nl - 1;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (!ok) break;
+            const int ox = q & 1, oy = (q >> 1) & 1, oz = q >> 2;
+            if (interior) {
+              const int idx = (i[0] + ox) + nl * ((i[1] + oy) + nl * (i[2] + oz));
+              ok = Wb[idx] > 0.0f;
+              F[q] = voxel_D<FP16>(blk, idx);
+            } else {
+              const int P[3] = {c[0] + ox * h[0], c[1] + oy * h[1], c[2] + oz * h[2]};
+              ok = corner_value<FP16, COLOR>(m, P, &F[q]);
+            }
+            if (ok && F[q] < 0.0f) cs |= 1 << q;
+          }
+        }
+        const int nt = ok ? (int)c_ntri[cs] : 0;
+        // reserve this pass's triangles with one atomic
+        int incl = nt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(~0u, incl, d);
+          if (lane >= d) incl += y;
+        }
+        unsigned long long first = 0;
+        if (lane == 31 && incl > 0) first = atomicAdd(o.count, (unsigned long long)incl);
+        first = __shfl_sync(~0u, first, 31) + (unsigned long long)(incl - nt);
+        for (int t = 0; t < nt; ++t) {
+          if (first + t >= o.cap) break;
+          float* dst = o.tris + 9 * (first + t);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const int e = c_tri[cs][3 * t + q];
+            const int ca = c_edge_end[e][0], cb = c_edge_end[e][1];
+            const float f = F[ca] / (F[ca] - F[cb]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const float pa = (float)(c[a] + ((ca >> a) & 1) * h[a]) * unit;
+              const float pb = (float)(c[a] + ((cb >> a) & 1) * h[a]) * unit;
+              dst[3 * q + a] = pa + f * (pb - pa);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+std::mutex g_table_mutex;
+bool g_table_on[64] = {};
+
+}  // namespace
+
+cudaError_t mesh_table_ready(int device) {
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (g_table_on[device]) return cudaSuccess;
+  static const CaseTable t = make_case_table();
+  if (!t.ok) return cudaErrorUnknown;
+  cudaError_t e = cudaMemcpyToSymbol(c_ntri, t.ntri, sizeof(t.ntri));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tri, t.tri, sizeof(t.tri));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_edge_end, t.edge_end, sizeof(t.edge_end));
+  if (e == cudaSuccess) g_table_on[device] = true;
+  return e;
+}
+
+void host_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {
+  static const CaseTable t = make_case_table();
+  std::memcpy(ntri, t.ntri, sizeof(t.ntri));
+  std::memcpy(tri, t.tri, sizeof(t.tri));
+  std::memcpy(edge_end, t.edge_end, sizeof(t.edge_end));
+}
+
+void launch_mesh(const MapDev& m, float* tris, uint64_t cap, unsigned long long* count, cudaStream_t s, int sms) {
+  const MeshOut o{tris, (unsigned long long)cap, count};
+  const int grid = sms * 8;
+  if (m.fp16) {
+    if (m.color) k_mesh<true, true><<<grid, 256, 0, s>>>(m, o);
+    else k_mesh<true, false><<<grid, 256, 0, s>>>(m, o);
+  } else {
+    if (m.color) k_mesh<false, true><<<grid, 256, 0, s>>>(m, o);
+    else k_mesh<false, false><<<grid, 256, 0, s>>>(m, o);
+  }
+}
+
+}  // namespace mrh

@@ -95,3 +95,16 @@ def test_invalid_params_rejected_before_any_device_call(lib):
         setattr(q, field, value)
         assert lib.mrh_map_create(ctypes.byref(q), 0, ctypes.byref(h)) == 1, field
     assert lib.mrh_map_create(None, 0, ctypes.byref(h)) == 1
+
+
+def test_mesh_case_table_matches_the_oracles(lib):
+    """The library builds its Marching Cubes case table on the host (no GPU call); it is an independent second
+    construction from the same definition as the oracle's, so the two must agree entry for entry."""
+    import numpy as np
+    import oracle
+    nt_g, tri_g, ec_g = mrh.mesh_case_table()
+    nt_o, tri_o, ec_o = oracle.mc_table()
+    assert np.array_equal(ec_g, ec_o)
+    assert np.array_equal(nt_g, nt_o)
+    for c in range(256):
+        assert np.array_equal(tri_g[c, :nt_g[c]], tri_o[c, :nt_o[c]]), c
