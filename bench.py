@@ -49,9 +49,10 @@ def parse_args():
     ap.add_argument("--no-lidar", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-mesh", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
-    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned"], default=None,
+    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh"], default=None,
                     help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
     return ap.parse_args()
 
@@ -77,6 +78,18 @@ def profile_case(kind: str) -> int:
             st = m.stats()
             print(json.dumps({"frame": k, "touched_level": st["touched_level"], "new_blocks": st["new_blocks"],
                               "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
+    elif kind == "mesh":
+        wl = synth.rgbd()
+        wl.max_blocks = (1 << 16, 1 << 14, 1 << 14)
+        m = mrh.Map(mrh.params_from(wl))
+        K = mrh.pinhole_from(wl)
+        for d, c, T in camera_frames(wl, 0, 30)[::5]:
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        for _ in range(3):
+            t = m.extract_mesh()
+        st = m.stats()
+        print(json.dumps({"triangles": int(t.shape[0]), "live_blocks": st["live_blocks"],
+                          "mesh_algorithmic_bytes": mesh_bytes(st, wl, int(t.shape[0]))}))
     elif kind == "lidar":
         wl = synth.lidar()
         wl.max_blocks = (1 << 18, 1 << 16, 1 << 16)
@@ -469,6 +482,59 @@ def run_camera_e2e(wl, frames, warmup, steps):
     return ms, h2d, d2h
 
 
+def mesh_bytes(stats, wl, n_tris):
+    """Algorithmic bytes of one mesh extraction: every voxel's distance and weight read once, 36 B per triangle."""
+    per_voxel = (2 if wl.fp16 else 4) + 4
+    voxels = sum(n * (8 >> l) ** 3 for l, n in enumerate(stats["live_blocks"]))
+    return voxels * per_voxel + 36 * n_tris
+
+
+def run_mesh(wl, m, reps=5, prefix=(0, 10, 20, 30)):
+    """Multi-resolution Marching Cubes (Sec. 3.4): the whole map the benchmark built (device time of the extraction
+    kernel, from the library's event profiler, average of `reps`), and a small map of the sequence's frames `prefix`
+    on the GPU and in the oracle (one thread), the same triangles timed on both."""
+    import torch
+    import oracle
+    import paper_2511_21459_b300 as mrh
+    n = len(m.extract_mesh())
+    m.set_profiling(True)
+    m.profile(reset=True)
+    for _ in range(reps):
+        m.extract_mesh(capacity=n)
+    torch.cuda.synchronize()
+    kms = m.profile()["mesh"][0] / reps
+    st = m.stats()
+    b = mesh_bytes(st, wl, n)
+    full = {"triangles": n, "ms": round(kms, 4), "triangles_per_s": n / (kms / 1000.0),
+            "algorithmic_bytes": b, "achieved_GBps": round(b / (kms / 1000.0) / 1e9, 1),
+            "live_blocks": st["live_blocks"]}
+    # the same small map on both sides
+    scene = wl.scene()
+    frames = [synth.render_depth(wl, k, scene=scene) for k in prefix]
+    g = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
+    o = oracle.OracleMap(oracle.params_from(wl, "f32s"))
+    Kg, Ko = mrh.pinhole_from(wl), oracle.pinhole_from(wl)
+    for d, c, T in frames:
+        g.integrate_depth(Kg, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        o.integrate_depth(Ko, T, d, c)
+    ng = len(g.extract_mesh())
+    g.set_profiling(True)
+    g.profile(reset=True)
+    for _ in range(reps):
+        g.extract_mesh(capacity=ng)
+    torch.cuda.synchronize()
+    gms = g.profile()["mesh"][0] / reps
+    t0 = time.perf_counter()
+    no = len(o.extract_mesh())
+    cms = 1000.0 * (time.perf_counter() - t0)
+    g.close()
+    o.close()
+    small = {"frames": list(prefix), "triangles_gpu": ng, "triangles_oracle": no, "gpu_ms": round(gms, 4),
+             "oracle_ms_1_thread": round(cms, 1), "gpu_triangles_per_s": ng / (gms / 1000.0),
+             "oracle_triangles_per_s": no / (cms / 1000.0)}
+    return {"full_map": full, "prefix_map": small}
+
+
 def run_lidar_gpu(wl, warmup, steps, flush):
     import torch
     import paper_2511_21459_b300 as mrh
@@ -700,10 +766,11 @@ def main():
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    res = run_camera_gpu(wl, frames, args.warmup, args.steps, flush)
+    res = run_camera_gpu(wl, frames, args.warmup, args.steps, flush, keep=True)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
+    main_map = res.pop("map")
 
     ms_max = max_over_ranks(res["ms"], world)
     rays_all = sum_over_ranks(res["rays"], world)
@@ -740,6 +807,11 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps,
                "note": "pinned host frames uploaded and raycast depth, normals and colours read back every step on a "
                        "second stream, overlapping the neighbouring frames' kernels; no L2 flush between steps"}
+
+    mesh = None
+    if rank == 0 and not args.no_mesh:
+        mesh = run_mesh(wl, main_map)
+    main_map.close()
 
     lidar = None
     if not args.no_lidar:
@@ -787,7 +859,7 @@ def main():
                 "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
-                "lidar": lidar, "batched": batched, "learned": learned}
+                "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -10,9 +10,9 @@
 // values blend across the boundary, Fig. 5); corners of zero weight are not read, and a cell with an unallocated or
 // unobserved read emits nothing. The surface crosses a cell edge where it is linear between the corner values.
 //
-// One warp per allocated block: lanes take the block's cells in index order; a cell whose corners all lie in its own
-// block (the interior) reads them straight from the payload, the others evaluate the field with hash lookups. Each
-// warp reserves its triangles with one atomic per pass over 32 cells. Compiled without multiply-add contraction, so
+// One warp per allocated block, in two passes: the interior cells (all 8 corners are voxel centres of the block) read
+// their corners straight from the payload; the shell of cells at the block's upper faces (the last voxel along some
+// axis) evaluates the field with hash lookups. Each warp reserves its triangles with one atomic per 32 cells. Compiled without multiply-add contraction, so
 // every vertex is the float result of the same operations the oracle performs.
 #include <cuda_fp16.h>
 
@@ -137,7 +137,7 @@ __device__ inline float voxel_D(const uint8_t* blk, int i) {
 
 // trilinear field at the unit point P on the grid of the block containing it (see the file comment)
 template <bool FP16, bool COLOR>
-__device__ bool corner_value(const MapDev& m, const int P[3], float* out) {
+__device__ __noinline__ bool corner_value(const MapDev& m, const int P[3], float* out) {
   const uint32_t v = block_val(m, P[0] >> 4, P[1] >> 4, P[2] >> 4);
   if (v == kValPending) return false;
   const int lp = (int)((v >> 28) & 3u);
@@ -185,6 +185,38 @@ struct MeshOut {
   unsigned long long* count;
 };
 
+// One pass of 32 cells (warp-collective): reserve the pass's triangles with one atomic, then each lane writes its
+// cell's triangles; vertex = low corner + f (high - low), f = F_low / (F_low - F_high), per coordinate in metres.
+__device__ inline void emit_cell(const MeshOut& o, int lane, bool ok, int cs, const float F[8], const int c[3],
+                                 const int h[3], float unit) {
+  const int nt = ok ? (int)c_ntri[cs] : 0;
+  int incl = nt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(~0u, incl, d);
+    if (lane >= d) incl += y;
+  }
+  unsigned long long first = 0;
+  if (lane == 31 && incl > 0) first = atomicAdd(o.count, (unsigned long long)incl);
+  first = __shfl_sync(~0u, first, 31) + (unsigned long long)(incl - nt);
+  for (int t = 0; t < nt; ++t) {
+    if (first + t >= o.cap) break;
+    float* dst = o.tris + 9 * (first + t);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int e = c_tri[cs][3 * t + q];
+      const int ca = c_edge_end[e][0], cb = c_edge_end[e][1];
+      const float f = F[ca] / (F[ca] - F[cb]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float pa = (float)(c[a] + ((ca >> a) & 1) * h[a]) * unit;
+        const float pb = (float)(c[a] + ((cb >> a) & 1) * h[a]) * unit;
+        dst[3 * q + a] = pa + f * (pb - pa);
+      }
+    }
+  }
+}
+
 template <bool FP16, bool COLOR>
 __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
   const int lane = threadIdx.x & 31;
@@ -213,11 +245,51 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
         h_last = nvl == kValPending ? 0 : s + (1 << ((nvl >> 28) & 3u));
       }
       const int hl[3] = {__shfl_sync(~0u, h_last, 0), __shfl_sync(~0u, h_last, 1), __shfl_sync(~0u, h_last, 2)};
-      for (int c0 = 0; c0 < nv; c0 += 32) {
-        const int cell = c0 + lane;
-        int i[3] = {cell % nl, (cell / nl) % nl, cell / (nl * nl)};
+      // interior cells: (nl - 1)^3 of them, corners read from the payload
+      const int ni = nl - 1, n_in = ni * ni * ni;
+      for (int b0 = 0; b0 < n_in; b0 += 32) {
+        const int cell = b0 + lane;
+        bool ok = cell < n_in;
+        const int i[3] = {cell % ni, (cell / ni) % ni, cell / (ni * ni)};
         int c[3], h[3];
-        bool ok = cell < nv;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          c[a] = K[a] * 16 + (2 * i[a] + 1) * s;
+          h[a] = 2 * s;
+        }
+        float F[8];
+        int cs = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int idx = (i[0] + (q & 1)) + nl * ((i[1] + ((q >> 1) & 1)) + nl * (i[2] + (q >> 2)));
+          F[q] = ok ? voxel_D<FP16>(blk, idx) : 0.0f;
+          ok = ok && Wb[idx] > 0.0f;
+          if (F[q] < 0.0f) cs |= 1 << q;
+        }
+        emit_cell(o, lane, ok, cs, F, c, h, unit);
+      }
+      // the shell at the upper faces: z = last slab (nl^2), then y = last (nl (nl - 1)), then x = last ((nl - 1)^2)
+      const int n_sh = nv - n_in;
+      for (int b0 = 0; b0 < n_sh; b0 += 32) {
+        const int b = b0 + lane;
+        bool ok = b < n_sh;
+        int i[3];
+        if (b < nl * nl) {
+          i[0] = b % nl;
+          i[1] = b / nl;
+          i[2] = nl - 1;
+        } else if (b < nl * nl + nl * ni) {
+          const int r = b - nl * nl;
+          i[0] = r % nl;
+          i[1] = nl - 1;
+          i[2] = r / nl;
+        } else {
+          const int r = b - nl * nl - nl * ni;
+          i[0] = nl - 1;
+          i[1] = r % (ni > 0 ? ni : 1);
+          i[2] = r / (ni > 0 ? ni : 1);
+        }
+        int c[3], h[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           c[a] = K[a] * 16 + (2 * i[a] + 1) * s;
@@ -226,50 +298,13 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
         }
         float F[8];
         int cs = 0;
-        if (ok) {
-          const bool interior = i[0] < nl - 1 && i[1] < nl - 1 && i[2] < nl - 1;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (!ok) break;
-            const int ox = q & 1, oy = (q >> 1) & 1, oz = q >> 2;
-            if (interior) {
-              const int idx = (i[0] + ox) + nl * ((i[1] + oy) + nl * (i[2] + oz));
-              ok = Wb[idx] > 0.0f;
-              F[q] = voxel_D<FP16>(blk, idx);
-            } else {
-              const int P[3] = {c[0] + ox * h[0], c[1] + oy * h[1], c[2] + oz * h[2]};
-              ok = corner_value<FP16, COLOR>(m, P, &F[q]);
-            }
-            if (ok && F[q] < 0.0f) cs |= 1 << q;
-          }
+#pragma unroll 1
+        for (int q = 0; q < 8 && ok; ++q) {
+          const int P[3] = {c[0] + (q & 1) * h[0], c[1] + ((q >> 1) & 1) * h[1], c[2] + (q >> 2) * h[2]};
+          ok = corner_value<FP16, COLOR>(m, P, &F[q]);
+          if (ok && F[q] < 0.0f) cs |= 1 << q;
         }
-        const int nt = ok ? (int)c_ntri[cs] : 0;
-        // reserve this pass's triangles with one atomic
-        int incl = nt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(~0u, incl, d);
-          if (lane >= d) incl += y;
-        }
-        unsigned long long first = 0;
-        if (lane == 31 && incl > 0) first = atomicAdd(o.count, (unsigned long long)incl);
-        first = __shfl_sync(~0u, first, 31) + (unsigned long long)(incl - nt);
-        for (int t = 0; t < nt; ++t) {
-          if (first + t >= o.cap) break;
-          float* dst = o.tris + 9 * (first + t);
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const int e = c_tri[cs][3 * t + q];
-            const int ca = c_edge_end[e][0], cb = c_edge_end[e][1];
-            const float f = F[ca] / (F[ca] - F[cb]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float pa = (float)(c[a] + ((ca >> a) & 1) * h[a]) * unit;
-              const float pb = (float)(c[a] + ((cb >> a) & 1) * h[a]) * unit;
-              dst[3 * q + a] = pa + f * (pb - pa);
-            }
-          }
-        }
+        emit_cell(o, lane, ok, cs, F, c, h, unit);
       }
     }
   }
