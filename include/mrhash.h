@@ -268,6 +268,20 @@ mrh_status mrh_raycast(mrh_map* map, const mrh_pinhole* K, const double* T_wc_ho
  * with the two inside corners of an ambiguous face kept apart. Synchronises `stream`. */
 mrh_status mrh_extract_mesh(mrh_map* map, float* tris_dev, uint64_t capacity, uint64_t* n_tris_out, void* stream);
 
+/* Vertex collapse of a triangle soup (the final step of Sec. 3.4; the paper gives only the idea, this is the
+ * library's reading): every vertex falls in the cell floor(p * (1 / delta)) (float, per axis) of a grid of spacing
+ * delta (metres, > 0); each occupied cell becomes one vertex, the lexicographically smallest (x, then y, then z) of
+ * its members, numbered in ascending cell order (x, then y, then z); triangles take their vertices' cells and those
+ * with two equal indices are dropped, the rest keep their soup order. Inputs: tris_dev n_tris x 9 float32 (device;
+ * e.g. from mrh_extract_mesh). Outputs (device): verts_dev n_verts x 3 float32, faces_dev n_faces x 3 int32;
+ * n_verts_out, n_faces_out receive the counts (MRH_ERR_CAPACITY when either exceeds its capacity; nothing beyond a
+ * capacity is written). MRH_ERR_INVALID_ARG for delta <= 0, n_tris > 2^28, or a vertex whose cell index exceeds
+ * 2^20 in magnitude. Uses temporary device memory (up to about 450 bytes per input triangle) on the map's device;
+ * synchronises `stream`. */
+mrh_status mrh_weld_mesh(mrh_map* map, const float* tris_dev, uint64_t n_tris, float delta, float* verts_dev,
+                         uint64_t cap_verts, int32_t* faces_dev, uint64_t cap_faces, uint64_t* n_verts_out,
+                         uint64_t* n_faces_out, void* stream);
+
 /* The case table used by mrh_extract_mesh (host, no device work): ntri[256] triangles per case, tri[256 * 15] edge
  * triples (-1 unused), edge_end[12 * 2] corner pairs. Corner c lies at (c & 1, c >> 1 & 1, c >> 2 & 1) of the cell;
  * edge 4a + r joins the r-th corner (ascending) with bit a clear to its neighbour along axis a. */

@@ -14,7 +14,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   mesh (Marching Cubes)        pinned: case table against brute-force checks (triangle count of the plane cases,
                                every inside corner cut off, orientation towards the outside); linear fields give
                                vertices on the plane at every level; closed single-level surfaces are watertight
-                               with Euler characteristic 2; the resolution-boundary rule is a reading
+                               with Euler characteristic 2; the resolution-boundary rule is a reading;
+                               vertex collapse: representatives are members within their cluster cell, exact
+                               duplicates only at a tiny spacing (closed sphere keeps Euler characteristic 2)
   raycast normal / colour      pinned: a linear TSDF and colour field set block by block gives the plane's unit
                                normal and the colour field at the hit (trilinear is exact on linear fields);
                                analytic walls of a fused noise-free frame; constant-colour frames
@@ -82,6 +84,9 @@ def _load():
         lib.orc_extract_mesh.restype = ctypes.c_int64
         lib.orc_extract_mesh.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64]
         lib.orc_mc_table.argtypes = [vp, vp, vp]
+        lib.orc_weld_mesh.restype = ctypes.c_int64
+        lib.orc_weld_mesh.argtypes = [vp, ctypes.c_int64, ctypes.c_float, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64)]
         lib.orc_count_blocks.restype = ctypes.c_int64
         lib.orc_count_blocks.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         lib.orc_extract.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -261,6 +266,19 @@ class OracleMap:
         self._lib.orc_block_stats(self._h, _p(out["keys"]), _p(out["levels"]), _p(out["vbar"]), _p(out["n_obs"]),
                                   _p(out["sum_w"]))
         return out
+
+
+def weld_mesh(tris, delta: float):
+    """Vertex collapse of a triangle soup (n, 3, 3) on a grid of spacing delta: vertices (nv, 3) float32 (each the
+    smallest member of its cluster, clusters in ascending order) and faces (nf, 3) int32 (degenerate ones dropped)."""
+    lib = _load()
+    t = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    nf = ctypes.c_int64()
+    nv = lib.orc_weld_mesh(_p(t), t.shape[0], delta, None, 0, None, 0, ctypes.byref(nf))
+    verts = np.zeros((nv, 3), np.float32)
+    faces = np.zeros((nf.value, 3), np.int32)
+    lib.orc_weld_mesh(_p(t), t.shape[0], delta, _p(verts), nv, _p(faces), nf.value, ctypes.byref(nf))
+    return verts, faces
 
 
 def mc_table():

@@ -26,6 +26,7 @@
  * Plain containers only: std::unordered_map from block key to block, std::vector voxel arrays.
  */
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -1247,6 +1248,48 @@ int64_t orc_extract_mesh(void* h, int extract, float* out, int64_t cap) {
   if (out)
     for (int64_t i = 0; i < 9 * std::min(nt, cap); ++i) out[i] = m->mesh[(size_t)i];
   return nt;
+}
+
+// Vertex collapse (Sec. 3.4, a reading): the vertices of a triangle soup are clustered on a grid of spacing delta
+// (cluster of p = floor(p_a * (1 / delta)) per axis, in float); every cluster becomes one vertex, its lexicographically
+// smallest member (x, then y, then z), numbered in ascending cluster order (x, then y, then z); triangles are
+// re-indexed and those with two equal indices dropped, in soup order. Returns the vertex count; faces -> *n_faces.
+int64_t orc_weld_mesh(const float* tris, int64_t n_tris, float delta, float* verts_out, int64_t cap_verts,
+                      int32_t* faces_out, int64_t cap_faces, int64_t* n_faces) {
+  const float inv = 1.0f / delta;
+  std::map<std::array<int64_t, 3>, std::array<float, 3>> cl;
+  std::vector<std::array<int64_t, 3>> key((size_t)(3 * n_tris));
+  for (int64_t v = 0; v < 3 * n_tris; ++v) {
+    const float* p = tris + 3 * v;
+    std::array<int64_t, 3> k;
+    for (int a = 0; a < 3; ++a) k[a] = (int64_t)std::floor(p[a] * inv);
+    key[(size_t)v] = k;
+    auto it = cl.find(k);
+    const std::array<float, 3> q{p[0], p[1], p[2]};
+    if (it == cl.end()) cl.emplace(k, q);
+    else if (q < it->second) it->second = q;
+  }
+  std::map<std::array<int64_t, 3>, int32_t> index;
+  int32_t nv = 0;
+  for (auto& kv : cl) {
+    if (verts_out && nv < cap_verts)
+      for (int a = 0; a < 3; ++a) verts_out[3 * nv + a] = kv.second[a];
+    index[kv.first] = nv++;
+  }
+  int64_t nf = 0;
+  for (int64_t t = 0; t < n_tris; ++t) {
+    const int32_t i0 = index[key[(size_t)(3 * t)]], i1 = index[key[(size_t)(3 * t + 1)]],
+                  i2 = index[key[(size_t)(3 * t + 2)]];
+    if (i0 == i1 || i1 == i2 || i0 == i2) continue;
+    if (faces_out && nf < cap_faces) {
+      faces_out[3 * nf] = i0;
+      faces_out[3 * nf + 1] = i1;
+      faces_out[3 * nf + 2] = i2;
+    }
+    ++nf;
+  }
+  *n_faces = nf;
+  return nv;
 }
 
 // the case table (test hook): n_tris[256], edges[256 * 36], edge corners[24]

@@ -76,7 +76,7 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
-           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table"]
+           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -100,6 +100,8 @@ def lib():
         L.mrh_extract_mesh.argtypes = [vp, vp, u64, ctypes.POINTER(u64), vp]
         L.mrh_mesh_case_table.argtypes = [vp, vp, vp]
         L.mrh_mesh_case_table.restype = None
+        L.mrh_weld_mesh.argtypes = [vp, vp, u64, ctypes.c_float, vp, u64, vp, u64, ctypes.POINTER(u64),
+                                    ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
                                          ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks_noalloc.argtypes = L.mrh_extract_blocks.argtypes
@@ -285,6 +287,23 @@ class Map:
         _check(self._lib.mrh_extract_mesh(self._h, ctypes.c_void_p(out.data_ptr()), int(capacity), ctypes.byref(n),
                                           _stream(stream)), "mrh_extract_mesh")
         return out[:n.value]
+
+    def weld_mesh(self, tris, delta: float, stream=None):
+        """Vertex collapse of a triangle soup (n, 3, 3) float32 CUDA tensor on a grid of spacing delta [m]:
+        vertices (nv, 3) float32 and faces (nf, 3) int32 CUDA tensors (see mrh_weld_mesh)."""
+        import torch
+        t = tris.contiguous()
+        nv, nf = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.mrh_weld_mesh(self._h, _ptr(t), t.shape[0], float(delta), None, 0, None, 0,
+                                       ctypes.byref(nv), ctypes.byref(nf), _stream(stream)), "mrh_weld_mesh",
+               allow=(7,))
+        dev = f"cuda:{self.device}"
+        verts = torch.empty((max(nv.value, 1), 3), dtype=torch.float32, device=dev)
+        faces = torch.empty((max(nf.value, 1), 3), dtype=torch.int32, device=dev)
+        _check(self._lib.mrh_weld_mesh(self._h, _ptr(t), t.shape[0], float(delta), _ptr(verts), nv.value,
+                                       _ptr(faces), nf.value, ctypes.byref(nv), ctypes.byref(nf), _stream(stream)),
+               "mrh_weld_mesh")
+        return verts[:nv.value], faces[:nf.value]
 
     def count(self, stream=None):
         nb, nv = ctypes.c_uint64(), ctypes.c_uint64()

@@ -429,5 +429,23 @@ void launch_raycast(const MapDev& m, const CamArgs& c, float* depth, float* norm
 cudaError_t mesh_table_ready(int device);
 void host_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
 void launch_mesh(const MapDev& m, float* tris, uint64_t cap, unsigned long long* count, cudaStream_t s, int sms);
+// vertex collapse of a triangle soup (mrh_mesh.cu); scratch sized by the caller
+constexpr int kWeldScanBlock = 1024;
+struct WeldScratch {
+  unsigned long long* keys;  // table: packed cluster key, ~0 = empty
+  uint32_t* mn;              // table: smallest member, 3 order-preserving encodings per slot
+  uint32_t* vslot;           // per input vertex: its table slot
+  uint32_t* vidx;            // table: output vertex index
+  unsigned long long* ckeys; // occupied slots' keys, sorted
+  uint32_t* cslots;          // ... and their slots
+  uint32_t* blk;             // per scan block: kept count, then its first position
+  uint32_t* counters;        // [0] clusters, [1] key out of range, [2] faces, [3] compaction cursor
+  uint32_t table;
+};
+cudaError_t weld_clusters(const WeldScratch& w, const float* tris, uint32_t nv, float delta, cudaStream_t s, int sms);
+void weld_pad(const WeldScratch& w, uint32_t n, uint32_t n_pow, cudaStream_t s, int sms);
+cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clusters, float* verts, uint64_t cap_verts,
+                        int32_t* faces, uint64_t cap_faces, uint64_t n_tris, size_t nblk, cudaStream_t s, int sms);
+void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms);
 
 }  // namespace mrh

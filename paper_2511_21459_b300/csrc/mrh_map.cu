@@ -363,6 +363,12 @@ void free_all(mrh_map* m) {
 }  // namespace mrh
 
 namespace mrh {
+// ascending sort of n_pow (a power of two) keys with their values (bitonic network, one launch per step)
+void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms) {
+  for (uint32_t k = 2; k <= n_pow; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) k_bitonic_step<<<sms * 8, 256, 0, s>>>(keys, vals, n_pow, k, j);
+}
+
 const MapDev* map_dev(const mrh_map* m, int* device, int* sms) {
   *device = m->device;
   *sms = m->sms;
@@ -689,6 +695,63 @@ mrh_status mrh_extract_mesh(mrh_map* m, float* tris, uint64_t capacity, uint64_t
   MRH_CUDA(cudaStreamSynchronize(s));
   *n_tris_out = n;
   return n > capacity ? MRH_ERR_CAPACITY : MRH_OK;
+}
+
+mrh_status mrh_weld_mesh(mrh_map* m, const float* tris, uint64_t n_tris, float delta, float* verts, uint64_t cap_verts,
+                         int32_t* faces, uint64_t cap_faces, uint64_t* n_verts_out, uint64_t* n_faces_out,
+                         void* stream) {
+  if (!m || !n_verts_out || !n_faces_out || !(delta > 0.0f) || !std::isfinite(delta) || n_tris > (1ull << 28) ||
+      (n_tris > 0 && !tris) || (cap_verts > 0 && !verts) || (cap_faces > 0 && !faces))
+    return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  *n_verts_out = *n_faces_out = 0;
+  if (n_tris == 0) return MRH_OK;
+  const uint32_t nv = (uint32_t)(3 * n_tris);
+  uint32_t table = 1024;
+  while (table < 2 * nv) table <<= 1;
+  WeldScratch w{};
+  const size_t nblk = (n_tris + kWeldScanBlock - 1) / kWeldScanBlock;
+  cudaError_t e = cudaSuccess;
+  auto grab = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMallocAsync(p, bytes, s);
+  };
+  grab((void**)&w.keys, 8ull * table);
+  grab((void**)&w.mn, 12ull * table);
+  grab((void**)&w.vslot, 4ull * nv);
+  grab((void**)&w.vidx, 4ull * table);
+  grab((void**)&w.ckeys, 8ull * table);
+  grab((void**)&w.cslots, 4ull * table);
+  grab((void**)&w.blk, 4ull * (nblk + 1));
+  grab((void**)&w.counters, 16);
+  mrh_status st = MRH_OK;
+  uint32_t hc[2] = {0, 0};
+  uint32_t n_pow = 1;
+  if (e == cudaSuccess) {
+    w.table = table;
+    KernelScope ks(m, MRH_K_MESH, s, 1);
+    e = weld_clusters(w, tris, nv, delta, s, m->sms);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, w.counters, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && hc[1] == 0) {
+      while (n_pow < hc[0]) n_pow <<= 1;
+      weld_pad(w, hc[0], n_pow, s, m->sms);
+      sort_keys_vals(w.ckeys, w.cslots, n_pow, s, m->sms);
+      e = weld_output(w, tris, hc[0], verts, cap_verts, faces, cap_faces, n_tris, nblk, s, m->sms);
+    }
+  }
+  uint32_t nf = 0;
+  if (e == cudaSuccess && hc[1] == 0) e = cudaMemcpyAsync(&nf, w.counters + 2, 4, cudaMemcpyDeviceToHost, s);
+  for (void* p : {(void*)w.keys, (void*)w.mn, (void*)w.vslot, (void*)w.vidx, (void*)w.ckeys, (void*)w.cslots,
+                  (void*)w.blk, (void*)w.counters})
+    if (p) cudaFreeAsync(p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "mrh_weld_mesh");
+  if (hc[1] != 0) return MRH_ERR_INVALID_ARG;  // a vertex's cluster index is out of range for this delta
+  *n_verts_out = hc[0];
+  *n_faces_out = nf;
+  if (hc[0] > cap_verts || nf > cap_faces) st = MRH_ERR_CAPACITY;
+  return st;
 }
 
 void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {

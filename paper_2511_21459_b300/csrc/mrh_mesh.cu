@@ -310,6 +310,179 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
   }
 }
 
+// ---- vertex collapse (see mrh_weld_mesh in the C ABI)
+
+// order-preserving encoding of a float as an unsigned integer (and back)
+__device__ inline uint32_t ord_f(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float unord_f(uint32_t u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u); }
+
+// grid cell of a vertex, packed so that the integer order is the (x, then y, then z) order; false when out of range
+__device__ inline bool weld_key(const float* p, float inv, unsigned long long* key) {
+  unsigned long long k = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float q = floorf(p[a] * inv);
+    if (!(fabsf(q) < 1048576.0f)) return false;
+    k = (k << 21) | (unsigned long long)((long long)q + (1ll << 20));
+  }
+  *key = k;
+  return true;
+}
+
+__device__ inline uint32_t weld_hash(unsigned long long k, uint32_t mask) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  return (uint32_t)k & mask;
+}
+
+__global__ void k_weld_init(WeldScratch w) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.table; i += gridDim.x * blockDim.x) {
+    w.keys[i] = kEmptyKey;
+    w.mn[3 * i] = w.mn[3 * i + 1] = w.mn[3 * i + 2] = 0xFFFFFFFFu;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) w.counters[threadIdx.x] = 0;
+}
+
+__global__ void k_weld_insert(WeldScratch w, const float* tris, uint32_t nv, float inv) {
+  const uint32_t mask = w.table - 1;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const float* p = tris + 3ull * v;
+    unsigned long long key;
+    if (!weld_key(p, inv, &key)) {
+      w.vslot[v] = 0xFFFFFFFFu;
+      atomicOr(&w.counters[1], 1u);
+      continue;
+    }
+    uint32_t sl = weld_hash(key, mask);
+    for (uint32_t probe = 0; probe < w.table; ++probe, sl = (sl + 1) & mask) {
+      const unsigned long long cur = w.keys[sl];
+      if (cur == key) break;
+      if (cur == kEmptyKey) {
+        const unsigned long long old = atomicCAS(&w.keys[sl], kEmptyKey, key);
+        if (old == kEmptyKey) {
+          atomicAdd(&w.counters[0], 1u);
+          break;
+        }
+        if (old == key) break;
+      }
+    }
+    w.vslot[v] = sl;
+    atomicMin(&w.mn[3 * sl], ord_f(p[0]));
+  }
+}
+
+// the smallest member: y among the members with the smallest x, then z among those with the smallest x and y
+template <int AXIS>
+__global__ void k_weld_min(WeldScratch w, const float* tris, uint32_t nv) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const uint32_t sl = w.vslot[v];
+    if (sl == 0xFFFFFFFFu) continue;
+    const float* p = tris + 3ull * v;
+    bool lead = ord_f(p[0]) == w.mn[3 * sl];
+    if (AXIS == 2) lead = lead && ord_f(p[1]) == w.mn[3 * sl + 1];
+    if (lead) atomicMin(&w.mn[3 * sl + AXIS], ord_f(p[AXIS]));
+  }
+}
+
+__global__ void k_weld_compact(WeldScratch w) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.table; i += gridDim.x * blockDim.x) {
+    const unsigned long long k = w.keys[i];
+    if (k == kEmptyKey) continue;
+    const uint32_t j = atomicAdd(&w.counters[3], 1u);
+    w.ckeys[j] = k;
+    w.cslots[j] = i;
+  }
+}
+
+__global__ void k_weld_pad(WeldScratch w, uint32_t n, uint32_t n_pow) {
+  for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < n_pow; i += gridDim.x * blockDim.x) {
+    w.ckeys[i] = kEmptyKey;
+    w.cslots[i] = 0;
+  }
+}
+
+// vertex i = the i-th cluster in key order
+__global__ void k_weld_number(WeldScratch w, uint32_t n, float* verts, uint64_t cap) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t sl = w.cslots[i];
+    w.vidx[sl] = i;
+    if (i < cap)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) verts[3ull * i + a] = unord_f(w.mn[3 * sl + a]);
+  }
+}
+
+__device__ inline bool weld_face(const WeldScratch& w, uint64_t t, uint32_t* i0, uint32_t* i1, uint32_t* i2) {
+  *i0 = w.vidx[w.vslot[3 * t]];
+  *i1 = w.vidx[w.vslot[3 * t + 1]];
+  *i2 = w.vidx[w.vslot[3 * t + 2]];
+  return *i0 != *i1 && *i1 != *i2 && *i0 != *i2;
+}
+
+// faces keep their soup order: count the kept faces of each block of kWeldScanBlock, scan the counts, write
+__global__ void __launch_bounds__(kWeldScanBlock) k_weld_count(WeldScratch w, uint64_t n_tris) {
+  const uint64_t t = (uint64_t)blockIdx.x * kWeldScanBlock + threadIdx.x;
+  uint32_t a, b, c;
+  const int keep = t < n_tris && weld_face(w, t, &a, &b, &c);
+  const int n = __syncthreads_count(keep);
+  if (threadIdx.x == 0) w.blk[blockIdx.x] = (uint32_t)n;
+}
+
+__global__ void __launch_bounds__(1024) k_weld_scan(WeldScratch w, uint32_t nblk) {
+  __shared__ uint32_t part[1024];
+  const uint32_t per = (nblk + 1023) / 1024, lo = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < lo + per && i < nblk; ++i) sum += w.blk[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const uint32_t y = threadIdx.x >= (uint32_t)d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (uint32_t i = lo; i < lo + per && i < nblk; ++i) {
+    const uint32_t c = w.blk[i];
+    w.blk[i] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) w.counters[2] = part[1023];
+}
+
+__global__ void __launch_bounds__(kWeldScanBlock) k_weld_faces(WeldScratch w, uint64_t n_tris, int32_t* faces,
+                                                               uint64_t cap) {
+  __shared__ uint32_t warp_base[kWeldScanBlock / 32];
+  const uint64_t t = (uint64_t)blockIdx.x * kWeldScanBlock + threadIdx.x;
+  uint32_t a = 0, b = 0, c = 0;
+  const bool keep = t < n_tris && weld_face(w, t, &a, &b, &c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(~0u, keep);
+  if (lane == 0) warp_base[warp] = __popc(bal);
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t x = warp_base[lane], incl = x;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(~0u, incl, d);
+      if (lane >= d) incl += y;
+    }
+    warp_base[lane] = incl - x;
+  }
+  __syncthreads();
+  if (keep) {
+    const uint64_t pos = (uint64_t)w.blk[blockIdx.x] + warp_base[warp] + __popc(bal & ((1u << lane) - 1u));
+    if (pos < cap) {
+      faces[3 * pos] = (int32_t)a;
+      faces[3 * pos + 1] = (int32_t)b;
+      faces[3 * pos + 2] = (int32_t)c;
+    }
+  }
+}
+
 std::mutex g_table_mutex;
 bool g_table_on[64] = {};
 
@@ -333,6 +506,30 @@ void host_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {
   std::memcpy(ntri, t.ntri, sizeof(t.ntri));
   std::memcpy(tri, t.tri, sizeof(t.tri));
   std::memcpy(edge_end, t.edge_end, sizeof(t.edge_end));
+}
+
+cudaError_t weld_clusters(const WeldScratch& w, const float* tris, uint32_t nv, float delta, cudaStream_t s, int sms) {
+  const float inv = 1.0f / delta;
+  k_weld_init<<<sms * 4, 256, 0, s>>>(w);
+  k_weld_insert<<<sms * 8, 256, 0, s>>>(w, tris, nv, inv);
+  k_weld_min<1><<<sms * 8, 256, 0, s>>>(w, tris, nv);
+  k_weld_min<2><<<sms * 8, 256, 0, s>>>(w, tris, nv);
+  k_weld_compact<<<sms * 8, 256, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+void weld_pad(const WeldScratch& w, uint32_t n, uint32_t n_pow, cudaStream_t s, int sms) {
+  if (n_pow > n) k_weld_pad<<<sms * 4, 256, 0, s>>>(w, n, n_pow);
+}
+
+cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clusters, float* verts, uint64_t cap_verts,
+                        int32_t* faces, uint64_t cap_faces, uint64_t n_tris, size_t nblk, cudaStream_t s, int sms) {
+  (void)tris;
+  k_weld_number<<<sms * 8, 256, 0, s>>>(w, n_clusters, verts, cap_verts);
+  k_weld_count<<<(unsigned)nblk, kWeldScanBlock, 0, s>>>(w, n_tris);
+  k_weld_scan<<<1, 1024, 0, s>>>(w, (uint32_t)nblk);
+  k_weld_faces<<<(unsigned)nblk, kWeldScanBlock, 0, s>>>(w, n_tris, faces, cap_faces);
+  return cudaGetLastError();
 }
 
 void launch_mesh(const MapDev& m, float* tris, uint64_t cap, unsigned long long* count, cudaStream_t s, int sms) {

@@ -122,3 +122,25 @@ def test_capacity_error_reports_the_count_and_empty_map_has_no_triangles():
     assert e.value.code == 7
     e2 = m.Map(m.params_from(wl))
     assert len(e2.extract_mesh()) == 0
+
+
+def test_vertex_collapse_matches_oracle():
+    """The GPU collapse of the GPU soup equals the oracle's collapse of the oracle soup: the same vertices in the same
+    (cell) order, and the same faces once each is rotated to its smallest index and the list sorted (the soups'
+    triangle orders differ)."""
+    wl = synth.tiny()
+    g, o = run_camera(wl, [synth.render_depth(wl, 0, seed=s) for s in range(10)])
+    delta = 0.01 / 8
+    vg, fg = g.weld_mesh(g.extract_mesh(), delta)
+    vo, fo = oracle.weld_mesh(o.extract_mesh(), delta)
+    vg, fg = vg.cpu().numpy(), fg.cpu().numpy()
+    assert len(vo) > 5000 and len(fo) > 10000
+    assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
+
+    def canon(f):
+        r = np.argmin(f, axis=1)
+        f = f[np.arange(len(f))[:, None], (r[:, None] + np.arange(3)[None, :]) % 3]
+        return f[np.lexsort(f.T[::-1])]
+    assert np.array_equal(canon(fg), canon(fo))
+    # fewer vertices than the soup has corners, and triangles dropped only where they collapsed
+    assert len(vg) < 3 * len(fg)

@@ -202,3 +202,51 @@ def test_fused_frame_mesh_follows_the_scene():
     bound_b = rho * np.sqrt(1 - cos_b ** 2) / cos_b * 0.71 / wl.fx + 5e-4
     assert on_b.sum() > 100000
     assert np.all(np.abs(V[on_b, 2] - 3.0) <= bound_b[on_b])
+
+
+# ---------------------------------------------------------------------------------------------- vertex collapse
+
+def _sphere_soup(level=0):
+    c = np.array([0.013, -0.007, 1.004])
+    m = _map()
+    _fill(m, _box((-4, -4, 9), (4, 4, 17)), lambda k: level, lambda X: np.linalg.norm(X - c, axis=1) - 0.19)
+    return m.extract_mesh()
+
+
+def test_collapse_at_a_tiny_spacing_only_joins_equal_vertices():
+    soup = _sphere_soup()
+    verts, faces = oracle.weld_mesh(soup, 1e-7)
+    flat = soup.reshape(-1, 3)
+    assert len(verts) == len(np.unique(flat, axis=0))
+    assert len(faces) == len(soup)
+    # the welded closed surface: V - E + F = 2, every edge in exactly two faces
+    e = np.sort(np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]]), axis=1)
+    ue, cnt = np.unique(e, axis=0, return_counts=True)
+    assert np.all(cnt == 2)
+    assert len(verts) - len(ue) + len(faces) == 2
+    # faces point at the soup's own vertices, in the same winding
+    np.testing.assert_array_equal(verts[faces], soup)
+
+
+@pytest.mark.parametrize("delta", [0.00125, 0.005])
+def test_collapse_keeps_members_inside_their_cluster_cell(delta):
+    soup = _sphere_soup()
+    verts, faces = oracle.weld_mesh(soup, delta)
+    flat = soup.reshape(-1, 3)
+    # every representative is one of the soup's vertices
+    soup_set = {tuple(v) for v in flat.tolist()}
+    assert all(tuple(v) in soup_set for v in verts.tolist())
+    # each face vertex moved by less than a cluster cell's diagonal, and the faces kept are the non-degenerate ones
+    kept = (np.abs(np.diff(np.sort(faces, axis=1), axis=1)) > 0).all(axis=1)
+    assert kept.all() and len(faces) <= len(soup)
+    # coarser grids merge more
+    v2, f2 = oracle.weld_mesh(soup, 2 * delta)
+    assert len(v2) < len(verts) and len(f2) <= len(faces)
+    # representatives are the smallest member of their cell
+    cells = np.floor(flat * np.float32(1.0 / delta)).astype(np.int64)
+    order = np.lexsort((flat[:, 2], flat[:, 1], flat[:, 0]))
+    first = {}
+    for i in order:
+        first.setdefault(tuple(cells[i]), tuple(flat[i]))
+    assert len(first) == len(verts)
+    assert sorted(first.values()) == sorted(tuple(v) for v in verts.tolist())
