@@ -508,6 +508,15 @@ def run_mesh(wl, m, reps=5, prefix=(0, 10, 20, 30)):
     full = {"triangles": n, "ms": round(kms, 4), "triangles_per_s": n / (kms / 1000.0),
             "algorithmic_bytes": b, "achieved_GBps": round(b / (kms / 1000.0) / 1e9, 1),
             "live_blocks": st["live_blocks"]}
+    # vertex collapse on a grid of an eighth of the finest voxel: the paper's vertex / face counts (memory proxy)
+    delta = wl.base_voxel / (1 << (wl.n_levels - 1)) / 8
+    soup = m.extract_mesh(capacity=n)
+    m.profile(reset=True)
+    verts, faces = m.weld_mesh(soup, delta)
+    torch.cuda.synchronize()
+    full.update({"collapse_delta_m": delta, "vertices": int(verts.shape[0]), "faces": int(faces.shape[0]),
+                 "collapse_ms": round(m.profile()["mesh"][0] / 2, 4)})
+    del soup, verts, faces
     # the same small map on both sides
     scene = wl.scene()
     frames = [synth.render_depth(wl, k, scene=scene) for k in prefix]
