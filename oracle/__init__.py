@@ -17,6 +17,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                                with Euler characteristic 2; the resolution-boundary rule is a reading;
                                vertex collapse: representatives are members within their cluster cell, exact
                                duplicates only at a tiny spacing (closed sphere keeps Euler characteristic 2)
+  quadtree (Sec. 3.5, Eq. 10)  pinned: closed-form contrast of two-colour and constant regions (byte units);
+                               leaves tile the image; thresholds below zero / above the maximum give single pixels /
+                               one leaf; a hand-built image gives the hand-counted leaves
   raycast normal / colour      pinned: a linear TSDF and colour field set block by block gives the plane's unit
                                normal and the colour field at the hit (trilinear is exact on linear fields);
                                analytic walls of a fused noise-free frame; constant-colour frames
@@ -31,7 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrh_oracle.cpp")
-_SRCS = [_SRC, os.path.join(_HERE, "level_predictor.cpp")]
+_SRCS = [_SRC, os.path.join(_HERE, "level_predictor.cpp"), os.path.join(_HERE, "quadtree.cpp")]
 _SO = os.path.join(_HERE, "libmrh_oracle.so")
 _lib = None
 
@@ -84,6 +87,10 @@ def _load():
         lib.orc_extract_mesh.restype = ctypes.c_int64
         lib.orc_extract_mesh.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64]
         lib.orc_mc_table.argtypes = [vp, vp, vp]
+        lib.orc_qt_contrast.restype = ctypes.c_double
+        lib.orc_qt_contrast.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.orc_quadtree.restype = ctypes.c_int64
+        lib.orc_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, ctypes.c_int64]
         lib.orc_weld_mesh.restype = ctypes.c_int64
         lib.orc_weld_mesh.argtypes = [vp, ctypes.c_int64, ctypes.c_float, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                       ctypes.POINTER(ctypes.c_int64)]
@@ -279,6 +286,22 @@ def weld_mesh(tris, delta: float):
     faces = np.zeros((nf.value, 3), np.int32)
     lib.orc_weld_mesh(_p(t), t.shape[0], delta, _p(verts), nv, _p(faces), nf.value, ctypes.byref(nf))
     return verts, faces
+
+
+def qt_contrast(rgb: np.ndarray, x0: int, y0: int, w: int, h: int) -> float:
+    """Contrast (Eq. 10) of the rectangle of an (H, W, 3) uint8 image, RGB in byte units."""
+    img = np.ascontiguousarray(rgb, dtype=np.uint8)
+    return _load().orc_qt_contrast(_p(img), img.shape[1], x0, y0, w, h)
+
+
+def quadtree(rgb: np.ndarray, threshold: float = 0.1, min_size: int = 1) -> np.ndarray:
+    """Leaves (n, 4) int32 (x, y, w, h) of the image's contrast quadtree (Sec. 3.5, Algorithm 1), depth first."""
+    img = np.ascontiguousarray(rgb, dtype=np.uint8)
+    lib = _load()
+    n = lib.orc_quadtree(_p(img), img.shape[1], img.shape[0], threshold, min_size, None, 0)
+    out = np.zeros((n, 4), np.int32)
+    lib.orc_quadtree(_p(img), img.shape[1], img.shape[0], threshold, min_size, _p(out), n)
+    return out
 
 
 def mc_table():
