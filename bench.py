@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-mesh", action="store_true")
+    ap.add_argument("--no-quadtree", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
     ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh"], default=None,
@@ -544,6 +545,41 @@ def run_mesh(wl, m, reps=5, prefix=(0, 10, 20, 30)):
     return {"full_map": full, "prefix_map": small}
 
 
+def run_quadtree(wl, frames, reps=3, threshold=0.1, min_size=1, oracle_frames=3):
+    """Contrast quadtree (Sec. 3.5, Eq. 10, Algorithm 1; the paper's threshold 0.1, minimum size 1 px) of the colour
+    frames of the sequence: device time per frame (CUDA events on the stream around the call, which includes its
+    scratch allocation and the leaf-count read-back), leaves per frame, and the oracle (one thread) on the first frames,
+    with the leaf sets checked equal."""
+    import torch
+    import oracle
+    import paper_2511_21459_b300 as mrh
+    imgs = [torch.from_numpy(c).cuda() for _, c, _ in frames]
+    stream = torch.cuda.current_stream()
+    for im in imgs[:2]:
+        mrh.quadtree(im, threshold, min_size)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_leaves = 0
+    a.record(stream)
+    for _ in range(reps):
+        for im in imgs:
+            n_leaves += int(mrh.quadtree(im, threshold, min_size).shape[0])
+    b.record(stream)
+    torch.cuda.synchronize()
+    gms = a.elapsed_time(b) / (reps * len(imgs))
+    t0 = time.perf_counter()
+    same = True
+    for (_, c, _), im in zip(frames[:oracle_frames], imgs):
+        o = oracle.quadtree(c, threshold, min_size)
+        g = mrh.quadtree(im, threshold, min_size).cpu().numpy()
+        same = same and len(o) == len(g) and np.array_equal(o[np.lexsort(o.T[::-1])], g[np.lexsort(g.T[::-1])])
+    cms = 1000.0 * (time.perf_counter() - t0) / oracle_frames
+    return {"frames": len(imgs), "threshold": threshold, "min_size": min_size,
+            "leaves_per_frame": n_leaves / (reps * len(imgs)), "gpu_ms_per_frame": round(gms, 4),
+            "frames_per_s": 1000.0 / gms, "oracle_ms_per_frame_1_thread": round(cms, 2),
+            "oracle_frames_checked_equal": same}
+
+
 def run_lidar_gpu(wl, warmup, steps, flush):
     import torch
     import paper_2511_21459_b300 as mrh
@@ -821,6 +857,9 @@ def main():
     if rank == 0 and not args.no_mesh:
         mesh = run_mesh(wl, main_map)
     main_map.close()
+    quad = None
+    if rank == 0 and not args.no_quadtree:
+        quad = run_quadtree(wl, frames[:20])
 
     lidar = None
     if not args.no_lidar:
@@ -868,7 +907,7 @@ def main():
                 "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
-                "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh}
+                "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh, "quadtree": quad}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

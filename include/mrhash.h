@@ -282,6 +282,18 @@ mrh_status mrh_weld_mesh(mrh_map* map, const float* tris_dev, uint64_t n_tris, f
                          uint64_t cap_verts, int32_t* faces_dev, uint64_t cap_faces, uint64_t* n_verts_out,
                          uint64_t* n_faces_out, void* stream);
 
+/* Contrast quadtree of an RGB image (the rendering branch, Sec. 3.5, Eq. 10, Algorithm 1; no map needed). rgb_dev:
+ * height x width x 3 uint8 (device, interleaved). A node's contrast is the Rec. 601 luma weights (0.2989, 0.5870,
+ * 0.1140) applied to the per-channel mean squared deviation of its pixels from their mean, in byte units, computed from
+ * exact integer sums ((n S2 - S1^2) / n^2 per channel). A node splits when its larger side exceeds `min_size` (>= 1)
+ * pixels and n^2 times its contrast, l0 N0 + l1 N1 + l2 N2 in double with N = n S2 - S1^2, exceeds threshold n n
+ * (double); it splits at its midpoints (x0 + w / 2, y0 + h / 2, rounded down) into its non-empty quarters; the
+ * others are leaves. Output: leaves_dev n x 4 int32
+ * (x, y, w, h) in no particular order; n_leaves_out receives n (MRH_ERR_CAPACITY when n > capacity; at most capacity
+ * are written). Uses temporary device memory (about 80 bytes per pixel) on `device`; synchronises `stream`. */
+mrh_status mrh_quadtree(const uint8_t* rgb_dev, int width, int height, double threshold, int min_size,
+                        int32_t* leaves_dev, uint64_t capacity, uint64_t* n_leaves_out, int device, void* stream);
+
 /* The case table used by mrh_extract_mesh (host, no device work): ntri[256] triangles per case, tri[256 * 15] edge
  * triples (-1 unused), edge_end[12 * 2] corner pairs. Corner c lies at (c & 1, c >> 1 & 1, c >> 2 & 1) of the cell;
  * edge 4a + r joins the r-th corner (ascending) with bit a clear to its neighbour along axis a. */

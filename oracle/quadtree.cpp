@@ -4,9 +4,10 @@
 // Reading: RGB values are the image's bytes (0..255; the paper does not give the scale, and at its threshold of 0.1 a
 // [0, 1] scale would leave a whole synthetic frame as one leaf). A node's contrast is the Rec. 601 luma weights applied
 // to the per-channel mean of squared deviations from the node's mean colour. It is evaluated from exact integer sums:
-// for a channel with n pixels, sum S1 and sum of squares S2, the mean squared deviation is (n S2 - S1^2) / n^2, the
-// numerator an exact integer, and the contrast l0 v0 + l1 v1 + l2 v2 is taken in double in that order, so that every
-// implementation reaches the same split decisions. A node whose contrast exceeds the threshold and whose larger
+// for a channel with n pixels, sum S1 and sum of squares S2, the mean squared deviation is (n S2 - S1^2) / n^2 with an
+// exact integer numerator N. A node splits when n^2 times its contrast exceeds n^2 times the threshold, both in double:
+// l0 N0 + l1 N1 + l2 N2 (in that order) against threshold n n, so that every implementation reaches the same split
+// decisions without a division. A node whose contrast exceeds the threshold and whose larger
 // side exceeds the minimum size splits at its midpoints (x0 + w/2, y0 + h/2, rounded down) into up to four children
 // (empty ones dropped); otherwise it is a leaf.
 #include <cstdint>
@@ -18,7 +19,8 @@ struct Leaf {
   int32_t x, y, w, h;
 };
 
-double contrast(const uint8_t* rgb, int width, int x0, int y0, int w, int h) {
+// n^2 times the contrast (and n^2 in *n2)
+double scaled_contrast(const uint8_t* rgb, int width, int x0, int y0, int w, int h, double* n2) {
   const int64_t n = (int64_t)w * h;
   int64_t s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
   for (int y = y0; y < y0 + h; ++y)
@@ -30,18 +32,16 @@ double contrast(const uint8_t* rgb, int width, int x0, int y0, int w, int h) {
       }
   const double luma[3] = {0.2989, 0.5870, 0.1140};
   double acc = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    const int64_t num = n * s2[c] - s1[c] * s1[c];
-    const double v = (double)num / ((double)n * (double)n);
-    acc = acc + luma[c] * v;
-  }
+  for (int c = 0; c < 3; ++c) acc = acc + luma[c] * (double)(n * s2[c] - s1[c] * s1[c]);
+  *n2 = (double)n * (double)n;
   return acc;
 }
 
 void split(const uint8_t* rgb, int width, int x0, int y0, int w, int h, double thr, int min_size,
            std::vector<Leaf>& out) {
   const int size = w > h ? w : h;
-  if (size > min_size && contrast(rgb, width, x0, y0, w, h) > thr) {
+  double n2 = 0.0;
+  if (size > min_size && scaled_contrast(rgb, width, x0, y0, w, h, &n2) > thr * n2) {
     const int hw = w / 2, hh = h / 2;
     const int xs[2] = {x0, x0 + hw}, ws[2] = {hw, w - hw};
     const int ys[2] = {y0, y0 + hh}, hs[2] = {hh, h - hh};
@@ -59,7 +59,9 @@ extern "C" {
 
 // contrast of one rectangle (test hook)
 double orc_qt_contrast(const uint8_t* rgb, int width, int x0, int y0, int w, int h) {
-  return contrast(rgb, width, x0, y0, w, h);
+  double n2 = 0.0;
+  const double c = scaled_contrast(rgb, width, x0, y0, w, h, &n2);
+  return c / n2;
 }
 
 // leaves (x, y, w, h) of the image's quadtree, in depth-first order (top-left, top-right, bottom-left, bottom-right);

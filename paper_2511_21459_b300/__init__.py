@@ -76,7 +76,7 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
-           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh"]
+           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -100,6 +100,8 @@ def lib():
         L.mrh_extract_mesh.argtypes = [vp, vp, u64, ctypes.POINTER(u64), vp]
         L.mrh_mesh_case_table.argtypes = [vp, vp, vp]
         L.mrh_mesh_case_table.restype = None
+        L.mrh_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, u64,
+                                   ctypes.POINTER(u64), ctypes.c_int, vp]
         L.mrh_weld_mesh.argtypes = [vp, vp, u64, ctypes.c_float, vp, u64, vp, u64, ctypes.POINTER(u64),
                                     ctypes.POINTER(u64), vp]
         L.mrh_extract_blocks.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, u64, ctypes.POINTER(u64),
@@ -148,6 +150,21 @@ def _check(code: int, what: str, allow=()):
     if code != 0 and code not in allow:
         err = lib().mrh_last_cuda_error().decode()
         raise MrhError(code, what + (f" [{err}]" if code == 6 and err else ""))
+
+
+def quadtree(rgb, threshold: float = 0.1, min_size: int = 1, stream=None):
+    """Contrast quadtree (Sec. 3.5) of an (H, W, 3) uint8 CUDA tensor: leaves (n, 4) int32 CUDA tensor (x, y, w, h),
+    in no particular order (see mrh_quadtree)."""
+    import torch
+    img = rgb.contiguous()
+    h, w = int(img.shape[0]), int(img.shape[1])
+    dev = img.device.index if img.device.index is not None else torch.cuda.current_device()
+    n = ctypes.c_uint64()
+    cap = w * h
+    out = torch.empty((cap, 4), dtype=torch.int32, device=img.device)
+    _check(lib().mrh_quadtree(_ptr(img), w, h, float(threshold), int(min_size), _ptr(out), cap, ctypes.byref(n), dev,
+                              _stream(stream)), "mrh_quadtree")
+    return out[:n.value]
 
 
 def mesh_case_table():

@@ -447,5 +447,12 @@ void weld_pad(const WeldScratch& w, uint32_t n, uint32_t n_pow, cudaStream_t s, 
 cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clusters, float* verts, uint64_t cap_verts,
                         int32_t* faces, uint64_t cap_faces, uint64_t n_tris, size_t nblk, cudaStream_t s, int sms);
 void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms);
+// stream-ordered scratch from a pool owned by the library (one per device, memory kept for reuse)
+cudaError_t scratch_alloc(void** p, size_t bytes, int device, cudaStream_t s);
+// contrast quadtree (mrh_quadtree.cu)
+size_t quadtree_scratch_bytes(int width, int height);
+cudaError_t launch_quadtree(const uint8_t* rgb, int width, int height, double threshold, int min_size,
+                            int32_t* leaves, uint64_t cap, void* scratch, unsigned long long** n_leaves_dev,
+                            cudaStream_t s, int sms);
 
 }  // namespace mrh

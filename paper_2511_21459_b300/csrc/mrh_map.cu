@@ -363,6 +363,36 @@ void free_all(mrh_map* m) {
 }  // namespace mrh
 
 namespace mrh {
+namespace {
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+// The scratch of the read-out calls (mesh collapse, quadtree) comes from one memory pool per device that keeps its
+// memory between calls (release threshold unlimited), so repeated calls do not map and unmap device memory.
+cudaError_t scratch_alloc(void** p, size_t bytes, int device, cudaStream_t s) {
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pool[device]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      cudaError_t e = cudaMemPoolCreate(&g_pool[device], &props);
+      if (e != cudaSuccess) {
+        g_pool[device] = nullptr;
+        return e;
+      }
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(g_pool[device], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = g_pool[device];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 // ascending sort of n_pow (a power of two) keys with their values (bitonic network, one launch per step)
 void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms) {
   for (uint32_t k = 2; k <= n_pow; k <<= 1)
@@ -714,7 +744,7 @@ mrh_status mrh_weld_mesh(mrh_map* m, const float* tris, uint64_t n_tris, float d
   const size_t nblk = (n_tris + kWeldScanBlock - 1) / kWeldScanBlock;
   cudaError_t e = cudaSuccess;
   auto grab = [&](void** p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) e = scratch_alloc(p, bytes, m->device, s);
   };
   grab((void**)&w.keys, 8ull * table);
   grab((void**)&w.mn, 12ull * table);
@@ -752,6 +782,28 @@ mrh_status mrh_weld_mesh(mrh_map* m, const float* tris, uint64_t n_tris, float d
   *n_faces_out = nf;
   if (hc[0] > cap_verts || nf > cap_faces) st = MRH_ERR_CAPACITY;
   return st;
+}
+
+mrh_status mrh_quadtree(const uint8_t* rgb, int width, int height, double threshold, int min_size, int32_t* leaves,
+                        uint64_t capacity, uint64_t* n_leaves_out, int device, void* stream) {
+  if (!rgb || !n_leaves_out || width < 1 || height < 1 || width > 16384 || height > 16384 || min_size < 1 ||
+      std::isnan(threshold) || (capacity > 0 && !leaves))
+    return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  void* scratch = nullptr;
+  MRH_CUDA(scratch_alloc(&scratch, quadtree_scratch_bytes(width, height), device, s));
+  unsigned long long* n_dev = nullptr;
+  cudaError_t e = launch_quadtree(rgb, width, height, threshold, min_size, leaves, capacity, scratch, &n_dev, s, sms);
+  unsigned long long n = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, n_dev, sizeof(n), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "mrh_quadtree");
+  *n_leaves_out = n;
+  return n > capacity ? MRH_ERR_CAPACITY : MRH_OK;
 }
 
 void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {
