@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-mesh", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="only the variance-threshold sweep (Sec. 5.1 analogue): one JSON line, then exit")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
     ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh"], default=None,
@@ -580,6 +582,49 @@ def run_quadtree(wl, frames, reps=3, threshold=0.1, min_size=1, oracle_frames=3)
             "oracle_frames_checked_equal": same}
 
 
+def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), views=(20, 50, 80, 110)):
+    """Variance-threshold sweep on the RGB-D sequence (the synthetic analogue of Sec. 5.1): for each sigma the
+    thresholds are (sigma^2, 4 sigma^2); after n_frames frames it reports the device time per frame (integration
+    only), blocks and payload bytes per level, the collapsed mesh's vertices and faces, and accuracy, completeness and
+    Chamfer-L1 of the map's raycast depth against noise-free renders at `views`."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    frames = camera_frames(wl, 0, n_frames)
+    dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
+    warm = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())  # first-use costs outside the timing
+    for d, c, T in dev[:10]:
+        warm.integrate_depth(mrh.pinhole_from(wl), T, d, c)
+    torch.cuda.synchronize()
+    warm.close()
+    out = []
+    for sig in sigmas:
+        w2 = dataclasses.replace(wl, var_threshold=(sig * sig, 4 * sig * sig))
+        m = mrh.Map(mrh.params_from(w2), device=torch.cuda.current_device())
+        K = mrh.pinhole_from(w2)
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for d, c, T in dev:
+            m.integrate_depth(K, T, d, c)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = m.stats()
+        vb = voxel_bytes(w2)
+        live = st["live_blocks"]
+        soup = m.extract_mesh()
+        verts, faces = m.weld_mesh(soup, w2.base_voxel / (1 << (w2.n_levels - 1)) / 8)
+        ch = chamfer_vs_truth(m, w2, views)
+        out.append({"sigma": sig, "theta": [sig * sig, 4 * sig * sig], "ms_per_frame": round(a.elapsed_time(b) / n_frames, 4),
+                    "live_blocks": live, "payload_MB": [round(n * (8 >> l) ** 3 * vb / 1e6, 1) for l, n in enumerate(live)],
+                    "vertices": int(verts.shape[0]), "faces": int(faces.shape[0]),
+                    "acc_mm": round(1e3 * ch["acc"], 3), "comp_mm": round(1e3 * ch["comp"], 3),
+                    "chamfer_mm": round(1e3 * ch["chamfer"], 3)})
+        del soup, verts, faces
+        m.close()
+    return out
+
+
 def run_lidar_gpu(wl, warmup, steps, flush):
     import torch
     import paper_2511_21459_b300 as mrh
@@ -783,6 +828,12 @@ def main():
         return 0
 
     import torch
+    if args.ablation:
+        from paper_2511_21459_b300 import build as _b
+        _b.build()
+        print(json.dumps({"ablation": run_ablation(wl), "workload": "rgbd-640x480 sequence, first 120 frames",
+                          "data": "synthetic"}))
+        return 0
     rank, world, local = dist_setup(args.gpus)
     from paper_2511_21459_b300 import build
     if rank == 0 or local == 0:
