@@ -226,24 +226,29 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def _reduce_over_ranks(x: float, world: int, op: str) -> float:
+    """All-reduce of one number over the ranks (a device tensor under NCCL, a host tensor under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return _reduce_over_ranks(x, world, "max")
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, world, "sum")
+
+
+def whole_job_rate(units: float, ms: float, world: int) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time (weak scaling)."""
+    return sum_over_ranks(units, world) / (max_over_ranks(ms, world) / 1000.0)
 
 
 def camera_frames(wl, start, count):
