@@ -17,6 +17,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
                                with Euler characteristic 2; the resolution-boundary rule is a reading;
                                vertex collapse: representatives are members within their cluster cell, exact
                                duplicates only at a tiny spacing (closed sphere keeps Euler characteristic 2)
+  streaming (Sec. 3.3)         pinned: nothing moves below the capacity fraction; above it exactly the blocks outside
+                               the view cone / radius (checked by direct geometry) leave, and a block allocated again
+                               comes back bit for bit; LiDAR and camera policies; the rule itself is a reading
   quadtree (Sec. 3.5, Eq. 10)  pinned: closed-form contrast of two-colour and constant regions (byte units);
                                leaves tile the image; thresholds below zero / above the maximum give single pixels /
                                one leaf; a hand-built image gives the hand-counted leaves
@@ -66,7 +69,7 @@ class Pinhole(ctypes.Structure):
 class FrameStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("valid_rays", "touched", "new_blocks", "merged", "split", "fp64_rechecks", "observations",
-                 "updated_voxels")]
+                 "updated_voxels", "evicted", "restored")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -87,6 +90,9 @@ def _load():
         lib.orc_extract_mesh.restype = ctypes.c_int64
         lib.orc_extract_mesh.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64]
         lib.orc_mc_table.argtypes = [vp, vp, vp]
+        lib.orc_set_streaming.argtypes = [vp, ctypes.c_float, ctypes.c_float, vp]
+        lib.orc_archived.restype = ctypes.c_int64
+        lib.orc_archived.argtypes = [vp]
         lib.orc_qt_contrast.restype = ctypes.c_double
         lib.orc_qt_contrast.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_quadtree.restype = ctypes.c_int64
@@ -195,6 +201,16 @@ class OracleMap:
         if not (normals or rgb):
             return out
         return (out,) + ((nrm,) if normals else ()) + ((col,) if rgb else ())
+
+    def set_streaming(self, fraction: float, radius: float, max_blocks):
+        """Capacity-driven streaming (Sec. 3.3): before each frame, when some level holds more than fraction of
+        max_blocks[level] blocks, the blocks outside the frame's view (camera) or farther than radius [m] from the
+        scan origin (LiDAR) move to the archive; a block allocated again returns from it. fraction 0 disables."""
+        mb = np.ascontiguousarray(list(max_blocks) + [0] * (3 - len(max_blocks)), dtype=np.int64)
+        self._lib.orc_set_streaming(self._h, fraction, radius, _p(mb))
+
+    def archived(self) -> int:
+        return int(self._lib.orc_archived(self._h))
 
     def extract_mesh(self) -> np.ndarray:
         """Multi-resolution Marching Cubes triangle soup (n, 3, 3) float32: blocks in key order, voxels in index

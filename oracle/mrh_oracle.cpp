@@ -254,6 +254,7 @@ struct orc_pinhole {
 struct orc_frame_stats {
   int64_t valid_rays, touched, new_blocks, merged, split, fp64_rechecks, observations;
   int64_t updated_voxels;  // distinct voxels updated by the frame
+  int64_t evicted, restored;  // streaming: blocks moved to the archive before the frame, and back by it
 };
 
 // learned level predictor (level_predictor.cpp)
@@ -288,6 +289,8 @@ struct MapBase {
   virtual int raycast(const orc_pinhole*, const double*, float*, float*, uint8_t*) = 0;
   virtual int set_block(const int32_t*, int, const double*, const double*, const double*, const double*) = 0;
   virtual void extract_mesh(std::vector<float>& tris) const = 0;
+  virtual void set_streaming(float fraction, float radius, const int64_t* max_blocks) = 0;
+  virtual int64_t archived() const = 0;
   std::vector<float> mesh;  // last extracted triangle soup
   virtual int64_t count_blocks(int64_t* n_voxels) = 0;
   virtual int extract(int32_t*, uint8_t*, int64_t*, double*, double*, double*, double*) = 0;
@@ -405,15 +408,86 @@ struct Map : MapBase {
     for (const Key& k : cells) {
       touched.insert(k);
       if (blocks.find(k) == blocks.end()) {
+        st->new_blocks++;
+        bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
+        auto ar = archive.find(k);
+        if (ar != archive.end()) {  // streamed back in: level and payload as they were archived
+          blocks[k] = std::move(ar->second);
+          archive.erase(ar);
+          st->restored++;
+          continue;
+        }
         Block<R, Sto>& b = blocks[k];
         b.level = 0;
         b.resize(n[0], P.has_color != 0);
         if (fresh) fresh->push_back(k);
-        st->new_blocks++;
-        bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
       }
     }
   }
+
+  // ---- capacity-driven streaming (Sec. 3.3). Reading: before a frame, when some level holds more blocks than
+  // `fraction` of its pool (float comparison of the counts), every block outside the frame's view moves to the archive
+  // (level and payload kept): for a camera, a block whose circumscribed sphere misses the pinhole's view cone between
+  // min and max depth; for a LiDAR scan, a block whose centre lies farther than `radius` from the scan origin. A block
+  // the frame allocates again comes back from the archive as it was.
+  bool stream_on = false;
+  float stream_fraction = 0.0f, stream_radius = 0.0f;
+  int64_t stream_max[3] = {0, 0, 0};
+  std::map<Key, Block<R, Sto>> archive;
+
+  bool stream_due() const {
+    if (!stream_on) return false;
+    int64_t cnt[3] = {0, 0, 0};
+    for (auto& kv : blocks) cnt[kv.second.level]++;
+    for (int l = 0; l < L; ++l)
+      if ((float)cnt[l] > stream_fraction * (float)stream_max[l]) return true;
+    return false;
+  }
+  void centre_of(const Key& k, float c[3]) const {
+    c[0] = ((float)k.x + 0.5f) * E_f;
+    c[1] = ((float)k.y + 0.5f) * E_f;
+    c[2] = ((float)k.z + 0.5f) * E_f;
+  }
+  template <class Outside>
+  void evict(Outside&& outside, orc_frame_stats* st) {
+    for (auto it = blocks.begin(); it != blocks.end();) {
+      float c[3];
+      centre_of(it->first, c);
+      if (outside(c)) {
+        archive[it->first] = std::move(it->second);
+        it = blocks.erase(it);
+        st->evicted++;
+      } else {
+        ++it;
+      }
+    }
+  }
+  void stream_out_camera(const orc_pinhole* K, const float Rf[9], const float tf[3], orc_frame_stats* st) {
+    if (!stream_due()) return;
+    const float rad = 0.8660254f * E_f;
+    const float tx = std::max(K->cx, (float)K->width - K->cx) / K->fx;
+    const float ty = std::max(K->cy, (float)K->height - K->cy) / K->fy;
+    const float kx = std::sqrt(1.0f + tx * tx), ky = std::sqrt(1.0f + ty * ty);
+    evict([&](const float c[3]) {
+      const float d0 = c[0] - tf[0], d1 = c[1] - tf[1], d2 = c[2] - tf[2];
+      const float xc = Rf[0] * d0 + Rf[3] * d1 + Rf[6] * d2;
+      const float yc = Rf[1] * d0 + Rf[4] * d1 + Rf[7] * d2;
+      const float zc = Rf[2] * d0 + Rf[5] * d1 + Rf[8] * d2;
+      const bool inside = zc + rad >= K->min_depth && zc - rad <= K->max_depth &&
+                          std::fabs(xc) <= zc * tx + rad * kx && std::fabs(yc) <= zc * ty + rad * ky;
+      return !inside;
+    }, st);
+  }
+  void stream_out_lidar(const double* T, orc_frame_stats* st) {
+    if (!stream_due()) return;
+    const float o[3] = {(float)T[3], (float)T[7], (float)T[11]};
+    const float r2 = stream_radius * stream_radius;
+    evict([&](const float c[3]) {
+      const float d0 = c[0] - o[0], d1 = c[1] - o[1], d2 = c[2] - o[2];
+      return d0 * d0 + d1 * d1 + d2 * d2 > r2;
+    }, st);
+  }
+  int64_t archived() const override { return (int64_t)archive.size(); }
 
   // ---- Eq. 3 with w_k = 1 in Welford's incremental form, and the Welford S2 update (Sec. 3.2.1).
   // The running mean D + (d - D)/(W + 1) equals (W D + d)/(W + 1) of Eq. 3 in exact arithmetic; this form keeps a
@@ -590,6 +664,7 @@ struct Map : MapBase {
     }
     const float tauf = P.truncation;
     const float Sfix = 65536.0f / E_f;
+    stream_out_camera(K, Rf, tf, st);
     std::set<Key> touched;
     std::vector<Key> fresh;  // blocks created by this frame
     for (int v_ = 0; v_ < K->height; ++v_) {
@@ -701,6 +776,7 @@ struct Map : MapBase {
   // ---- LiDAR integration (Sec. 3.1.1, Eq. 1)
   int integrate_points(const double* T, const float* xyz, int64_t npts, orc_frame_stats* st) override {
     std::memset(st, 0, sizeof(*st));
+    stream_out_lidar(T, st);
     const double tau_d = (double)P.truncation;
     const double Sfix = 65536.0 / (double)E_f;
     const double rmin2 = (double)P.min_range * (double)P.min_range, rmax2 = (double)P.max_range * (double)P.max_range;
@@ -1000,6 +1076,13 @@ struct Map : MapBase {
     return 0;
   }
 
+  void set_streaming(float fraction, float radius, const int64_t* max_blocks) override {
+    stream_on = fraction > 0.0f;
+    stream_fraction = fraction;
+    stream_radius = radius;
+    for (int l = 0; l < 3; ++l) stream_max[l] = max_blocks[l];
+  }
+
   // ---- test hook: write one block (created at `level` if missing) with the given payload
   int set_block(const int32_t* key, int level, const double* D, const double* W, const double* S2,
                 const double* C) override {
@@ -1235,6 +1318,12 @@ int orc_set_block(void* h, const int32_t* key, int level, const double* D, const
                   const double* C) {
   return ((MapBase*)h)->set_block(key, level, D, W, S2, C);
 }
+
+// capacity-driven streaming (fraction 0 disables); max_blocks[3] = pool capacity per level
+void orc_set_streaming(void* h, float fraction, float radius, const int64_t* max_blocks) {
+  ((MapBase*)h)->set_streaming(fraction, radius, max_blocks);
+}
+int64_t orc_archived(void* h) { return ((MapBase*)h)->archived(); }
 
 // Extract the mesh; returns the triangle count. out (9 floats per triangle) may be NULL or smaller (cap triangles):
 // the extraction is kept and later calls with out != NULL and extract == 0 copy it.
