@@ -96,6 +96,9 @@ typedef struct {
                                 once) */
   uint64_t lidar_restaged;   /* LiDAR: points of the last scan whose observations exceeded the per-point stage and
                                 were written by a second walk (correct either way; a cost diagnostic) */
+  uint64_t evicted;          /* streaming: blocks moved to the archive before the last frame */
+  uint64_t restored;         /* streaming: archived blocks the last frame allocated again (brought back) */
+  uint64_t archived;         /* streaming: blocks in the archive now */
   uint32_t status;           /* sticky device status bits (see mrh_status) */
 } mrh_stats;
 
@@ -109,7 +112,8 @@ enum {
   MRH_K_RELEASE = 5,   /* freed heap blocks back to their free stacks */
   MRH_K_RAYCAST = 6,   /* raycast */
   MRH_K_MESH = 7,      /* Marching Cubes mesh extraction */
-  MRH_K_COUNT = 8
+  MRH_K_STREAM = 8,    /* streaming: eviction before a frame, restore after binning */
+  MRH_K_COUNT = 9
 };
 
 /* Create a map on CUDA device `device`. Allocates the hash table, one block heap per level and per-frame lists.
@@ -298,6 +302,22 @@ mrh_status mrh_quadtree(const uint8_t* rgb_dev, int width, int height, double th
  * triples (-1 unused), edge_end[12 * 2] corner pairs. Corner c lies at (c & 1, c >> 1 & 1, c >> 2 & 1) of the cell;
  * edge 4a + r joins the r-th corner (ascending) with bit a clear to its neighbour along axis a. */
 void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
+
+/* Capacity-driven streaming (Sec. 3.3; the selection rule is this library's reading). Before each integration call,
+ * when some level holds more than `fraction` (0 < fraction <= 1) of its max_blocks (float comparison of the counts),
+ * every resident block outside the frame's view moves to the archive with its level and payload: for a depth frame, a
+ * block whose circumscribed sphere misses the pinhole's view cone between min_depth and max_depth; for a point scan, a
+ * block whose centre lies farther than `radius` metres from the scan origin. Its hash slot becomes a tombstone (not
+ * reused: size hash_slots_log2 for every block the map will ever hold) and its heap block is freed. A later frame that
+ * allocates the key again gets the block back at its archived level before fusion. The archive holds archive_blocks
+ * blocks in pinned host memory (archive_blocks x the level-0 block size), mapped into the device's address space, so
+ * neither direction needs a host round trip; a key keeps its archive slot. Extraction, meshing and raycasting see the
+ * resident blocks only. fraction = 0 switches streaming off (archived blocks stay archived; it cannot be switched on
+ * again). MRH_ERR_INVALID_ARG with a predictor or feature capture set (they are not combined), for a new capacity while
+ * the archive holds blocks, or for arguments out of range; MRH_ERR_OUT_OF_MEMORY if the archive cannot be allocated.
+ * A full archive leaves the remaining blocks resident and reports MRH_ERR_CAPACITY through the status. Maps with
+ * streaming are not accepted by mrh_batch_create. Synchronises the device. */
+mrh_status mrh_set_streaming(mrh_map* map, float fraction, float radius, uint32_t archive_blocks);
 
 /* Number of allocated blocks and voxels (synchronises `stream`). */
 mrh_status mrh_count_blocks(mrh_map* map, uint64_t* n_blocks, uint64_t* n_voxels, void* stream);

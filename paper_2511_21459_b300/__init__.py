@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("new_blocks", ctypes.c_uint64), ("merged", ctypes.c_uint64), ("split", ctypes.c_uint64),
                 ("fp64_rechecks", ctypes.c_uint64), ("live_blocks", ctypes.c_uint64 * 3),
                 ("touched_level", ctypes.c_uint64 * 3), ("observations", ctypes.c_uint64),
-                ("updated_voxels", ctypes.c_uint64), ("lidar_restaged", ctypes.c_uint64), ("status", ctypes.c_uint32)]
+                ("updated_voxels", ctypes.c_uint64), ("lidar_restaged", ctypes.c_uint64), ("evicted", ctypes.c_uint64),
+                ("restored", ctypes.c_uint64), ("archived", ctypes.c_uint64), ("status", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("live_blocks", "touched_level")}
@@ -59,7 +60,7 @@ class Stats(ctypes.Structure):
         return d
 
 
-KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast", "mesh"]
+KERNEL_GROUPS = ["begin", "alloc", "bin", "lidar_obs", "fuse", "release", "raycast", "mesh", "stream"]
 
 MRH_BATCH_GRAPH, MRH_BATCH_AUTOTUNE = 1, 2
 
@@ -76,7 +77,8 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
-           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree"]
+           "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree",
+           "mrh_set_streaming"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -100,6 +102,7 @@ def lib():
         L.mrh_extract_mesh.argtypes = [vp, vp, u64, ctypes.POINTER(u64), vp]
         L.mrh_mesh_case_table.argtypes = [vp, vp, vp]
         L.mrh_mesh_case_table.restype = None
+        L.mrh_set_streaming.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
         L.mrh_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, u64,
                                    ctypes.POINTER(u64), ctypes.c_int, vp]
         L.mrh_weld_mesh.argtypes = [vp, vp, u64, ctypes.c_float, vp, u64, vp, u64, ctypes.POINTER(u64),
@@ -304,6 +307,12 @@ class Map:
         _check(self._lib.mrh_extract_mesh(self._h, ctypes.c_void_p(out.data_ptr()), int(capacity), ctypes.byref(n),
                                           _stream(stream)), "mrh_extract_mesh")
         return out[:n.value]
+
+    def set_streaming(self, fraction: float, radius: float = 0.0, archive_blocks: int = 1 << 16):
+        """Capacity-driven streaming (see mrh_set_streaming): fraction of a level's pool that triggers eviction, the
+        LiDAR radius [m], and the archive's capacity in blocks."""
+        _check(self._lib.mrh_set_streaming(self._h, float(fraction), float(radius), int(archive_blocks)),
+               "mrh_set_streaming")
 
     def weld_mesh(self, tris, delta: float, stream=None):
         """Vertex collapse of a triangle soup (n, 3, 3) float32 CUDA tensor on a grid of spacing delta [m]:

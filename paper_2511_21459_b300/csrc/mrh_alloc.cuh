@@ -213,14 +213,36 @@ __device__ inline void alloc_points_cta(const MapDev& m, const PoseD& P, const f
   if (threadIdx.x == 0 && *s_valid) atomicAdd(&m.st->valid_rays, *s_valid);
 }
 
+// Archive entry of a key (streaming), or -1.
+__device__ inline int archive_find(const MapDev& m, unsigned long long key) {
+  uint32_t e = (uint32_t)hash_key(key, m.ar_mask);
+  for (uint32_t p = 0; p <= m.ar_mask; ++p, e = (e + 1) & m.ar_mask) {
+    const unsigned long long k = m.ar_keys[e];
+    if (k == key) return (int)e;
+    if (k == kEmptyKey) return -1;
+  }
+  return -1;
+}
+
 // Touched entry i of this frame, first half: a new block gets a heap block of the finest level (Sec. 3.2.1: "we
 // initialize the voxel blocks to the finest resolution"), or of new_level when the learned predictor gave one, and
-// its brick is recorded for the raycaster. Returns the block's level and heap value, or -1 when the block has no
-// storage (its level's heap is empty: it is not fused and is retried in later frames).
+// its brick is recorded for the raycaster; a block streamed out earlier comes back at its archived level and queues
+// the copy of its payload (Sec. 3.3). Returns the block's level and heap value, or -1 when the block has no storage
+// (its level's heap is empty: it is not fused and is retried in later frames).
 __device__ inline int bin_entry(const MapDev& m, uint32_t s, int new_level, uint32_t* val_out) {
   uint32_t val = m.slots[s].val;
   if (val == kValPending) {
-    const int l = new_level;
+    int l = new_level;
+    int ar = -1;
+    uint32_t ar_val = 0;
+    if (m.ar_keys) {
+      ar = archive_find(m, m.slots[s].key);
+      if (ar >= 0) {
+        ar_val = m.ar_vals[ar];
+        if (ar_val & kArPresent) l = (int)((ar_val >> 28) & 3u);
+        else ar = -1;
+      }
+    }
     {
       int bx, by, bz;
       unpack_key(m.slots[s].key, &bx, &by, &bz);
@@ -237,9 +259,16 @@ __device__ inline int bin_entry(const MapDev& m, uint32_t s, int new_level, uint
       return -1;
     }
     uint32_t id = m.free_stack[l][t - 1];
-    val = id | ((uint32_t)l << 28) | kValNew;
+    val = id | ((uint32_t)l << 28) | (ar >= 0 ? 0u : kValNew);
     m.slots[s].val = val;
     atomicAdd(&m.st->new_blocks, 1u);
+    if (ar >= 0) {
+      const uint32_t j = atomicAdd(&m.st->n_restore, 1u);
+      m.restore_jobs[j] = make_uint2(val, ar_val & 0x0FFFFFFFu);
+      m.ar_vals[ar] = ar_val & ~kArPresent;
+      atomicAdd(&m.st->restored, 1u);
+      atomicSub(&m.st->ar_present, 1u);
+    }
   }
   *val_out = val;
   return (int)((val >> 28) & 3u);
@@ -304,6 +333,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->updated_voxels = 0;
   st->n_over = 0;
   st->item_next = 0;
+  st->evicted = st->restored = st->n_restore = 0;
 }
 
 }  // namespace

@@ -299,6 +299,10 @@ mrh_status mrh_batch_create(mrh_map* const* maps, const mrh_pinhole* cams, int n
   const MapDev* d0 = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!maps[i]) return MRH_ERR_INVALID_ARG;
+    {
+      int dv = 0, sm = 0;
+      if (map_dev(maps[i], &dv, &sm)->ar_keys) return MRH_ERR_INVALID_ARG;  // streaming maps are not batched
+    }
     int dev = 0, s = 0;
     const MapDev* d = map_dev(maps[i], &dev, &s);
     if (i == 0) {

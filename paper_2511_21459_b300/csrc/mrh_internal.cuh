@@ -49,6 +49,9 @@ constexpr uint32_t kStListFull = 1u << 2;
 constexpr uint32_t kStSegment = 1u << 3;
 constexpr uint32_t kStObsFull = 1u << 4;
 constexpr uint32_t kStTimeout = 1u << 5;  // a bounded wait on an async copy gave up
+constexpr uint32_t kStArchiveFull = 1u << 6;  // streaming: the archive had no slot for a block (it stayed resident)
+constexpr unsigned long long kTombKey = ~1ull;  // a hash slot whose block was streamed out (never a valid key)
+constexpr uint32_t kArPresent = 1u << 30;       // archive entry: its payload is in the archive (not resident)
 
 struct __align__(16) Slot {
   unsigned long long key;
@@ -77,6 +80,11 @@ struct DevState {
   uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
   uint32_t n_over;     // LiDAR: points in stage_over
   uint32_t item_next;  // LiDAR point fusion: next work item to hand out
+  uint32_t evicted, restored;  // streaming: blocks moved to the archive before this frame, and back by it
+  uint32_t n_restore;          // streaming: restore jobs of this frame
+  uint32_t ar_used;            // streaming: archive slots handed out (each key keeps its slot)
+  uint32_t ar_present;         // streaming: blocks currently in the archive
+  uint32_t evict_go;           // streaming: this frame's capacity check (taken once, before any eviction)
   unsigned long long mesh_tris;  // triangles counted by the last mesh extraction
 };
 
@@ -136,6 +144,18 @@ struct MapDev {
   double thr_merge[3], thr_split[3];
   float thr_merge_f[3], thr_split_f[3];
   float min_range, max_range;
+  // capacity-driven streaming (off when ar_keys is null): the archive index (key -> slot | level << 28 | kArPresent,
+  // linear probing), the archive itself (ar_slot_bytes per slot, pinned host memory mapped into the device's address
+  // space) and this frame's restore jobs {heap value, archive slot}
+  float stream_fraction;
+  float stream_radius;
+  unsigned long long* ar_keys;
+  uint32_t* ar_vals;
+  uint32_t ar_mask;
+  uint32_t ar_cap;
+  uint32_t ar_slot_bytes;
+  uint8_t* ar_data;
+  uint2* restore_jobs;
 };
 
 struct CamArgs {
@@ -449,6 +469,10 @@ cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clus
 void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms);
 // stream-ordered scratch from a pool owned by the library (one per device, memory kept for reuse)
 cudaError_t scratch_alloc(void** p, size_t bytes, int device, cudaStream_t s);
+// capacity-driven streaming (mrh_stream.cu)
+void launch_evict_camera(const MapDev& m, const CamArgs& c, cudaStream_t s, int sms);
+void launch_evict_lidar(const MapDev& m, const double* T, cudaStream_t s, int sms);
+void launch_restore(const MapDev& m, cudaStream_t s, int sms);
 // contrast quadtree (mrh_quadtree.cu)
 size_t quadtree_scratch_bytes(int width, int height);
 cudaError_t launch_quadtree(const uint8_t* rgb, int width, int height, double threshold, int min_size,

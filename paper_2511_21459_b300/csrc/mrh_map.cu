@@ -40,6 +40,8 @@ struct mrh_map {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   // per-frame images for the camera path (range image, packed colour), grown to the largest frame seen
+  // streaming archive (pinned host memory, mapped into the device's address space)
+  uint8_t* archive_host = nullptr;
   float* rho_img = nullptr;
   uint32_t* rgb_img = nullptr;
   size_t img_pixels = 0;
@@ -97,6 +99,7 @@ mrh_status status_from_bits(uint32_t bits) {
   if (bits & kStListFull) return MRH_ERR_LIST_FULL;
   if (bits & kStObsFull) return MRH_ERR_LIST_FULL;
   if (bits & kStSegment) return MRH_ERR_INVALID_ARG;
+  if (bits & kStArchiveFull) return MRH_ERR_CAPACITY;
   return MRH_OK;
 }
 
@@ -334,6 +337,8 @@ void free_capture(mrh_map* m) {
 void free_all(mrh_map* m) {
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
+  if (m->archive_host) cudaFreeHost(m->archive_host);
+  m->archive_host = nullptr;
   if (m->rho_img) cudaFree(m->rho_img);
   if (m->rgb_img) cudaFree(m->rgb_img);
   if (m->pred_buf) cudaFree(m->pred_buf);
@@ -567,8 +572,68 @@ mrh_status mrh_map_destroy(mrh_map* m) {
   return MRH_OK;
 }
 
+mrh_status mrh_set_streaming(mrh_map* m, float fraction, float radius, uint32_t archive_blocks) {
+  if (!m || !(fraction >= 0.0f && fraction <= 1.0f) || !(radius >= 0.0f) || !std::isfinite(radius))
+    return MRH_ERR_INVALID_ARG;
+  if (fraction > 0.0f && (m->d.pred_w || m->d.cap_feat)) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  MRH_CUDA(cudaDeviceSynchronize());
+  MapDev& d = m->d;
+  if (fraction == 0.0f) {  // off: archived blocks stay archived
+    d.stream_fraction = 0.0f;
+    d.ar_keys = nullptr;
+    return MRH_OK;
+  }
+  if (!m->archive_host || archive_blocks != d.ar_cap) {
+    DevState hs;
+    MRH_CUDA(cudaMemcpy(&hs, d.st, sizeof(hs), cudaMemcpyDeviceToHost));
+    if (m->archive_host && hs.ar_present > 0) return MRH_ERR_INVALID_ARG;  // the archive holds blocks
+    if (archive_blocks == 0 || archive_blocks > (1u << 27)) return MRH_ERR_INVALID_ARG;
+    if (m->archive_host) {
+      cudaFreeHost(m->archive_host);
+      m->archive_host = nullptr;
+    }
+    uint32_t entries = 1024;
+    while (entries < 2u * archive_blocks) entries <<= 1;
+    const size_t slot_bytes = d.block_bytes[0];
+    cudaError_t e = cudaHostAlloc((void**)&m->archive_host, (size_t)archive_blocks * slot_bytes,
+                                  cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+      m->archive_host = nullptr;
+      return MRH_ERR_OUT_OF_MEMORY;
+    }
+    void* dev_ptr = nullptr;
+    MRH_CUDA(cudaHostGetDevicePointer(&dev_ptr, m->archive_host, 0));
+    unsigned long long* keys = nullptr;
+    uint32_t* vals = nullptr;
+    uint2* jobs = nullptr;
+    if (dev_alloc(m, &keys, entries) != MRH_OK || dev_alloc(m, &vals, entries) != MRH_OK ||
+        dev_alloc(m, &jobs, d.max_touched) != MRH_OK)
+      return MRH_ERR_OUT_OF_MEMORY;
+    MRH_CUDA(cudaMemset(keys, 0xFF, (size_t)entries * sizeof(unsigned long long)));
+    hs.ar_used = 0;
+    hs.ar_present = 0;
+    MRH_CUDA(cudaMemcpy(&d.st->ar_used, &hs.ar_used, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    MRH_CUDA(cudaMemcpy(&d.st->ar_present, &hs.ar_present, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    d.ar_keys = keys;
+    d.ar_vals = vals;
+    d.ar_mask = entries - 1;
+    d.ar_cap = archive_blocks;
+    d.ar_slot_bytes = (uint32_t)slot_bytes;
+    d.ar_data = (uint8_t*)dev_ptr;
+    d.restore_jobs = jobs;
+  } else if (!d.ar_keys) {
+    return MRH_ERR_INVALID_ARG;  // re-enabling after switching off is not supported
+  }
+  d.stream_fraction = fraction;
+  d.stream_radius = radius;
+  return MRH_OK;
+}
+
 mrh_status mrh_set_predictor(mrh_map* m, const uint16_t* bf16_weights_host, uint64_t n_params) {
   if (!m) return MRH_ERR_INVALID_ARG;
+  if (bf16_weights_host && m->d.ar_keys) return MRH_ERR_INVALID_ARG;  // not combined with streaming
   if (!bf16_weights_host) {
     m->d.pred_w = nullptr;
     return MRH_OK;
@@ -586,7 +651,7 @@ mrh_status mrh_set_predictor(mrh_map* m, const uint16_t* bf16_weights_host, uint
 }
 
 mrh_status mrh_set_feature_capture(mrh_map* m, uint32_t capacity) {
-  if (!m) return MRH_ERR_INVALID_ARG;
+  if (!m || (capacity > 0 && m->d.ar_keys)) return MRH_ERR_INVALID_ARG;
   DeviceGuard guard(m->device);
   if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
   MRH_CUDA(cudaDeviceSynchronize());
@@ -649,8 +714,16 @@ mrh_status mrh_integrate_depth(mrh_map* m, const mrh_pinhole* K, const double* T
   }
   const uint8_t* rgb_in = m->p.has_color ? rgb : nullptr;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
+  if (m->d.ar_keys) {
+    KernelScope ks(m, MRH_K_STREAM, s, 1);
+    launch_evict_camera(m->d, c, s, m->sms);
+  }
   { KernelScope ks(m, MRH_K_ALLOC, s, 1); launch_alloc_depth(m->d, c, depth, rgb_in, m->rho_img, m->rgb_img, s); }
   { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin_camera(m->d, c, m->rho_img, s, m->sms); }
+  if (m->d.ar_keys) {
+    KernelScope ks(m, MRH_K_STREAM, s, 1);
+    launch_restore(m->d, s, m->sms);
+  }
   {
     KernelScope ks(m, MRH_K_FUSE, s, 1);
     launch_fuse_depth(m->d, c, m->rho_img, rgb_in ? m->rgb_img : nullptr, s, m->sms);
@@ -683,8 +756,16 @@ mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz
   m->d.stage_len = m->stage_len;
   m->d.stage_over = m->stage_over;
   { KernelScope ks(m, MRH_K_BEGIN, s, 1); k_begin<<<1, 1, 0, s>>>(m->d.st); }
+  if (m->d.ar_keys) {
+    KernelScope ks(m, MRH_K_STREAM, s, 1);
+    launch_evict_lidar(m->d, T_ws, s, m->sms);
+  }
   { KernelScope ks(m, MRH_K_ALLOC, s, n ? 1 : 0); launch_alloc_points(m->d, T_ws, xyz, n, s); }
   { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
+  if (m->d.ar_keys) {
+    KernelScope ks(m, MRH_K_STREAM, s, 1);
+    launch_restore(m->d, s, m->sms);
+  }
   { KernelScope ks(m, MRH_K_LIDAR_OBS, s, n ? 4 : 2); launch_lidar_observations(m->d, T_ws, xyz, n, s, m->sms); }
   { KernelScope ks(m, MRH_K_FUSE, s, 1); launch_fuse_points(m->d, T_ws, xyz, n, s, m->sms); }
   { KernelScope ks(m, MRH_K_RELEASE, s, 1); k_release<<<m->sms, 256, 0, s>>>(m->d); }
@@ -940,6 +1021,9 @@ mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
   out->observations = hs.observations;
   out->updated_voxels = hs.updated_voxels;
   out->lidar_restaged = hs.n_over;
+  out->evicted = hs.evicted;
+  out->restored = hs.restored;
+  out->archived = hs.ar_present;
   out->status = hs.status;
   return status_from_bits(hs.status);
 }
