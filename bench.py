@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-mesh", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
+    ap.add_argument("--no-streaming", action="store_true")
     ap.add_argument("--ablation", action="store_true",
                     help="only the variance-threshold sweep (Sec. 5.1 analogue): one JSON line, then exit")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -630,6 +631,53 @@ def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), v
     return out
 
 
+def run_streaming(wl, n_scans=150, pools=(1 << 18, 1 << 16, 1 << 16), fraction=0.5, radius=80.0,
+                  archive=1 << 19):
+    """Capacity-driven streaming (Sec. 3.3) on the LiDAR street: n_scans full scans 1 m apart into pools of `pools`
+    blocks, streaming on at `fraction` with a `radius` m LiDAR radius; the same scans without streaming for the block
+    count it would reach. Device time per scan (CUDA events over all scans, eviction and restore included)."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    w2 = dataclasses.replace(wl, max_blocks=pools)
+    scene = w2.scene()
+    scans = [synth.render_lidar(w2, k, scene=scene) for k in range(n_scans)]
+    dev = [(torch.from_numpy(x).cuda(), T) for x, T in scans]
+    res = {}
+    for on in (True, False):
+        m = mrh.Map(mrh.params_from(w2), device=torch.cuda.current_device())
+        if on:
+            m.set_streaming(fraction, radius, archive)
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = rs = rays = done = 0
+        peak = 0
+        a.record(stream)
+        for x, T in dev:
+            m.integrate_points(T, x)
+            st = m.stats()
+            if st["status_code"] != 0:
+                break
+            done += 1
+            ev += st["evicted"]
+            rs += st["restored"]
+            rays += st["valid_rays"]
+            peak = max(peak, sum(st["live_blocks"]))
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = m.stats()
+        key = "streaming" if on else "no_streaming"
+        res[key] = {"scans": done, "status": st["status_code"],
+                    "ms_per_scan": round(a.elapsed_time(b) / max(done, 1), 4),
+                    "points_per_s": rays / (a.elapsed_time(b) / 1000.0), "peak_resident_blocks": peak,
+                    "resident_blocks_end": sum(st["live_blocks"]), "evicted": ev, "restored": rs,
+                    "archived_end": st["archived"]}
+        m.close()
+    res.update({"pools": list(pools), "fraction": fraction, "radius_m": radius, "archive_blocks": archive,
+                "note": "stats are read after every scan (a host sync inside the timed span, both runs alike)"})
+    return res
+
+
 def run_lidar_gpu(wl, warmup, steps, flush):
     import torch
     import paper_2511_21459_b300 as mrh
@@ -931,6 +979,10 @@ def main():
                              if v[1] > 0},
                  "fuse_achieved_GBps": round(lres["fuse_bytes"] / (lprof["fuse"][0] / 1000.0) / 1e9, 1)}
 
+    streaming = None
+    if rank == 0 and not args.no_lidar and not args.no_streaming:
+        streaming = run_streaming(synth.lidar())
+
     batched = None
     if not args.no_batched:
         bres = run_batched(6, args.batched_steps, flush)
@@ -963,7 +1015,8 @@ def main():
                 "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
-                "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh, "quadtree": quad}
+                "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh, "quadtree": quad,
+                "streaming": streaming}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
