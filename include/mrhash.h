@@ -319,6 +319,17 @@ void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
  * streaming are not accepted by mrh_batch_create. Synchronises the device. */
 mrh_status mrh_set_streaming(mrh_map* map, float fraction, float radius, uint32_t archive_blocks);
 
+/* Save the map to a file (the persistence half of streaming, Sec. 3.3): the creation parameters, then every resident
+ * block and every archived block (key, level, payload in the library's block layout; resident ones first, each group
+ * in key order). Synchronises `stream` and the device copies it needs. MRH_ERR_INVALID_ARG when the file cannot be
+ * written. */
+mrh_status mrh_save_map(mrh_map* map, const char* path, void* stream);
+
+/* Create a map on `device` from a file written by mrh_save_map, with every saved block resident (archived ones
+ * included; streaming is off). MRH_ERR_INVALID_ARG for a missing or malformed file; MRH_ERR_HASH_FULL /
+ * MRH_ERR_POOL_EMPTY when the saved blocks do not fit the saved capacities. *out is NULL on error. */
+mrh_status mrh_load_map(const char* path, int device, mrh_map** out);
+
 /* Number of allocated blocks and voxels (synchronises `stream`). */
 mrh_status mrh_count_blocks(mrh_map* map, uint64_t* n_blocks, uint64_t* n_voxels, void* stream);
 

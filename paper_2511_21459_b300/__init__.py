@@ -78,7 +78,7 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
            "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree",
-           "mrh_set_streaming"]
+           "mrh_set_streaming", "mrh_save_map", "mrh_load_map"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -103,6 +103,8 @@ def lib():
         L.mrh_mesh_case_table.argtypes = [vp, vp, vp]
         L.mrh_mesh_case_table.restype = None
         L.mrh_set_streaming.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
+        L.mrh_save_map.argtypes = [vp, ctypes.c_char_p, vp]
+        L.mrh_load_map.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(vp)]
         L.mrh_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, u64,
                                    ctypes.POINTER(u64), ctypes.c_int, vp]
         L.mrh_weld_mesh.argtypes = [vp, vp, u64, ctypes.c_float, vp, u64, vp, u64, ctypes.POINTER(u64),
@@ -245,6 +247,20 @@ class Map:
         _check(self._lib.mrh_map_create(ctypes.byref(params), device, ctypes.byref(h)), "mrh_map_create")
         self._h = h
 
+    @classmethod
+    def load(cls, path: str, device: int = 0) -> "Map":
+        """A map on ``device`` from a file written by ``Map.save`` (see mrh_load_map)."""
+        self = cls.__new__(cls)
+        self._lib = lib()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self._lib.mrh_load_map(os.fsencode(path), device, ctypes.byref(h)), "mrh_load_map")
+        self._h = h
+        with open(path, "rb") as f:  # the creation parameters follow the magic, version and size words
+            f.seek(16)
+            self.params = Params.from_buffer_copy(f.read(ctypes.sizeof(Params)))
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.mrh_map_destroy(self._h)
@@ -313,6 +329,10 @@ class Map:
         LiDAR radius [m], and the archive's capacity in blocks."""
         _check(self._lib.mrh_set_streaming(self._h, float(fraction), float(radius), int(archive_blocks)),
                "mrh_set_streaming")
+
+    def save(self, path: str, stream=None):
+        """Write the map (resident and archived blocks) to a file (see mrh_save_map)."""
+        _check(self._lib.mrh_save_map(self._h, os.fsencode(path), _stream(stream)), "mrh_save_map")
 
     def weld_mesh(self, tris, delta: float, stream=None):
         """Vertex collapse of a triangle soup (n, 3, 3) float32 CUDA tensor on a grid of spacing delta [m]:

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "mrhash.h"
 
 namespace mrh {
@@ -473,6 +475,15 @@ cudaError_t scratch_alloc(void** p, size_t bytes, int device, cudaStream_t s);
 void launch_evict_camera(const MapDev& m, const CamArgs& c, cudaStream_t s, int sms);
 void launch_evict_lidar(const MapDev& m, const double* T, cudaStream_t s, int sms);
 void launch_restore(const MapDev& m, cudaStream_t s, int sms);
+// map save / load (mrh_io.cu): block payloads to and from a host blob (one staging copy each way)
+cudaError_t io_blocks_to_blob(const MapDev& m, const std::vector<uint32_t>& level_ids,
+                              const std::vector<uint64_t>& offsets, uint8_t* blob_host, uint64_t blob_bytes,
+                              cudaStream_t s, int sms);
+cudaError_t io_blob_to_blocks(const MapDev& m, const std::vector<int32_t>& keys, const std::vector<uint32_t>& levels,
+                              const std::vector<uint64_t>& offsets, const uint8_t* blob_host, uint64_t blob_bytes,
+                              cudaStream_t s, int sms);
+const char* io_magic();
+uint32_t io_version();
 // contrast quadtree (mrh_quadtree.cu)
 size_t quadtree_scratch_bytes(int width, int height);
 cudaError_t launch_quadtree(const uint8_t* rgb, int width, int height, double threshold, int min_size,

@@ -887,6 +887,131 @@ mrh_status mrh_quadtree(const uint8_t* rgb, int width, int height, double thresh
   return n > capacity ? MRH_ERR_CAPACITY : MRH_OK;
 }
 
+mrh_status mrh_save_map(mrh_map* m, const char* path, void* stream) {
+  if (!m || !path) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(m->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  MRH_CUDA(cudaStreamSynchronize(s));
+  const MapDev& d = m->d;
+  struct Rec {
+    int32_t key[3];
+    uint32_t level;
+    uint32_t level_id;        // resident: level << 28 | heap id
+    const uint8_t* archived;  // archived: its payload in the host archive
+  };
+  std::vector<Rec> res, arc;
+  {
+    std::vector<Slot> slots((size_t)d.slot_mask + 1);
+    MRH_CUDA(cudaMemcpy(slots.data(), d.slots, slots.size() * sizeof(Slot), cudaMemcpyDeviceToHost));
+    for (const Slot& sl : slots) {
+      if (sl.key == kEmptyKey || sl.key == kTombKey || sl.val == kValPending || (sl.val & kValNew)) continue;
+      Rec r{};
+      unpack_key(sl.key, &r.key[0], &r.key[1], &r.key[2]);
+      r.level = (sl.val >> 28) & 3u;
+      r.level_id = sl.val & (kPtrMask | (3u << 28));
+      res.push_back(r);
+    }
+  }
+  if (d.ar_keys && m->archive_host) {
+    std::vector<unsigned long long> keys((size_t)d.ar_mask + 1);
+    std::vector<uint32_t> vals(keys.size());
+    MRH_CUDA(cudaMemcpy(keys.data(), d.ar_keys, keys.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    MRH_CUDA(cudaMemcpy(vals.data(), d.ar_vals, vals.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < keys.size(); ++i) {
+      if (keys[i] == kEmptyKey || !(vals[i] & kArPresent)) continue;
+      Rec r{};
+      unpack_key(keys[i], &r.key[0], &r.key[1], &r.key[2]);
+      r.level = (vals[i] >> 28) & 3u;
+      r.archived = m->archive_host + (size_t)(vals[i] & 0x0FFFFFFFu) * d.ar_slot_bytes;
+      arc.push_back(r);
+    }
+  }
+  auto by_key = [](const Rec& a, const Rec& b) {
+    return std::lexicographical_compare(a.key, a.key + 3, b.key, b.key + 3);
+  };
+  std::sort(res.begin(), res.end(), by_key);
+  std::sort(arc.begin(), arc.end(), by_key);
+  std::vector<uint32_t> ids(res.size());
+  std::vector<uint64_t> offs(res.size());
+  uint64_t blob_bytes = 0;
+  for (size_t i = 0; i < res.size(); ++i) {
+    ids[i] = res[i].level_id;
+    offs[i] = blob_bytes;
+    blob_bytes += d.block_bytes[res[i].level];
+  }
+  std::vector<uint8_t> blob(blob_bytes);
+  MRH_CUDA(io_blocks_to_blob(d, ids, offs, blob.data(), blob_bytes, s, m->sms));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return MRH_ERR_INVALID_ARG;
+  const uint32_t ver = io_version(), psz = (uint32_t)sizeof(mrh_map_params);
+  const uint64_t n = res.size() + arc.size();
+  bool ok = std::fwrite(io_magic(), 1, 8, f) == 8 && std::fwrite(&ver, 4, 1, f) == 1 && std::fwrite(&psz, 4, 1, f) == 1 &&
+            std::fwrite(&m->p, sizeof(mrh_map_params), 1, f) == 1 && std::fwrite(&n, 8, 1, f) == 1;
+  for (int part = 0; part < 2 && ok; ++part)
+    for (size_t i = 0; i < (part ? arc.size() : res.size()) && ok; ++i) {
+      const Rec& r = part ? arc[i] : res[i];
+      const uint8_t lvl[4] = {(uint8_t)r.level, 0, 0, 0};
+      const uint32_t nb = d.block_bytes[r.level];
+      const uint8_t* src = part ? r.archived : blob.data() + offs[i];
+      ok = std::fwrite(r.key, 4, 3, f) == 3 && std::fwrite(lvl, 1, 4, f) == 4 && std::fwrite(&nb, 4, 1, f) == 1 &&
+           std::fwrite(src, 1, nb, f) == nb;
+    }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MRH_OK : MRH_ERR_INVALID_ARG;
+}
+
+mrh_status mrh_load_map(const char* path, int device, mrh_map** out) {
+  if (!path || !out) return MRH_ERR_INVALID_ARG;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return MRH_ERR_INVALID_ARG;
+  char magic[8];
+  uint32_t ver = 0, psz = 0;
+  mrh_map_params p{};
+  uint64_t n = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, io_magic(), 8) == 0 &&
+            std::fread(&ver, 4, 1, f) == 1 && ver == io_version() && std::fread(&psz, 4, 1, f) == 1 &&
+            psz == sizeof(mrh_map_params) && std::fread(&p, sizeof(p), 1, f) == 1 && std::fread(&n, 8, 1, f) == 1;
+  mrh_map* m = nullptr;
+  if (ok && mrh_map_create(&p, device, &m) != MRH_OK) ok = false;
+  std::vector<int32_t> keys;
+  std::vector<uint32_t> levels;
+  std::vector<uint64_t> offs;
+  std::vector<uint8_t> blob;
+  for (uint64_t i = 0; i < n && ok; ++i) {
+    int32_t k[3];
+    uint8_t lvl[4];
+    uint32_t nb = 0;
+    ok = std::fread(k, 4, 3, f) == 3 && std::fread(lvl, 1, 4, f) == 4 && std::fread(&nb, 4, 1, f) == 1 &&
+         lvl[0] < (uint32_t)m->d.L && nb == m->d.block_bytes[lvl[0]] && key_ok(k[0], k[1], k[2]);
+    if (!ok) break;
+    keys.insert(keys.end(), k, k + 3);
+    levels.push_back(lvl[0]);
+    offs.push_back(blob.size());
+    blob.resize(blob.size() + nb);
+    ok = std::fread(blob.data() + offs.back(), 1, nb, f) == nb;
+  }
+  std::fclose(f);
+  if (!ok) {
+    if (m) mrh_map_destroy(m);
+    return MRH_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(device);
+  const cudaError_t e = io_blob_to_blocks(m->d, keys, levels, offs, blob.data(), blob.size(), 0, m->sms);
+  if (e != cudaSuccess) {
+    mrh_map_destroy(m);
+    return cuda_fail(e, "mrh_load_map");
+  }
+  DevState hs;
+  if (cudaMemcpy(&hs, m->d.st, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess || hs.status != 0) {
+    const mrh_status st = status_from_bits(hs.status);
+    mrh_map_destroy(m);
+    return st != MRH_OK ? st : MRH_ERR_CUDA;
+  }
+  *out = m;
+  return MRH_OK;
+}
+
 void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end) {
   if (ntri && tri && edge_end) host_case_table(ntri, tri, edge_end);
 }

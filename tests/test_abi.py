@@ -97,6 +97,22 @@ def test_invalid_params_rejected_before_any_device_call(lib):
     assert lib.mrh_map_create(None, 0, ctypes.byref(h)) == 1
 
 
+def test_map_files_rejected_before_any_device_call(lib, tmp_path):
+    """mrh_load_map validates the header (magic, version, parameter size) before it creates a map."""
+    h = ctypes.c_void_p(1)
+    assert lib.mrh_load_map(os.fsencode(str(tmp_path / "missing.mrhmap")), 0, ctypes.byref(h)) == 1
+    assert h.value is None
+    size = ctypes.sizeof(mrh.Params)
+    good = b"MRHMAP\0\1" + (1).to_bytes(4, "little") + size.to_bytes(4, "little")
+    for bad in (b"", b"MRHMAP", b"MRHMAQ\0\1" + good[8:], good[:8] + (2).to_bytes(4, "little") + good[12:],
+                good[:12] + (size + 4).to_bytes(4, "little"), good):  # the last one stops inside the parameters
+        f = tmp_path / "bad.mrhmap"
+        f.write_bytes(bad)
+        assert lib.mrh_load_map(os.fsencode(str(f)), 0, ctypes.byref(h)) == 1, bad
+    assert lib.mrh_load_map(None, 0, ctypes.byref(h)) == 1
+    assert lib.mrh_save_map(None, os.fsencode(str(tmp_path / "x")), None) == 1
+
+
 def test_mesh_case_table_matches_the_oracles(lib):
     """The library builds its Marching Cubes case table on the host (no GPU call); it is an independent second
     construction from the same definition as the oracle's, so the two must agree entry for entry."""
