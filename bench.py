@@ -56,7 +56,8 @@ def parse_args():
                     help="only the variance-threshold sweep (Sec. 5.1 analogue): one JSON line, then exit")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
-    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh"], default=None,
+    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh", "quadtree", "stream"],
+                    default=None,
                     help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
     return ap.parse_args()
 
@@ -94,6 +95,31 @@ def profile_case(kind: str) -> int:
         st = m.stats()
         print(json.dumps({"triangles": int(t.shape[0]), "live_blocks": st["live_blocks"],
                           "mesh_algorithmic_bytes": mesh_bytes(st, wl, int(t.shape[0]))}))
+    elif kind == "quadtree":
+        wl = synth.rgbd()
+        imgs = [torch.from_numpy(c).cuda() for _, c, _ in camera_frames(wl, 0, 4)]
+        leaves = 0
+        for _ in range(3):
+            for im in imgs:
+                leaves = int(mrh.quadtree(im, 0.1, 1).shape[0])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": kind, "leaves_last": leaves}))
+        return 0
+    elif kind == "stream":
+        # the streaming leg's LiDAR street, its pools and settings, 80 scans (eviction starts part way)
+        import dataclasses
+        wl = dataclasses.replace(synth.lidar(), max_blocks=(1 << 18, 1 << 16, 1 << 16))
+        m = mrh.Map(mrh.params_from(wl))
+        m.set_streaming(0.5, 80.0, 1 << 19)
+        scene = wl.scene()
+        ev = rs = 0
+        for k in range(80):
+            xyz, T = synth.render_lidar(wl, k, scene=scene)
+            m.integrate_points(T, torch.from_numpy(xyz).cuda())
+            st = m.stats()
+            ev += st["evicted"]
+            rs += st["restored"]
+        print(json.dumps({"evicted": ev, "restored": rs, "archived": st["archived"]}))
     elif kind == "lidar":
         wl = synth.lidar()
         wl.max_blocks = (1 << 18, 1 << 16, 1 << 16)
