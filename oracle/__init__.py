@@ -23,6 +23,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   quadtree (Sec. 3.5, Eq. 10)  pinned: closed-form contrast of two-colour and constant regions (byte units);
                                leaves tile the image; thresholds below zero / above the maximum give single pixels /
                                one leaf; a hand-built image gives the hand-counted leaves
+  splats (Sec. 3.5, Eqs. 7-9)  pinned: projection against the closed form on the optical axis and a finite-difference
+                               Jacobian off axis; invariance under moving camera and Gaussians together; one
+                               Gaussian gives a C at its centre, a exp(-q/2) C around it, nothing beyond three
+                               standard deviations; two Gaussians blend in depth order whatever their index; an opaque
+                               front Gaussian hides the back one; the cut-off is a reading
   raycast normal / colour      pinned: a linear TSDF and colour field set block by block gives the plane's unit
                                normal and the colour field at the hit (trilinear is exact on linear fields);
                                analytic walls of a fused noise-free frame; constant-colour frames
@@ -37,7 +42,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrh_oracle.cpp")
-_SRCS = [_SRC, os.path.join(_HERE, "level_predictor.cpp"), os.path.join(_HERE, "quadtree.cpp")]
+_SRCS = [_SRC, os.path.join(_HERE, "level_predictor.cpp"), os.path.join(_HERE, "quadtree.cpp"),
+         os.path.join(_HERE, "splat.cpp")]
 _SO = os.path.join(_HERE, "libmrh_oracle.so")
 _lib = None
 
@@ -97,6 +103,10 @@ def _load():
         lib.orc_qt_contrast.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_quadtree.restype = ctypes.c_int64
         lib.orc_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, ctypes.c_int64]
+        lib.orc_splat_project.restype = ctypes.c_int
+        lib.orc_splat_project.argtypes = [vp, vp, vp, vp, vp]
+        lib.orc_splat_render.restype = ctypes.c_int64
+        lib.orc_splat_render.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         lib.orc_weld_mesh.restype = ctypes.c_int64
         lib.orc_weld_mesh.argtypes = [vp, ctypes.c_int64, ctypes.c_float, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                       ctypes.POINTER(ctypes.c_int64)]
@@ -318,6 +328,42 @@ def quadtree(rgb: np.ndarray, threshold: float = 0.1, min_size: int = 1) -> np.n
     out = np.zeros((n, 4), np.int32)
     lib.orc_quadtree(_p(img), img.shape[1], img.shape[0], threshold, min_size, _p(out), n)
     return out
+
+
+def _k6(K) -> np.ndarray:
+    return np.array([K.fx, K.fy, K.cx, K.cy, K.min_depth, K.max_depth], np.float32)
+
+
+def splat_project(mean, cov, K, T):
+    """Eq. 7 for one Gaussian: None when it is not drawn, else a dict with z, mu (u, v), cov (Sigma_I uu, uv, vv) and
+    conic (its inverse), all float32. mean (3,), cov (6,) = Sigma_W xx, xy, xz, yy, yz, zz; K a Pinhole (fx, fy, cx,
+    cy, min_depth, max_depth are used); T the camera-to-world pose."""
+    mean = np.ascontiguousarray(mean, np.float32)
+    cov = np.ascontiguousarray(cov, np.float32)
+    Tm = np.ascontiguousarray(T, np.float64)
+    out = np.zeros(9, np.float32)
+    k6 = _k6(K)
+    if not _load().orc_splat_project(_p(mean), _p(cov), _p(k6), _p(Tm), _p(out)):
+        return None
+    return {"z": out[0], "mu": out[1:3].copy(), "cov": out[3:6].copy(), "conic": out[6:9].copy()}
+
+
+def splat_render(means, covs, opacity, colors, K, T):
+    """Eqs. 7-9: colour (H, W, 3) and transmittance (H, W), float64, of n Gaussians (means (n, 3), covs (n, 6),
+    opacity (n,), colors (n, 3), float32) seen by the pinhole K (a Pinhole) at camera-to-world pose T; also returns the
+    number of Gaussians drawn."""
+    means = np.ascontiguousarray(means, np.float32).reshape(-1, 3)
+    n = means.shape[0]
+    covs = np.ascontiguousarray(covs, np.float32).reshape(n, 6)
+    opacity = np.ascontiguousarray(opacity, np.float32).reshape(n)
+    colors = np.ascontiguousarray(colors, np.float32).reshape(n, 3)
+    Tm = np.ascontiguousarray(T, np.float64)
+    rgb = np.zeros((K.height, K.width, 3), np.float64)
+    tr = np.zeros((K.height, K.width), np.float64)
+    k6 = _k6(K)
+    drawn = _load().orc_splat_render(n, _p(means), _p(covs), _p(opacity), _p(colors), _p(k6), _p(Tm), K.width,
+                                     K.height, _p(rgb), _p(tr))
+    return rgb, tr, int(drawn)
 
 
 def mc_table():
