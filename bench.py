@@ -52,11 +52,13 @@ def parse_args():
     ap.add_argument("--no-mesh", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
+    ap.add_argument("--no-splat", action="store_true")
     ap.add_argument("--ablation", action="store_true",
                     help="only the variance-threshold sweep (Sec. 5.1 analogue): one JSON line, then exit")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
-    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh", "quadtree", "stream"],
+    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh", "quadtree", "stream",
+                                               "splat"],
                     default=None,
                     help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
     return ap.parse_args()
@@ -104,6 +106,16 @@ def profile_case(kind: str) -> int:
                 leaves = int(mrh.quadtree(im, 0.1, 1).shape[0])
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": kind, "leaves_last": leaves}))
+        return 0
+    elif kind == "splat":
+        wl = synth.rgbd()
+        g = {k: torch.from_numpy(v).cuda() for k, v in synth.gaussians(wl, 1_000_000).items()}
+        K = mrh.pinhole_from(wl)
+        pairs = 0
+        for k in range(3):
+            _, _, pairs = mrh.splat_render(g["means"], g["covs"], g["opacity"], g["colors"], K, wl.pose(10 * k))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": kind, "pairs_last": pairs}))
         return 0
     elif kind == "stream":
         # the streaming leg's LiDAR street, its pools and settings, 80 scans (eviction starts part way)
@@ -657,6 +669,60 @@ def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), v
     return out
 
 
+def run_splat(wl, n=1_000_000, views=tuple(range(0, 300, 20)), reps=3, small=((150, 110), 20000, 20)):
+    """Tile-based splat rendering (Sec. 3.5, Eqs. 7-9): n seeded Gaussians on the scene's surfaces rendered at the
+    640 x 480 camera from `views` of the orbit, `reps` times each (CUDA events around the calls, which include the
+    library's one host read of the pair count per render); and a small camera and Gaussian set rendered by the GPU
+    and by the oracle (one thread, brute force over every pixel and Gaussian), the images checked within 2e-4."""
+    import dataclasses
+    import torch
+    import oracle
+    import paper_2511_21459_b300 as mrh
+    g = synth.gaussians(wl, n)
+    gd = {k: torch.from_numpy(v).cuda() for k, v in g.items()}
+    K = mrh.pinhole_from(wl)
+    out = torch.empty((wl.height, wl.width, 3), device="cuda")
+    tr = torch.empty((wl.height, wl.width), device="cuda")
+    args = (gd["means"], gd["covs"], gd["opacity"], gd["colors"], K)
+    for v in views[:3]:
+        mrh.splat_render(*args, wl.pose(v), out=out, trans=tr)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pairs = 0
+    a.record(stream)
+    for _ in range(reps):
+        for v in views:
+            pairs += mrh.splat_render(*args, wl.pose(v), out=out, trans=tr)[2]
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / (reps * len(views))
+    (w, h), n_small, view = small
+    s = w / wl.width
+    ws = dataclasses.replace(wl, width=w, height=h, fx=wl.fx * s, fy=wl.fy * s, cx=(w - 1) / 2, cy=(h - 1) / 2)
+    gs = synth.gaussians(wl, n_small)
+    gsd = {k: torch.from_numpy(v).cuda() for k, v in gs.items()}
+    Ks = mrh.pinhole_from(ws)
+    T = ws.pose(view)
+    mrh.splat_render(gsd["means"], gsd["covs"], gsd["opacity"], gsd["colors"], Ks, T)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(10):
+        rgb_g, tr_g, _ = mrh.splat_render(gsd["means"], gsd["covs"], gsd["opacity"], gsd["colors"], Ks, T)
+    b.record(stream)
+    torch.cuda.synchronize()
+    small_gpu_ms = a.elapsed_time(b) / 10
+    t0 = time.perf_counter()
+    rgb_o, tr_o, _ = oracle.splat_render(gs["means"], gs["covs"], gs["opacity"], gs["colors"], oracle.pinhole_from(ws), T)
+    small_cpu_ms = 1000.0 * (time.perf_counter() - t0)
+    err = max(float(np.abs(rgb_g.cpu().numpy() - rgb_o).max()), float(np.abs(tr_g.cpu().numpy() - tr_o).max()))
+    return {"gaussians": n, "views": len(views), "reps": reps, "ms_per_frame": round(ms, 4),
+            "frames_per_s": round(1000.0 / ms, 1), "gaussians_per_s": n * 1000.0 / ms,
+            "pairs_per_frame": pairs / (reps * len(views)),
+            "small_case": {"camera": [w, h], "gaussians": n_small, "gpu_ms": round(small_gpu_ms, 4),
+                           "oracle_ms_1_thread": round(small_cpu_ms, 1), "max_abs_diff": err, "within_2e-4": err <= 2e-4}}
+
+
 def run_streaming(wl, n_scans=150, pools=(1 << 18, 1 << 16, 1 << 16), fraction=0.5, radius=80.0,
                   archive=1 << 19):
     """Capacity-driven streaming (Sec. 3.3) on the LiDAR street: n_scans full scans 1 m apart into pools of `pools`
@@ -1009,6 +1075,10 @@ def main():
     if rank == 0 and not args.no_lidar and not args.no_streaming:
         streaming = run_streaming(synth.lidar())
 
+    splat = None
+    if rank == 0 and not args.no_splat:
+        splat = run_splat(wl)
+
     batched = None
     if not args.no_batched:
         bres = run_batched(6, args.batched_steps, flush)
@@ -1042,7 +1112,7 @@ def main():
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
                 "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh, "quadtree": quad,
-                "streaming": streaming}
+                "streaming": streaming, "splat": splat}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -319,6 +319,26 @@ void mrh_mesh_case_table(uint8_t* ntri, int8_t* tri, int8_t* edge_end);
  * streaming are not accepted by mrh_batch_create. Synchronises the device. */
 mrh_status mrh_set_streaming(mrh_map* map, float fraction, float radius, uint32_t archive_blocks);
 
+/* Tile-based Gaussian-splat rendering (the rendering branch, Sec. 3.5, Eqs. 7-9; no map needed). Inputs (device,
+ * float32): means_dev n x 3 (world), covs_dev n x 6 (world covariance Sigma_W as xx, xy, xz, yy, yz, zz), opacity_dev n
+ * (alpha, expected in [0, 1]), colors_dev n x 3 (any units); n < 2^32. K: pinhole (fx, fy > 0, 0 < min_depth <=
+ * max_depth); T_wc_host: camera-to-world pose, 4 x 4 row-major double.
+ * Each Gaussian is projected (Eq. 7): camera-frame mean R^T (mu - t), image mean by the pinhole, image covariance
+ * Sigma_I = J R^T Sigma_W R J^T with J the projection's Jacobian at the camera-frame mean; it is not drawn when its
+ * camera z lies outside [min_depth, max_depth] or Sigma_I is not positive definite. Gaussian m reaches pixel (u, v)
+ * (image coordinates u, v) when its squared Mahalanobis distance q <= 9 and |u - mu_u| <= 3 sqrt(Sigma_uu),
+ * |v - mu_v| <= 3 sqrt(Sigma_vv) (all float, fixed operation order). Pixel colour (Eq. 8) = sum over the Gaussians
+ * that reach it, in increasing camera z (ties by index), of C_m a_m exp(-q_m / 2) times the product of
+ * (1 - a_l exp(-q_l / 2)) over those in front (Eq. 9); a pixel stops once that product (its transmittance) is below
+ * 1e-4, which changes its colour by less than 1e-4 times the largest colour.
+ * Outputs (device): rgb_out_dev height x width x 3 float32; trans_out_dev height x width float32 (the remaining
+ * transmittance; nullable). n_pairs_out (nullable) receives the number of (16 x 16 tile, Gaussian) pairs; more than
+ * 2^31 - 1 gives MRH_ERR_CAPACITY and nothing is rendered. Uses temporary device memory (about 88 bytes per Gaussian
+ * and 25 per pair) on `device`; synchronises `stream` once (to size the pair buffers). */
+mrh_status mrh_splat_render(const float* means_dev, const float* covs_dev, const float* opacity_dev,
+                            const float* colors_dev, uint64_t n, const mrh_pinhole* K, const double* T_wc_host,
+                            float* rgb_out_dev, float* trans_out_dev, uint64_t* n_pairs_out, int device, void* stream);
+
 /* Save the map to a file (the persistence half of streaming, Sec. 3.3): the creation parameters, then every resident
  * block and every archived block (key, level, payload in the library's block layout; resident ones first, each group
  * in key order). Synchronises `stream` and the device copies it needs. MRH_ERR_INVALID_ARG when the file cannot be

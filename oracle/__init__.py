@@ -107,6 +107,8 @@ def _load():
         lib.orc_splat_project.argtypes = [vp, vp, vp, vp, vp]
         lib.orc_splat_render.restype = ctypes.c_int64
         lib.orc_splat_render.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        lib.orc_splat_pixels.restype = ctypes.c_int64
+        lib.orc_splat_pixels.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp]
         lib.orc_weld_mesh.restype = ctypes.c_int64
         lib.orc_weld_mesh.argtypes = [vp, ctypes.c_int64, ctypes.c_float, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                       ctypes.POINTER(ctypes.c_int64)]
@@ -364,6 +366,23 @@ def splat_render(means, covs, opacity, colors, K, T):
     drawn = _load().orc_splat_render(n, _p(means), _p(covs), _p(opacity), _p(colors), _p(k6), _p(Tm), K.width,
                                      K.height, _p(rgb), _p(tr))
     return rgb, tr, int(drawn)
+
+
+def splat_pixels(means, covs, opacity, colors, K, T, uv):
+    """splat_render at the listed pixels only: uv (k, 2) int (u, v); returns rgb (k, 3), trans (k,) float64."""
+    means = np.ascontiguousarray(means, np.float32).reshape(-1, 3)
+    n = means.shape[0]
+    covs = np.ascontiguousarray(covs, np.float32).reshape(n, 6)
+    opacity = np.ascontiguousarray(opacity, np.float32).reshape(n)
+    colors = np.ascontiguousarray(colors, np.float32).reshape(n, 3)
+    uv = np.ascontiguousarray(uv, np.int32).reshape(-1, 2)
+    Tm = np.ascontiguousarray(T, np.float64)
+    rgb = np.zeros((uv.shape[0], 3), np.float64)
+    tr = np.zeros(uv.shape[0], np.float64)
+    k6 = _k6(K)
+    _load().orc_splat_pixels(n, _p(means), _p(covs), _p(opacity), _p(colors), _p(k6), _p(Tm), uv.shape[0], _p(uv),
+                             _p(rgb), _p(tr))
+    return rgb, tr
 
 
 def mc_table():

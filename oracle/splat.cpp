@@ -119,41 +119,73 @@ int orc_splat_project(const float* mean, const float* cov, const float* K6, cons
   return 1;
 }
 
+}  // extern "C"
+
+namespace {
+
+// the drawn Gaussians (projections and indices) in blending order: increasing z, ties by index
+struct DepthOrder {
+  std::vector<Projected> proj;
+  std::vector<int64_t> ids;
+  std::vector<size_t> order;
+};
+
+DepthOrder depth_order(const Camera& c, int64_t n, const float* means, const float* covs) {
+  DepthOrder d;
+  for (int64_t m = 0; m < n; ++m) {
+    Projected p;
+    if (project(c, means + 3 * m, covs + 6 * m, &p)) {
+      d.proj.push_back(p);
+      d.ids.push_back(m);
+    }
+  }
+  d.order.resize(d.proj.size());
+  std::iota(d.order.begin(), d.order.end(), (size_t)0);
+  std::sort(d.order.begin(), d.order.end(), [&](size_t a, size_t b) {
+    return d.proj[a].z < d.proj[b].z || (d.proj[a].z == d.proj[b].z && d.ids[a] < d.ids[b]);
+  });
+  return d;
+}
+
+// Eq. 8 at one pixel: colour sum and the remaining product of (1 - alpha G)
+void blend_pixel(const DepthOrder& d, const float* opacity, const float* colors, int u, int v, double* C,
+                 double* Tr) {
+  C[0] = C[1] = C[2] = 0.0;
+  *Tr = 1.0;
+  for (size_t k : d.order) {
+    const float q = support_q(d.proj[k], u, v);
+    if (q < 0.0f) continue;
+    const int64_t m = d.ids[k];
+    const double w = (double)opacity[m] * std::exp(-0.5 * (double)q);  // alpha G, Eq. 9
+    for (int ch = 0; ch < 3; ++ch) C[ch] += (double)colors[3 * m + ch] * w * *Tr;
+    *Tr *= 1.0 - w;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 // Eqs. 7-9 for n Gaussians (means n x 3, covs n x 6, opacity n, colors n x 3) on a width x height image: colour
 // (height x width x 3) and transmittance (height x width), both double. Returns the number of Gaussians drawn.
 int64_t orc_splat_render(int64_t n, const float* means, const float* covs, const float* opacity, const float* colors,
                          const float* K6, const double* T, int width, int height, double* rgb, double* trans) {
-  const Camera c = camera(K6, T);
-  std::vector<Projected> proj;
-  std::vector<int64_t> ids;
-  for (int64_t m = 0; m < n; ++m) {
-    Projected p;
-    if (project(c, means + 3 * m, covs + 6 * m, &p)) {
-      proj.push_back(p);
-      ids.push_back(m);
-    }
-  }
-  std::vector<size_t> order(proj.size());
-  std::iota(order.begin(), order.end(), (size_t)0);
-  std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-    return proj[a].z < proj[b].z || (proj[a].z == proj[b].z && ids[a] < ids[b]);
-  });
+  const DepthOrder d = depth_order(camera(K6, T), n, means, covs);
   for (int v = 0; v < height; ++v)
     for (int u = 0; u < width; ++u) {
-      double C[3] = {0.0, 0.0, 0.0}, Tr = 1.0;
-      for (size_t k : order) {
-        const float q = support_q(proj[k], u, v);
-        if (q < 0.0f) continue;
-        const int64_t m = ids[k];
-        const double w = (double)opacity[m] * std::exp(-0.5 * (double)q);
-        for (int ch = 0; ch < 3; ++ch) C[ch] += (double)colors[3 * m + ch] * w * Tr;
-        Tr *= 1.0 - w;
-      }
       const int64_t px = (int64_t)v * width + u;
-      for (int ch = 0; ch < 3; ++ch) rgb[3 * px + ch] = C[ch];
-      trans[px] = Tr;
+      blend_pixel(d, opacity, colors, u, v, rgb + 3 * px, trans + px);
     }
-  return (int64_t)proj.size();
+  return (int64_t)d.proj.size();
+}
+
+// the same at n_px listed pixels (uv: n_px x 2 int32, u then v): rgb n_px x 3, trans n_px
+int64_t orc_splat_pixels(int64_t n, const float* means, const float* covs, const float* opacity, const float* colors,
+                         const float* K6, const double* T, int64_t n_px, const int32_t* uv, double* rgb,
+                         double* trans) {
+  const DepthOrder d = depth_order(camera(K6, T), n, means, covs);
+  for (int64_t i = 0; i < n_px; ++i) blend_pixel(d, opacity, colors, uv[2 * i], uv[2 * i + 1], rgb + 3 * i, trans + i);
+  return (int64_t)d.proj.size();
 }
 
 }  // extern "C"

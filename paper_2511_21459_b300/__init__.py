@@ -78,7 +78,7 @@ EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_inte
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
            "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree",
-           "mrh_set_streaming", "mrh_save_map", "mrh_load_map"]
+           "mrh_set_streaming", "mrh_save_map", "mrh_load_map", "mrh_splat_render"]
 
 MLP_IN, MLP_HIDDEN, MLP_LEVELS = 16, 64, 3
 MLP_PARAMS = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_LEVELS + \
@@ -104,6 +104,8 @@ def lib():
         L.mrh_mesh_case_table.restype = None
         L.mrh_set_streaming.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
         L.mrh_save_map.argtypes = [vp, ctypes.c_char_p, vp]
+        L.mrh_splat_render.argtypes = [vp, vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(Pinhole), vp, vp, vp,
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
         L.mrh_load_map.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(vp)]
         L.mrh_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, u64,
                                    ctypes.POINTER(u64), ctypes.c_int, vp]
@@ -170,6 +172,30 @@ def quadtree(rgb, threshold: float = 0.1, min_size: int = 1, stream=None):
     _check(lib().mrh_quadtree(_ptr(img), w, h, float(threshold), int(min_size), _ptr(out), cap, ctypes.byref(n), dev,
                               _stream(stream)), "mrh_quadtree")
     return out[:n.value]
+
+
+def splat_render(means, covs, opacity, colors, K: Pinhole, T_wc, out=None, trans=None, stream=None):
+    """Gaussian-splat rendering (see mrh_splat_render): means (n, 3), covs (n, 6), opacity (n,), colors (n, 3)
+    float32 CUDA tensors on one device; returns (rgb (h, w, 3), transmittance (h, w), pairs). ``out`` / ``trans``:
+    optional CUDA tensors to write into; trans=False skips the transmittance."""
+    import torch
+    dev = means.device
+    n = int(means.shape[0])
+    for t, shape in ((means, (n, 3)), (covs, (n, 6)), (opacity, (n,)), (colors, (n, 3))):
+        if t.device != dev or t.dtype != torch.float32 or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 {shape} tensor on {dev}")
+    if out is None:
+        out = torch.empty((K.height, K.width, 3), dtype=torch.float32, device=dev)
+    if trans is None:
+        trans = torch.empty((K.height, K.width), dtype=torch.float32, device=dev)
+    tr = trans if trans is not False else None
+    T = _pose(T_wc)
+    pairs = ctypes.c_uint64()
+    _check(lib().mrh_splat_render(_ptr(means), _ptr(covs), _ptr(opacity), _ptr(colors), n, ctypes.byref(K),
+                                  ctypes.c_void_p(T.ctypes.data), _ptr(out), _ptr(tr), ctypes.byref(pairs),
+                                  dev.index if dev.index is not None else torch.cuda.current_device(),
+                                  _stream(stream)), "mrh_splat_render")
+    return out, tr, pairs.value
 
 
 def mesh_case_table():

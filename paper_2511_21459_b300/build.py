@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrhash.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["mrh_map.cu", "mrh_alloc.cu", "mrh_fuse.cu", "mrh_raycast.cu", "mrh_batch.cu", "mrh_mlp.cu", "mrh_mesh.cu",
-           "mrh_quadtree.cu", "mrh_stream.cu", "mrh_io.cu"]
+           "mrh_quadtree.cu", "mrh_stream.cu", "mrh_io.cu",
+           "mrh_splat.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE]

@@ -482,6 +482,18 @@ cudaError_t io_blocks_to_blob(const MapDev& m, const std::vector<uint32_t>& leve
 cudaError_t io_blob_to_blocks(const MapDev& m, const std::vector<int32_t>& keys, const std::vector<uint32_t>& levels,
                               const std::vector<uint64_t>& offsets, const uint8_t* blob_host, uint64_t blob_bytes,
                               cudaStream_t s, int sms);
+// Gaussian splats (mrh_splat.cu)
+struct SplatInputs {
+  const float* means;    // n x 3
+  const float* covs;     // n x 6: Sigma_W xx, xy, xz, yy, yz, zz
+  const float* opacity;  // n
+  const float* colors;   // n x 3
+  uint64_t n;
+};
+constexpr uint64_t kSplatMaxPairs = 0x7FFFFFFFull;  // tile-Gaussian pairs of one render
+cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, float* trans, uint64_t* n_pairs,
+                         int device, cudaStream_t s, int sms);
+
 const char* io_magic();
 uint32_t io_version();
 // contrast quadtree (mrh_quadtree.cu)

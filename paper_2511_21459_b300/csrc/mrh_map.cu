@@ -887,6 +887,28 @@ mrh_status mrh_quadtree(const uint8_t* rgb, int width, int height, double thresh
   return n > capacity ? MRH_ERR_CAPACITY : MRH_OK;
 }
 
+mrh_status mrh_splat_render(const float* means, const float* covs, const float* opacity, const float* colors,
+                            uint64_t n, const mrh_pinhole* K, const double* T_wc, float* rgb_out, float* trans_out,
+                            uint64_t* n_pairs_out, int device, void* stream) {
+  if (!K || !T_wc || !rgb_out || n >= (1ull << 32) || (n > 0 && (!means || !covs || !opacity || !colors)) ||
+      K->width < 1 || K->height < 1 || K->width > 16384 || K->height > 16384 || !(K->fx > 0.0f) || !(K->fy > 0.0f) ||
+      !(K->min_depth > 0.0f) || !(K->max_depth >= K->min_depth) || !std::isfinite(K->cx) || !std::isfinite(K->cy))
+    return MRH_ERR_INVALID_ARG;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(T_wc[i])) return MRH_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+  const cudaStream_t s = (cudaStream_t)stream;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const SplatInputs in{means, covs, opacity, colors, n};
+  uint64_t pairs = 0;
+  const cudaError_t e = splat_render(in, cam_args(K, T_wc), rgb_out, trans_out, &pairs, device, s, sms);
+  if (n_pairs_out) *n_pairs_out = pairs;
+  if (e != cudaSuccess) return cuda_fail(e, "mrh_splat_render");
+  return pairs > kSplatMaxPairs ? MRH_ERR_CAPACITY : MRH_OK;
+}
+
 mrh_status mrh_save_map(mrh_map* m, const char* path, void* stream) {
   if (!m || !path) return MRH_ERR_INVALID_ARG;
   DeviceGuard guard(m->device);

@@ -1,0 +1,435 @@
+// Tile-based Gaussian-splat rasteriser of the rendering branch (Sec. 3.5): every 3D Gaussian is projected to the
+// image (Eq. 7) and the projected Gaussians are alpha-blended front to back at every pixel (Eqs. 8, 9).
+//
+// What a pixel receives. Camera-frame mean R^T (mu - t) with the camera-to-world pose (R, t); Gaussians whose camera z
+// lies outside [min_depth, max_depth] or whose image covariance Sigma_I = J R^T Sigma_W R J^T is not positive definite
+// are not drawn. Gaussian m reaches pixel (u, v) (image coordinates u, v) when its squared Mahalanobis distance
+// q <= 9 and |u - mu_u| <= 3 sqrt(Sigma_uu), |v - mu_v| <= 3 sqrt(Sigma_vv). The pixel's colour is
+// sum_m C_m a_m exp(-q_m / 2) prod_{l in front of m} (1 - a_l exp(-q_l / 2)) over the Gaussians that reach it in
+// increasing camera z (ties by index); the remaining product is its transmittance. The projection, the reach test and
+// the depth order are float computations with a fixed operation order (this file is compiled without multiply-add
+// contraction). A pixel stops once its transmittance falls below kSplatStop: the colour it would still receive is
+// below kSplatStop times the largest colour, and its transmittance is off by less than kSplatStop.
+//
+// The work (one stream; one host read, of the number of tile-Gaussian pairs):
+//   k_splat_project  one thread per Gaussian: Eq. 7, the three-sigma box, the tiles it overlaps (16 x 16 pixels)
+//                    and a 48-byte record {mu_u, mu_v, ru, rv}, {conic uu, 2 conic uv, conic vv, alpha},
+//                    {colour, z}
+//   scan             exclusive prefix of the per-Gaussian pair counts
+//   k_splat_pairs    every (tile, Gaussian) pair as key tile << 32 | bits of z (positive floats order as their bits),
+//                    value the Gaussian's index, written in Gaussian order
+//   radix sort       stable least-significant-digit passes of 8 bits over the key's 32 + tile bits, so a tile's
+//                    pairs end up contiguous, by depth, equal depths in Gaussian order
+//   k_splat_ranges   each tile's first and last pair
+//   k_splat_render   one CTA of 16 x 16 threads per tile; the tile's records are staged 256 at a time in shared
+//                    memory and every thread blends its pixel through them; the CTA leaves when all its pixels
+//                    have stopped
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "mrh_internal.cuh"
+
+namespace mrh {
+namespace {
+
+constexpr int kTile = 16;
+constexpr float kSplatStop = 1e-4f;
+
+struct SplatRec {
+  float4 a;  // mu_u, mu_v, ru, rv
+  float4 b;  // conic uu, 2 conic uv, conic vv, alpha
+  float4 c;  // colour r, g, b, camera z
+};
+
+struct SplatGeo {
+  int width, height, tiles_x, tiles_y;
+};
+
+// ---------------------------------------------------------------------------------------------------- projection
+
+__global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c, SplatGeo g, SplatRec* rec,
+                                                       int4* rect, unsigned long long* count) {
+  for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < in.n; m += (uint64_t)gridDim.x * blockDim.x) {
+    unsigned long long pairs = 0;
+    int4 box = make_int4(0, 0, 0, 0);  // tiles [x, z) x [y, w); empty when the Gaussian is not drawn
+    const float* mean = in.means + 3 * m;
+    const float* cv = in.covs + 6 * m;
+    const float* R = c.R;
+    const float d0 = mean[0] - c.t[0], d1 = mean[1] - c.t[1], d2 = mean[2] - c.t[2];
+    const float x = R[0] * d0 + R[3] * d1 + R[6] * d2;
+    const float y = R[1] * d0 + R[4] * d1 + R[7] * d2;
+    const float z = R[2] * d0 + R[5] * d1 + R[8] * d2;
+    if (z >= c.min_depth && z <= c.max_depth) {
+      const float iz = 1.0f / z;
+      const float xz = x * iz, yz = y * iz;
+      const float mu_u = c.fx * xz + c.cx, mu_v = c.fy * yz + c.cy;
+      const float j00 = c.fx * iz, j02 = -(j00 * xz), j11 = c.fy * iz, j12 = -(j11 * yz);
+      float M0[3], M1[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        M0[a] = j00 * R[3 * a] + j02 * R[3 * a + 2];
+        M1[a] = j11 * R[3 * a + 1] + j12 * R[3 * a + 2];
+      }
+      const float S[3][3] = {{cv[0], cv[1], cv[2]}, {cv[1], cv[3], cv[4]}, {cv[2], cv[4], cv[5]}};
+      float V0[3], V1[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        V0[a] = S[a][0] * M0[0] + S[a][1] * M0[1] + S[a][2] * M0[2];
+        V1[a] = S[a][0] * M1[0] + S[a][1] * M1[1] + S[a][2] * M1[2];
+      }
+      const float suu = M0[0] * V0[0] + M0[1] * V0[1] + M0[2] * V0[2];
+      const float suv = M1[0] * V0[0] + M1[1] * V0[1] + M1[2] * V0[2];
+      const float svv = M1[0] * V1[0] + M1[1] * V1[1] + M1[2] * V1[2];
+      const float det = suu * svv - suv * suv;
+      if (det > 0.0f && suu > 0.0f) {
+        const float ru = 3.0f * sqrtf(suu), rv = 3.0f * sqrtf(svv);
+        // pixels within the box, widened by one pixel against rounding of the bounds, clamped to the image
+        const float u0 = fmaxf(floorf(mu_u - ru) - 1.0f, 0.0f), u1 = fminf(ceilf(mu_u + ru) + 1.0f, g.width - 1.0f);
+        const float v0 = fmaxf(floorf(mu_v - rv) - 1.0f, 0.0f), v1 = fminf(ceilf(mu_v + rv) + 1.0f, g.height - 1.0f);
+        if (u0 <= u1 && v0 <= v1) {  // false for NaN bounds as well
+          box = make_int4((int)u0 / kTile, (int)v0 / kTile, (int)u1 / kTile + 1, (int)v1 / kTile + 1);
+          pairs = (unsigned long long)(box.z - box.x) * (unsigned long long)(box.w - box.y);
+          SplatRec o;
+          o.a = make_float4(mu_u, mu_v, ru, rv);
+          const float cb = -(suv / det);
+          o.b = make_float4(svv / det, cb + cb, suu / det, in.opacity[m]);
+          o.c = make_float4(in.colors[3 * m], in.colors[3 * m + 1], in.colors[3 * m + 2], z);
+          rec[m] = o;
+        }
+      }
+    }
+    rect[m] = box;
+    count[m] = pairs;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------- scans
+
+// exclusive prefix sums of x[0, n) in place, in chunks of kScanChunk; sums[b] = total of chunk b
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanChunk = kScanThreads * kScanItems;
+
+template <class T>
+__device__ inline T block_exclusive(T v, T* s_warp, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T y = __shfl_up_sync(~0u, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const T w = s_warp[lane];
+    T wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const T y = __shfl_up_sync(~0u, wi, d);
+      if (lane >= d) wi += y;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  return s_warp[warp] + incl - v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(T* x, uint64_t n, T* sums) {
+  __shared__ T s_warp[32];
+  __shared__ T s_total;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? x[base + k] : T(0);
+    sum += v[k];
+  }
+  T run = block_exclusive<T>(sum, s_warp, &s_total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) x[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = s_total;
+}
+
+// exclusive prefix of the chunk sums (one CTA; each thread a contiguous run); *total = their sum
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(T* sums, uint32_t nb, T* total) {
+  __shared__ T s_warp[32];
+  __shared__ T s_total;
+  const uint32_t per = (nb + kScanThreads - 1) / kScanThreads, lo = threadIdx.x * per;
+  T sum = 0;
+  for (uint32_t i = lo; i < lo + per && i < nb; ++i) sum += sums[i];
+  T run = block_exclusive<T>(sum, s_warp, &s_total);
+  for (uint32_t i = lo; i < lo + per && i < nb; ++i) {
+    const T c = sums[i];
+    sums[i] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0 && total) *total = s_total;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(T* x, uint64_t n, const T* sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+  const T off = sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) x[base + k] += off;
+}
+
+template <class T>
+void exclusive_scan(T* x, uint64_t n, T* sums, T* total, cudaStream_t s) {
+  const uint32_t nb = (uint32_t)((n + kScanChunk - 1) / kScanChunk);
+  if (nb == 0) {
+    if (total) cudaMemsetAsync(total, 0, sizeof(T), s);
+    return;
+  }
+  k_scan_chunks<T><<<nb, kScanThreads, 0, s>>>(x, n, sums);
+  k_scan_sums<T><<<1, kScanThreads, 0, s>>>(sums, nb, total);
+  k_scan_add<T><<<nb, kScanThreads, 0, s>>>(x, n, sums);
+}
+
+size_t scan_sums_count(uint64_t n) { return (size_t)((n + kScanChunk - 1) / kScanChunk) + 1; }
+
+// ---------------------------------------------------------------------------------------------------- pairs
+
+__global__ void __launch_bounds__(256) k_splat_pairs(uint64_t n, const int4* rect, const unsigned long long* offset,
+                                                     const SplatRec* rec, int tiles_x, unsigned long long* keys,
+                                                     uint32_t* vals) {
+  for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
+    const int4 r = rect[m];
+    if (r.z <= r.x || r.w <= r.y) continue;
+    const unsigned long long zb = __float_as_uint(rec[m].c.w);
+    unsigned long long o = offset[m];
+    for (int ty = r.y; ty < r.w; ++ty)
+      for (int tx = r.x; tx < r.z; ++tx, ++o) {
+        keys[o] = ((unsigned long long)(ty * tiles_x + tx) << 32) | zb;
+        vals[o] = (uint32_t)m;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------- radix sort
+
+constexpr int kRsThreads = 256, kRsItems = 16, kRsChunk = kRsThreads * kRsItems;
+
+// digit counts of each chunk, stored digit-major (hist[d * nb + b]) so that one exclusive scan gives every
+// (digit, chunk) its first output position
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* keys, uint32_t n, int shift,
+                                                        uint32_t* hist, uint32_t nb) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t base = blockIdx.x * (uint32_t)kRsChunk;
+  for (int r = 0; r < kRsItems; ++r) {
+    const uint32_t i = base + r * kRsThreads + threadIdx.x;
+    const uint32_t d = i < n ? (uint32_t)(keys[i] >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(~0u, d);  // one shared-memory add per distinct digit of the warp
+    if (d < 256u && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// stable scatter of one chunk: items are ranked in order (rounds of 256 in thread order; within a warp by lane,
+// across warps by warp) on top of the chunk's scanned first position per digit
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long long* kin, const uint32_t* vin,
+                                                           unsigned long long* kout, uint32_t* vout, uint32_t n,
+                                                           int shift, const uint32_t* hist, uint32_t nb) {
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_warp[kRsThreads / 32][256];
+  __shared__ uint32_t s_tot[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  s_base[threadIdx.x] = hist[threadIdx.x * nb + blockIdx.x];
+  const uint32_t base = blockIdx.x * (uint32_t)kRsChunk;
+  for (int r = 0; r < kRsItems; ++r) {
+    if (base + r * kRsThreads >= n) break;  // uniform over the CTA
+#pragma unroll
+    for (int w = 0; w < kRsThreads / 32; ++w) s_warp[w][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t i = base + r * kRsThreads + threadIdx.x;
+    const bool live = i < n;
+    const unsigned long long key = live ? kin[i] : 0ull;
+    const uint32_t val = live ? vin[i] : 0u;
+    const uint32_t d = live ? (uint32_t)(key >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(~0u, d);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (live && rank == 0) s_warp[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int w = 0; w < kRsThreads / 32; ++w) {
+        const uint32_t c = s_warp[w][threadIdx.x];
+        s_warp[w][threadIdx.x] = acc;
+        acc += c;
+      }
+      s_tot[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (live) {
+      const uint32_t pos = s_base[d] + s_warp[warp][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    s_base[threadIdx.x] += s_tot[threadIdx.x];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------- render
+
+__global__ void __launch_bounds__(256) k_splat_ranges(const unsigned long long* keys, uint32_t n, uint2* ranges) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
+    if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+  }
+}
+
+__global__ void __launch_bounds__(kTile * kTile) k_splat_render(const uint2* ranges, const uint32_t* vals,
+                                                               const SplatRec* rec, SplatGeo g, float* rgb,
+                                                               float* trans) {
+  __shared__ float4 s_a[kTile * kTile], s_b[kTile * kTile], s_c[kTile * kTile];
+  const int tile = blockIdx.x;
+  const int px = (tile % g.tiles_x) * kTile + (threadIdx.x % kTile);
+  const int py = (tile / g.tiles_x) * kTile + (threadIdx.x / kTile);
+  const bool inside = px < g.width && py < g.height;
+  const uint2 r = ranges[tile];
+  const float fu = (float)px, fv = (float)py;
+  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+  bool done = !inside;
+  for (uint32_t start = r.x; start < r.y; start += kTile * kTile) {
+    // also the barrier before the shared records are overwritten
+    if (__syncthreads_count(done) == kTile * kTile) break;
+    const uint32_t j = start + threadIdx.x;
+    if (j < r.y) {
+      const SplatRec& o = rec[vals[j]];
+      s_a[threadIdx.x] = o.a;
+      s_b[threadIdx.x] = o.b;
+      s_c[threadIdx.x] = o.c;
+    }
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)(kTile * kTile), r.y - start);
+    for (int k = 0; k < cnt && !done; ++k) {
+      const float4 a = s_a[k];
+      const float du = fu - a.x, dv = fv - a.y;
+      if (!(fabsf(du) <= a.z && fabsf(dv) <= a.w)) continue;
+      const float4 b = s_b[k];
+      const float q = (b.x * (du * du) + b.y * (du * dv)) + b.z * (dv * dv);
+      if (!(q <= 9.0f)) continue;
+      const float w = b.w * expf(-0.5f * q);
+      const float4 cc = s_c[k];
+      C0 = C0 + (cc.x * w) * T;
+      C1 = C1 + (cc.y * w) * T;
+      C2 = C2 + (cc.z * w) * T;
+      T = T * (1.0f - w);
+      if (T < kSplatStop) done = true;
+    }
+  }
+  if (inside) {
+    const size_t p = (size_t)py * g.width + px;
+    rgb[3 * p] = C0;
+    rgb[3 * p + 1] = C1;
+    rgb[3 * p + 2] = C2;
+    if (trans) trans[p] = T;
+  }
+}
+
+template <class T>
+T* carve(uint8_t*& p, size_t count) {
+  T* out = reinterpret_cast<T*>(p);
+  p += (count * sizeof(T) + 255) & ~(size_t)255;
+  return out;
+}
+
+}  // namespace
+
+cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, float* trans, uint64_t* n_pairs,
+                         int device, cudaStream_t s, int sms) {
+  SplatGeo g{c.width, c.height, (c.width + kTile - 1) / kTile, (c.height + kTile - 1) / kTile};
+  const uint32_t n_tiles = (uint32_t)(g.tiles_x * g.tiles_y);
+  *n_pairs = 0;
+  // phase 1: projection and the pair count
+  const uint64_t n = in.n;
+  const size_t nsum = scan_sums_count(n);
+  const size_t bytes1 = ((n * sizeof(SplatRec) + 255) & ~(size_t)255) + ((n * sizeof(int4) + 255) & ~(size_t)255) +
+                        ((n * 8 + 255) & ~(size_t)255) + ((nsum * 8 + 255) & ~(size_t)255) + 256;
+  void* scratch1 = nullptr;
+  cudaError_t e = scratch_alloc(&scratch1, bytes1, device, s);
+  if (e != cudaSuccess) return e;
+  uint8_t* p = (uint8_t*)scratch1;
+  SplatRec* rec = carve<SplatRec>(p, n);
+  int4* rect = carve<int4>(p, n);
+  unsigned long long* count = carve<unsigned long long>(p, n);
+  unsigned long long* sums = carve<unsigned long long>(p, nsum);
+  unsigned long long* total = carve<unsigned long long>(p, 1);
+  if (n > 0) {
+    const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 16);
+    k_splat_project<<<grid, 256, 0, s>>>(in, c, g, rec, rect, count);
+  }
+  exclusive_scan<unsigned long long>(count, n, sums, total, s);  // count becomes each Gaussian's first pair
+  unsigned long long P = 0;
+  e = cudaMemcpyAsync(&P, total, sizeof(P), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch1, s);
+    return e;
+  }
+  *n_pairs = P;
+  if (P > kSplatMaxPairs) {  // the caller reports the capacity error; nothing is rendered
+    cudaFreeAsync(scratch1, s);
+    return cudaSuccess;
+  }
+  // phase 2: pairs, sort, ranges, render
+  const uint32_t np = (uint32_t)P;
+  const uint32_t nb = (np + kRsChunk - 1) / kRsChunk;
+  const uint64_t nh = 256ull * nb;
+  const size_t nsum2 = scan_sums_count(nh);
+  const size_t bytes2 = 2 * ((np * 8ull + 255) & ~255ull) + 2 * ((np * 4ull + 255) & ~255ull) +
+                        ((nh * 4 + 255) & ~255ull) + ((nsum2 * 4 + 255) & ~255ull) + ((n_tiles * 8ull + 255) & ~255ull) +
+                        256;
+  void* scratch2 = nullptr;
+  e = scratch_alloc(&scratch2, bytes2, device, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch1, s);
+    return e;
+  }
+  p = (uint8_t*)scratch2;
+  unsigned long long* keys[2] = {carve<unsigned long long>(p, np), carve<unsigned long long>(p, np)};
+  uint32_t* vals[2] = {carve<uint32_t>(p, np), carve<uint32_t>(p, np)};
+  uint32_t* hist = carve<uint32_t>(p, nh);
+  uint32_t* sums2 = carve<uint32_t>(p, nsum2);
+  uint2* ranges = carve<uint2>(p, n_tiles);
+  cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
+  int cur = 0;
+  if (np > 0) {
+    // the count array now holds each Gaussian's first pair
+    k_splat_pairs<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(
+        n, rect, count, rec, g.tiles_x, keys[0], vals[0]);
+    int tile_bits = 1;
+    while ((1u << tile_bits) < n_tiles) ++tile_bits;
+    for (int shift = 0; shift < 32 + tile_bits; shift += 8) {
+      k_rs_hist<<<nb, kRsThreads, 0, s>>>(keys[cur], np, shift, hist, nb);
+      exclusive_scan<uint32_t>(hist, nh, sums2, nullptr, s);
+      k_rs_scatter<<<nb, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np, shift, hist, nb);
+      cur ^= 1;
+    }
+    k_splat_ranges<<<(unsigned)std::min<uint64_t>((np + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(keys[cur], np,
+                                                                                                     ranges);
+  }
+  k_splat_render<<<n_tiles, kTile * kTile, 0, s>>>(ranges, vals[cur], rec, g, rgb, trans);
+  e = cudaGetLastError();
+  cudaFreeAsync(scratch2, s);
+  cudaFreeAsync(scratch1, s);
+  return e;
+}
+
+}  // namespace mrh

@@ -303,3 +303,43 @@ def render_lidar(wl: Workload, frame: int, scene: np.ndarray | None = None, pose
                            wl.elev_deg[1], _ptr(T, ctypes.c_double), wl.range_noise, wl.r_min, wl.r_max, wl.seed,
                            frame, _ptr(xyz, ctypes.c_float), _threads())
     return xyz, T
+
+
+def gaussians(wl: Workload, n: int, frames=(0, 40, 80, 120, 160, 200, 240, 280), seed: int = 7,
+              footprint_px=(1.5, 6.0)) -> dict:
+    """Seeded 3D Gaussians on the scene's surfaces, depth-seeded like the splats of the rendering branch: n pixels
+    drawn at random from noise-free depth renders of camera workload ``wl`` at ``frames`` are back-projected to
+    world points (the means), coloured by their pixel (RGB / 255), given a random orientation and per-axis standard
+    deviations of U(footprint_px) pixels at their depth times U(0.3, 1) anisotropy, and an opacity of U(0.3, 0.95).
+    Returns means (n, 3), covs (n, 6: xx, xy, xz, yy, yz, zz), opacity (n,), colors (n, 3), all float32."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    clean = dataclasses.replace(wl, noise_coef=0.0, dropout=0.0)
+    sc = wl.scene()
+    per = [n // len(frames) + (1 if i < n % len(frames) else 0) for i in range(len(frames))]
+    means, cols, dist = [], [], []
+    for k, cnt in zip(frames, per):
+        depth, rgb, T = render_depth(clean, k, scene=sc)
+        vv, uu = np.nonzero(depth > 0)
+        pick = rng.choice(vv.size, size=cnt, replace=vv.size < cnt)
+        u, v = uu[pick].astype(np.float64), vv[pick].astype(np.float64)
+        z = depth[vv[pick], uu[pick]].astype(np.float64)
+        pc = np.stack([(u - wl.cx) / wl.fx * z, (v - wl.cy) / wl.fy * z, z], 1)
+        means.append(pc @ T[:3, :3].T + T[:3, 3])
+        cols.append(rgb[vv[pick], uu[pick]].astype(np.float64) / 255.0)
+        dist.append(np.linalg.norm(pc, axis=1))  # distance from the camera that saw the point
+    mu = np.concatenate(means)
+    col = np.concatenate(cols)
+    dist = np.concatenate(dist)
+    # standard deviations: a footprint in pixels at that distance
+    s = (dist / wl.fx)[:, None] * rng.uniform(*footprint_px, size=(n, 1)) * rng.uniform(0.3, 1.0, size=(n, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, zq = q.T
+    Rm = np.stack([1 - 2 * (y * y + zq * zq), 2 * (x * y - w * zq), 2 * (x * zq + w * y),
+                   2 * (x * y + w * zq), 1 - 2 * (x * x + zq * zq), 2 * (y * zq - w * x),
+                   2 * (x * zq - w * y), 2 * (y * zq + w * x), 1 - 2 * (x * x + y * y)], 1).reshape(n, 3, 3)
+    S = np.einsum("nij,nj,nkj->nik", Rm, s * s, Rm)
+    covs = np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1)
+    return {"means": mu.astype(np.float32), "covs": covs.astype(np.float32),
+            "opacity": rng.uniform(0.3, 0.95, n).astype(np.float32), "colors": col.astype(np.float32)}
