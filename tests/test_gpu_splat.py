@@ -58,7 +58,7 @@ def test_whole_images_match_the_oracle(size, n, frame):
     assert drawn > n // 10 and pairs > 0
     assert np.abs(rgb_g - rgb_o).max() <= TOL
     assert np.abs(tr_g - tr_o).max() <= TOL
-    assert (tr_o < 0.5).mean() > 0.3  # the images are mostly covered
+    assert (tr_o < 0.99).mean() > 0.3  # most pixels receive some Gaussian
 
 
 def test_full_size_camera_at_sampled_pixels():
