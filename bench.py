@@ -626,11 +626,14 @@ def run_quadtree(wl, frames, reps=3, threshold=0.1, min_size=1, oracle_frames=3)
             "oracle_frames_checked_equal": same}
 
 
-def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), views=(20, 50, 80, 110)):
+def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.006, 0.01, 0.02, 0.04), views=(20, 50, 80, 110),
+                 singles=(0.01, 0.02, 0.04)):
     """Variance-threshold sweep on the RGB-D sequence (the synthetic analogue of Sec. 5.1): for each sigma the
-    thresholds are (sigma^2, 4 sigma^2); after n_frames frames it reports the device time per frame (integration
-    only), blocks and payload bytes per level, the collapsed mesh's vertices and faces, and accuracy, completeness and
-    Chamfer-L1 of the map's raycast depth against noise-free renders at `views`."""
+    thresholds are (sigma^2, 4 sigma^2); then single-resolution maps with one level of each voxel size in `singles`
+    (the single- vs multi-resolution comparison), same truncation. After n_frames frames each row reports the device
+    time per frame (integration only), blocks and payload bytes per level, the collapsed mesh's vertices and faces
+    (one collapse spacing for every row: an eighth of the finest multi-resolution voxel), and accuracy, completeness
+    and Chamfer-L1 of the map's raycast depth against noise-free renders at `views`."""
     import dataclasses
     import torch
     import paper_2511_21459_b300 as mrh
@@ -642,8 +645,10 @@ def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), v
     torch.cuda.synchronize()
     warm.close()
     out = []
-    for sig in sigmas:
-        w2 = dataclasses.replace(wl, var_threshold=(sig * sig, 4 * sig * sig))
+    delta = wl.voxel0 / 8
+    rows = [(f"sigma {sig}", dataclasses.replace(wl, var_threshold=(sig * sig, 4 * sig * sig)), sig) for sig in sigmas]
+    rows += [(f"single {v * 100:g} cm", dataclasses.replace(wl, base_voxel=v, n_levels=1), None) for v in singles]
+    for label, w2, sig in rows:
         m = mrh.Map(mrh.params_from(w2), device=torch.cuda.current_device())
         K = mrh.pinhole_from(w2)
         stream = torch.cuda.current_stream()
@@ -657,9 +662,11 @@ def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.0045, 0.006, 0.01), v
         vb = voxel_bytes(w2)
         live = st["live_blocks"]
         soup = m.extract_mesh()
-        verts, faces = m.weld_mesh(soup, w2.base_voxel / (1 << (w2.n_levels - 1)) / 8)
+        verts, faces = m.weld_mesh(soup, delta)
         ch = chamfer_vs_truth(m, w2, views)
-        out.append({"sigma": sig, "theta": [sig * sig, 4 * sig * sig], "ms_per_frame": round(a.elapsed_time(b) / n_frames, 4),
+        out.append({"map": label, "levels_cm": [round(100 * w2.voxel0 * (1 << l), 3) for l in range(w2.n_levels)],
+                    "sigma": sig, "theta": [sig * sig, 4 * sig * sig] if sig else None,
+                    "ms_per_frame": round(a.elapsed_time(b) / n_frames, 4),
                     "live_blocks": live, "payload_MB": [round(n * (8 >> l) ** 3 * vb / 1e6, 1) for l, n in enumerate(live)],
                     "vertices": int(verts.shape[0]), "faces": int(faces.shape[0]),
                     "acc_mm": round(1e3 * ch["acc"], 3), "comp_mm": round(1e3 * ch["comp"], 3),
