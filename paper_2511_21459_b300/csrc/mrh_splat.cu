@@ -12,14 +12,15 @@
 // below kSplatStop times the largest colour, and its transmittance is off by less than kSplatStop.
 //
 // The work (one stream; one host read, of the number of tile-Gaussian pairs):
-//   k_splat_project  one thread per Gaussian: Eq. 7, the three-sigma box, the tiles it overlaps (16 x 16 pixels)
-//                    and a 48-byte record {mu_u, mu_v, ru, rv}, {conic uu, 2 conic uv, conic vv, alpha},
-//                    {colour, z}
-//   scan             exclusive prefix of the per-Gaussian pair counts
-//   k_splat_pairs    every (tile, Gaussian) pair as key tile << 32 | bits of z (positive floats order as their bits),
-//                    value the Gaussian's index, written in Gaussian order
-//   radix sort       stable least-significant-digit passes of 8 bits over the key's 32 + tile bits, so a tile's
-//                    pairs end up contiguous, by depth, equal depths in Gaussian order
+//   k_splat_project  one thread per Gaussian: Eq. 7, the three-sigma box, the tiles it overlaps (16 x 16 pixels),
+//                    a 48-byte record {mu_u, mu_v, ru, rv}, {conic uu, 2 conic uv, conic vv, alpha}, {colour, z}
+//                    and its depth key (the bits of z: positive floats order as their bits; all ones when not drawn)
+//   depth sort       stable least-significant-digit radix sort (8-bit digits) of the Gaussians by depth key, so
+//                    equal depths stay in index order
+//   scan             exclusive prefix of the pair counts in depth order
+//   k_splat_pairs    every (tile, Gaussian) pair, key = tile, value = Gaussian index, laid out in depth order
+//   tile sort        the same stable radix sort over the tile bits only: a tile's pairs end up contiguous and keep
+//                    the depth order
 //   k_splat_ranges   each tile's first and last pair
 //   k_splat_render   one CTA of 16 x 16 threads per tile; the tile's records are staged 256 at a time in shared
 //                    memory and every thread blends its pixel through them; the CTA leaves when all its pixels
@@ -50,7 +51,7 @@ struct SplatGeo {
 // ---------------------------------------------------------------------------------------------------- projection
 
 __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c, SplatGeo g, SplatRec* rec,
-                                                       int4* rect, unsigned long long* count) {
+                                                       int4* rect, uint32_t* zkey, uint32_t* zval) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < in.n; m += (uint64_t)gridDim.x * blockDim.x) {
     unsigned long long pairs = 0;
     int4 box = make_int4(0, 0, 0, 0);  // tiles [x, z) x [y, w); empty when the Gaussian is not drawn
@@ -101,7 +102,19 @@ __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c
       }
     }
     rect[m] = box;
-    count[m] = pairs;
+    zkey[m] = pairs ? __float_as_uint(z) : 0xFFFFFFFFu;
+    zval[m] = (uint32_t)m;
+  }
+}
+
+// pair count of each Gaussian in depth order, and each Gaussian's rank in that order
+__global__ void __launch_bounds__(256) k_splat_counts(uint64_t n, const uint32_t* order, const int4* rect,
+                                                      unsigned long long* count, uint32_t* rank) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = order[i];
+    const int4 r = rect[m];
+    count[i] = (unsigned long long)(r.z - r.x) * (unsigned long long)(r.w - r.y);
+    rank[m] = (uint32_t)i;
   }
 }
 
@@ -199,17 +212,18 @@ size_t scan_sums_count(uint64_t n) { return (size_t)((n + kScanChunk - 1) / kSca
 
 // ---------------------------------------------------------------------------------------------------- pairs
 
-__global__ void __launch_bounds__(256) k_splat_pairs(uint64_t n, const int4* rect, const unsigned long long* offset,
-                                                     const SplatRec* rec, int tiles_x, unsigned long long* keys,
+// Gaussians in index order (near ones, which overlap the most tiles, are spread over the grid that way), each
+// writing its pairs at its place in the depth order (rank = position in the depth-sorted order)
+__global__ void __launch_bounds__(256) k_splat_pairs(uint64_t n, const uint32_t* rank, const int4* rect,
+                                                     const unsigned long long* offset, int tiles_x, uint32_t* keys,
                                                      uint32_t* vals) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
     const int4 r = rect[m];
     if (r.z <= r.x || r.w <= r.y) continue;
-    const unsigned long long zb = __float_as_uint(rec[m].c.w);
-    unsigned long long o = offset[m];
+    unsigned long long o = offset[rank[m]];
     for (int ty = r.y; ty < r.w; ++ty)
       for (int tx = r.x; tx < r.z; ++tx, ++o) {
-        keys[o] = ((unsigned long long)(ty * tiles_x + tx) << 32) | zb;
+        keys[o] = (uint32_t)(ty * tiles_x + tx);
         vals[o] = (uint32_t)m;
       }
   }
@@ -221,16 +235,23 @@ constexpr int kRsThreads = 256, kRsItems = 16, kRsChunk = kRsThreads * kRsItems;
 
 // digit counts of each chunk, stored digit-major (hist[d * nb + b]) so that one exclusive scan gives every
 // (digit, chunk) its first output position
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* keys, uint32_t n, int shift,
-                                                        uint32_t* hist, uint32_t nb) {
+template <class K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* keys, uint32_t n, int shift, uint32_t* hist,
+                                                        uint32_t nb) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t base = blockIdx.x * (uint32_t)kRsChunk;
+  uint32_t dig[kRsItems];  // all of the chunk's loads issued before the first count
+#pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
     const uint32_t i = base + r * kRsThreads + threadIdx.x;
-    const uint32_t d = i < n ? (uint32_t)(keys[i] >> shift) & 255u : 256u;
+    dig[r] = i < n ? (uint32_t)(keys[i] >> shift) & 255u : 256u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    const uint32_t d = dig[r];
     const unsigned peers = __match_any_sync(~0u, d);  // one shared-memory add per distinct digit of the warp
     if (d < 256u && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
@@ -239,58 +260,67 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long
 }
 
 // stable scatter of one chunk: items are ranked in order (rounds of 256 in thread order; within a warp by lane,
-// across warps by warp) on top of the chunk's scanned first position per digit
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long long* kin, const uint32_t* vin,
-                                                           unsigned long long* kout, uint32_t* vout, uint32_t n,
-                                                           int shift, const uint32_t* hist, uint32_t nb) {
+// across warps by warp) on top of the chunk's scanned first position per digit; the chunk's keys and values are
+// loaded up front
+template <class K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                                                           uint32_t n, int shift, const uint32_t* hist, uint32_t nb) {
   __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_warp[kRsThreads / 32][256];
   __shared__ uint32_t s_tot[256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   s_base[threadIdx.x] = hist[threadIdx.x * nb + blockIdx.x];
   const uint32_t base = blockIdx.x * (uint32_t)kRsChunk;
+  K key[kRsItems];
+  uint32_t val[kRsItems];
+#pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
-    if (base + r * kRsThreads >= n) break;  // uniform over the CTA
-#pragma unroll
-    for (int w = 0; w < kRsThreads / 32; ++w) s_warp[w][threadIdx.x] = 0;
-    __syncthreads();
     const uint32_t i = base + r * kRsThreads + threadIdx.x;
-    const bool live = i < n;
-    const unsigned long long key = live ? kin[i] : 0ull;
-    const uint32_t val = live ? vin[i] : 0u;
-    const uint32_t d = live ? (uint32_t)(key >> shift) & 255u : 256u;
-    const unsigned peers = __match_any_sync(~0u, d);
-    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    if (live && rank == 0) s_warp[warp][d] = (uint32_t)__popc(peers);
-    __syncthreads();
-    {
-      uint32_t acc = 0;
+    key[r] = i < n ? kin[i] : K(0);
+    val[r] = i < n ? vin[i] : 0u;
+  }
 #pragma unroll
-      for (int w = 0; w < kRsThreads / 32; ++w) {
-        const uint32_t c = s_warp[w][threadIdx.x];
-        s_warp[w][threadIdx.x] = acc;
-        acc += c;
+  for (int r = 0; r < kRsItems; ++r) {
+    if (base + r * kRsThreads < n) {  // uniform over the CTA
+#pragma unroll
+      for (int w = 0; w < kRsThreads / 32; ++w) s_warp[w][threadIdx.x] = 0;
+      __syncthreads();
+      const uint32_t i = base + r * kRsThreads + threadIdx.x;
+      const bool live = i < n;
+      const uint32_t d = live ? (uint32_t)(key[r] >> shift) & 255u : 256u;
+      const unsigned peers = __match_any_sync(~0u, d);
+      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      if (live && rank == 0) s_warp[warp][d] = (uint32_t)__popc(peers);
+      __syncthreads();
+      {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w) {
+          const uint32_t c = s_warp[w][threadIdx.x];
+          s_warp[w][threadIdx.x] = acc;
+          acc += c;
+        }
+        s_tot[threadIdx.x] = acc;
       }
-      s_tot[threadIdx.x] = acc;
+      __syncthreads();
+      if (live) {
+        const uint32_t pos = s_base[d] + s_warp[warp][d] + rank;
+        kout[pos] = key[r];
+        vout[pos] = val[r];
+      }
+      __syncthreads();
+      s_base[threadIdx.x] += s_tot[threadIdx.x];
     }
-    __syncthreads();
-    if (live) {
-      const uint32_t pos = s_base[d] + s_warp[warp][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
-    __syncthreads();
-    s_base[threadIdx.x] += s_tot[threadIdx.x];
   }
 }
 
 // ---------------------------------------------------------------------------------------------------- render
 
-__global__ void __launch_bounds__(256) k_splat_ranges(const unsigned long long* keys, uint32_t n, uint2* ranges) {
+__global__ void __launch_bounds__(256) k_splat_ranges(const uint32_t* keys, uint32_t n, uint2* ranges) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
-    if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+    if (i + 1 == n || keys[i + 1] != t) ranges[t].y = i + 1;
   }
 }
 
@@ -350,6 +380,29 @@ T* carve(uint8_t*& p, size_t count) {
   return out;
 }
 
+size_t carve_bytes(size_t count, size_t size) { return (count * size + 255) & ~(size_t)255; }
+
+// Stable radix sort of (key, value) pairs over key bits [0, bits): 8-bit digits, ping-pong between the two buffers
+// of keys and vals; returns the index (0 or 1) of the buffer holding the result.
+template <class K>
+int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t n, int bits, uint32_t* hist, uint32_t* sums, cudaStream_t s) {
+  const uint32_t nb = (n + kRsChunk - 1) / kRsChunk;
+  int cur = 0;
+  if (n == 0) return cur;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<K><<<nb, kRsThreads, 0, s>>>(keys[cur], n, shift, hist, nb);
+    exclusive_scan<uint32_t>(hist, 256ull * nb, sums, nullptr, s);
+    k_rs_scatter<K><<<nb, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, nb);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+size_t radix_scratch_words(uint32_t n) {
+  const uint64_t nb = (n + kRsChunk - 1) / kRsChunk;
+  return 256 * nb;
+}
+
 }  // namespace
 
 cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, float* trans, uint64_t* n_pairs,
@@ -357,23 +410,32 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   SplatGeo g{c.width, c.height, (c.width + kTile - 1) / kTile, (c.height + kTile - 1) / kTile};
   const uint32_t n_tiles = (uint32_t)(g.tiles_x * g.tiles_y);
   *n_pairs = 0;
-  // phase 1: projection and the pair count
-  const uint64_t n = in.n;
-  const size_t nsum = scan_sums_count(n);
-  const size_t bytes1 = ((n * sizeof(SplatRec) + 255) & ~(size_t)255) + ((n * sizeof(int4) + 255) & ~(size_t)255) +
-                        ((n * 8 + 255) & ~(size_t)255) + ((nsum * 8 + 255) & ~(size_t)255) + 256;
+  const uint32_t n = (uint32_t)in.n;  // n < 2^32, checked by the caller
+  const unsigned grid_n = (unsigned)std::min<uint64_t>((n + 255) / 256 + 1, (uint64_t)sms * 16);
+  // phase 1: projection, depth order, pair counts
+  const size_t nh1 = radix_scratch_words(n);
+  const size_t bytes1 = carve_bytes(n, sizeof(SplatRec)) + carve_bytes(n, sizeof(int4)) + 5 * carve_bytes(n, 4) +
+                        carve_bytes(n, 8) + carve_bytes(scan_sums_count(n), 8) + carve_bytes(nh1, 4) +
+                        carve_bytes(scan_sums_count(nh1), 4) + 256;
   void* scratch1 = nullptr;
   cudaError_t e = scratch_alloc(&scratch1, bytes1, device, s);
   if (e != cudaSuccess) return e;
   uint8_t* p = (uint8_t*)scratch1;
   SplatRec* rec = carve<SplatRec>(p, n);
   int4* rect = carve<int4>(p, n);
+  uint32_t* zkey[2] = {carve<uint32_t>(p, n), carve<uint32_t>(p, n)};
+  uint32_t* zval[2] = {carve<uint32_t>(p, n), carve<uint32_t>(p, n)};
+  uint32_t* rank = carve<uint32_t>(p, n);
   unsigned long long* count = carve<unsigned long long>(p, n);
-  unsigned long long* sums = carve<unsigned long long>(p, nsum);
+  unsigned long long* sums = carve<unsigned long long>(p, scan_sums_count(n));
+  uint32_t* hist1 = carve<uint32_t>(p, nh1);
+  uint32_t* sums1 = carve<uint32_t>(p, scan_sums_count(nh1));
   unsigned long long* total = carve<unsigned long long>(p, 1);
+  int zc = 0;
   if (n > 0) {
-    const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 16);
-    k_splat_project<<<grid, 256, 0, s>>>(in, c, g, rec, rect, count);
+    k_splat_project<<<grid_n, 256, 0, s>>>(in, c, g, rec, rect, zkey[0], zval[0]);
+    zc = radix_sort<uint32_t>(zkey, zval, n, 32, hist1, sums1, s);
+    k_splat_counts<<<grid_n, 256, 0, s>>>(n, zval[zc], rect, count, rank);
   }
   exclusive_scan<unsigned long long>(count, n, sums, total, s);  // count becomes each Gaussian's first pair
   unsigned long long P = 0;
@@ -388,14 +450,11 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
     cudaFreeAsync(scratch1, s);
     return cudaSuccess;
   }
-  // phase 2: pairs, sort, ranges, render
+  // phase 2: pairs in depth order, stable sort by tile, ranges, render
   const uint32_t np = (uint32_t)P;
-  const uint32_t nb = (np + kRsChunk - 1) / kRsChunk;
-  const uint64_t nh = 256ull * nb;
-  const size_t nsum2 = scan_sums_count(nh);
-  const size_t bytes2 = 2 * ((np * 8ull + 255) & ~255ull) + 2 * ((np * 4ull + 255) & ~255ull) +
-                        ((nh * 4 + 255) & ~255ull) + ((nsum2 * 4 + 255) & ~255ull) + ((n_tiles * 8ull + 255) & ~255ull) +
-                        256;
+  const size_t nh2 = radix_scratch_words(np);
+  const size_t bytes2 = 4 * carve_bytes(np, 4) + carve_bytes(nh2, 4) + carve_bytes(scan_sums_count(nh2), 4) +
+                        carve_bytes(n_tiles, sizeof(uint2)) + 256;
   void* scratch2 = nullptr;
   e = scratch_alloc(&scratch2, bytes2, device, s);
   if (e != cudaSuccess) {
@@ -403,25 +462,18 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
     return e;
   }
   p = (uint8_t*)scratch2;
-  unsigned long long* keys[2] = {carve<unsigned long long>(p, np), carve<unsigned long long>(p, np)};
+  uint32_t* keys[2] = {carve<uint32_t>(p, np), carve<uint32_t>(p, np)};
   uint32_t* vals[2] = {carve<uint32_t>(p, np), carve<uint32_t>(p, np)};
-  uint32_t* hist = carve<uint32_t>(p, nh);
-  uint32_t* sums2 = carve<uint32_t>(p, nsum2);
+  uint32_t* hist2 = carve<uint32_t>(p, nh2);
+  uint32_t* sums2 = carve<uint32_t>(p, scan_sums_count(nh2));
   uint2* ranges = carve<uint2>(p, n_tiles);
   cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
   int cur = 0;
   if (np > 0) {
-    // the count array now holds each Gaussian's first pair
-    k_splat_pairs<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(
-        n, rect, count, rec, g.tiles_x, keys[0], vals[0]);
+    k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, count, g.tiles_x, keys[0], vals[0]);
     int tile_bits = 1;
     while ((1u << tile_bits) < n_tiles) ++tile_bits;
-    for (int shift = 0; shift < 32 + tile_bits; shift += 8) {
-      k_rs_hist<<<nb, kRsThreads, 0, s>>>(keys[cur], np, shift, hist, nb);
-      exclusive_scan<uint32_t>(hist, nh, sums2, nullptr, s);
-      k_rs_scatter<<<nb, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np, shift, hist, nb);
-      cur ^= 1;
-    }
+    cur = radix_sort<uint32_t>(keys, vals, np, tile_bits, hist2, sums2, s);
     k_splat_ranges<<<(unsigned)std::min<uint64_t>((np + 255) / 256, (uint64_t)sms * 16), 256, 0, s>>>(keys[cur], np,
                                                                                                      ranges);
   }
