@@ -12,9 +12,10 @@
 // below kSplatStop times the largest colour, and its transmittance is off by less than kSplatStop.
 //
 // The work (one stream; one host read, of the number of tile-Gaussian pairs):
-//   k_splat_project  one thread per Gaussian: Eq. 7, the three-sigma box, the tiles it overlaps (16 x 16 pixels),
-//                    a 48-byte record {mu_u, mu_v, ru, rv}, {conic uu, 2 conic uv, conic vv, alpha}, {colour, z}
-//                    and its depth key (the bits of z: positive floats order as their bits; all ones when not drawn)
+//   k_splat_project  one thread per Gaussian: Eq. 7, the three-sigma box, the tiles it overlaps (16 x 16 pixels)
+//                    less those its q <= 9 ellipse cannot reach (tile_reached), a 48-byte record {mu_u, mu_v, ru,
+//                    rv}, {conic uu, 2 conic uv, conic vv, alpha}, {colour, z} and its depth key (the bits of z:
+//                    positive floats order as their bits; all ones when not drawn)
 //   depth sort       stable least-significant-digit radix sort (8-bit digits) of the Gaussians by depth key, so
 //                    equal depths stay in index order
 //   scan             exclusive prefix of the pair counts in depth order
@@ -48,10 +49,37 @@ struct SplatGeo {
   int width, height, tiles_x, tiles_y;
 };
 
+// Gaussians whose box covers at most this many tiles have each tile tested against their ellipse; larger ones keep
+// every tile of the box, so that no thread loops long
+constexpr int kEllipseTest = 64;
+
+// false when no pixel centre of tile (tx, ty) can satisfy the float reach test q <= 9: the least q over the
+// rectangle spanned by the tile's pixel centres (zero when it holds the mean, else the least of the four edges'
+// constrained minima) exceeds 9 by more than the float evaluations of q, here and per pixel, can err (a few ulps of
+// a u^2 + 2 |b u v| + c v^2 over the rectangle, allowed for with a factor of 1e-5, plus 1e-3)
+__device__ inline bool tile_reached(const SplatRec& o, int tx, int ty) {
+  const float u0 = (float)(tx * kTile) - o.a.x, u1 = (float)(tx * kTile + kTile - 1) - o.a.x;
+  const float v0 = (float)(ty * kTile) - o.a.y, v1 = (float)(ty * kTile + kTile - 1) - o.a.y;
+  if (u0 <= 0.0f && u1 >= 0.0f && v0 <= 0.0f && v1 >= 0.0f) return true;
+  const float a = o.b.x, b = 0.5f * o.b.y, c = o.b.z;
+  float qmin = 3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float ue = e ? u1 : u0, ve = e ? v1 : v0;
+    const float dv = fminf(fmaxf(-(b * ue) / c, v0), v1);  // edge u = ue
+    qmin = fminf(qmin, a * ue * ue + 2.0f * b * ue * dv + c * dv * dv);
+    const float du = fminf(fmaxf(-(b * ve) / a, u0), u1);  // edge v = ve
+    qmin = fminf(qmin, a * du * du + 2.0f * b * du * ve + c * ve * ve);
+  }
+  const float U = fmaxf(fabsf(u0), fabsf(u1)), V = fmaxf(fabsf(v0), fabsf(v1));
+  const float mag = a * U * U + 2.0f * fabsf(b) * U * V + c * V * V;
+  return !(qmin > 9.0f + 1e-5f * mag + 1e-3f);
+}
+
 // ---------------------------------------------------------------------------------------------------- projection
 
 __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c, SplatGeo g, SplatRec* rec,
-                                                       int4* rect, uint32_t* zkey, uint32_t* zval) {
+                                                       int4* rect, uint32_t* npairs, uint32_t* zkey, uint32_t* zval) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < in.n; m += (uint64_t)gridDim.x * blockDim.x) {
     unsigned long long pairs = 0;
     int4 box = make_int4(0, 0, 0, 0);  // tiles [x, z) x [y, w); empty when the Gaussian is not drawn
@@ -91,29 +119,35 @@ __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c
         const float v0 = fmaxf(floorf(mu_v - rv) - 1.0f, 0.0f), v1 = fminf(ceilf(mu_v + rv) + 1.0f, g.height - 1.0f);
         if (u0 <= u1 && v0 <= v1) {  // false for NaN bounds as well
           box = make_int4((int)u0 / kTile, (int)v0 / kTile, (int)u1 / kTile + 1, (int)v1 / kTile + 1);
-          pairs = (unsigned long long)(box.z - box.x) * (unsigned long long)(box.w - box.y);
           SplatRec o;
           o.a = make_float4(mu_u, mu_v, ru, rv);
           const float cb = -(suv / det);
           o.b = make_float4(svv / det, cb + cb, suu / det, in.opacity[m]);
           o.c = make_float4(in.colors[3 * m], in.colors[3 * m + 1], in.colors[3 * m + 2], z);
           rec[m] = o;
+          const int tiles = (box.z - box.x) * (box.w - box.y);
+          if (tiles <= kEllipseTest) {
+            for (int ty = box.y; ty < box.w; ++ty)
+              for (int tx = box.x; tx < box.z; ++tx) pairs += tile_reached(o, tx, ty) ? 1 : 0;
+          } else {
+            pairs = (unsigned long long)tiles;
+          }
         }
       }
     }
     rect[m] = box;
+    npairs[m] = (uint32_t)pairs;
     zkey[m] = pairs ? __float_as_uint(z) : 0xFFFFFFFFu;
     zval[m] = (uint32_t)m;
   }
 }
 
 // pair count of each Gaussian in depth order, and each Gaussian's rank in that order
-__global__ void __launch_bounds__(256) k_splat_counts(uint64_t n, const uint32_t* order, const int4* rect,
+__global__ void __launch_bounds__(256) k_splat_counts(uint64_t n, const uint32_t* order, const uint32_t* npairs,
                                                       unsigned long long* count, uint32_t* rank) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t m = order[i];
-    const int4 r = rect[m];
-    count[i] = (unsigned long long)(r.z - r.x) * (unsigned long long)(r.w - r.y);
+    count[i] = npairs[m];
     rank[m] = (uint32_t)i;
   }
 }
@@ -215,16 +249,20 @@ size_t scan_sums_count(uint64_t n) { return (size_t)((n + kScanChunk - 1) / kSca
 // Gaussians in index order (near ones, which overlap the most tiles, are spread over the grid that way), each
 // writing its pairs at its place in the depth order (rank = position in the depth-sorted order)
 __global__ void __launch_bounds__(256) k_splat_pairs(uint64_t n, const uint32_t* rank, const int4* rect,
-                                                     const unsigned long long* offset, int tiles_x, uint32_t* keys,
-                                                     uint32_t* vals) {
+                                                     const SplatRec* rec, const unsigned long long* offset,
+                                                     int tiles_x, uint32_t* keys, uint32_t* vals) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
     const int4 r = rect[m];
     if (r.z <= r.x || r.w <= r.y) continue;
-    unsigned long long o = offset[rank[m]];
+    const bool test = (r.z - r.x) * (r.w - r.y) <= kEllipseTest;  // the same choice as the count's
+    const SplatRec o = rec[m];
+    unsigned long long p = offset[rank[m]];
     for (int ty = r.y; ty < r.w; ++ty)
-      for (int tx = r.x; tx < r.z; ++tx, ++o) {
-        keys[o] = (uint32_t)(ty * tiles_x + tx);
-        vals[o] = (uint32_t)m;
+      for (int tx = r.x; tx < r.z; ++tx) {
+        if (test && !tile_reached(o, tx, ty)) continue;
+        keys[p] = (uint32_t)(ty * tiles_x + tx);
+        vals[p] = (uint32_t)m;
+        ++p;
       }
   }
 }
@@ -414,7 +452,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   const unsigned grid_n = (unsigned)std::min<uint64_t>((n + 255) / 256 + 1, (uint64_t)sms * 16);
   // phase 1: projection, depth order, pair counts
   const size_t nh1 = radix_scratch_words(n);
-  const size_t bytes1 = carve_bytes(n, sizeof(SplatRec)) + carve_bytes(n, sizeof(int4)) + 5 * carve_bytes(n, 4) +
+  const size_t bytes1 = carve_bytes(n, sizeof(SplatRec)) + carve_bytes(n, sizeof(int4)) + 6 * carve_bytes(n, 4) +
                         carve_bytes(n, 8) + carve_bytes(scan_sums_count(n), 8) + carve_bytes(nh1, 4) +
                         carve_bytes(scan_sums_count(nh1), 4) + 256;
   void* scratch1 = nullptr;
@@ -426,6 +464,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   uint32_t* zkey[2] = {carve<uint32_t>(p, n), carve<uint32_t>(p, n)};
   uint32_t* zval[2] = {carve<uint32_t>(p, n), carve<uint32_t>(p, n)};
   uint32_t* rank = carve<uint32_t>(p, n);
+  uint32_t* npairs = carve<uint32_t>(p, n);
   unsigned long long* count = carve<unsigned long long>(p, n);
   unsigned long long* sums = carve<unsigned long long>(p, scan_sums_count(n));
   uint32_t* hist1 = carve<uint32_t>(p, nh1);
@@ -433,9 +472,9 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   unsigned long long* total = carve<unsigned long long>(p, 1);
   int zc = 0;
   if (n > 0) {
-    k_splat_project<<<grid_n, 256, 0, s>>>(in, c, g, rec, rect, zkey[0], zval[0]);
+    k_splat_project<<<grid_n, 256, 0, s>>>(in, c, g, rec, rect, npairs, zkey[0], zval[0]);
     zc = radix_sort<uint32_t>(zkey, zval, n, 32, hist1, sums1, s);
-    k_splat_counts<<<grid_n, 256, 0, s>>>(n, zval[zc], rect, count, rank);
+    k_splat_counts<<<grid_n, 256, 0, s>>>(n, zval[zc], npairs, count, rank);
   }
   exclusive_scan<unsigned long long>(count, n, sums, total, s);  // count becomes each Gaussian's first pair
   unsigned long long P = 0;
@@ -470,7 +509,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
   int cur = 0;
   if (np > 0) {
-    k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, count, g.tiles_x, keys[0], vals[0]);
+    k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, rec, count, g.tiles_x, keys[0], vals[0]);
     int tile_bits = 1;
     while ((1u << tile_bits) < n_tiles) ++tile_bits;
     cur = radix_sort<uint32_t>(keys, vals, np, tile_bits, hist2, sums2, s);

@@ -61,6 +61,33 @@ def test_whole_images_match_the_oracle(size, n, frame):
     assert (tr_o < 0.99).mean() > 0.3  # most pixels receive some Gaussian
 
 
+def test_needles_and_discs_match_the_oracle():
+    """Thin, tilted Gaussians (standard deviations 100:1:1 and 1:1:0.01): elongated image ellipses, whose boxes hold
+    many tiles the ellipse misses; the culled tiles must be ones no pixel of which the ellipse reaches."""
+    rng = np.random.default_rng(21)
+    wl = small_camera(synth.rgbd(), 160, 120)
+    n = 3000
+    T = wl.pose(30)
+    pc = np.stack([rng.uniform(-1.2, 1.2, n), rng.uniform(-0.9, 0.9, n), rng.uniform(1.0, 4.0, n)], 1)
+    means = pc @ T[:3, :3].T + T[:3, 3]
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y), 2 * (x * y + w * z),
+                  1 - 2 * (x * x + z * z), 2 * (y * z - w * x), 2 * (x * z - w * y), 2 * (y * z + w * x),
+                  1 - 2 * (x * x + y * y)], 1).reshape(n, 3, 3)
+    sd = np.where(rng.uniform(size=(n, 1)) < 0.5, [0.08, 0.0008, 0.0008], [0.03, 0.03, 0.0003])
+    S = np.einsum("nij,nj,nkj->nik", R, sd * sd, R)
+    g = {"means": means.astype(np.float32),
+         "covs": np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1).astype(np.float32),
+         "opacity": rng.uniform(0.3, 0.95, n).astype(np.float32), "colors": rng.uniform(0, 1, (n, 3)).astype(np.float32)}
+    rgb_o, tr_o, drawn = oracle.splat_render(g["means"], g["covs"], g["opacity"], g["colors"], oracle.pinhole_from(wl), T)
+    rgb_g, tr_g, pairs = render_gpu(to_dev(g), mrh().pinhole_from(wl), T)
+    assert drawn > n // 2 and pairs > 0
+    assert np.abs(rgb_g - rgb_o).max() <= TOL
+    assert np.abs(tr_g - tr_o).max() <= TOL
+
+
 def test_full_size_camera_at_sampled_pixels():
     wl = synth.rgbd()
     g = synth.gaussians(wl, 1_000_000)
