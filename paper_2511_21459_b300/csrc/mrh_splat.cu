@@ -79,7 +79,8 @@ __device__ inline bool tile_reached(const SplatRec& o, int tx, int ty) {
 // ---------------------------------------------------------------------------------------------------- projection
 
 __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c, SplatGeo g, SplatRec* rec,
-                                                       int4* rect, uint32_t* npairs, uint32_t* zkey, uint32_t* zval) {
+                                                       int4* rect, unsigned long long* reach, uint32_t* npairs,
+                                                       uint32_t* zkey, uint32_t* zval) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < in.n; m += (uint64_t)gridDim.x * blockDim.x) {
     unsigned long long pairs = 0;
     int4 box = make_int4(0, 0, 0, 0);  // tiles [x, z) x [y, w); empty when the Gaussian is not drawn
@@ -126,9 +127,14 @@ __global__ void __launch_bounds__(256) k_splat_project(SplatInputs in, CamArgs c
           o.c = make_float4(in.colors[3 * m], in.colors[3 * m + 1], in.colors[3 * m + 2], z);
           rec[m] = o;
           const int tiles = (box.z - box.x) * (box.w - box.y);
-          if (tiles <= kEllipseTest) {
+          if (tiles <= kEllipseTest) {  // bit (ty - y) * width + (tx - x) of the box: tile reached
+            unsigned long long bits = 0;
+            int k = 0;
             for (int ty = box.y; ty < box.w; ++ty)
-              for (int tx = box.x; tx < box.z; ++tx) pairs += tile_reached(o, tx, ty) ? 1 : 0;
+              for (int tx = box.x; tx < box.z; ++tx, ++k)
+                if (tile_reached(o, tx, ty)) bits |= 1ull << k;
+            reach[m] = bits;
+            pairs = (unsigned long long)__popcll(bits);
           } else {
             pairs = (unsigned long long)tiles;
           }
@@ -249,21 +255,26 @@ size_t scan_sums_count(uint64_t n) { return (size_t)((n + kScanChunk - 1) / kSca
 // Gaussians in index order (near ones, which overlap the most tiles, are spread over the grid that way), each
 // writing its pairs at its place in the depth order (rank = position in the depth-sorted order)
 __global__ void __launch_bounds__(256) k_splat_pairs(uint64_t n, const uint32_t* rank, const int4* rect,
-                                                     const SplatRec* rec, const unsigned long long* offset,
+                                                     const unsigned long long* reach, const unsigned long long* offset,
                                                      int tiles_x, uint32_t* keys, uint32_t* vals) {
   for (uint64_t m = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
     const int4 r = rect[m];
-    if (r.z <= r.x || r.w <= r.y) continue;
-    const bool test = (r.z - r.x) * (r.w - r.y) <= kEllipseTest;  // the same choice as the count's
-    const SplatRec o = rec[m];
+    const int w = r.z - r.x, tiles = w * (r.w - r.y);
+    if (tiles <= 0) continue;
     unsigned long long p = offset[rank[m]];
-    for (int ty = r.y; ty < r.w; ++ty)
-      for (int tx = r.x; tx < r.z; ++tx) {
-        if (test && !tile_reached(o, tx, ty)) continue;
-        keys[p] = (uint32_t)(ty * tiles_x + tx);
+    if (tiles <= kEllipseTest) {  // the reached tiles of the box, in row-major order
+      for (unsigned long long bits = reach[m]; bits; bits &= bits - 1, ++p) {
+        const int k = __ffsll((long long)bits) - 1;
+        keys[p] = (uint32_t)((r.y + k / w) * tiles_x + r.x + k % w);
         vals[p] = (uint32_t)m;
-        ++p;
       }
+    } else {
+      for (int ty = r.y; ty < r.w; ++ty)
+        for (int tx = r.x; tx < r.z; ++tx, ++p) {
+          keys[p] = (uint32_t)(ty * tiles_x + tx);
+          vals[p] = (uint32_t)m;
+        }
+    }
   }
 }
 
@@ -453,6 +464,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   // phase 1: projection, depth order, pair counts
   const size_t nh1 = radix_scratch_words(n);
   const size_t bytes1 = carve_bytes(n, sizeof(SplatRec)) + carve_bytes(n, sizeof(int4)) + 6 * carve_bytes(n, 4) +
+                        carve_bytes(n, 8) +
                         carve_bytes(n, 8) + carve_bytes(scan_sums_count(n), 8) + carve_bytes(nh1, 4) +
                         carve_bytes(scan_sums_count(nh1), 4) + 256;
   void* scratch1 = nullptr;
@@ -465,6 +477,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   uint32_t* zval[2] = {carve<uint32_t>(p, n), carve<uint32_t>(p, n)};
   uint32_t* rank = carve<uint32_t>(p, n);
   uint32_t* npairs = carve<uint32_t>(p, n);
+  unsigned long long* reach = carve<unsigned long long>(p, n);
   unsigned long long* count = carve<unsigned long long>(p, n);
   unsigned long long* sums = carve<unsigned long long>(p, scan_sums_count(n));
   uint32_t* hist1 = carve<uint32_t>(p, nh1);
@@ -472,7 +485,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   unsigned long long* total = carve<unsigned long long>(p, 1);
   int zc = 0;
   if (n > 0) {
-    k_splat_project<<<grid_n, 256, 0, s>>>(in, c, g, rec, rect, npairs, zkey[0], zval[0]);
+    k_splat_project<<<grid_n, 256, 0, s>>>(in, c, g, rec, rect, reach, npairs, zkey[0], zval[0]);
     zc = radix_sort<uint32_t>(zkey, zval, n, 32, hist1, sums1, s);
     k_splat_counts<<<grid_n, 256, 0, s>>>(n, zval[zc], npairs, count, rank);
   }
@@ -509,7 +522,7 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
   int cur = 0;
   if (np > 0) {
-    k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, rec, count, g.tiles_x, keys[0], vals[0]);
+    k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, reach, count, g.tiles_x, keys[0], vals[0]);
     int tile_bits = 1;
     while ((1u << tile_bits) < n_tiles) ++tile_bits;
     cur = radix_sort<uint32_t>(keys, vals, np, tile_bits, hist2, sums2, s);
