@@ -919,6 +919,7 @@ mrh_status mrh_save_map(mrh_map* m, const char* path, void* stream) {
     int32_t key[3];
     uint32_t level;
     uint32_t level_id;        // resident: level << 28 | heap id
+    bool fresh;               // resident and not yet fused: its payload is the zero state
     const uint8_t* archived;  // archived: its payload in the host archive
   };
   std::vector<Rec> res, arc;
@@ -926,11 +927,13 @@ mrh_status mrh_save_map(mrh_map* m, const char* path, void* stream) {
     std::vector<Slot> slots((size_t)d.slot_mask + 1);
     MRH_CUDA(cudaMemcpy(slots.data(), d.slots, slots.size() * sizeof(Slot), cudaMemcpyDeviceToHost));
     for (const Slot& sl : slots) {
-      if (sl.key == kEmptyKey || sl.key == kTombKey || sl.val == kValPending || (sl.val & kValNew)) continue;
+      // the blocks mrh_count_blocks / mrh_extract_blocks report; one still marked new is saved in its zero state
+      if (sl.key == kEmptyKey || sl.key == kTombKey || sl.val == kValPending) continue;
       Rec r{};
       unpack_key(sl.key, &r.key[0], &r.key[1], &r.key[2]);
       r.level = (sl.val >> 28) & 3u;
       r.level_id = sl.val & (kPtrMask | (3u << 28));
+      r.fresh = (sl.val & kValNew) != 0;
       res.push_back(r);
     }
   }
@@ -963,6 +966,8 @@ mrh_status mrh_save_map(mrh_map* m, const char* path, void* stream) {
   }
   std::vector<uint8_t> blob(blob_bytes);
   MRH_CUDA(io_blocks_to_blob(d, ids, offs, blob.data(), blob_bytes, s, m->sms));
+  for (size_t i = 0; i < res.size(); ++i)
+    if (res[i].fresh) std::memset(blob.data() + offs[i], 0, d.block_bytes[res[i].level]);
   FILE* f = std::fopen(path, "wb");
   if (!f) return MRH_ERR_INVALID_ARG;
   const uint32_t ver = io_version(), psz = (uint32_t)sizeof(mrh_map_params);

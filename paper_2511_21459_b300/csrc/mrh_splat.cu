@@ -519,7 +519,12 @@ cudaError_t splat_render(const SplatInputs& in, const CamArgs& c, float* rgb, fl
   uint32_t* hist2 = carve<uint32_t>(p, nh2);
   uint32_t* sums2 = carve<uint32_t>(p, scan_sums_count(nh2));
   uint2* ranges = carve<uint2>(p, n_tiles);
-  cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
+  e = cudaMemsetAsync(ranges, 0, n_tiles * sizeof(uint2), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch2, s);
+    cudaFreeAsync(scratch1, s);
+    return e;
+  }
   int cur = 0;
   if (np > 0) {
     k_splat_pairs<<<grid_n, 256, 0, s>>>(n, rank, rect, reach, count, g.tiles_x, keys[0], vals[0]);
