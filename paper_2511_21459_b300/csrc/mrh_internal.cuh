@@ -88,6 +88,7 @@ struct DevState {
   uint32_t ar_present;         // streaming: blocks currently in the archive
   uint32_t evict_go;           // streaming: this frame's capacity check (taken once, before any eviction)
   unsigned long long mesh_tris;  // triangles counted by the last mesh extraction
+  uint32_t mesh_next;            // mesh extraction: next chunk of 32 hash slots to hand out
 };
 
 // Everything a kernel needs, passed by value.

@@ -135,10 +135,22 @@ __device__ inline float voxel_D(const uint8_t* blk, int i) {
   return reinterpret_cast<const float*>(blk)[i];
 }
 
+// The values of the 3 x 3 x 3 blocks around the block a warp meshes (looked up once, one lane each, into shared
+// memory); a lookup outside the neighbourhood goes to the hash table.
+struct Neighbourhood {
+  const uint32_t* val;  // 27 entries, index (dx + 1) + 3 (dy + 1) + 9 (dz + 1)
+  int K[3];
+  __device__ inline uint32_t get(const MapDev& m, int x, int y, int z) const {
+    const int dx = x - K[0] + 1, dy = y - K[1] + 1, dz = z - K[2] + 1;
+    if ((unsigned)dx < 3u && (unsigned)dy < 3u && (unsigned)dz < 3u) return val[dx + 3 * dy + 9 * dz];
+    return block_val(m, x, y, z);
+  }
+};
+
 // trilinear field at the unit point P on the grid of the block containing it (see the file comment)
 template <bool FP16, bool COLOR>
-__device__ __noinline__ bool corner_value(const MapDev& m, const int P[3], float* out) {
-  const uint32_t v = block_val(m, P[0] >> 4, P[1] >> 4, P[2] >> 4);
+__device__ __noinline__ bool corner_value(const MapDev& m, const Neighbourhood& nb, const int P[3], float* out) {
+  const uint32_t v = nb.get(m, P[0] >> 4, P[1] >> 4, P[2] >> 4);
   if (v == kValPending) return false;
   const int lp = (int)((v >> 28) & 3u);
   const int s = 1 << lp, s2 = 2 * s;
@@ -166,13 +178,13 @@ __device__ __noinline__ bool corner_value(const MapDev& m, const int P[3], float
       cx = kx;
       cy = ky;
       cz = kz;
-      cv = block_val(m, kx, ky, kz);
+      cv = nb.get(m, kx, ky, kz);
     }
     if (cv == kValPending) return false;
-    const int lb = (int)((cv >> 28) & 3u), nb = kFineDim >> lb, sh = lb + 1;
-    const int idx = ((C[0] - kx * 16) >> sh) + nb * (((C[1] - ky * 16) >> sh) + nb * ((C[2] - kz * 16) >> sh));
+    const int lb = (int)((cv >> 28) & 3u), nbs = kFineDim >> lb, sh = lb + 1;
+    const int idx = ((C[0] - kx * 16) >> sh) + nbs * (((C[1] - ky * 16) >> sh) + nbs * ((C[2] - kz * 16) >> sh));
     const uint8_t* blk = payload(m, cv);
-    if (!(reinterpret_cast<const float*>(blk + off_W(nb * nb * nb, FP16, COLOR))[idx] > 0.0f)) return false;
+    if (!(reinterpret_cast<const float*>(blk + off_W(nbs * nbs * nbs, FP16, COLOR))[idx] > 0.0f)) return false;
     acc = acc + w * voxel_D<FP16>(blk, idx);
   }
   *out = acc;
@@ -183,6 +195,7 @@ struct MeshOut {
   float* tris;
   unsigned long long cap;
   unsigned long long* count;
+  uint32_t* next;  // chunks of 32 hash slots are handed out from this counter (zero at launch)
 };
 
 // One pass of 32 cells (warp-collective): reserve the pass's triangles with one atomic, then each lane writes its
@@ -219,11 +232,16 @@ __device__ inline void emit_cell(const MeshOut& o, int lane, bool ok, int cs, co
 
 template <bool FP16, bool COLOR>
 __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
+  __shared__ uint32_t s_nbr[8][27];
   const int lane = threadIdx.x & 31;
   const uint32_t nslots = m.slot_mask + 1;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const float unit = m.E / 16.0f;
-  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; base < nslots; base += nw * 32u) {
+  for (;;) {
+    // blocks cost very different amounts (surface crossings, shell lookups): warps take chunks as they finish
+    uint32_t chunk = 0;
+    if (lane == 0) chunk = atomicAdd(o.next, 1u);
+    const uint32_t base = __shfl_sync(~0u, chunk, 0) * 32u;
+    if (base >= nslots) break;
     const uint32_t sl = base + lane;
     const unsigned long long key_l = sl < nslots ? m.slots[sl].key : kEmptyKey;
     const uint32_t val_l = sl < nslots ? m.slots[sl].val : kValPending;
@@ -238,18 +256,24 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
       const int l = (int)((val >> 28) & 3u), nl = kFineDim >> l, nv = nl * nl * nl, s = 1 << l;
       const uint8_t* blk = payload(m, val);
       const float* Wb = reinterpret_cast<const float*>(blk + off_W(nv, FP16, COLOR));
+      uint32_t* s_nb = s_nbr[threadIdx.x >> 5];
+      __syncwarp();  // the previous block's shell is done with the table
+      if (lane < 27) s_nb[lane] = lane == 13 ? val : block_val(m, K[0] + lane % 3 - 1, K[1] + (lane / 3) % 3 - 1,
+                                                               K[2] + lane / 9 - 1);
+      __syncwarp();
+      const Neighbourhood nb{s_nb, {K[0], K[1], K[2]}};
       // extent of the cells of the last voxel along each axis: to the first centre of the neighbouring block
-      int h_last = 0;
-      if (lane < 3) {
-        const uint32_t nvl = block_val(m, K[0] + (lane == 0), K[1] + (lane == 1), K[2] + (lane == 2));
-        h_last = nvl == kValPending ? 0 : s + (1 << ((nvl >> 28) & 3u));
+      int hl[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const uint32_t nvl = s_nb[13 + (a == 0 ? 1 : a == 1 ? 3 : 9)];
+        hl[a] = nvl == kValPending ? 0 : s + (1 << ((nvl >> 28) & 3u));
       }
-      const int hl[3] = {__shfl_sync(~0u, h_last, 0), __shfl_sync(~0u, h_last, 1), __shfl_sync(~0u, h_last, 2)};
       // interior cells: (nl - 1)^3 of them, corners read from the payload
       const int ni = nl - 1, n_in = ni * ni * ni;
       for (int b0 = 0; b0 < n_in; b0 += 32) {
         const int cell = b0 + lane;
-        bool ok = cell < n_in;
+        const bool in = cell < n_in;
         const int i[3] = {cell % ni, (cell / ni) % ni, cell / (ni * ni)};
         int c[3], h[3];
 #pragma unroll
@@ -257,13 +281,20 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
           c[a] = K[a] * 16 + (2 * i[a] + 1) * s;
           h[a] = 2 * s;
         }
-        float F[8];
-        int cs = 0;
+        // the 16 loads of the cell's corners are independent (all in the block for an interior cell) and issued
+        // together; the observed test and the case index follow
+        float F[8], Wq[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int idx = (i[0] + (q & 1)) + nl * ((i[1] + ((q >> 1) & 1)) + nl * (i[2] + (q >> 2)));
-          F[q] = ok ? voxel_D<FP16>(blk, idx) : 0.0f;
-          ok = ok && Wb[idx] > 0.0f;
+          F[q] = in ? voxel_D<FP16>(blk, idx) : 0.0f;
+          Wq[q] = in ? Wb[idx] : 0.0f;
+        }
+        bool ok = in;
+        int cs = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          ok = ok && Wq[q] > 0.0f;
           if (F[q] < 0.0f) cs |= 1 << q;
         }
         emit_cell(o, lane, ok, cs, F, c, h, unit);
@@ -301,7 +332,7 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev m, MeshOut o) {
 #pragma unroll 1
         for (int q = 0; q < 8 && ok; ++q) {
           const int P[3] = {c[0] + (q & 1) * h[0], c[1] + ((q >> 1) & 1) * h[1], c[2] + (q >> 2) * h[2]};
-          ok = corner_value<FP16, COLOR>(m, P, &F[q]);
+          ok = corner_value<FP16, COLOR>(m, nb, P, &F[q]);
           if (ok && F[q] < 0.0f) cs |= 1 << q;
         }
         emit_cell(o, lane, ok, cs, F, c, h, unit);
@@ -533,8 +564,9 @@ cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clus
 }
 
 void launch_mesh(const MapDev& m, float* tris, uint64_t cap, unsigned long long* count, cudaStream_t s, int sms) {
-  const MeshOut o{tris, (unsigned long long)cap, count};
-  const int grid = sms * 8;
+  const MeshOut o{tris, (unsigned long long)cap, count, &m.st->mesh_next};
+  cudaMemsetAsync(o.next, 0, sizeof(uint32_t), s);
+  const int grid = sms * 4;  // resident at once; the warps take slot chunks until none are left
   if (m.fp16) {
     if (m.color) k_mesh<true, true><<<grid, 256, 0, s>>>(m, o);
     else k_mesh<true, false><<<grid, 256, 0, s>>>(m, o);
