@@ -466,7 +466,6 @@ struct WeldScratch {
   uint32_t table;
 };
 cudaError_t weld_clusters(const WeldScratch& w, const float* tris, uint32_t nv, float delta, cudaStream_t s, int sms);
-void weld_pad(const WeldScratch& w, uint32_t n, uint32_t n_pow, cudaStream_t s, int sms);
 cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clusters, float* verts, uint64_t cap_verts,
                         int32_t* faces, uint64_t cap_faces, uint64_t n_tris, size_t nblk, cudaStream_t s, int sms);
 void sort_keys_vals(unsigned long long* keys, uint32_t* vals, uint32_t n_pow, cudaStream_t s, int sms);

@@ -19,6 +19,7 @@
 
 #include "mrh_alloc.cuh"
 #include "mrh_internal.cuh"
+#include "mrh_sort.cuh"
 
 using namespace mrh;
 
@@ -833,11 +834,20 @@ mrh_status mrh_weld_mesh(mrh_map* m, const float* tris, uint64_t n_tris, float d
   grab((void**)&w.vidx, 4ull * table);
   grab((void**)&w.ckeys, 8ull * table);
   grab((void**)&w.cslots, 4ull * table);
+  // the cluster keys' radix sort: second key / value buffers, digit counts and their scan sums
+  unsigned long long* ckeys2 = nullptr;
+  uint32_t *cslots2 = nullptr, *hist = nullptr, *hsums = nullptr;
+  const size_t nh = radix_scratch_words(table);
+  grab((void**)&ckeys2, 8ull * table);
+  grab((void**)&cslots2, 4ull * table);
+  grab((void**)&hist, 4ull * nh);
+  grab((void**)&hsums, 4ull * scan_sums_count(nh));
+  unsigned long long* const ckeys_alloc = w.ckeys;
+  uint32_t* const cslots_alloc = w.cslots;
   grab((void**)&w.blk, 4ull * (nblk + 1));
   grab((void**)&w.counters, 16);
   mrh_status st = MRH_OK;
   uint32_t hc[2] = {0, 0};
-  uint32_t n_pow = 1;
   if (e == cudaSuccess) {
     w.table = table;
     KernelScope ks(m, MRH_K_MESH, s, 1);
@@ -845,16 +855,19 @@ mrh_status mrh_weld_mesh(mrh_map* m, const float* tris, uint64_t n_tris, float d
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc, w.counters, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && hc[1] == 0) {
-      while (n_pow < hc[0]) n_pow <<= 1;
-      weld_pad(w, hc[0], n_pow, s, m->sms);
-      sort_keys_vals(w.ckeys, w.cslots, n_pow, s, m->sms);
+      // the cluster keys are distinct 63-bit values: sort them (with their slots) in key order
+      unsigned long long* kk[2] = {w.ckeys, ckeys2};
+      uint32_t* vv[2] = {w.cslots, cslots2};
+      const int cur = radix_sort<unsigned long long>(kk, vv, hc[0], 63, hist, hsums, s);
+      w.ckeys = kk[cur];
+      w.cslots = vv[cur];
       e = weld_output(w, tris, hc[0], verts, cap_verts, faces, cap_faces, n_tris, nblk, s, m->sms);
     }
   }
   uint32_t nf = 0;
   if (e == cudaSuccess && hc[1] == 0) e = cudaMemcpyAsync(&nf, w.counters + 2, 4, cudaMemcpyDeviceToHost, s);
-  for (void* p : {(void*)w.keys, (void*)w.mn, (void*)w.vslot, (void*)w.vidx, (void*)w.ckeys, (void*)w.cslots,
-                  (void*)w.blk, (void*)w.counters})
+  for (void* p : {(void*)w.keys, (void*)w.mn, (void*)w.vslot, (void*)w.vidx, (void*)ckeys_alloc, (void*)cslots_alloc,
+                  (void*)w.blk, (void*)w.counters, (void*)ckeys2, (void*)cslots2, (void*)hist, (void*)hsums})
     if (p) cudaFreeAsync(p, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "mrh_weld_mesh");

@@ -429,13 +429,6 @@ __global__ void k_weld_compact(WeldScratch w) {
   }
 }
 
-__global__ void k_weld_pad(WeldScratch w, uint32_t n, uint32_t n_pow) {
-  for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < n_pow; i += gridDim.x * blockDim.x) {
-    w.ckeys[i] = kEmptyKey;
-    w.cslots[i] = 0;
-  }
-}
-
 // vertex i = the i-th cluster in key order
 __global__ void k_weld_number(WeldScratch w, uint32_t n, float* verts, uint64_t cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -547,10 +540,6 @@ cudaError_t weld_clusters(const WeldScratch& w, const float* tris, uint32_t nv, 
   k_weld_min<2><<<sms * 8, 256, 0, s>>>(w, tris, nv);
   k_weld_compact<<<sms * 8, 256, 0, s>>>(w);
   return cudaGetLastError();
-}
-
-void weld_pad(const WeldScratch& w, uint32_t n, uint32_t n_pow, cudaStream_t s, int sms) {
-  if (n_pow > n) k_weld_pad<<<sms * 4, 256, 0, s>>>(w, n, n_pow);
 }
 
 cudaError_t weld_output(const WeldScratch& w, const float* tris, uint32_t n_clusters, float* verts, uint64_t cap_verts,
