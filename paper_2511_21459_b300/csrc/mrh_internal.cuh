@@ -383,51 +383,6 @@ __device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* x
          key_ok(floor_div(B[0], kBlockUnit), floor_div(B[1], kBlockUnit), floor_div(B[2], kBlockUnit));
 }
 
-// ---------------------------------------------------------------------------------------------------- async copies
-// Bulk (non-tensor) asynchronous copies between global and shared memory, completed through an mbarrier (loads) or a
-// per-thread bulk group (stores). Addresses must be 16-byte aligned and sizes multiples of 16.
-
-__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ inline void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-// arrive once and add `bytes` to the transaction count of the current phase
-__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false when the phase did not complete within the iteration limit
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter = 1u << 22) {
-  for (uint32_t i = 0; i < max_iter; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ inline void bulk_load(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-__device__ inline void bulk_store(void* dst_gmem, const void* src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem), "r"(smem_addr(src_smem)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ inline void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// order this thread's generic-proxy shared-memory writes before later async-proxy accesses
-__device__ inline void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // ---------------------------------------------------------------------------------------------------- host side
 
 // the device-side view of a map (mrh_map.cu), for the batched path
