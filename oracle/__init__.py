@@ -251,10 +251,13 @@ class OracleMap:
         """All blocks sorted by key: keys (n,3) int32, levels (n,) uint8, offsets (n+1,) int64, D/W/S2 (V,) float64,
         C (V,3) float64. Voxel i of a block of side n is at x + n (y + n z)."""
         nb, nv = self.count()
+        color = bool(self.params.has_color)
         out = dict(keys=np.zeros((nb, 3), np.int32), levels=np.zeros(nb, np.uint8), offsets=np.zeros(nb + 1, np.int64),
-                   D=np.zeros(nv), W=np.zeros(nv), S2=np.zeros(nv), C=np.zeros((nv, 3)))
+                   D=np.empty(nv), W=np.empty(nv), S2=np.empty(nv), C=np.empty((nv, 3)) if color else None)
         self._lib.orc_extract(self._h, _p(out["keys"]), _p(out["levels"]), _p(out["offsets"]), _p(out["D"]),
                               _p(out["W"]), _p(out["S2"]), _p(out["C"]))
+        if not color:  # a map without colour: zeros, without the memory
+            out["C"] = np.broadcast_to(np.zeros(1), (nv, 3))
         return out
 
     def resample_block(self, level: int, direction: int, D, W, S2, C=None) -> dict:

@@ -24,6 +24,20 @@ def _centres(keys, E):
     return (keys.astype(np.float64) + 0.5) * E
 
 
+def _voxels(ex, blocks):
+    """Positions, in the extract's voxel arrays, of the voxels of the given blocks (in that block order)."""
+    starts = ex["offsets"][blocks]
+    lens = ex["offsets"][blocks + 1] - starts
+    first = np.cumsum(lens) - lens
+    return np.repeat(starts - first, lens) + np.arange(int(lens.sum()))
+
+
+def _match(a, b):
+    """Indices into b of a's blocks (every key of a must be in b)."""
+    kb = {tuple(k): i for i, k in enumerate(b["keys"].tolist())}
+    return np.array([kb[tuple(k)] for k in a["keys"].tolist()], dtype=np.int64)
+
+
 def test_nothing_moves_below_the_capacity_fraction():
     wl, sc = _rgbd()
     m = _map(wl)
@@ -63,13 +77,11 @@ def test_camera_streaming_moves_blocks_without_changing_any():
             assert not far_out.any()
     assert ev > 1000 and rs > 100
     a, b = m.extract(), ctl.extract()
-    kb = {tuple(k): i for i, k in enumerate(b["keys"].tolist())}
-    idx = np.array([kb[tuple(k)] for k in a["keys"].tolist()])
+    idx = _match(a, b)
     assert np.array_equal(a["levels"], b["levels"][idx])
+    pa, pb = _voxels(a, np.arange(len(idx))), _voxels(b, idx)
     for f in ("D", "W", "S2"):
-        va = np.concatenate([a[f][a["offsets"][i]:a["offsets"][i + 1]] for i in range(len(idx))])
-        vb = np.concatenate([b[f][b["offsets"][j]:b["offsets"][j + 1]] for j in idx])
-        assert np.array_equal(va, vb), f
+        assert np.array_equal(a[f][pa], b[f][pb]), f
     assert len(a["keys"]) + m.archived() == len(b["keys"])
 
 
@@ -93,8 +105,5 @@ def test_lidar_streaming_keeps_the_radius_and_the_blocks():
     assert ev > 0
     a, b = m.extract(), ctl.extract()
     assert len(a["keys"]) + m.archived() == len(b["keys"])
-    kb = {tuple(k): i for i, k in enumerate(b["keys"].tolist())}
-    idx = np.array([kb[tuple(k)] for k in a["keys"].tolist()])
-    va = np.concatenate([a["D"][a["offsets"][i]:a["offsets"][i + 1]] for i in range(len(idx))])
-    vb = np.concatenate([b["D"][b["offsets"][j]:b["offsets"][j + 1]] for j in idx])
-    assert np.array_equal(va, vb)
+    idx = _match(a, b)
+    assert np.array_equal(a["D"][_voxels(a, np.arange(len(idx)))], b["D"][_voxels(b, idx)])
