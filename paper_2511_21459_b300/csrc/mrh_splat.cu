@@ -18,7 +18,7 @@
 //                    positive floats order as their bits; all ones when not drawn)
 //   depth sort       stable least-significant-digit radix sort (8-bit digits) of the Gaussians by depth key, so
 //                    equal depths stay in index order
-//   scan             exclusive prefix of the pair counts in depth order
+//   k_splat_counts   the pair counts in depth order and each Gaussian's rank in it; then their exclusive prefix
 //   k_splat_pairs    every (tile, Gaussian) pair, key = tile, value = Gaussian index, laid out in depth order
 //   tile sort        the same stable radix sort over the tile bits only: a tile's pairs end up contiguous and keep
 //                    the depth order
