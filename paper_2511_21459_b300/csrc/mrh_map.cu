@@ -1085,34 +1085,45 @@ mrh_status mrh_extract_blocks(mrh_map* m, int32_t* keys, uint8_t* levels, uint64
   if (nb > cap_blocks || nv > cap_voxels) return MRH_ERR_CAPACITY;
   DeviceGuard guard(m->device);
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t npow = 1;
-  while (npow < nb) npow <<= 1;
-  unsigned long long *skeys = nullptr, *soff = nullptr;
-  uint32_t *sslots = nullptr, *scount = nullptr;
-  MRH_CUDA(cudaMallocAsync(&skeys, sizeof(unsigned long long) * npow + 16, s));
-  MRH_CUDA(cudaMallocAsync(&sslots, sizeof(uint32_t) * npow + 16, s));
-  MRH_CUDA(cudaMallocAsync(&soff, sizeof(unsigned long long) * (nb + 1), s));
-  MRH_CUDA(cudaMallocAsync(&scount, sizeof(uint32_t), s));
-  MRH_CUDA(cudaMemsetAsync(scount, 0, sizeof(uint32_t), s));
-  k_compact<<<m->sms * 8, 256, 0, s>>>(m->d, skeys, sslots, scount, npow);
-  uint32_t hcount = 0;
-  MRH_CUDA(cudaMemcpyAsync(&hcount, scount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  MRH_CUDA(cudaStreamSynchronize(s));
-  uint32_t n = std::min<uint32_t>(hcount, (uint32_t)nb);
-  if (npow > n) k_pad_keys<<<m->sms * 4, 256, 0, s>>>(skeys, n, npow);
-  for (uint32_t k = 2; k <= npow; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) k_bitonic_step<<<m->sms * 8, 256, 0, s>>>(skeys, sslots, npow, k, j);
-  if (n > 0) {
-    k_voxel_offsets<<<1, 1024, 0, s>>>(m->d, sslots, n, soff);
-    k_extract<<<m->sms * 8, 128, 0, s>>>(m->d, sslots, n, soff, keys, levels, (unsigned long long*)voxel_offset,
-                                          tsdf, weight, s2, color);
-  } else {
-    MRH_CUDA(cudaMemsetAsync(voxel_offset, 0, sizeof(uint64_t), s));
+  // compacted keys and slots (two buffers each for the radix sort), digit counts and their scan sums
+  const size_t cap = nb + 1, nh = radix_scratch_words((uint32_t)cap);
+  unsigned long long *skeys[2] = {nullptr, nullptr}, *soff = nullptr;
+  uint32_t *sslots[2] = {nullptr, nullptr}, *scount = nullptr, *hist = nullptr, *hsums = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto grab = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMallocAsync(p, bytes, s);
+  };
+  for (int b = 0; b < 2; ++b) {
+    grab((void**)&skeys[b], sizeof(unsigned long long) * cap);
+    grab((void**)&sslots[b], sizeof(uint32_t) * cap);
   }
-  cudaFreeAsync(skeys, s);
-  cudaFreeAsync(sslots, s);
-  cudaFreeAsync(soff, s);
-  cudaFreeAsync(scount, s);
+  grab((void**)&soff, sizeof(unsigned long long) * (nb + 1));
+  grab((void**)&scount, sizeof(uint32_t));
+  grab((void**)&hist, sizeof(uint32_t) * nh);
+  grab((void**)&hsums, sizeof(uint32_t) * scan_sums_count(nh));
+  uint32_t hcount = 0, n = 0;
+  if (e == cudaSuccess) e = cudaMemsetAsync(scount, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    k_compact<<<m->sms * 8, 256, 0, s>>>(m->d, skeys[0], sslots[0], scount, (uint32_t)cap);
+    e = cudaMemcpyAsync(&hcount, scount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    n = std::min<uint32_t>(hcount, (uint32_t)nb);
+    // the packed keys order as (x, then y, then z) and are distinct: a radix sort of all 64 bits
+    const int cur = radix_sort<unsigned long long>(skeys, sslots, n, 64, hist, hsums, s);
+    if (n > 0) {
+      k_voxel_offsets<<<1, 1024, 0, s>>>(m->d, sslots[cur], n, soff);
+      k_extract<<<m->sms * 8, 128, 0, s>>>(m->d, sslots[cur], n, soff, keys, levels,
+                                            (unsigned long long*)voxel_offset, tsdf, weight, s2, color);
+    } else {
+      e = cudaMemsetAsync(voxel_offset, 0, sizeof(uint64_t), s);
+    }
+  }
+  for (void* p : {(void*)skeys[0], (void*)skeys[1], (void*)sslots[0], (void*)sslots[1], (void*)soff, (void*)scount,
+                  (void*)hist, (void*)hsums})
+    if (p) cudaFreeAsync(p, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mrh_extract_blocks");
   MRH_CUDA(cudaGetLastError());
   MRH_CUDA(cudaStreamSynchronize(s));
   if (n != nb) return MRH_ERR_CUDA;
