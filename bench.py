@@ -377,9 +377,9 @@ def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False)
     return out
 
 
-def chamfer_vs_truth(m, wl, views):
-    """Chamfer-L1 (Sec. 4.1.2) of the map's raycast depth at the given frames against noise-free renders of the same
-    views, both back-projected (every 2nd pixel)."""
+def chamfer_vs_truth(m, wl, views, poses=None):
+    """Chamfer-L1 (Sec. 4.1.2) of the map's raycast depth at the given frames (or camera-to-world `poses`) against
+    noise-free renders of the same views, both back-projected (every 2nd pixel)."""
     import dataclasses
     import paper_2511_21459_b300 as mrh
     from paper_2511_21459_b300 import metrics
@@ -387,11 +387,11 @@ def chamfer_vs_truth(m, wl, views):
     clean = dataclasses.replace(wl, noise_coef=0.0, dropout=0.0)
     scene = wl.scene()
     rec, gt = [], []
-    for k in views:
-        T = wl.pose(k)
+    for i, k in enumerate(views):
+        T = wl.pose(k) if poses is None else poses[i]
         d = m.raycast(K, T).cpu().numpy()
         rec.append(metrics.backproject(d, wl.fx, wl.fy, wl.cx, wl.cy, T, stride=2))
-        g, _, _ = synth.render_depth(clean, k, scene=scene)
+        g, _, _ = synth.render_depth(clean, k, scene=scene, pose=T)
         g = np.where((g >= wl.min_depth) & (g <= wl.max_depth), g, 0.0)
         gt.append(metrics.backproject(g, wl.fx, wl.fy, wl.cx, wl.cy, T, stride=2))
     return metrics.chamfer(np.concatenate(rec), np.concatenate(gt))
@@ -672,6 +672,48 @@ def run_ablation(wl, n_frames=120, sigmas=(0.001, 0.003, 0.006, 0.01, 0.02, 0.04
                     "acc_mm": round(1e3 * ch["acc"], 3), "comp_mm": round(1e3 * ch["comp"], 3),
                     "chamfer_mm": round(1e3 * ch["chamfer"], 3)})
         del soup, verts, faces
+        m.close()
+    return out
+
+
+def run_ablation_lidar(n_scans=40, sigmas=(0.01, 0.02, 0.04, 0.08), singles=(0.05, 0.1, 0.2),
+                       view_x=(5.0, 15.0, 25.0, 35.0)):
+    """The same sweep on the LiDAR street (FP16 storage): n_scans scans, thresholds (sigma^2, 4 sigma^2), then
+    single-resolution maps of each voxel size in `singles` (same truncation). Chamfer-L1 of the map's raycast depth
+    from 640 x 480 pinhole views at 1.8 m height looking down the street from x = `view_x`, against noise-free renders
+    of the street from the same views."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    lw = synth.lidar()
+    scene = lw.scene()
+    scans = [synth.render_lidar(lw, k, scene=scene) for k in range(n_scans)]
+    dev = [(torch.from_numpy(x).cuda(), T) for x, T in scans]
+    poses = [synth.look_at((x, 0.0, 1.8), (x + 10.0, 0.0, 1.5)) for x in view_x]
+    out = []
+    rows = [(f"sigma {sig}", dataclasses.replace(lw, var_threshold=(sig * sig, 4 * sig * sig)), sig) for sig in sigmas]
+    rows += [(f"single {v * 100:g} cm", dataclasses.replace(lw, base_voxel=v, n_levels=1), None) for v in singles]
+    for label, w2, sig in rows:
+        m = mrh.Map(mrh.params_from(w2), device=torch.cuda.current_device())
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for x, T in dev:
+            m.integrate_points(T, x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = m.stats()
+        vb = voxel_bytes(w2)
+        live = st["live_blocks"]
+        cam = dataclasses.replace(w2, sensor="camera", width=640, height=480, fx=400.0, fy=400.0, cx=319.5, cy=239.5,
+                                  min_depth=0.5, max_depth=60.0, extra={"scene": "lidar"})
+        ch = chamfer_vs_truth(m, cam, list(range(len(poses))), poses=poses)
+        out.append({"map": label, "levels_cm": [round(100 * w2.voxel0 * (1 << l), 3) for l in range(w2.n_levels)],
+                    "sigma": sig, "theta": [sig * sig, 4 * sig * sig] if sig else None,
+                    "ms_per_scan": round(a.elapsed_time(b) / n_scans, 4), "status": st["status_code"],
+                    "live_blocks": live, "payload_MB": [round(n * (8 >> l) ** 3 * vb / 1e6, 1) for l, n in enumerate(live)],
+                    "acc_mm": round(1e3 * ch["acc"], 3), "comp_mm": round(1e3 * ch["comp"], 3),
+                    "chamfer_mm": round(1e3 * ch["chamfer"], 3)})
         m.close()
     return out
 
@@ -984,6 +1026,7 @@ def main():
         from paper_2511_21459_b300 import build as _b
         _b.build()
         print(json.dumps({"ablation": run_ablation(wl), "workload": "rgbd-640x480 sequence, first 120 frames",
+                          "lidar": run_ablation_lidar(), "lidar_workload": "lidar-128x2048 street, first 40 scans",
                           "data": "synthetic"}))
         return 0
     rank, world, local = dist_setup(args.gpus)
