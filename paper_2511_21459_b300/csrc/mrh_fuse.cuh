@@ -330,25 +330,51 @@ struct LidarObs {
   }
 
   // the observations of one voxel with three or more, in point order (about 10 % of observed voxels in a street
-  // scan, 93 % of them with at most 8)
-  __device__ static void apply_long(uint2* rec, uint32_t cnt, float& D, float& W, float& S2) {
+  // scan, 93 % of them with at most 8; coarse voxels can hold hundreds)
+  __device__ static void apply_long(const uint2* rec, uint32_t cnt, float& D, float& W, float& S2) {
     if (cnt <= 8) {
       apply_sorted<8>(rec, cnt, D, W, S2);
     } else if (cnt <= (uint32_t)kLocalSort) {
       apply_sorted<kLocalSort>(rec, cnt, D, W, S2);
     } else {
-      for (uint32_t i = 1; i < cnt; ++i) {
-        const uint2 r = rec[i];
-        uint32_t j = i;
-        while (j > 0 && rec[j - 1].x > r.x) {
-          rec[j] = rec[j - 1];
-          --j;
+      // the observations in point order without moving them: each pass over the voxel's records keeps the 8
+      // smallest keys above the last one applied in a sorted register array, then applies them (a voxel's keys are
+      // distinct: one observation per ray); reads only, so the records stay in L1
+      uint32_t last = 0;
+      bool started = false;
+      for (uint32_t done = 0; done < cnt;) {
+        uint32_t a[8], d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          a[j] = 0xFFFFFFFFu;
+          d[j] = 0u;
         }
-        rec[j] = r;
-      }
-      for (uint32_t i = 0; i < cnt; ++i) {
-        float Wn;
-        welford<FP16>(__uint_as_float(rec[i].y), D, W, S2, Wn);
+        for (uint32_t i = 0; i < cnt; ++i) {
+          const uint2 r = rec[i];
+          uint32_t kk = r.x, dd = r.y;
+          if (started && kk <= last) continue;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (kk < a[j]) {
+              const uint32_t tk = a[j], td = d[j];
+              a[j] = kk;
+              d[j] = dd;
+              kk = tk;
+              dd = td;
+            }
+          }
+        }
+        const uint32_t take = cnt - done < 8u ? cnt - done : 8u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if ((uint32_t)j < take) {
+            float Wn;
+            welford<FP16>(__uint_as_float(d[j]), D, W, S2, Wn);
+            last = a[j];
+          }
+        }
+        started = true;
+        done += take;
       }
     }
   }
