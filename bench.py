@@ -185,6 +185,20 @@ def profile_case(kind: str) -> int:
     return 0 if st["status_code"] == 0 else 1
 
 
+def host_cpu() -> dict:
+    """CPU model and logical core count of the host the oracle runs on."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -328,14 +342,30 @@ def voxel_bytes(wl):
 
 # ----------------------------------------------------------------------------------------------------- GPU arm
 
-def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False):
+def timed_frames(n_frames, warmup, steps):
+    """Indices of the timed frames: `steps` frames spread evenly over the sequence after the warm-up frames (every
+    frame is integrated in order; the others untimed), so the timing covers the young and the grown map alike."""
+    last = n_frames - 1
+    if steps <= 1:
+        return [min(warmup, last)]
+    idx = sorted({warmup + (i * (last - warmup)) // (steps - 1) for i in range(steps)})
+    if len(idx) < steps:  # more steps than frames after the warm-up: consecutive frames
+        idx = list(range(warmup, min(warmup + steps, n_frames)))
+    return idx
+
+
+def run_camera_gpu(wl, frames, warmup, timed, flush, predictor=None, keep=False):
+    """Integrate frames[0 .. max(timed)] in order; the first `warmup` with a raycast each, untimed; every frame in
+    `timed` as one timed step (integrate + raycast of depth, normals and colour between CUDA events on the launching
+    stream, L2 flushed before each); the others integrated untimed."""
     import torch
     import paper_2511_21459_b300 as mrh
     K = mrh.pinhole_from(wl)
     m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
     if predictor is not None:
         m.set_predictor(predictor)
-    dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames]
+    last = max(timed)
+    dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), T) for d, c, T in frames[:last + 1]]
     out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
     nrm = torch.empty((wl.height, wl.width, 3), dtype=torch.float32, device="cuda")
     col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
@@ -345,31 +375,43 @@ def run_camera_gpu(wl, frames, warmup, steps, flush, predictor=None, keep=False)
         m.integrate_depth(K, T, d, c)
         m.raycast(K, T, out, normals=nrm, rgb=col)
     torch.cuda.synchronize()
-    m.set_profiling(True)
-    m.profile(reset=True)
-    times, rays, fbytes, obs = [], 0, 0, 0
+    tset = set(timed)
+    rays, fbytes, obs = 0, 0, 0
     touched = [0, 0, 0]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for k in range(steps):
+    ev = []
+    prof = {}
+    for k in range(warmup, last + 1):
+        d, c, T = dev[k]
+        if k not in tset:
+            m.integrate_depth(K, T, d, c)
+            continue
         flush.zero_()
-        d, c, T = dev[warmup + k]
-        ev[k][0].record(stream)
+        torch.cuda.synchronize()
+        m.set_profiling(True)
+        m.profile(reset=True)
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        e[0].record(stream)
         m.integrate_depth(K, T, d, c)
         m.raycast(K, T, out, normals=nrm, rgb=col)
-        ev[k][1].record(stream)
+        e[1].record(stream)
+        ev.append(e)
         st = m.stats()  # synchronises (outside the timed events)
+        for g, v in m.profile().items():
+            a = prof.setdefault(g, [0.0, 0])
+            a[0] += v[0]
+            a[1] += v[1]
+        m.set_profiling(False)
         if st["status_code"] != 0:
-            raise RuntimeError(f"map status {st['status_code']} at step {k}")
+            raise RuntimeError(f"map status {st['status_code']} at frame {k}")
         rays += st["valid_rays"]
         obs += st["observations"]
         touched = [a + b for a, b in zip(touched, st["touched_level"])]
         fbytes += fuse_bytes_camera(st, wl, voxel_bytes(wl))
     torch.cuda.synchronize()
     times = [a.elapsed_time(b) for a, b in ev]
-    prof = m.profile()
     final = m.stats()
-    out = dict(ms=sum(times), ms_steps=times, rays=rays, fuse_bytes=fbytes, prof=prof, final=final, observations=obs,
-               touched_level=touched)
+    out = dict(ms=sum(times), ms_steps=times, rays=rays, fuse_bytes=fbytes, prof={g: tuple(v) for g, v in prof.items()},
+               final=final, observations=obs, touched_level=touched)
     if keep:
         out["map"] = m
     else:
@@ -397,7 +439,7 @@ def chamfer_vs_truth(m, wl, views, poses=None):
     return metrics.chamfer(np.concatenate(rec), np.concatenate(gt))
 
 
-def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epochs=30):
+def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epochs=30):
     """The learned level predictor against the plain rule on the same frames: train on the plain rule's levels of a
     different seeded scene (features recorded by the library, labels = final levels), then time the same sequence
     with the predictor set, and compare fused work, misclassification and Chamfer error."""
@@ -426,11 +468,12 @@ def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epoch
     train_err = float((predictor.predicted_levels(net, x) != y).float().mean().item())
     _, w_bf16 = net.weights()
     # misclassification on the evaluation sequence: the features of its new blocks do not depend on levels
-    xe, ye = captured_run(wl, frames[:warmup + steps])
+    xe, ye = captured_run(wl, frames[:max(timed) + 1])
     misclass = float((predictor.predicted_levels(net, xe) != ye).float().mean().item())
-    learned = run_camera_gpu(wl, frames, warmup, steps, flush, predictor=w_bf16, keep=True)
-    plain_map = run_camera_gpu(wl, frames, warmup, steps, flush, keep=True)
-    views = list(range(warmup, warmup + steps, max(1, steps // 10)))
+    learned = run_camera_gpu(wl, frames, warmup, timed, flush, predictor=w_bf16, keep=True)
+    plain_map = run_camera_gpu(wl, frames, warmup, timed, flush, keep=True)
+    steps = len(timed)
+    views = timed[::max(1, steps // 10)]
     ch_l = chamfer_vs_truth(learned["map"], wl, views)
     ch_p = chamfer_vs_truth(plain_map["map"], wl, views)
     learned["map"].close()
@@ -454,75 +497,52 @@ def run_learned(wl, frames, warmup, steps, flush, plain, train_frames=150, epoch
             "wall_s": round(time.perf_counter() - t0, 1)}
 
 
-def run_camera_e2e(wl, frames, warmup, steps):
-    """Same workload through the public API with host buffers: every step copies its depth + colour frame from pinned
-    host memory to the device, integrates it, raycasts it and copies the raycast depth, normals and colours back to
-    pinned host memory, all inside the timed events. Copies run on a second stream with two device buffers each way, so frame k + 1 is
-    uploaded and frame k - 1's depth read back while frame k is computed (stream order: the upload of a buffer waits
-    for the integration that last read it; the integration waits for its upload; the read-back waits for the
-    raycast)."""
+def run_camera_e2e(wl, frames, warmup, timed, flush):
+    """The same timed frames through the public API with host buffers: each timed step copies its depth + colour
+    frame from pinned host memory to the device, integrates it, raycasts it and copies the raycast depth, normals and
+    colours back to pinned host memory, all on one stream between the step's CUDA events (no overlap with other
+    steps), with L2 flushed before each step as in the device-timed arm. Untimed frames are integrated from device
+    copies made outside the timed region."""
     import torch
     import paper_2511_21459_b300 as mrh
     K = mrh.pinhole_from(wl)
     m = mrh.Map(mrh.params_from(wl), device=torch.cuda.current_device())
-    host = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(c).pin_memory(), T) for d, c, T in frames]
-    d_dev = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
-    c_dev = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    out = [torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda") for _ in range(2)]
-    nrm = [torch.empty((wl.height, wl.width, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
-    col = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    out_host = [torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory() for _ in range(2)]
-    nrm_host = [torch.empty((wl.height, wl.width, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
-    col_host = [torch.empty((wl.height, wl.width, 3), dtype=torch.uint8).pin_memory() for _ in range(2)]
-    compute = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
-    uploaded = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
-    rendered = [torch.cuda.Event() for _ in range(2)]
-    read = [torch.cuda.Event() for _ in range(2)]
-    for b in range(2):
-        consumed[b].record(compute)
-        read[b].record(copy)
-
-    def upload(k):
-        b = k % 2
-        d, c, _ = host[k]
-        with torch.cuda.stream(copy):
-            copy.wait_event(consumed[b])
-            d_dev[b].copy_(d, non_blocking=True)
-            c_dev[b].copy_(c, non_blocking=True)
-            uploaded[b].record(copy)
-
-    def step(k, last):
-        b = k % 2
-        compute.wait_event(uploaded[b])
-        compute.wait_event(read[b])  # out[b] free again
-        m.integrate_depth(K, host[k][2], d_dev[b], c_dev[b], stream=compute)
-        consumed[b].record(compute)
-        if k + 1 <= last:
-            upload(k + 1)
-        m.raycast(K, host[k][2], out[b], stream=compute, normals=nrm[b], rgb=col[b])
-        rendered[b].record(compute)
-        with torch.cuda.stream(copy):
-            copy.wait_event(rendered[b])
-            out_host[b].copy_(out[b], non_blocking=True)
-            nrm_host[b].copy_(nrm[b], non_blocking=True)
-            col_host[b].copy_(col[b], non_blocking=True)
-            read[b].record(copy)
-
-    upload(0)
-    for k in range(warmup):
-        step(k, warmup - 1)
-    torch.cuda.synchronize()
-    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(compute)
-    upload(warmup)
-    for k in range(warmup, warmup + steps):
-        step(k, warmup + steps - 1)
-    compute.wait_stream(copy)
-    z.record(compute)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(z)
+    last = max(timed)
+    tset = set(timed)
+    host = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(c).pin_memory(), T) for d, c, T in frames[:last + 1]]
+    d_dev = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    c_dev = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((wl.height, wl.width), dtype=torch.float32, device="cuda")
+    nrm = torch.empty((wl.height, wl.width, 3), dtype=torch.float32, device="cuda")
+    col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
+    out_host = torch.empty((wl.height, wl.width), dtype=torch.float32).pin_memory()
+    nrm_host = torch.empty((wl.height, wl.width, 3), dtype=torch.float32).pin_memory()
+    col_host = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream()
+    ms = 0.0
+    for k in range(last + 1):
+        d, c, T = host[k]
+        if k < warmup or k not in tset:
+            d_dev.copy_(d, non_blocking=True)
+            c_dev.copy_(c, non_blocking=True)
+            m.integrate_depth(K, T, d_dev, c_dev)
+            if k < warmup:
+                m.raycast(K, T, out, normals=nrm, rgb=col)
+            continue
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_dev.copy_(d, non_blocking=True)
+        c_dev.copy_(c, non_blocking=True)
+        m.integrate_depth(K, T, d_dev, c_dev)
+        m.raycast(K, T, out, normals=nrm, rgb=col)
+        out_host.copy_(out, non_blocking=True)
+        nrm_host.copy_(nrm, non_blocking=True)
+        col_host.copy_(col, non_blocking=True)
+        z.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(z)
     m.close()
     h2d = wl.width * wl.height * (4 + 3)
     d2h = wl.width * wl.height * (4 + 12 + 3)
@@ -1016,7 +1036,8 @@ def main():
                 "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm) + 640x480 raycast "
                                        "(depth, normal, colour)"},
                 "frames_per_s": n / t_total,
-                "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                 "host": host_cpu()},
                 "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
@@ -1035,14 +1056,15 @@ def main():
         build.build()
     barrier(world)
 
-    n_frames = args.warmup + args.steps
+    n_frames = max(wl.n_frames, args.warmup + args.steps)
     frames = camera_frames(wl, 0, n_frames)
+    timed = timed_frames(n_frames, args.warmup, args.steps)
 
     # CPU baseline first (host only, before the GPU work is timed)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rays_c, t_c, n_c = oracle_camera_sample(wl, frames, args.cpu_budget_s, 8)
-        cpu = {"value": rays_c / t_c, "unit": "points/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rays_c / t_c, "unit": "points/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"first {n_c} frames of the RGB-D sequence, integrate + full 640x480 raycast (depth, "
                          f"normal, colour) each, f32s mode, single thread ({t_c:.1f} s)"}
         n_procs = max(1, min(args.cpu_replicas, os.cpu_count() or 1))
@@ -1057,7 +1079,7 @@ def main():
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    res = run_camera_gpu(wl, frames, args.warmup, args.steps, flush, keep=True)
+    res = run_camera_gpu(wl, frames, args.warmup, timed, flush, keep=True)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -1092,12 +1114,13 @@ def main():
 
     e2e = None
     if world >= 1:
-        e_ms, h2d, d2h = run_camera_e2e(wl, frames, args.warmup, args.steps)
+        e_ms, h2d, d2h = run_camera_e2e(wl, frames, args.warmup, timed, flush)
         e_ms = max_over_ranks(e_ms, world)
         e2e = {"value": rays_all / (e_ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps,
-               "note": "pinned host frames uploaded and raycast depth, normals and colours read back every step on a "
-                       "second stream, overlapping the neighbouring frames' kernels; no L2 flush between steps"}
+               "note": "each timed step uploads its depth + colour frame from pinned host memory, integrates, raycasts "
+                       "and reads depth, normals and colours back to pinned host memory on one stream, with no overlap "
+                       "between steps; L2 flushed before each step as in the device-timed arm"}
 
     mesh = None
     if rank == 0 and not args.no_mesh:
@@ -1108,6 +1131,7 @@ def main():
         quad = run_quadtree(wl, frames[:20])
 
     lidar = None
+    roofline_lidar = None
     if not args.no_lidar:
         lw = synth.lidar()
         lres = run_lidar_gpu(lw, 3, args.lidar_steps, flush)
@@ -1120,6 +1144,17 @@ def main():
                  "kernels": {g: {"ms_total": round(v[0], 3), "launches": int(v[1])} for g, v in lprof.items()
                              if v[1] > 0},
                  "fuse_achieved_GBps": round(lres["fuse_bytes"] / (lprof["fuse"][0] / 1000.0) / 1e9, 1)}
+        # fusion of a scan = the observation passes (grouping the rays' voxel crossings) + the fusion kernel
+        l_fuse_ms = lprof["fuse"][0] + lprof.get("lidar_obs", (0.0, 0))[0]
+        l_ach = lres["fuse_bytes"] / (l_fuse_ms / 1000.0) / 1e9
+        roofline_lidar = {"kernel": "LiDAR fusion: observation passes + k_fuse_points (fusion + block variance + "
+                                    "re-level)", "bound": "hbm", "achieved": round(l_ach, 1), "peak": hbm,
+                          "unit": "GB/s", "frac": round(l_ach / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                          "algorithmic_bytes_per_launch": int(lres["fuse_bytes"] / lres["steps"]),
+                          "launch_ms_avg": round(l_fuse_ms / lres["steps"], 5),
+                          "bytes_formula": "12 N_points + 2 s_v updated_voxels + 16 touched (s_v = 10 B, FP16, no "
+                                           "colour)"}
+        lidar["roofline"] = roofline_lidar
 
     streaming = None
     if rank == 0 and not args.no_lidar and not args.no_streaming:
@@ -1145,7 +1180,7 @@ def main():
 
     learned = None
     if not args.no_learned:
-        learned = run_learned(wl, frames, args.warmup, args.steps, flush, res)
+        learned = run_learned(wl, frames, args.warmup, timed, flush, res)
 
     if rank == 0:
         final = res["final"]
@@ -1155,10 +1190,13 @@ def main():
                 "data": "synthetic (seeded procedural RGB-D room sequence; stands in for ScanNet/Replica)",
                 "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm, 2^20 hash, colour, FP32 "
                                        "storage) + 640x480 raycast (depth, normal, colour) per frame",
-                           "frames": f"{args.warmup}..{args.warmup + args.steps - 1} timed after {args.warmup} warm-up",
+                           "frames": f"{len(timed)} timed frames spread over the {n_frames}-frame orbit ({timed[0]}, "
+                                     f"{timed[1] if len(timed) > 1 else ''}, ... {timed[-1]}); {args.warmup} warm-up "
+                                     f"frames, every other frame integrated untimed in sequence order",
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "frames_per_s": fps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "frames_per_s": fps, "roofline": roofline, "roofline_lidar": roofline_lidar, "cpu_baseline": cpu,
+                "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
                 "lidar": lidar, "batched": batched, "learned": learned, "mesh": mesh, "quadtree": quad,

@@ -50,7 +50,9 @@ typedef enum {
                                 max_observations); the excess was not fused */
   MRH_ERR_CUDA = 6,          /* a CUDA runtime call failed (see mrh_last_cuda_error) */
   MRH_ERR_CAPACITY = 7,      /* caller-provided output buffers are too small */
-  MRH_ERR_STATIC_LIMIT = 8   /* more blocks than mrh_extract_blocks_noalloc's fixed scratch holds */
+  MRH_ERR_STATIC_LIMIT = 8,  /* more blocks than mrh_extract_blocks_noalloc's fixed scratch holds */
+  MRH_ERR_INCONSISTENT = 9   /* the hash table's committed blocks disagree with the heaps' live-block count (a
+                                read-out would drop or invent blocks); the outputs are not valid */
 } mrh_status;
 
 enum { MRH_STORAGE_FP32 = 0, MRH_STORAGE_FP16 = 1 };
@@ -356,7 +358,9 @@ mrh_status mrh_count_blocks(mrh_map* map, uint64_t* n_blocks, uint64_t* n_voxels
 /* Copy every allocated block out, sorted by key (x, then y, then z). Outputs (device): keys_dev n x 3 int32,
  * levels_dev n uint8, voxel_offset_dev n + 1 uint64 (voxels of block b are [off[b], off[b+1])), tsdf_dev, weight_dev,
  * s2_dev V float32 each (FP16 storage is widened exactly), color_dev V x 3 float32 or NULL. Capacities are in blocks
- * and voxels; MRH_ERR_CAPACITY if too small. Synchronises `stream`. */
+ * and voxels; MRH_ERR_CAPACITY if too small. When counting the blocks fails (MRH_ERR_CUDA) nothing is queued;
+ * MRH_ERR_INCONSISTENT when the hash table holds a different number of committed blocks than the heaps report live.
+ * Synchronises `stream`. */
 mrh_status mrh_extract_blocks(mrh_map* map, int32_t* keys_dev, uint8_t* levels_dev, uint64_t* voxel_offset_dev,
                               float* tsdf_dev, float* weight_dev, float* s2_dev, float* color_dev,
                               uint64_t capacity_blocks, uint64_t capacity_voxels, uint64_t* n_blocks_out,
@@ -369,11 +373,12 @@ mrh_status mrh_extract_blocks(mrh_map* map, int32_t* keys_dev, uint8_t* levels_d
  * synchronise the device) is not acceptable. Its sort and offset scratch is one file-scope device array of
  * MRH_NOALLOC_MAX_BLOCKS blocks (about 5 MiB) that every GPU loading the library holds until the process exits;
  * maps holding more blocks return MRH_ERR_STATIC_LIMIT before any work is queued.
- * The first call on a device looks up that array's device address (once per device, with the map's device
- * current); make that first call before any stream capture. Every call shares the one array per device and keeps
- * the last call's contents (the call clears what must start at zero itself), so calls whose GPU work overlaps in
- * time, on any stream or map of the same device, race: order them on one stream or synchronise between them.
- * Arguments, outputs, ordering and the synchronisation of `stream` are those of mrh_extract_blocks. */
+ * Every call looks up that array's device address with the map's device current (so no address survives a device
+ * reset). Every call shares the one array per device and keeps the last call's contents (the call clears what must
+ * start at zero itself), so calls whose GPU work overlaps in time, on any stream or map of the same device, race:
+ * order them on one stream or synchronise between them. Arguments, outputs, ordering, the synchronisation of
+ * `stream`, the early return on a failed count and the other status codes are those of mrh_extract_blocks; a
+ * MRH_ERR_STATIC_LIMIT return writes nothing to the outputs. */
 #define MRH_NOALLOC_MAX_BLOCKS (1u << 18)
 mrh_status mrh_extract_blocks_noalloc(mrh_map* map, int32_t* keys_dev, uint8_t* levels_dev,
                                       uint64_t* voxel_offset_dev, float* tsdf_dev, float* weight_dev, float* s2_dev,

@@ -81,10 +81,10 @@ class FrameStats(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
-def _load():
+def _load(path: str | None = None):
     global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+    if path is not None or _lib is None:
+        lib = ctypes.CDLL(path or build())
         vp = ctypes.c_void_p
         lib.orc_create.restype = vp
         lib.orc_create.argtypes = [ctypes.POINTER(Params)]
@@ -92,6 +92,8 @@ def _load():
         lib.orc_integrate_depth.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, ctypes.POINTER(FrameStats)]
         lib.orc_integrate_points.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(FrameStats)]
         lib.orc_raycast.argtypes = [vp, ctypes.POINTER(Pinhole), vp, vp, vp, vp]
+        lib.orc_raycast_pixels.argtypes = [vp, ctypes.POINTER(Pinhole), vp, ctypes.c_int64, vp, vp, vp, vp]
+        lib.orc_probe_points.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, vp]
         lib.orc_set_block.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
         lib.orc_extract_mesh.restype = ctypes.c_int64
         lib.orc_extract_mesh.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64]
@@ -132,8 +134,28 @@ def _load():
         lib.orc_set_capture.argtypes = [vp, ctypes.c_int]
         lib.orc_get_features.restype = ctypes.c_int64
         lib.orc_get_features.argtypes = [vp, vp, vp, ctypes.c_int64]
+        if path is not None:
+            return lib
         _lib = lib
     return _lib
+
+
+class use_library:
+    """Test hook: maps created inside ``with oracle.use_library(path):`` run on another build of the oracle source
+    (the mutation tests compile copies with one deliberate mistake each and check that a pin catches it)."""
+
+    def __init__(self, path: str):
+        self.lib = _load(path)
+
+    def __enter__(self):
+        global _lib
+        self._saved, _lib = _lib, self.lib
+        return self.lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
 
 
 def _p(a):
@@ -213,6 +235,31 @@ class OracleMap:
         if not (normals or rgb):
             return out
         return (out,) + ((nrm,) if normals else ()) + ((col,) if rgb else ())
+
+    def raycast_pixels(self, K: Pinhole, T_wc: np.ndarray, pix, normals: bool = False, rgb: bool = False):
+        """The raycast of the listed pixels only (flat indices v * width + u): z-depth (n,) and optionally normals
+        (n, 3) and colours (n, 3), as ``raycast`` gives them for those pixels."""
+        T = np.ascontiguousarray(T_wc, dtype=np.float64)
+        pix = np.ascontiguousarray(pix, dtype=np.int64).ravel()
+        out = np.zeros(pix.size, dtype=np.float32)
+        nrm = np.zeros((pix.size, 3), dtype=np.float32) if normals else None
+        col = np.zeros((pix.size, 3), dtype=np.uint8) if rgb else None
+        self._lib.orc_raycast_pixels(self._h, ctypes.byref(K), _p(T), pix.size, _p(pix), _p(out), _p(nrm), _p(col))
+        if not (normals or rgb):
+            return out
+        return (out,) + ((nrm,) if normals else ()) + ((col,) if rgb else ())
+
+    def probe(self, xyz: np.ndarray):
+        """The raycast's field at world points (n, 3): F (n,) float64, valid (n,) bool, and the unit normal (n, 3)
+        and colour (n, 3) uint8 the raycast reports for a hit at each point (zeros where it reports none)."""
+        x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        n = x.shape[0]
+        F = np.zeros(n)
+        ok = np.zeros(n, np.int8)
+        nrm = np.zeros((n, 3), np.float32)
+        col = np.zeros((n, 3), np.uint8)
+        self._lib.orc_probe_points(self._h, n, _p(x), _p(F), _p(ok), _p(nrm), _p(col))
+        return F, ok.astype(bool), nrm, col
 
     def set_streaming(self, fraction: float, radius: float, max_blocks):
         """Capacity-driven streaming (Sec. 3.3): before each frame, when some level holds more than fraction of

@@ -46,8 +46,6 @@ constexpr int64_t kBlockUnit = int64_t(1) << kFracBits;
 constexpr int64_t kVoxelUnit = kBlockUnit / kFineDim;  // one finest voxel
 constexpr int64_t kKeyLimit = (int64_t(1) << 20) - 2;  // |block coordinate| bound (21-bit packed keys)
 constexpr int kMaxLevels = 3;
-constexpr int kRaycastMaxIter = 8192;
-constexpr int64_t kBrick = 4;  // raycast empty-space skipping cell: 4 x 4 x 4 blocks
 
 struct Key {
   int64_t x, y, z;
@@ -287,6 +285,9 @@ struct MapBase {
   virtual int integrate_depth(const orc_pinhole*, const double*, const float*, const uint8_t*, orc_frame_stats*) = 0;
   virtual int integrate_points(const double*, const float*, int64_t, orc_frame_stats*) = 0;
   virtual int raycast(const orc_pinhole*, const double*, float*, float*, uint8_t*) = 0;
+  virtual int raycast_pixels(const orc_pinhole*, const double*, int64_t, const int64_t*, float*, float*,
+                             uint8_t*) const = 0;
+  virtual void probe_points(int64_t, const double*, double*, int8_t*, float*, uint8_t*) const = 0;
   virtual int set_block(const int32_t*, int, const double*, const double*, const double*, const double*) = 0;
   virtual void extract_mesh(std::vector<float>& tris) const = 0;
   virtual void set_streaming(float fraction, float radius, const int64_t* max_blocks) = 0;
@@ -388,7 +389,6 @@ struct Map : MapBase {
   int n[kMaxLevels];      // voxels per block side per level
   float E_f;              // block edge (float), the unit of the fixed-point key coordinates
   std::unordered_map<Key, Block<R, Sto>, KeyHash> blocks;
-  std::unordered_set<Key, KeyHash> bricks;  // 4x4x4-block cells holding at least one allocated block (raycast)
 
   explicit Map(const orc_params& p) : P(p), L(p.n_levels) {
     tau = (R)p.truncation;
@@ -409,7 +409,6 @@ struct Map : MapBase {
       touched.insert(k);
       if (blocks.find(k) == blocks.end()) {
         st->new_blocks++;
-        bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
         auto ar = archive.find(k);
         if (ar != archive.end()) {  // streamed back in: level and payload as they were archived
           blocks[k] = std::move(ar->second);
@@ -864,216 +863,253 @@ struct Map : MapBase {
     return 0;
   }
 
-  // ---- raycast (the rendering branch of Fig. 2): first +/- zero crossing of the trilinear TSDF along each pixel ray.
-  // Reading (the paper renders through Gaussian splats and gives no raycaster): march from min to max depth; a
-  // sample in an empty 4x4x4-block brick jumps to the brick's exit face, a sample in an unallocated block of a
-  // non-empty brick to the block's exit face; inside a block of level l the field is trilinear over the 8 nearest
-  // voxel centres of that level's grid, a corner in another block uses that block's voxel containing the corner
-  // centre (any level), and a sample counts only when all 8 corners are observed; the next sample is
-  // min(v_l, tau/2) ahead, or 0.75 F ahead when the sample is valid with F larger than that (F <= tau underestimates
-  // the distance to the surface, so the step cannot cross the negative band); on the first sign change take the
-  // linear root, evaluate there once more and take one more secant step. Output z-depth; 0 = no hit.
+  // ---- raycast (the rendering branch of Fig. 2; the paper renders through Gaussian splats and gives no raycaster).
+  // Definition: along the ray of pixel (u, v), between min_depth and max_depth (as z-depth), the first place where the
+  // trilinear TSDF passes from positive to non-positive. The field F(x) exists where the block holding x is allocated
+  // and the 8 voxel centres of that block's level nearest to x are all observed (W > 0); a corner is read from the
+  // block holding the corner centre, from that block's voxel containing it, whatever the block's level. Everything
+  // here is double arithmetic on the stored values, in both modes.
+  // Search: the grid t_j = t_min + j h, with h = min(v_0, tau / 2) (the sampling step of the finest level). The first
+  // two consecutive grid samples that both have a field, with F_j > 0 >= F_{j+1}, bracket the crossing; bisection
+  // narrows the bracket below 1e-9 m and the crossing is the linear root of the last bracket (a midpoint without a
+  // field ends the bisection at that midpoint). A grid sample in an unallocated block has no field, and neither has
+  // any other sample of that block, so the search continues at the first grid sample past the block's exit face.
+  // Output z-depth, 0 where there is no crossing; optionally the normal and colour at the crossing (shade_at()).
+  static constexpr double kRayBisectTol = 1e-9;  // bracket width [m] at which the bisection stops
+
+  // Block lookups of one ray, remembered (the same block answers most corner lookups in a row).
+  struct Lookup {
+    const Map* map;
+    Key k[2];
+    const Block<R, Sto>* b[2] = {nullptr, nullptr};
+    bool have[2] = {false, false};
+    const Block<R, Sto>* get(const Key& key) {
+      for (int i = 0; i < 2; ++i)
+        if (have[i] && k[i] == key) return b[i];
+      k[1] = k[0];
+      b[1] = b[0];
+      have[1] = have[0];
+      auto it = map->blocks.find(key);
+      k[0] = key;
+      b[0] = it == map->blocks.end() ? nullptr : &it->second;
+      have[0] = true;
+      return b[0];
+    }
+  };
+
   const Block<R, Sto>* find(const Key& k) const {
     auto it = blocks.find(k);
     return it == blocks.end() ? nullptr : &it->second;
   }
 
-  bool field(const R x[3], int l, R* out) const {
-    R inv = (R)1 / v[l];
+  double vd(int l) const { return (double)(E_f / (float)kFineDim) * (double)(1 << l); }  // voxel edge of level l
+
+  // the 8 corners of x on the level-l grid: block, voxel index and trilinear weight of each (corner k has offset
+  // (k & 1, (k >> 1) & 1, k >> 2)); false when a corner's block is unallocated or the corner is unobserved
+  bool corners(Lookup& lk, const double x[3], int l, const Block<R, Sto>* cb[8], size_t ci[8], double cw[8],
+               double fr[3]) const {
+    const double vl = vd(l);
     int64_t j0[3];
-    R fr[3];
     for (int a = 0; a < 3; ++a) {
-      R g = x[a] * inv - (R)0.5;
-      R fl = std::floor(g);
+      const double g = x[a] / vl - 0.5;
+      const double fl = std::floor(g);
       j0[a] = (int64_t)fl;
       fr[a] = g - fl;
     }
-    R acc = 0;
+    const int nl = n[l];
     for (int k = 0; k < 8; ++k) {
-      int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
-      int64_t j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
-      int nl = n[l];
-      Key bk{floor_div(j[0], nl), floor_div(j[1], nl), floor_div(j[2], nl)};
-      const Block<R, Sto>* b = find(bk);
+      const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+      const int64_t j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
+      const Key bk{floor_div(j[0], nl), floor_div(j[1], nl), floor_div(j[2], nl)};
+      const Block<R, Sto>* b = lk.get(bk);
       if (!b) return false;
       size_t idx;
       if (b->level == l) {
         idx = vox(nl, (int)(j[0] - bk.x * nl), (int)(j[1] - bk.y * nl), (int)(j[2] - bk.z * nl));
       } else {
-        // finest-level cell that holds the corner centre, then the voxel of block bk's level containing it
-        int lb = b->level, nb = n[lb];
+        // the finest-level cell holding the corner centre, then the voxel of block bk's level containing it
+        const int lb = b->level, nb = n[lb];
         int64_t cf[3];
         for (int a = 0; a < 3; ++a) cf[a] = l == 0 ? j[a] : j[a] * ((int64_t)1 << l) + ((int64_t)1 << (l - 1));
         idx = vox(nb, (int)(floor_div(cf[0], (int64_t)1 << lb) - bk.x * nb),
                   (int)(floor_div(cf[1], (int64_t)1 << lb) - bk.y * nb),
                   (int)(floor_div(cf[2], (int64_t)1 << lb) - bk.z * nb));
       }
-      if (!(b->W[idx] > (R)0)) return false;
-      R wx = ax ? fr[0] : (R)1 - fr[0];
-      R wy = ay ? fr[1] : (R)1 - fr[1];
-      R wz = az ? fr[2] : (R)1 - fr[2];
-      acc = acc + ((wx * wy) * wz) * (R)Store<Sto>::get(b->D[idx]);
-    }
-    *out = acc;
-    return true;
-  }
-
-  // Surface attributes at a hit point x inside a block of level l, over the same 8 corners as field(): g is the
-  // gradient of the trilinear interpolant up to the positive factor 1 / v_l (d/dx of the x weight is +1 for the
-  // upper corner, -1 for the lower), summed in corner order; c is the trilinear mean of the stored colour. False when
-  // a corner's block is unallocated or a corner is unobserved.
-  bool shade(const R x[3], int l, R g[3], R c[3]) const {
-    R inv = (R)1 / v[l];
-    int64_t j0[3];
-    R fr[3];
-    for (int a = 0; a < 3; ++a) {
-      R gg = x[a] * inv - (R)0.5;
-      R fl = std::floor(gg);
-      j0[a] = (int64_t)fl;
-      fr[a] = gg - fl;
-    }
-    for (int a = 0; a < 3; ++a) g[a] = c[a] = 0;
-    for (int k = 0; k < 8; ++k) {
-      int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
-      int64_t j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
-      int nl = n[l];
-      Key bk{floor_div(j[0], nl), floor_div(j[1], nl), floor_div(j[2], nl)};
-      const Block<R, Sto>* b = find(bk);
-      if (!b) return false;
-      size_t idx;
-      if (b->level == l) {
-        idx = vox(nl, (int)(j[0] - bk.x * nl), (int)(j[1] - bk.y * nl), (int)(j[2] - bk.z * nl));
-      } else {
-        int lb = b->level, nb = n[lb];
-        int64_t cf[3];
-        for (int a = 0; a < 3; ++a) cf[a] = l == 0 ? j[a] : j[a] * ((int64_t)1 << l) + ((int64_t)1 << (l - 1));
-        idx = vox(nb, (int)(floor_div(cf[0], (int64_t)1 << lb) - bk.x * nb),
-                  (int)(floor_div(cf[1], (int64_t)1 << lb) - bk.y * nb),
-                  (int)(floor_div(cf[2], (int64_t)1 << lb) - bk.z * nb));
-      }
-      if (!(b->W[idx] > (R)0)) return false;
-      R wx = ax ? fr[0] : (R)1 - fr[0];
-      R wy = ay ? fr[1] : (R)1 - fr[1];
-      R wz = az ? fr[2] : (R)1 - fr[2];
-      R d = (R)Store<Sto>::get(b->D[idx]);
-      R tx = (wy * wz) * d, ty = (wx * wz) * d, tz = (wx * wy) * d;
-      g[0] = ax ? g[0] + tx : g[0] - tx;
-      g[1] = ay ? g[1] + ty : g[1] - ty;
-      g[2] = az ? g[2] + tz : g[2] - tz;
-      if (P.has_color) {
-        R w = (wx * wy) * wz;
-        for (int q = 0; q < 3; ++q) c[q] = c[q] + w * (R)Store<Sto>::get(b->C[q][idx]);
-      }
+      if (!((double)b->W[idx] > 0.0)) return false;
+      cb[k] = b;
+      ci[k] = idx;
+      cw[k] = (ax ? fr[0] : 1.0 - fr[0]) * (ay ? fr[1] : 1.0 - fr[1]) * (az ? fr[2] : 1.0 - fr[2]);
     }
     return true;
   }
 
-  // sample at parameter t: returns false when the block is unallocated; *valid tells whether the field exists
-  bool sample(const R o[3], const R r[3], R t, R invE, int* level, bool* valid, R* F) const {
-    R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
-    Key bk{(int64_t)std::floor(x[0] * invE), (int64_t)std::floor(x[1] * invE), (int64_t)std::floor(x[2] * invE)};
-    const Block<R, Sto>* b = find(bk);
+  // F at x: false when x's block is unallocated or the field does not exist there
+  bool field_at(Lookup& lk, const double x[3], double* F) const {
+    const double E = (double)E_f;
+    const Block<R, Sto>* b =
+        lk.get(Key{(int64_t)std::floor(x[0] / E), (int64_t)std::floor(x[1] / E), (int64_t)std::floor(x[2] / E)});
     if (!b) return false;
-    *level = b->level;
-    *valid = field(x, b->level, F);
+    const Block<R, Sto>* cb[8];
+    size_t ci[8];
+    double cw[8], fr[3];
+    if (!corners(lk, x, b->level, cb, ci, cw, fr)) return false;
+    double acc = 0.0;
+    for (int k = 0; k < 8; ++k) acc += cw[k] * (double)Store<Sto>::get(cb[k]->D[ci[k]]);
+    *F = acc;
     return true;
+  }
+
+  // Surface attributes at x, over the 8 corners of the level of x's block: g = the gradient of the trilinear
+  // interpolant (times v_l: the derivative of a corner's weight along axis a is the product of its other two weights,
+  // + for the upper corner, - for the lower), c = the trilinear mean of the stored colour. False when x's block is
+  // unallocated or a corner is missing or unobserved.
+  bool shade_at(Lookup& lk, const double x[3], double g[3], double c[3]) const {
+    const double E = (double)E_f;
+    for (int a = 0; a < 3; ++a) g[a] = c[a] = 0.0;
+    const Block<R, Sto>* b =
+        lk.get(Key{(int64_t)std::floor(x[0] / E), (int64_t)std::floor(x[1] / E), (int64_t)std::floor(x[2] / E)});
+    if (!b) return false;
+    const Block<R, Sto>* cb[8];
+    size_t ci[8];
+    double cw[8], fr[3];
+    if (!corners(lk, x, b->level, cb, ci, cw, fr)) return false;
+    for (int k = 0; k < 8; ++k) {
+      const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
+      const double wx = ax ? fr[0] : 1.0 - fr[0], wy = ay ? fr[1] : 1.0 - fr[1], wz = az ? fr[2] : 1.0 - fr[2];
+      const double d = (double)Store<Sto>::get(cb[k]->D[ci[k]]);
+      g[0] += (ax ? 1.0 : -1.0) * wy * wz * d;
+      g[1] += (ay ? 1.0 : -1.0) * wx * wz * d;
+      g[2] += (az ? 1.0 : -1.0) * wx * wy * d;
+      if (P.has_color)
+        for (int q = 0; q < 3; ++q) c[q] += cw[k] * (double)Store<Sto>::get(cb[k]->C[q][ci[k]]);
+    }
+    return true;
+  }
+
+  // unit normal and u8 colour at x (zeros when shade_at fails); returns whether it succeeded
+  bool surface(Lookup& lk, const double x[3], float* normal, uint8_t* rgb) const {
+    double g[3], c[3];
+    const bool ok = shade_at(lk, x, g, c);
+    if (normal) {
+      const double nn = ok ? std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : 0.0;
+      for (int a = 0; a < 3; ++a) normal[a] = nn > 0.0 ? (float)(g[a] / nn) : 0.0f;
+    }
+    if (rgb)
+      for (int q = 0; q < 3; ++q) {
+        const double cv = ok ? std::floor(c[q] + 0.5) : 0.0;
+        rgb[q] = (uint8_t)(cv <= 0.0 ? 0 : cv >= 255.0 ? 255 : (int)cv);
+      }
+    return ok;
+  }
+
+  // One pixel: the crossing's ray parameter t (0 = none); rc = unit ray in the camera frame, r = in the world.
+  double cast(const orc_pinhole* K, const double Rm[9], const double o[3], int u, int vv, double rc[3],
+              double r[3]) const {
+    const double qx = ((double)u - (double)K->cx) / (double)K->fx, qy = ((double)vv - (double)K->cy) / (double)K->fy;
+    const double nq = std::sqrt(qx * qx + qy * qy + 1.0);
+    rc[0] = qx / nq;
+    rc[1] = qy / nq;
+    rc[2] = 1.0 / nq;
+    for (int a = 0; a < 3; ++a) r[a] = Rm[3 * a + 0] * rc[0] + Rm[3 * a + 1] * rc[1] + Rm[3 * a + 2] * rc[2];
+    const double E = (double)E_f, h = std::min(vd(0), 0.5 * (double)tau);
+    const double t_min = (double)K->min_depth * nq, t_max = (double)K->max_depth * nq;
+    Lookup lk{this};
+    bool have_prev = false;
+    double t_prev = 0.0, F_prev = 0.0;
+    for (int64_t j = 0;;) {
+      const double t = t_min + (double)j * h;
+      if (t > t_max) return 0.0;
+      const double x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+      const Key bk{(int64_t)std::floor(x[0] / E), (int64_t)std::floor(x[1] / E), (int64_t)std::floor(x[2] / E)};
+      if (!lk.get(bk)) {
+        // no sample of this block has a field: continue at the first grid sample past its exit face
+        double t_exit = t_max + 1.0;
+        for (int a = 0; a < 3; ++a) {
+          if (r[a] == 0.0) continue;
+          const double face = (double)(r[a] > 0.0 ? (&bk.x)[a] + 1 : (&bk.x)[a]) * E;
+          t_exit = std::min(t_exit, (face - o[a]) / r[a]);
+        }
+        const int64_t jn = (int64_t)std::ceil((t_exit - t_min) / h);
+        j = jn > j ? jn : j + 1;
+        have_prev = false;
+        continue;
+      }
+      double F = 0.0;
+      const bool valid = field_at(lk, x, &F);
+      if (valid && have_prev && F_prev > 0.0 && !(F > 0.0)) {
+        double a = t_prev, b = t, Fa = F_prev, Fb = F;
+        while (b - a > kRayBisectTol) {
+          const double m = 0.5 * (a + b);
+          const double xm[3] = {o[0] + m * r[0], o[1] + m * r[1], o[2] + m * r[2]};
+          double Fm = 0.0;
+          if (!field_at(lk, xm, &Fm)) return m;  // the bracket holds a point without a field: stop there
+          if (Fm > 0.0) {
+            a = m;
+            Fa = Fm;
+          } else {
+            b = m;
+            Fb = Fm;
+          }
+        }
+        return a + (b - a) * (Fa / (Fa - Fb));  // the linear root of the final bracket (exact on a linear field)
+      }
+      have_prev = valid;
+      t_prev = t;
+      F_prev = F;
+      ++j;
+    }
+  }
+
+  void pose_d(const double* T, double Rm[9], double o[3]) const {
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) Rm[3 * a + b] = T[4 * a + b];
+      o[a] = T[4 * a + 3];
+    }
+  }
+
+  // pixels pix[0 .. n) (index v * width + u) into depth[i], normal[3 i], rgb[3 i]
+  int raycast_pixels(const orc_pinhole* K, const double* T, int64_t n_pix, const int64_t* pix, float* out,
+                     float* normal, uint8_t* rgb) const override {
+    double Rm[9], o[3];
+    pose_d(T, Rm, o);
+    for (int64_t i = 0; i < n_pix; ++i) {
+      const int u = (int)(pix[i] % K->width), vv = (int)(pix[i] / K->width);
+      double rc[3], r[3];
+      const double t = cast(K, Rm, o, u, vv, rc, r);
+      out[i] = (float)(t * rc[2]);
+      if (normal || rgb) {
+        float nz[3] = {0.0f, 0.0f, 0.0f};
+        uint8_t cz[3] = {0, 0, 0};
+        if (t > 0.0) {
+          Lookup lk{this};
+          const double xh[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+          surface(lk, xh, normal ? nz : nullptr, rgb ? cz : nullptr);
+        }
+        if (normal) std::memcpy(normal + 3 * i, nz, sizeof nz);
+        if (rgb) std::memcpy(rgb + 3 * i, cz, sizeof cz);
+      }
+    }
+    return 0;
   }
 
   int raycast(const orc_pinhole* K, const double* T, float* out, float* normal, uint8_t* rgb) override {
-    R Rm[9], o[3];
-    pose(T, Rm, o);
-    const R fx = (R)K->fx, fy = (R)K->fy, cx = (R)K->cx, cy = (R)K->cy;
-    const R E = (R)E_f, invE = (R)1 / E;
-    const R half_tau = tau * (R)0.5;
-    const R eps = (R)1e-4 * E;
-    for (int vv = 0; vv < K->height; ++vv)
-      for (int u = 0; u < K->width; ++u) {
-        R qx = ((R)u - cx) / fx, qy = ((R)vv - cy) / fy;
-        R nq = std::sqrt(qx * qx + qy * qy + (R)1);
-        R rc[3] = {qx / nq, qy / nq, (R)1 / nq};
-        R r[3], inv_r[3];
-        for (int a = 0; a < 3; ++a) {
-          r[a] = Rm[3 * a + 0] * rc[0] + Rm[3 * a + 1] * rc[1] + Rm[3 * a + 2] * rc[2];
-          inv_r[a] = r[a] != (R)0 ? (R)1 / r[a] : (R)0;
-        }
-        R t = (R)K->min_depth * nq, t_far = (R)K->max_depth * nq;
-        bool have_prev = false;
-        R t_prev = 0, F_prev = 0, hit = 0, t_hit = 0;
-        for (int it = 0; it < kRaycastMaxIter && t <= t_far; ++it) {
-          R x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
-          int64_t bk[3] = {(int64_t)std::floor(x[0] * invE), (int64_t)std::floor(x[1] * invE),
-                           (int64_t)std::floor(x[2] * invE)};
-          Key brick{floor_div(bk[0], kBrick), floor_div(bk[1], kBrick), floor_div(bk[2], kBrick)};
-          const bool brick_empty = bricks.find(brick) == bricks.end();
-          const Block<R, Sto>* blk = brick_empty ? nullptr : find(Key{bk[0], bk[1], bk[2]});
-          if (!blk) {
-            // leave the empty brick (or the empty block): smallest parameter at which the ray reaches a far face
-            const int64_t cell[3] = {brick_empty ? brick.x : bk[0], brick_empty ? brick.y : bk[1],
-                                     brick_empty ? brick.z : bk[2]};
-            const int64_t span = brick_empty ? kBrick : 1;
-            R t_exit = t_far + (R)1;
-            for (int a = 0; a < 3; ++a) {
-              if (r[a] == (R)0) continue;
-              R face = (R)((r[a] > (R)0 ? cell[a] + 1 : cell[a]) * span) * E;
-              R ta = (face - o[a]) * inv_r[a];
-              if (ta < t_exit) t_exit = ta;
-            }
-            R step_min = t + eps;
-            R tn = t_exit + eps;
-            t = tn > step_min ? tn : step_min;
-            have_prev = false;
-            continue;
-          }
-          const int l = blk->level;
-          R F = 0;
-          const bool valid = field(x, l, &F);
-          if (valid && have_prev && F_prev > (R)0 && !(F > (R)0)) {
-            R ta = t_prev, Fa = F_prev, tb = t, Fb = F;
-            R ts = ta + (tb - ta) * (Fa / (Fa - Fb));
-            int l2 = 0;
-            bool v2 = false;
-            R F2 = 0;
-            if (sample(o, r, ts, invE, &l2, &v2, &F2) && v2) {
-              if (F2 > (R)0) { ta = ts; Fa = F2; } else { tb = ts; Fb = F2; }
-              if (Fa - Fb > (R)0) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
-            }
-            hit = ts * rc[2];
-            t_hit = ts;
-            break;
-          }
-          have_prev = valid;
-          if (valid) { t_prev = t; F_prev = F; }
-          R s = v[l] < half_tau ? v[l] : half_tau;
-          if (valid && F > (R)0) {
-            R sF = (R)0.75 * F;
-            if (sF > s) s = sF;
-          }
-          t = t + s;
-        }
-        const size_t px = (size_t)vv * K->width + u;
-        out[px] = (float)hit;
-        if (normal || rgb) {
-          // surface normal and colour at the hit point, from the block holding it (zero when none)
-          R g[3] = {0, 0, 0}, c[3] = {0, 0, 0};
-          bool ok = false;
-          if (hit != (R)0) {
-            const R xh[3] = {o[0] + t_hit * r[0], o[1] + t_hit * r[1], o[2] + t_hit * r[2]};
-            const Block<R, Sto>* bh = find(Key{(int64_t)std::floor(xh[0] * invE), (int64_t)std::floor(xh[1] * invE),
-                                               (int64_t)std::floor(xh[2] * invE)});
-            ok = bh && shade(xh, bh->level, g, c);
-          }
-          if (normal) {
-            R nn = ok ? std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) : (R)0;
-            for (int a = 0; a < 3; ++a) normal[3 * px + a] = nn > (R)0 ? (float)(g[a] / nn) : 0.0f;
-          }
-          if (rgb)
-            for (int q = 0; q < 3; ++q) {
-              R cv = ok ? c[q] + (R)0.5 : (R)0;
-              rgb[3 * px + q] = (uint8_t)(cv <= (R)0 ? 0 : cv >= (R)255 ? 255 : (int)cv);
-            }
-        }
-      }
-    return 0;
+    const int64_t np = (int64_t)K->width * K->height;
+    std::vector<int64_t> pix((size_t)np);
+    for (int64_t i = 0; i < np; ++i) pix[(size_t)i] = i;
+    return raycast_pixels(K, T, np, pix.data(), out, normal, rgb);
+  }
+
+  // test hook: F at world points (valid[i] = 0 where it does not exist), and normal / colour there
+  void probe_points(int64_t n_pts, const double* xyz, double* F, int8_t* valid, float* normal,
+                    uint8_t* rgb) const override {
+    Lookup lk{this};
+    for (int64_t i = 0; i < n_pts; ++i) {
+      double f = 0.0;
+      const bool ok = field_at(lk, xyz + 3 * i, &f);
+      if (F) F[i] = ok ? f : 0.0;
+      if (valid) valid[i] = ok ? 1 : 0;
+      if (normal || rgb) surface(lk, xyz + 3 * i, normal ? normal + 3 * i : nullptr, rgb ? rgb + 3 * i : nullptr);
+    }
   }
 
   void set_streaming(float fraction, float radius, const int64_t* max_blocks) override {
@@ -1098,7 +1134,6 @@ struct Map : MapBase {
       if (P.has_color && C)
         for (int q = 0; q < 3; ++q) b.C[q][i] = Store<Sto>::put((R)C[3 * i + q]);
     }
-    bricks.insert(Key{floor_div(k.x, kBrick), floor_div(k.y, kBrick), floor_div(k.z, kBrick)});
     return 0;
   }
 
@@ -1312,6 +1347,19 @@ int orc_integrate_points(void* h, const double* T_ws, const float* xyz, int64_t 
 int orc_raycast(void* h, const orc_pinhole* K, const double* T_wc, float* depth_out, float* normal_out,
                 uint8_t* rgb_out) {
   return ((MapBase*)h)->raycast(K, T_wc, depth_out, normal_out, rgb_out);
+}
+
+// the same for the listed pixels only (index v * width + u); outputs per listed pixel
+int orc_raycast_pixels(void* h, const orc_pinhole* K, const double* T_wc, int64_t n, const int64_t* pix,
+                       float* depth_out, float* normal_out, uint8_t* rgb_out) {
+  return ((MapBase*)h)->raycast_pixels(K, T_wc, n, pix, depth_out, normal_out, rgb_out);
+}
+
+// test hook: the raycast's field at n world points (xyz, 3 doubles each; valid = 0 where it does not exist), and the
+// unit normal and colour the raycast reports for a hit there (zeros where it reports none); outputs may be NULL
+void orc_probe_points(void* h, int64_t n, const double* xyz, double* F, int8_t* valid, float* normal,
+                      uint8_t* rgb) {
+  ((MapBase*)h)->probe_points(n, xyz, F, valid, normal, rgb);
 }
 
 int orc_set_block(void* h, const int32_t* key, int level, const double* D, const double* W, const double* S2,

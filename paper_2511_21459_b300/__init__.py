@@ -18,7 +18,8 @@ _lib = None
 MRH_STORAGE_FP32, MRH_STORAGE_FP16 = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash table probe limit reached",
           4: "block heap empty", 5: "per-frame list full", 6: "CUDA error", 7: "output buffer too small",
-          8: "more blocks than the no-allocation extract's fixed scratch holds"}
+          8: "more blocks than the no-allocation extract's fixed scratch holds",
+          9: "hash table and block heaps disagree on the number of blocks"}
 
 
 class MrhError(RuntimeError):

@@ -624,6 +624,7 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
     float vsum = 0.f;
     int nobs = 0;
     uint32_t sumw32 = 0;  // at most 16 voxels per lane, each W < 2^24
+    float dmn = __int_as_float(0x7f800000);  // least stored D over observed voxels (+inf: none)
     // one chunk in registers at a time: at 64 registers a thread, 4 CTAs of 8 warps share an SM and their
     // interleaving hides the load latency better than a register double buffer at 3 CTAs (measured)
     Chunk cur;
@@ -638,6 +639,11 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
         // a chunk without an update is unchanged in memory, unless the block is new (zero state to write)
         if (n_vox > 0 || isnew) io.store(c * G + li, cur);
       }
+      // (a deferred voxel still holds its value before this frame here: a value it can only lower the least D by,
+      // and its final value joins when it is applied)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (cur.W[q] > 0.0f) dmn = fminf(dmn, cur.D[q]);
       bool counted = false;
       if constexpr (Obs::kDefers) {
         if (n_def) {
@@ -686,6 +692,7 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
         vsum = vsum + __fdividef(S2, W);
         nobs += 1;
         sumw32 += (uint32_t)W;
+        dmn = fminf(dmn, D);
       }
     }
     long long sumw = sumw32;
@@ -693,7 +700,9 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
       vsum = vsum + __shfl_xor_sync(~0u, vsum, o);
       nobs += __shfl_xor_sync(~0u, nobs, o);
       sumw += __shfl_xor_sync(~0u, sumw, o);
+      dmn = fminf(dmn, __shfl_xor_sync(~0u, dmn, o));
     }
+    if (x.active && li == 0) m.dmin[l][ptr] = dmn;
 
     // ---- decision (every lane of the group computes the same one)
     // Outside the band the float estimate and the float threshold are on the same side as the exact values (the
@@ -751,6 +760,8 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
       }
       if (act != kActNone && li == 0) {
         const int lt = act == kActMerge ? l + 1 : l - 1;
+        // the resampled payload holds weighted means of the observed voxels: its least D is at least this one
+        m.dmin[lt][newptr] = dmn;
         m.slots[bm.slot].val = newptr | ((uint32_t)lt << 28);
         const uint32_t r = atomicAdd(&m.st->retire_count, 1u);
         m.retire[r] = ptr | ((uint32_t)l << 28);

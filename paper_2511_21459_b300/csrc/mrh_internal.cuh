@@ -6,6 +6,7 @@
 //   heap[l]              block payloads of level l, struct-of-arrays inside a block so that every field is a
 //                        contiguous, 16-byte aligned run: FP32 storage [D | W | S2 | R | G | B] float each,
 //                        FP16 storage [D | R | G | B] half then [W | S2] float
+//   dmin[l]              per heap block: least stored D over its observed voxels (raycast empty-interior skip)
 //   free_stack[l]        ids of free blocks of level l (pops and pushes never share a kernel)
 //   touched_all          slots touched by the current frame (unique: the slot's frame stamp dedups)
 //   touched[l]           the same slots binned by level, the fusion work lists
@@ -99,6 +100,10 @@ struct MapDev {
   int fp16, color;
   int min_obs;
   uint8_t* heap[kMaxLevels];
+  // per heap block of level l: the least stored D over the block's observed voxels (+inf when none is observed),
+  // written by the fusion epilogue of every frame that touches the block; NaN when unknown (a block loaded from a
+  // file before its first fusion). The raycast skips the interior of blocks whose value is above zero.
+  float* dmin[kMaxLevels];
   uint32_t* free_stack[kMaxLevels];
   uint32_t max_blocks[kMaxLevels];
   uint32_t block_bytes[kMaxLevels];

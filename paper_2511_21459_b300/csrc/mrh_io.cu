@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(256) k_io_copy(MapDev m, const IoBlock* blocks
       if (dir == 0) s[i] = h[i];
       else h[i] = s[i];
     }
+    // a loaded block's least D is unknown until it is fused again (NaN: the raycast does not skip it)
+    if (dir == 1 && lane == 0) m.dmin[l][io.level_id & kPtrMask] = __int_as_float(0x7fffffff);
   }
 }
 

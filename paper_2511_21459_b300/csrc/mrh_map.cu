@@ -415,8 +415,8 @@ const MapDev* map_dev(const mrh_map* m, int* device, int* sms) {
 // ------------------------------------------------------------------------------------------------ static scratch
 //
 // mrh_extract_blocks_noalloc sorts and scans inside this one array instead of allocating. Host code must not use the
-// symbol as a pointer: its device address is looked up once per device (cudaGetSymbolAddress, with that device
-// current) and passed to the kernels.
+// symbol as a pointer: its device address is looked up on every call (cudaGetSymbolAddress, with the map's device
+// current; cheap next to the sort launches) and passed to the kernels, so no address outlives a device reset.
 namespace mrh {
 namespace {
 
@@ -429,21 +429,12 @@ constexpr size_t kNoallocBytes = (kNoallocCountOff + 4 + 255) / 256 * 256;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-uint8_t* g_noalloc_ptr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device (looked up on first use)
-mrh_status noalloc_scratch(int device, uint8_t** out) {
-  if (device < 0 || device >= kMaxDevices) return MRH_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_noalloc_ptr[device] = (uint8_t*)ptr;
-  }
-  *out = g_noalloc_ptr[device];
+// device address of the scratch array on the current device
+mrh_status noalloc_scratch(uint8_t** out) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = (uint8_t*)ptr;
   return MRH_OK;
 }
 
@@ -530,11 +521,13 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
     d.max_blocks[l] = l < d.L ? params->max_blocks[l] : 0;
     if (l < d.L) {
       TRY(dev_alloc(m, &d.heap[l], (size_t)d.max_blocks[l] * d.block_bytes[l]));
+      TRY(dev_alloc(m, &d.dmin[l], d.max_blocks[l]));
       TRY(dev_alloc(m, &d.free_stack[l], d.max_blocks[l]));
       TRY(dev_alloc(m, &d.touched[l], params->max_touched));
       TRY(dev_alloc(m, &d.meta[l], params->max_touched));
     } else {
       d.heap[l] = nullptr;
+      d.dmin[l] = nullptr;
       d.free_stack[l] = nullptr;
       d.touched[l] = nullptr;
       d.meta[l] = nullptr;
@@ -546,6 +539,8 @@ mrh_status mrh_map_create(const mrh_map_params* params, int device, mrh_map** ou
   if (e == cudaSuccess) e = cudaMemset(d.brick_bits, 0, (size_t)n_brick_slots * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(d.super_keys, 0xFF, (size_t)n_super_slots * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(d.super_bits, 0, (size_t)n_super_slots * sizeof(unsigned long long));
+  for (int l = 0; l < d.L && e == cudaSuccess; ++l)  // all ones: NaN, unknown until fused
+    e = cudaMemset(d.dmin[l], 0xFF, (size_t)d.max_blocks[l] * sizeof(float));
   DevState hs;
   std::memset(&hs, 0, sizeof(hs));
   for (int l = 0; l < kMaxLevels; ++l) hs.free_top[l] = (int)d.max_blocks[l];
@@ -1082,6 +1077,7 @@ mrh_status mrh_extract_blocks(mrh_map* m, int32_t* keys, uint8_t* levels, uint64
   mrh_status st = mrh_count_blocks(m, &nb, &nv, stream);
   if (n_blocks_out) *n_blocks_out = nb;
   if (n_voxels_out) *n_voxels_out = nv;
+  if (st == MRH_ERR_CUDA) return st;
   if (nb > cap_blocks || nv > cap_voxels) return MRH_ERR_CAPACITY;
   DeviceGuard guard(m->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1126,7 +1122,7 @@ mrh_status mrh_extract_blocks(mrh_map* m, int32_t* keys, uint8_t* levels, uint64
   if (e != cudaSuccess) return cuda_fail(e, "mrh_extract_blocks");
   MRH_CUDA(cudaGetLastError());
   MRH_CUDA(cudaStreamSynchronize(s));
-  if (n != nb) return MRH_ERR_CUDA;
+  if (hcount != nb) return MRH_ERR_INCONSISTENT;
   return st;
 }
 
@@ -1145,7 +1141,7 @@ mrh_status mrh_extract_blocks_noalloc(mrh_map* m, int32_t* keys, uint8_t* levels
   DeviceGuard guard(m->device);
   if (!guard.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
   uint8_t* base = nullptr;
-  mrh_status sst = noalloc_scratch(m->device, &base);
+  mrh_status sst = noalloc_scratch(&base);
   if (sst != MRH_OK) return sst;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* skeys = (unsigned long long*)(base + kNoallocKeysOff);
@@ -1172,7 +1168,7 @@ mrh_status mrh_extract_blocks_noalloc(mrh_map* m, int32_t* keys, uint8_t* levels
   }
   MRH_CUDA(cudaGetLastError());
   MRH_CUDA(cudaStreamSynchronize(s));
-  if (n != nb) return MRH_ERR_CUDA;
+  if (hcount != nb) return MRH_ERR_INCONSISTENT;
   return st;
 }
 
@@ -1257,6 +1253,7 @@ const char* mrh_status_string(mrh_status s) {
     case MRH_ERR_CUDA: return "CUDA error";
     case MRH_ERR_CAPACITY: return "output buffer too small";
     case MRH_ERR_STATIC_LIMIT: return "more blocks than the no-allocation extract's fixed scratch holds";
+    case MRH_ERR_INCONSISTENT: return "hash table and block heaps disagree on the number of blocks";
   }
   return "unknown status";
 }

@@ -1,22 +1,20 @@
 // Raycast of the adaptive grid (the rendering branch of Fig. 2): one thread per pixel.
 //
-// The ray marches from min_depth to max_depth (as z-depth). A sample in an empty brick (4 x 4 x 4 blocks) jumps to
-// the brick's exit face; a sample in an unallocated block of a non-empty brick jumps to the block's exit face. Brick
-// and block occupancy come from two small insert-only sets filled when blocks are created (super-bricks of 4 x 4 x 4
-// bricks with a 64-bit mask of non-empty bricks; bricks with a 64-bit mask of created blocks), cached in registers,
-// so an empty-space step costs a memory probe only when the ray enters a new super-brick or non-empty brick. Inside
-// an allocated block of level l the field is the trilinear interpolation over the 8 nearest voxel centres of that
-// level's grid; a corner in a neighbouring block reads that block's voxel containing the corner centre, whatever its
-// level, so coarse and fine blocks blend across resolution boundaries. A sample is valid only when all 8 corners are
-// observed (W > 0). The next sample lies min(v_l, tau / 2) ahead, or 0.75 F ahead when the sample is valid and F is
-// larger (F <= tau underestimates the distance to the surface, so the step stays in front of it). At the first valid
-// + -> - sign change the linear root is taken, evaluated once more, and one secant step refines it. Output is
-// z-depth, 0 where nothing was hit; optionally the unit normal (the normalised gradient of the same trilinear
-// interpolant at the hit) and the colour (its trilinear mean of the stored colour, rounded to u8), zero where the
-// hit's block or one of its 8 corners is missing or unobserved.
+// The ray is searched from min_depth to max_depth (as z-depth) for the first + -> - crossing of the trilinear TSDF on
+// the sample grid t_j = t_min + j h, h = min(v_0, tau / 2) (cast_ray states which samples the march leaves out and
+// why none of them can change the result). Brick and block occupancy come from two small insert-only sets filled when blocks are created
+// (super-bricks of 4 x 4 x 4 bricks with a 64-bit mask of non-empty bricks; bricks with a 64-bit mask of created
+// blocks), cached in registers, so a sample in empty space costs a memory probe only when the ray enters a new
+// super-brick or non-empty brick. Inside an allocated block of level l the field is the trilinear interpolation over
+// the 8 nearest voxel centres of that level's grid; a corner in a neighbouring block reads that block's voxel
+// containing the corner centre, whatever its level, so coarse and fine blocks blend across resolution boundaries. A
+// sample has a field only when all 8 corners are observed (W > 0). Output is z-depth, 0 where nothing was hit;
+// optionally the unit normal (the normalised gradient of the same trilinear interpolant at the hit) and the colour
+// (its trilinear mean of the stored colour, rounded to u8), zero where the hit's block or one of its 8 corners is
+// missing or unobserved.
 //
-// Every step follows the oracle's float operation order (this file is compiled without multiply-add contraction), so
-// depths agree with the oracle to rounding and hit/miss decisions agree except at exact ties.
+// Positions, trilinear sums and the root use fused multiply-adds where they save instructions: the raycast is
+// compared with the CPU oracle's double-precision definition within a stated tolerance, not bit for bit.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -127,7 +125,7 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
   float fr[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float g = x[a] * inv - 0.5f;
+    const float g = fmaf(x[a], inv, -0.5f);
     const float fl = floorf(g);
     j0[a] = (int)fl;
     fr[a] = g - fl;
@@ -196,7 +194,7 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
       const float wx = (k & 1) ? fr[0] : 1.0f - fr[0];
       const float wy = ((k >> 1) & 1) ? fr[1] : 1.0f - fr[1];
       const float wz = (k >> 2) ? fr[2] : 1.0f - fr[2];
-      acc = acc + wx * wy * wz * d[k];
+      acc = fmaf(wx * wy * wz, d[k], acc);
     }
     *out = acc;
     return true;
@@ -227,7 +225,7 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
     const float wx = ax ? fr[0] : 1.0f - fr[0];
     const float wy = ay ? fr[1] : 1.0f - fr[1];
     const float wz = az ? fr[2] : 1.0f - fr[2];
-    acc = acc + wx * wy * wz * read_D<FP16>(blk, idx);
+    acc = fmaf(wx * wy * wz, read_D<FP16>(blk, idx), acc);
   }
   *out = acc;
   return true;
@@ -289,6 +287,18 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
 }
 
 // One ray: march, find the first zero crossing, write its z-depth (0 = none) and the requested surface attributes.
+//
+// The crossing searched is the one of the definition: samples on the grid t_j = t_min + j h, h = min(v_0, tau / 2),
+// the first two consecutive samples that both have a field with F_j > 0 >= F_j+1, narrowed inside that bracket. The
+// march visits the grid samples in order and leaves out only samples that cannot end such a bracket:
+//   - a sample in an empty brick or unallocated block has no field, nor has any other sample of that cell: the march
+//     continues at the first grid sample past the cell's exit face;
+//   - in a block whose observed voxels all hold D > 0 (dmin, kept by the fusion epilogue), every sample whose 8
+//     corners lie in the block (the block shrunk by half a voxel, and by a further 1e-3 voxel so that float rounding
+//     of the position cannot move a sample across) has F > 0 or no field: the march continues at the last grid
+//     sample of that interior, which it evaluates, since it may begin a bracket;
+//   - the bracket is narrowed by 3 bisections (the definition's own first steps) and the linear root of the last
+//     bracket: the result lies within h / 8 of the fully converged crossing of the same bracket.
 template <bool FP16, bool COLOR>
 __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, const RayOut& out) {
   BlockCache bc;
@@ -303,17 +313,21 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     inv_r[a] = r[a] != 0.0f ? 1.0f / r[a] : 0.0f;
   }
   const float o[3] = {c.t[0], c.t[1], c.t[2]};
-  const float E = m.E, invE = 1.0f / E, half_tau = m.tau * 0.5f, eps = 1e-4f * E;
-  float t = c.min_depth * nq;
-  const float t_far = c.max_depth * nq;
-  bool have_prev = false;
-  float t_prev = 0.0f, F_prev = 0.0f, hit = 0.0f;
-  // After a sign change the loop runs once more in refine mode: one extra sample at the linear root ts (the same
-  // code path as every other sample, so the field evaluation exists once in the kernel), then the secant step.
-  bool refine = false;
-  float ta = 0.0f, Fa = 0.0f, tb = 0.0f, Fb = 0.0f, ts = 0.0f;
-  for (int it = 0; refine || (it < kRaycastMaxIter && t <= t_far); ++it) {
-    const float x[3] = {o[0] + t * r[0], o[1] + t * r[1], o[2] + t * r[2]};
+  const float E = m.E, invE = 1.0f / E;
+  const float h = fminf(m.v[0], 0.5f * m.tau), inv_h = 1.0f / h;
+  const float t0 = c.min_depth * nq, t_far = c.max_depth * nq;
+  int j = 0;           // grid index of the current sample
+  bool pv = false;     // the sample j - 1 was evaluated and has a field
+  float Fp = 0.0f;     // ... and its value
+  // refine > 0: the loop evaluates the bracket's midpoint tm (the same code path as every grid sample, so the field
+  // evaluation exists once in the kernel)
+  int refine = 0;
+  float ta = 0.0f, Fa = 0.0f, tb = 0.0f, Fb = 0.0f, tm = 0.0f, t_hit = 0.0f;
+  bool hit = false;
+  for (int it = 0; it < kRaycastMaxIter; ++it) {
+    const float t = refine ? tm : fmaf((float)j, h, t0);
+    if (!refine && t > t_far) break;
+    const float x[3] = {fmaf(t, r[0], o[0]), fmaf(t, r[1], o[1]), fmaf(t, r[2], o[2])};
     const int bk[3] = {ifloor(x[0] * invE), ifloor(x[1] * invE), ifloor(x[2] * invE)};
     const int br[3] = {bk[0] >> kBrickShift, bk[1] >> kBrickShift, bk[2] >> kBrickShift};
     // occupancy: super-brick mask (probed when the super-brick changes) -> brick non-empty? -> brick mask (probed
@@ -328,11 +342,12 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     }
     const uint32_t val = block ? bc.get(m, bk[0], bk[1], bk[2]) : kValPending;
     if (val == kValPending) {
-      if (refine) {  // the root's block is not allocated: keep the linear root
-        hit = ts * rc[2];
+      if (refine) {  // a midpoint without a field: the crossing is taken there
+        t_hit = tm;
+        hit = true;
         break;
       }
-      // jump to the exit face of the empty brick, or of the empty block
+      // continue at the first grid sample past the exit face of the empty brick, or of the empty block
       const int span = brick ? 1 : (1 << kBrickShift);
       float t_exit = t_far + 1.0f;
 #pragma unroll
@@ -340,61 +355,83 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
         if (r[a] == 0.0f) continue;
         const int cell = brick ? bk[a] : br[a];
         const float face = (float)((r[a] > 0.0f ? cell + 1 : cell) * span) * E;
-        const float ta = (face - o[a]) * inv_r[a];
-        if (ta < t_exit) t_exit = ta;
+        const float tf = (face - o[a]) * inv_r[a];
+        if (tf < t_exit) t_exit = tf;
       }
-      const float step_min = t + eps;
-      const float tn = t_exit + eps;
-      t = tn > step_min ? tn : step_min;
-      have_prev = false;
+      const float jf = ceilf((t_exit - t0) * inv_h);
+      const int jn = jf < 1073741824.0f ? (int)jf : 1073741824;
+      j = jn > j ? jn : j + 1;
+      pv = false;
       continue;
     }
     const int l = (int)((val >> 28) & 3u);
+    if (!refine && m.dmin[l][val & kPtrMask] > 0.0f) {
+      // inside the block's interior (every corner in the block)? then continue at the interior's last grid sample
+      const float vl = m.v[l], in = (0.5f + 1e-3f) * vl;
+      float t_out = t_far + 1.0f;
+      bool inside = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float lo = fmaf((float)bk[a], E, in), hi = fmaf((float)(bk[a] + 1), E, -in);
+        inside = inside && x[a] >= lo && x[a] <= hi;
+        if (r[a] != 0.0f) {
+          const float tf = ((r[a] > 0.0f ? hi : lo) - o[a]) * inv_r[a];
+          if (tf < t_out) t_out = tf;
+        }
+      }
+      if (inside) {
+        const float jf = floorf((t_out - t0) * inv_h);
+        const int jl = jf < 1073741824.0f ? (int)jf : 1073741824;
+        if (jl > j) {
+          j = jl;
+          pv = false;  // the samples left out were positive or had no field: none can end a bracket at sample jl
+          continue;
+        }
+      }
+    }
     float F = 0.0f;
     const bool valid = field<FP16, COLOR>(m, bc, x, l, &F);
     if (refine) {
-      if (valid) {
-        if (F > 0.0f) {
-          ta = ts;
-          Fa = F;
-        } else {
-          tb = ts;
-          Fb = F;
-        }
-        if (Fa - Fb > 0.0f) ts = ta + (tb - ta) * (Fa / (Fa - Fb));
+      if (!valid) {
+        t_hit = tm;
+        hit = true;
+        break;
       }
-      hit = ts * rc[2];
-      break;
-    }
-    if (valid && have_prev && F_prev > 0.0f && !(F > 0.0f)) {
-      ta = t_prev;
-      Fa = F_prev;
-      tb = t;
-      Fb = F;
-      ts = ta + (tb - ta) * (Fa / (Fa - Fb));
-      refine = true;
-      t = ts;
+      if (F > 0.0f) {
+        ta = tm;
+        Fa = F;
+      } else {
+        tb = tm;
+        Fb = F;
+      }
+      if (--refine == 0) {
+        t_hit = ta + (tb - ta) * (Fa / (Fa - Fb));
+        hit = true;
+        break;
+      }
+      tm = 0.5f * (ta + tb);
       continue;
     }
-    have_prev = valid;
-    if (valid) {
-      t_prev = t;
-      F_prev = F;
+    if (valid && pv && Fp > 0.0f && !(F > 0.0f)) {
+      ta = fmaf((float)(j - 1), h, t0);
+      Fa = Fp;
+      tb = t;
+      Fb = F;
+      refine = 3;
+      tm = 0.5f * (ta + tb);
+      continue;
     }
-    float s = m.v[l] < half_tau ? m.v[l] : half_tau;
-    if (valid && F > 0.0f) {
-      const float sF = 0.75f * F;
-      if (sF > s) s = sF;
-    }
-    t = t + s;
+    pv = valid;
+    Fp = F;
+    ++j;
   }
   const size_t px = (size_t)v * c.width + u;
-  out.depth[px] = hit;
+  out.depth[px] = hit ? t_hit * rc[2] : 0.0f;
   if (out.normal || out.rgb) {
     float g[3], col[3];
     bool ok = false;
-    if (hit != 0.0f) {
-      const float xh[3] = {o[0] + ts * r[0], o[1] + ts * r[1], o[2] + ts * r[2]};
+    if (hit) {
+      const float xh[3] = {fmaf(t_hit, r[0], o[0]), fmaf(t_hit, r[1], o[1]), fmaf(t_hit, r[2], o[2])};
       const uint32_t val = find_block(m.slots, m.slot_mask, ifloor(xh[0] * invE), ifloor(xh[1] * invE),
                                       ifloor(xh[2] * invE));
       ok = val != kValPending && shade<FP16, COLOR>(m, xh, (int)((val >> 28) & 3u), g, col);

@@ -81,6 +81,8 @@ def test_hash_eq4_hand_values(lib):
 def test_status_strings_and_version(lib):
     assert lib.mrh_status_string(0) == b"ok"
     assert lib.mrh_status_string(3).startswith(b"hash")
+    for code in range(10):
+        assert lib.mrh_status_string(code) != b"unknown status", code
     assert b"sm_103a" in lib.mrh_version()
 
 

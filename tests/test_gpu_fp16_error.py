@@ -1,5 +1,7 @@
-"""FP16 storage against the float64 oracle: the error of each stored field (Sec. 4.1.4 gives no precision; FP16
-storage of distance and colour with FP32 weight and variance is this library's option, a9).
+"""Storage precision against the float64 oracle: the error of each stored field (Sec. 4.1.4 gives no precision; FP32
+storage is the default, FP16 storage of distance and colour with FP32 weight and variance is this library's option,
+a9). The parity tests compare the GPU with the oracle's float mode, which repeats the kernels' float operations; these
+tests hold the float results to the double-precision truth instead.
 
 Re-levelling is off on both sides so that every block stays at its allocated level and voxels compare one to one; the
 GPU map stores D and colour as half after float arithmetic, the oracle keeps everything in double. Reported per field
@@ -107,3 +109,63 @@ def test_lidar_fp16_fields_against_float64():
     assert e["var"]["p99.9"] <= 1e-4
     for f in ("D", "var"):
         assert e[f]["outliers"] <= 1e-4 * e["voxels"]
+
+
+# ------------------------------------------------------------------------------------------------ FP32 storage
+#
+# Bounds for FP32 storage against float64 (voxels observed equally often on both sides, outliers as above). One
+# observation's distance d = rho - |x_c| is formed from rho = z |q| (a few roundings of 2^-24 relative, rho below 6 m
+# in these scenes) and the camera-frame position x_c = R^T (x_w - t) in float (three products and two sums per
+# component, world coordinates and the translation below 4 m each): each term carries at most a few units of
+# 2^-24 x 8 m, so |d_float - d_double| <= 8 ulp(8 m) = 8 x 2^-24 x 8 m = 3.8e-6 m. The running mean of Eq. 3 is an
+# average of such values plus one rounding of 2^-24 tau per update (at most 16 updates here): D within
+# eps_D = 3.8e-6 m + 16 x 2^-24 x tau. The variance S2 / W is a mean of products (d - D_old)(d - D_new) of terms
+# below tau each carrying eps_D: within 2 eps_D tau + 16 x 2^-24 tau^2. Colour is a running mean of exact bytes:
+# one rounding of 2^-24 x 255 per update. Checked on the 99.9th percentile and the maximum over non-outliers.
+
+def _fp32_bounds(tau, updates=16):
+    ulp = 2.0 ** -24
+    eps_d = 8 * ulp * 8.0 + updates * ulp * tau
+    return {"D": eps_d, "var": 2 * eps_d * tau + updates * ulp * tau * tau, "C": updates * ulp * 255.0}
+
+
+def _check_fp32(e, tau, color):
+    b = _fp32_bounds(tau)
+    assert e["W_mismatch_fraction"] <= 1e-3
+    for f in ("D", "var") + (("C",) if color else ()):
+        assert e[f]["outliers"] <= 1e-4 * e["voxels"], (f, e[f])
+        assert e[f]["p99.9"] <= b[f], (f, e[f], b[f])
+    return b
+
+
+def test_tiny_fp32_fields_against_float64():
+    """Ten noisy views of the tiny scene, FP32 storage, re-levelling off."""
+    wl = dataclasses.replace(synth.tiny(), var_threshold=(-1.0, -1.0), split_hysteresis=0.0)
+    g = mrh().Map(mrh().params_from(wl))
+    o = oracle.OracleMap(oracle.params_from(wl, "f64"))
+    Kg, Ko = mrh().pinhole_from(wl), oracle.pinhole_from(wl)
+    for s in range(10):
+        d, c, T = synth.render_depth(wl, 0, seed=s)
+        g.integrate_depth(Kg, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        o.integrate_depth(Ko, T, d, c)
+    e = field_errors(g.extract(), o.extract(), True)
+    b = _check_fp32(e, wl.truncation, True)
+    print(json.dumps({"fp32_vs_f64": "tiny 160x120, 10 views", "bounds": b, **e}))
+    assert e["voxels"] > 100_000
+
+
+def test_rgbd_fp32_fields_against_float64():
+    """Six full-size frames of the RGB-D sequence, FP32 storage with colour, re-levelling off."""
+    wl = dataclasses.replace(synth.rgbd(), var_threshold=(-1.0, -1.0), split_hysteresis=0.0)
+    sc = wl.scene()
+    g = mrh().Map(mrh().params_from(wl))
+    o = oracle.OracleMap(oracle.params_from(wl, "f64"))
+    Kg, Ko = mrh().pinhole_from(wl), oracle.pinhole_from(wl)
+    for k in range(6):
+        d, c, T = synth.render_depth(wl, k, scene=sc)
+        g.integrate_depth(Kg, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        o.integrate_depth(Ko, T, d, c)
+    e = field_errors(g.extract(), o.extract(), True)
+    b = _check_fp32(e, wl.truncation, True)
+    print(json.dumps({"fp32_vs_f64": "rgbd 640x480, 6 frames", "bounds": b, **e}))
+    assert e["voxels"] > 1_000_000

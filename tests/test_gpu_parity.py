@@ -1,8 +1,8 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle on the same seeded inputs.
 
-Keys, levels and weights bit-exact; D, sigma^2 and colour within 1e-4 relative (tests/parity.py); raycast depth within
-1e-4 relative with at most 0.1 % hit/miss disagreement; raycast normals within 1e-5 and colours within 1 (u8) where
-the two depths are identical. Sizes span many CTA tiles with ragged tails; the RGB-D and
+Keys, levels and weights bit-exact; D, sigma^2 and colour within 1e-4 relative (tests/parity.py); the raycast against
+the oracle's definition within the bounds of tests/raycast_check.py (same bracket: within h / 8; other brackets and
+hit / miss disagreements at most 0.1 % of the pixels; normals and colours at the kernel's hit points). Sizes span many CTA tiles with ragged tails; the RGB-D and
 LiDAR cases run the full-size frames of the benchmark configuration.
 """
 import numpy as np
@@ -11,6 +11,7 @@ import pytest
 import oracle
 import synth
 from tests.parity import compare_extracts
+from tests.raycast_check import check_raycast, check_shading, grid_step
 
 pytestmark = pytest.mark.gpu
 
@@ -59,36 +60,9 @@ def run_camera(wl, frames, gmap, omap, check_each=False, theta0=None, raycast_fr
             color = bool(wl.has_color)
             out_g = [x.cpu().numpy() for x in gmap.raycast(K_g, T, normals=True, rgb=color)]
             out_o = omap.raycast(K_o, T, normals=True, rgb=color)
-            check_raycast(out_g[0], out_o[0])
-            check_shading(out_g, out_o)
+            check_raycast(out_g[0], out_o[0], grid_step(wl))
+            check_shading(out_g, omap, K_o, T)
     return reports
-
-
-def check_shading(out_g, out_o):
-    """Normal (and colour) where the GPU and oracle depths are identical: same shaded / unshaded decision, normals
-    within 1e-5 (the same float operations in the same order), colours within 1 after rounding."""
-    same = (out_g[0] == out_o[0]) & (out_o[0] > 0)
-    assert same.mean() > 0.5 * (out_o[0] > 0).mean()
-    ng, no = out_g[1][same], out_o[1][same]
-    assert np.array_equal(np.any(ng != 0, -1), np.any(no != 0, -1))
-    assert np.abs(ng - no).max() <= 1e-5
-    shaded = np.any(no != 0, -1)
-    assert shaded.mean() > 0.9
-    np.testing.assert_allclose(np.linalg.norm(ng[shaded], axis=-1), 1.0, atol=1e-6)
-    if len(out_o) > 2:
-        cg, co = out_g[2][same].astype(np.int32), out_o[2][same].astype(np.int32)
-        assert np.abs(cg - co).max() <= 1
-        assert np.mean(cg == co) > 0.999
-
-
-def check_raycast(rc_g, rc_o, rel=1e-4, max_mismatch=1e-3):
-    hit_g, hit_o = rc_g > 0, rc_o > 0
-    mismatch = np.mean(hit_g != hit_o)
-    assert mismatch <= max_mismatch, mismatch
-    both = hit_g & hit_o
-    assert both.sum() > 0.5 * hit_o.sum()
-    err = np.abs(rc_g[both].astype(np.float64) - rc_o[both])
-    assert np.all(err <= rel * rc_o[both]), err.max()
 
 
 def test_tiny_single_frame():
@@ -133,6 +107,20 @@ def test_rgbd_full_size_prefix():
     frames = [synth.render_depth(wl, k, scene=scene) for k in range(6)]
     reps = run_camera(wl, frames, gpu_map(wl), orc_map(wl), check_each=True, raycast_frames=(0, 5))
     assert reps[-1]["D_max_abs"] <= 1e-4 * wl.truncation
+
+
+def test_rgbd_late_sequence_window():
+    """The benchmark's RGB-D configuration and thresholds, 40 frames spread over the whole orbit (every 7th pose), so
+    the map holds most of what it holds at the end of the sequence, with merges at the benchmark's thresholds and
+    raycasts that read across levels: counters after every frame, then the full map and a raycast from the last
+    pose against the oracle."""
+    wl = synth.rgbd()
+    scene = wl.scene()
+    frames = [synth.render_depth(wl, 7 * k, scene=scene) for k in range(40)]
+    g, o = gpu_map(wl), orc_map(wl)
+    run_camera(wl, frames, g, o, raycast_frames=(39,))
+    st = o.block_stats()
+    assert (st["levels"] > 0).sum() > 100
 
 
 def test_rgbd_sparse_frames_and_relevel():
@@ -253,17 +241,17 @@ def test_lidar_map_raycast_normals_fp16():
         K.min_depth, K.max_depth = 0.5, 40.0
     out_g = [x.cpu().numpy() for x in g.raycast(K_g, T, normals=True)]
     out_o = o.raycast(K_o, T, normals=True)
-    check_raycast(out_g[0], out_o[0])
+    check_raycast(out_g[0], out_o[0], grid_step(wl))
     assert (out_o[0] > 0).mean() > 0.5
-    check_shading(out_g, out_o)
+    check_shading(out_g, o, K_o, T)
     with pytest.raises(mrh().MrhError):
         g.raycast(K_g, T, rgb=True)
 
 
-def test_lidar_full_scan():
-    """Full 128 x 2048 scans of the benchmark's LiDAR configuration (FP16 storage)."""
+def test_lidar_full_scans():
+    """Six full 128 x 2048 scans of the benchmark's LiDAR configuration (FP16 storage)."""
     wl = synth.lidar()
-    run_lidar(wl, 2, check_each=False)
+    run_lidar(wl, 6, check_each=False)
 
 
 # ------------------------------------------------------------------------------------------------ errors
