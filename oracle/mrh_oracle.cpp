@@ -869,9 +869,11 @@ struct Map : MapBase {
   // and the 8 voxel centres of that block's level nearest to x are all observed (W > 0); a corner is read from the
   // block holding the corner centre, from that block's voxel containing it, whatever the block's level. Everything
   // here is double arithmetic on the stored values, in both modes.
-  // Search: the grid t_j = t_min + j h, with h = min(v_0, tau / 2) (the sampling step of the finest level). The first
-  // two consecutive grid samples that both have a field, with F_j > 0 >= F_{j+1}, bracket the crossing; bisection
-  // narrows the bracket below 1e-9 m and the crossing is the linear root of the last bracket (a midpoint without a
+  // Search: samples on the grid t_j = t_min + j h, with h = min(v_0, tau / 2) (the sampling step of the finest
+  // level). A level-l block is sampled at its own voxel pitch, min(v_l, tau / 2): every 2^l-th grid sample from its
+  // first one, and the first grid sample past its exit face follows in any case. Two consecutive samples that both
+  // have a field, with F > 0 at the first and F <= 0 at the second, bracket the crossing; the first such bracket is
+  // narrowed by bisection below 1e-9 m and the crossing is the linear root of the last bracket (a midpoint without a
   // field ends the bisection at that midpoint). A grid sample in an unallocated block has no field, and neither has
   // any other sample of that block, so the search continues at the first grid sample past the block's exit face.
   // Output z-depth, 0 where there is no crossing; optionally the normal and colour at the crossing (shade_at()).
@@ -1034,6 +1036,7 @@ struct Map : MapBase {
         have_prev = false;
         continue;
       }
+      const Block<R, Sto>* blk = lk.get(bk);
       double F = 0.0;
       const bool valid = field_at(lk, x, &F);
       if (valid && have_prev && F_prev > 0.0 && !(F > 0.0)) {
@@ -1056,6 +1059,20 @@ struct Map : MapBase {
       have_prev = valid;
       t_prev = t;
       F_prev = F;
+      if (blk->level > 0) {
+        // a level-l block is sampled every 2^l grid steps (its own voxel pitch), counted from its first sample; the
+        // first sample past its exit face is taken in any case
+        double t_exit = t_max + 1.0;
+        for (int a = 0; a < 3; ++a) {
+          if (r[a] == 0.0) continue;
+          const double face = (double)(r[a] > 0.0 ? (&bk.x)[a] + 1 : (&bk.x)[a]) * E;
+          t_exit = std::min(t_exit, (face - o[a]) / r[a]);
+        }
+        const int64_t jn = (int64_t)std::ceil((t_exit - t_min) / h);
+        const int64_t step = std::min((int64_t)1 << blk->level, jn > j ? jn - j : (int64_t)1);
+        j += step;
+        continue;
+      }
       ++j;
     }
   }

@@ -291,14 +291,17 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
 // The crossing searched is the one of the definition: samples on the grid t_j = t_min + j h, h = min(v_0, tau / 2),
 // the first two consecutive samples that both have a field with F_j > 0 >= F_j+1, narrowed inside that bracket. The
 // march visits the grid samples in order and leaves out only samples that cannot end such a bracket:
+//   - a level-l block is sampled at its own voxel pitch (the definition's min(v_l, tau / 2)): every 2^l-th grid sample
+//     from its first one, then the first grid sample past its exit face;
 //   - a sample in an empty brick or unallocated block has no field, nor has any other sample of that cell: the march
 //     continues at the first grid sample past the cell's exit face;
 //   - in a block whose observed voxels all hold D > 0 (dmin, kept by the fusion epilogue), every sample whose 8
 //     corners lie in the block (the block shrunk by half a voxel, and by a further 1e-3 voxel so that float rounding
 //     of the position cannot move a sample across) has F > 0 or no field: the march continues at the last grid
-//     sample of that interior, which it evaluates, since it may begin a bracket;
-//   - the bracket is narrowed by 3 bisections (the definition's own first steps) and the linear root of the last
-//     bracket: the result lies within h / 8 of the fully converged crossing of the same bracket.
+//     sample of that interior (of the block's pitch), which it evaluates, since it may begin a bracket;
+//   - the bracket (1 to 4 grid steps wide) is narrowed by bisections (the definition's own first steps) down to h / 8
+//     and the linear root of the last bracket: the result lies within h / 8 of the fully converged crossing of the
+//     same bracket.
 template <bool FP16, bool COLOR>
 __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v, const RayOut& out) {
   BlockCache bc;
@@ -317,8 +320,11 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
   const float h = fminf(m.v[0], 0.5f * m.tau), inv_h = 1.0f / h;
   const float t0 = c.min_depth * nq, t_far = c.max_depth * nq;
   int j = 0;           // grid index of the current sample
-  bool pv = false;     // the sample j - 1 was evaluated and has a field
-  float Fp = 0.0f;     // ... and its value
+  bool pv = false;     // the previous sample (index jp, parameter tp) was evaluated, with nothing skipped since, and
+  float Fp = 0.0f;     // has a field of value Fp
+  int jp = 0;
+  float tp = 0.0f;
+  int cb0 = 0x7FFFFFFF, cb1 = 0, cb2 = 0, jb = 0;  // the allocated block of the last sample and its first sample
   // refine > 0: the loop evaluates the bracket's midpoint tm (the same code path as every grid sample, so the field
   // evaluation exists once in the kernel)
   int refine = 0;
@@ -365,6 +371,12 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       continue;
     }
     const int l = (int)((val >> 28) & 3u);
+    if (!refine && (bk[0] != cb0 || bk[1] != cb1 || bk[2] != cb2)) {
+      cb0 = bk[0];
+      cb1 = bk[1];
+      cb2 = bk[2];
+      jb = j;
+    }
     if (!refine && m.dmin[l][val & kPtrMask] > 0.0f) {
       // inside the block's interior (every corner in the block)? then continue at the interior's last grid sample
       const float vl = m.v[l], in = (0.5f + 1e-3f) * vl;
@@ -381,7 +393,8 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       }
       if (inside) {
         const float jf = floorf((t_out - t0) * inv_h);
-        const int jl = jf < 1073741824.0f ? (int)jf : 1073741824;
+        int jl = jf < 1073741824.0f ? (int)jf : 1073741824;
+        jl = jb + (((jl - jb) >> l) << l);  // a sample of the block's pitch
         if (jl > j) {
           j = jl;
           pv = false;  // the samples left out were positive or had no field: none can end a bracket at sample jl
@@ -413,17 +426,35 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       continue;
     }
     if (valid && pv && Fp > 0.0f && !(F > 0.0f)) {
-      ta = fmaf((float)(j - 1), h, t0);
+      ta = tp;
       Fa = Fp;
       tb = t;
       Fb = F;
-      refine = 3;
+      const int steps = j - jp;  // bisections down to h / 8
+      refine = 3 + (steps > 1 ? 1 : 0) + (steps > 2 ? 1 : 0);
       tm = 0.5f * (ta + tb);
       continue;
     }
     pv = valid;
     Fp = F;
-    ++j;
+    jp = j;
+    tp = t;
+    int step = 1;
+    if (l > 0) {
+      // the block's pitch, but not past the first grid sample beyond its exit face
+      float t_exit = t_far + 1.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (r[a] == 0.0f) continue;
+        const float face = (float)(r[a] > 0.0f ? bk[a] + 1 : bk[a]) * E;
+        const float tf = (face - o[a]) * inv_r[a];
+        if (tf < t_exit) t_exit = tf;
+      }
+      const float jf = ceilf((t_exit - t0) * inv_h);
+      const int jn = jf < 1073741824.0f ? (int)jf : 1073741824;
+      step = min(1 << l, jn > j ? jn - j : 1);
+    }
+    j += step;
   }
   const size_t px = (size_t)v * c.width + u;
   out.depth[px] = hit ? t_hit * rc[2] : 0.0f;

@@ -1,6 +1,7 @@
 """Pins for the raycast's search (the rendering branch of Fig. 2; the paper gives no raycaster, so the definition is a
 reading): the first +/- crossing of the trilinear TSDF along the pixel ray, found on the grid t_j = t_min + j h
-(h = min(v_0, tau / 2)), then narrowed to convergence.
+(h = min(v_0, tau / 2); a level-l block sampled every 2^l grid steps from its first sample), then narrowed to
+convergence.
 
 What pins the search independently of the oracle's own march:
 - isolated negative voxels ("pockets") in front of a wall: on a ray through a pocket's voxel centre along an axis the
@@ -181,6 +182,7 @@ def check_brute_force(m, K, T, n_pix=500, seed=3):
 
 def _fused_tiny(precision="f32s", frames=4):
     wl = synth.tiny()
+    wl.var_threshold = (-1.0,)  # every block stays at level 0: the brute force samples every grid point
     m = oracle.OracleMap(oracle.params_from(wl, precision))
     K = oracle.pinhole_from(wl)
     for s in range(frames):
@@ -204,11 +206,71 @@ def test_brute_force_search_on_a_fused_frame_from_another_pose(precision):
     assert hits > 300
 
 
+def brute_force_levels(m, K, T, pix, h, E, levels):
+    """The same brute force on a map with coarse blocks: every grid sample is classified by its block (dict of key ->
+    level); a level-l block's samples are those 2^l apart from its first grid sample; samples without a block break
+    the chain of consecutive samples."""
+    nq, rc, r = _rays(K, T, pix)
+    o = T[:3, 3]
+    out = []
+    for i in range(pix.size):
+        t_min = np.float64(np.float32(K.min_depth)) * nq[i]
+        t_max = np.float64(np.float32(K.max_depth)) * nq[i]
+        j = np.arange(int((t_max - t_min) / h) + 2)
+        t = t_min + j.astype(np.float64) * h
+        t = t[t <= t_max]
+        x = np.stack([o[a] + t * r[i, a] for a in range(3)], -1)
+        keys = np.floor(x / E).astype(np.int64)
+        F, ok, _, _ = m.probe(x)
+        found, prev, first = None, None, {}
+        for q in range(t.size):
+            k = tuple(keys[q])
+            if k not in levels:
+                prev = None
+                continue
+            q0 = first.setdefault(k, q)
+            if (q - q0) % (1 << levels[k]):
+                continue
+            if prev is not None and ok[prev] and ok[q] and F[prev] > 0 and not F[q] > 0:
+                found = (t[prev], t[q])
+                break
+            prev = q
+        out.append(found)
+    return out, rc
+
+
+def test_brute_force_search_with_coarse_blocks():
+    """Ten noisy views of the tiny scene, merges on: level-1 blocks are sampled at their own pitch (two grid steps)."""
+    wl = synth.tiny()
+    m = oracle.OracleMap(oracle.params_from(wl, "f32s"))
+    K = oracle.pinhole_from(wl)
+    for s in range(10):
+        depth, rgb, T = synth.render_depth(wl, 0, seed=s)
+        m.integrate_depth(K, T, depth, rgb)
+    st = m.block_stats()
+    levels = {tuple(k): int(l) for k, l in zip(st["keys"].tolist(), st["levels"].tolist())}
+    assert sum(levels.values()) > 100
+    E = np.float64(np.float32(V0 * 8))
+    T = _side_pose()
+    pix = np.random.default_rng(5).choice(K.width * K.height, 400, replace=False)
+    br, rc = brute_force_levels(m, K, T, pix, H, E, levels)
+    d = m.raycast_pixels(K, T, pix).astype(np.float64)
+    hits = 0
+    for i in range(pix.size):
+        if br[i] is None:
+            assert d[i] == 0.0, (i, d[i])
+            continue
+        hits += 1
+        t = d[i] / rc[i, 2]
+        assert br[i][0] - 2e-7 * t <= t <= br[i][1] + 2e-7 * t, (i, t, br[i])
+    assert hits > 200
+
+
 # ------------------------------------------------------------------------------------------------ mutation tests
 
 MUTANTS = {
     # a sample skipped after every sample
-    "skip_sample": ("      F_prev = F;\n      ++j;\n", "      F_prev = F;\n      j += 2;\n"),
+    "skip_sample": ("        continue;\n      }\n      ++j;\n", "        continue;\n      }\n      j += 2;\n"),
     # the first grid sample past an unallocated block's exit face skipped
     "late_jump": ("        j = jn > j ? jn : j + 1;\n", "        j = jn + 1 > j ? jn + 1 : j + 1;\n"),
     # the last sample with a field kept across samples without one (brackets across unobserved stretches)
