@@ -251,10 +251,19 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
     col[a] = 0.0f;
   }
   const int sh = 3 - l, nl = 1 << sh, mask = nl - 1;
+  int lb0 = 0x7FFFFFFF, lb1 = 0, lb2 = 0;  // the last corner's block and its heap value (corners share blocks)
+  uint32_t lval = kValPending;
   for (int k = 0; k < 8; ++k) {
     const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
     const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
-    const uint32_t val = find_block(m.slots, m.slot_mask, j[0] >> sh, j[1] >> sh, j[2] >> sh);
+    const int c0 = j[0] >> sh, c1 = j[1] >> sh, c2 = j[2] >> sh;
+    if (c0 != lb0 || c1 != lb1 || c2 != lb2) {
+      lb0 = c0;
+      lb1 = c1;
+      lb2 = c2;
+      lval = find_block(m.slots, m.slot_mask, c0, c1, c2);
+    }
+    const uint32_t val = lval;
     if (val == kValPending) return false;
     const int lb = (int)((val >> 28) & 3u);
     const int nb = kFineDim >> lb, nv = nb * nb * nb;
@@ -353,13 +362,14 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
         hit = true;
         break;
       }
-      // continue at the first grid sample past the exit face of the empty brick, or of the empty block
-      const int span = brick ? 1 : (1 << kBrickShift);
+      // continue at the first grid sample past the exit face of the empty super-brick, brick, or block
+      const bool sempty = sbits == 0ull;
+      const int span = brick ? 1 : sempty ? (1 << (kBrickShift + kSuperShift)) : (1 << kBrickShift);
       float t_exit = t_far + 1.0f;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (r[a] == 0.0f) continue;
-        const int cell = brick ? bk[a] : br[a];
+        const int cell = brick ? bk[a] : sempty ? (br[a] >> kSuperShift) : br[a];
         const float face = (float)((r[a] > 0.0f ? cell + 1 : cell) * span) * E;
         const float tf = (face - o[a]) * inv_r[a];
         if (tf < t_exit) t_exit = tf;
