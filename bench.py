@@ -57,10 +57,9 @@ def parse_args():
                     help="only the variance-threshold sweep (Sec. 5.1 analogue): one JSON line, then exit")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--cpu-replicas", type=int, default=32, help="oracle replicas on the host cores (1 = none)")
-    ap.add_argument("--profile-case", choices=["rgbd", "lidar", "batched", "learned", "mesh", "quadtree", "stream",
-                                               "splat"],
-                    default=None,
-                    help="small case for profiler captures: 6 frames of the sequence with reduced heap capacity")
+    ap.add_argument("--profile-case", choices=["rgbd", "rgbd-grown", "lidar", "batched", "learned", "mesh", "quadtree",
+                                               "stream", "splat"],
+                    default=None, help="small case for profiler captures (reduced heap capacity)")
     return ap.parse_args()
 
 
@@ -85,6 +84,23 @@ def profile_case(kind: str) -> int:
             st = m.stats()
             print(json.dumps({"frame": k, "touched_level": st["touched_level"], "new_blocks": st["new_blocks"],
                               "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
+    elif kind == "rgbd-grown":
+        # the whole 300-frame orbit integrated (heaps reduced to about 2 GB), then three raycasts with normals and
+        # colour from poses spread over the orbit: the map the timed frames of the benchmark see late in the sequence
+        wl = synth.rgbd()
+        wl.max_blocks = (1 << 17, 1 << 15, 1 << 15)
+        m = mrh.Map(mrh.params_from(wl))
+        K = mrh.pinhole_from(wl)
+        for d, c, T in camera_frames(wl, 0, wl.n_frames):
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+        out = torch.empty((wl.height, wl.width), device="cuda")
+        nrm = torch.empty((wl.height, wl.width, 3), device="cuda")
+        col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")
+        for k in (40, 150, 299):
+            m.raycast(K, wl.pose(k), out, normals=nrm, rgb=col)
+        st = m.stats()
+        print(json.dumps({"live_blocks": st["live_blocks"], "touched_level_last": st["touched_level"],
+                          "fuse_algorithmic_bytes_last": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
     elif kind == "mesh":
         wl = synth.rgbd()
         wl.max_blocks = (1 << 16, 1 << 14, 1 << 14)
@@ -888,7 +904,7 @@ def run_batched(warmup, steps, flush):
     outs = [torch.empty((wl.height, wl.width), device="cuda") for wl in wls]
     stream = torch.cuda.Stream()
 
-    def timed(step_fn):
+    def timed(step_fn, after=None):
         ms, rays = 0.0, 0
         for k in range(n_frames):
             flush.zero_()
@@ -901,6 +917,8 @@ def run_batched(warmup, steps, flush):
             stream.synchronize()
             if k >= warmup:
                 ms += a.elapsed_time(b)
+            if after is not None:
+                after(k)
         return ms
 
     plain_maps = [mrh.Map(mrh.params_from(wl)) for wl in wls]
@@ -917,12 +935,22 @@ def run_batched(warmup, steps, flush):
         rays += m.stats()["valid_rays"]
     batch_maps = [mrh.Map(mrh.params_from(wl)) for wl in wls]
     batch = mrh.Batch(batch_maps, cams)
+    fuse = {"ms": 0.0, "bytes": 0, "steps": 0}
 
     def batch_step(k):
         batch.integrate([(frames[i][k][2], frames[i][k][0], frames[i][k][1], outs[i]) for i in range(len(wls))],
                         stream=stream)
 
-    ms_batch = timed(batch_step)
+    def batch_fuse_account(k):
+        # the fusion kernel's own device time (events at the phase boundaries of the step, inside the graph) and the
+        # algorithmic bytes of every map's fusion in this step
+        if k < warmup:
+            return
+        fuse["ms"] += batch.last_step_ms()["fuse"]
+        fuse["bytes"] += sum(fuse_bytes_camera(m.stats(), wl, voxel_bytes(wl)) for m, wl in zip(batch_maps, wls))
+        fuse["steps"] += 1
+
+    ms_batch = timed(batch_step, after=batch_fuse_account)
     # valid rays of the timed steps (identical in both forms; counted from the depth images)
     rays_timed = 0
     for i, wl in enumerate(wls):
@@ -934,7 +962,7 @@ def run_batched(warmup, steps, flush):
     for m in plain_maps + batch_maps:
         m.close()
     return dict(rays=rays_timed, ms_plain=ms_plain, ms_batch=ms_batch, config=cfg,
-                sizes=[f"{wl.width}x{wl.height}" for wl in wls])
+                sizes=[f"{wl.width}x{wl.height}" for wl in wls], fuse=fuse)
 
 
 # ----------------------------------------------------------------------------------------------------- CPU oracle
@@ -1177,6 +1205,14 @@ def main():
                    "workload": "16 RGB-D-style maps, frame sizes " + ",".join(bres["sizes"]) +
                                " (1/2/4 cm, FP16 storage, colour) + raycast per map per step",
                    "tuned_config": bres["config"]}
+        bf = bres["fuse"]
+        if bf["steps"] and bf["ms"] > 0:
+            b_ach = bf["bytes"] / (bf["ms"] / 1000.0) / 1e9
+            batched["roofline"] = {"kernel": "k_batch_fuse (all maps' fusion + block variance + re-level, one launch)",
+                                   "bound": "hbm", "achieved": round(b_ach, 1), "peak": hbm, "unit": "GB/s",
+                                   "frac": round(b_ach / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                                   "algorithmic_bytes_per_launch": int(bf["bytes"] / bf["steps"]),
+                                   "launch_ms_avg": round(bf["ms"] / bf["steps"], 5)}
 
     learned = None
     if not args.no_learned:

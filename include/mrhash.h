@@ -101,6 +101,8 @@ typedef struct {
   uint64_t evicted;          /* streaming: blocks moved to the archive before the last frame */
   uint64_t restored;         /* streaming: archived blocks the last frame allocated again (brought back) */
   uint64_t archived;         /* streaming: blocks in the archive now */
+  uint64_t lidar_max_voxel_obs; /* LiDAR: the most observations one voxel received in the last scan (a coarse voxel
+                                   near the sensor collects hundreds; they are applied in point order) */
   uint32_t status;           /* sticky device status bits (see mrh_status) */
 } mrh_stats;
 
@@ -170,6 +172,12 @@ mrh_status mrh_batch_integrate(mrh_batch* batch, const mrh_batch_frame* frames, 
 /* The launch shapes in use: {alloc tile width, alloc tile height, probe width, fusion warps per CTA, fusion CTAs per
  * SM, raycast warp tile (0: 8x4, 1: 16x2), tuned (0/1), graph captured (0/1)}. */
 mrh_status mrh_batch_config(const mrh_batch* batch, int* config_out8);
+
+/* Device time of the phases of the last mrh_batch_integrate call, in ms (waits for it): ms_out4[0] allocation,
+ * [1] binning, [2] fusion (the fusion kernel alone), [3] re-level release + raycast. The step records its phase
+ * boundaries with CUDA events on its stream (inside the captured graph as well). MRH_ERR_INVALID_ARG before the
+ * first step. */
+mrh_status mrh_batch_last_step_ms(const mrh_batch* batch, float* ms_out4);
 
 /* Release the batch (not its maps). NULL is accepted. */
 mrh_status mrh_batch_destroy(mrh_batch* batch);

@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("fp64_rechecks", ctypes.c_uint64), ("live_blocks", ctypes.c_uint64 * 3),
                 ("touched_level", ctypes.c_uint64 * 3), ("observations", ctypes.c_uint64),
                 ("updated_voxels", ctypes.c_uint64), ("lidar_restaged", ctypes.c_uint64), ("evicted", ctypes.c_uint64),
-                ("restored", ctypes.c_uint64), ("archived", ctypes.c_uint64), ("status", ctypes.c_uint32)]
+                ("restored", ctypes.c_uint64), ("archived", ctypes.c_uint64),
+                ("lidar_max_voxel_obs", ctypes.c_uint64), ("status", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("live_blocks", "touched_level")}
@@ -75,7 +76,8 @@ class BatchFrame(ctypes.Structure):
 EXPORTS = ["mrh_map_create", "mrh_map_destroy", "mrh_integrate_depth", "mrh_integrate_points", "mrh_raycast",
            "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc", "mrh_get_stats", "mrh_sync",
            "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create", "mrh_batch_integrate",
-           "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor", "mrh_set_feature_capture",
+           "mrh_batch_config", "mrh_batch_last_step_ms", "mrh_batch_destroy", "mrh_set_predictor",
+           "mrh_set_feature_capture",
            "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy", "mrh_mlp_train_step", "mrh_mlp_loss_grad",
            "mrh_mlp_predict", "mrh_mlp_get_weights", "mrh_hash_slot", "mrh_status_string", "mrh_last_cuda_error",
            "mrh_version", "mrh_extract_mesh", "mrh_mesh_case_table", "mrh_weld_mesh", "mrh_quadtree",
@@ -123,6 +125,7 @@ def lib():
         L.mrh_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Pinhole), i32, i32, ctypes.POINTER(vp)]
         L.mrh_batch_integrate.argtypes = [vp, ctypes.POINTER(BatchFrame), vp]
         L.mrh_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.mrh_batch_last_step_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.mrh_batch_destroy.argtypes = [vp]
         L.mrh_set_predictor.argtypes = [vp, vp, u64]
         L.mrh_set_feature_capture.argtypes = [vp, ctypes.c_uint32]
@@ -143,7 +146,8 @@ def lib():
                      "mrh_raycast", "mrh_count_blocks", "mrh_extract_blocks", "mrh_extract_blocks_noalloc",
                      "mrh_get_stats", "mrh_sync",
                      "mrh_clear_status", "mrh_set_profiling", "mrh_get_profile", "mrh_batch_create",
-                     "mrh_batch_integrate", "mrh_batch_config", "mrh_batch_destroy", "mrh_set_predictor",
+                     "mrh_batch_integrate", "mrh_batch_config", "mrh_batch_last_step_ms", "mrh_batch_destroy",
+                     "mrh_set_predictor",
                      "mrh_set_feature_capture", "mrh_get_features", "mrh_mlp_create", "mrh_mlp_destroy",
                      "mrh_mlp_train_step", "mrh_mlp_loss_grad", "mrh_mlp_predict", "mrh_mlp_get_weights"):
             getattr(L, name).restype = ctypes.c_int
@@ -547,6 +551,12 @@ class Batch:
         _check(self._lib.mrh_batch_config(self._h, c), "mrh_batch_config")
         return dict(alloc_tile=(c[0], c[1]), probe_width=c[2], fuse_warps=c[3], fuse_ctas_per_sm=c[4],
                     raycast_warp_tile="16x2" if c[5] else "8x4", tuned=bool(c[6]), graph=bool(c[7]))
+
+    def last_step_ms(self) -> dict:
+        """Device time of the last step's phases (waits for it): allocation, binning, fusion, release + raycast."""
+        c = (ctypes.c_float * 4)()
+        _check(self._lib.mrh_batch_last_step_ms(self._h, c), "mrh_batch_last_step_ms")
+        return dict(alloc=c[0], bin=c[1], fuse=c[2], raycast=c[3])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -332,6 +332,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->observations = 0;
   st->updated_voxels = 0;
   st->n_over = 0;
+  st->max_vox_obs = 0;
   st->item_next = 0;
   st->evicted = st->restored = st->n_restore = 0;
 }

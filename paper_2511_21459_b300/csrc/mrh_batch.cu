@@ -4,8 +4,9 @@
 //   k_batch_begin     per-map frame counters
 //   k_batch_alloc     one grid over every map's pixel tiles (a CTA finds its map from the tile offsets)
 //   k_batch_bin       one grid row per map
-//   k_batch_fuse      persistent warps pull (map, work item) pairs from one device queue, so maps with large and
-//                     small frames share the GPU without per-map launches or idle tails
+//   k_batch_fuse      persistent warps stride over the work items of all maps laid end to end (a warp finds an
+//                     item's map from the running totals), so maps with large and small frames share the GPU without
+//                     per-map launches or idle tails
 //   k_batch_release   one grid row per map
 //   k_batch_raycast   one grid over every map's pixel tiles (maps without a raycast output skip)
 //
@@ -119,13 +120,10 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch_fuse(BatchDev 
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = s_end[b.n - 1];
-  for (;;) {
-    uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(b.queue, 1u);
-    item = __shfl_sync(~0u, item, 0);
-    if (item >= total) break;
-    int mi = 0;
-    while (s_end[mi] <= item) ++mi;
+  const uint32_t nwarps = gridDim.x * WARPS;
+  int mi = 0;
+  for (uint32_t item = blockIdx.x * WARPS + warp; item < total; item += nwarps) {  // warp-uniform
+    while (s_end[mi] <= item) ++mi;  // items rise, so the map index only moves forward
     const uint32_t local = item - (mi > 0 ? s_end[mi - 1] : 0u);
     const MapDev& m = b.maps[mi];
     const BatchFrame& f = b.frames[mi];
@@ -200,7 +198,9 @@ struct mrh_batch {
   bool tuned = false;
   double trial_ms[3][kTrials] = {};
   int trial_n[3][kTrials] = {};
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // phase boundaries of a step: after begin, after allocation, after binning, after fusion, after raycast (recorded
+  // by every step, inside the captured graph too)
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -267,18 +267,25 @@ void launch_raycast_shape(const mrh_batch* b, int shape, cudaStream_t s) {
 }
 
 // one step with the given shapes; events (optional) bracket allocation, fusion and raycast
-void launch_step(const mrh_batch* b, int as, int fs, int rs, cudaStream_t s, const cudaEvent_t* ev) {
+void launch_step(const mrh_batch* b, int as, int fs, int rs, cudaStream_t s, const cudaEvent_t* ev, bool capturing) {
   const BatchDev d = batch_dev(b);
+  // under stream capture the records are external, so that they become event-record nodes of the graph
+  auto mark = [&](int k) {
+    if (!ev) return;
+    if (capturing) cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal);
+    else cudaEventRecord(ev[k], s);
+  };
   k_batch_begin<<<1, kBatchMaxMaps, 0, s>>>(d);
-  if (ev) cudaEventRecord(ev[0], s);
+  mark(0);
   launch_alloc(b, as, s);
-  if (ev) cudaEventRecord(ev[1], s);
+  mark(1);
   k_batch_bin<<<dim3(b->sms / 4 + 1, b->n), 256, 0, s>>>(d);
+  mark(2);
   launch_fuse(b, fs, s);
-  if (ev) cudaEventRecord(ev[2], s);
+  mark(3);
   k_batch_release<<<dim3(8, b->n), 256, 0, s>>>(d);
   launch_raycast_shape(b, rs, s);
-  if (ev) cudaEventRecord(ev[3], s);
+  mark(4);
 }
 
 void destroy_graph(mrh_batch* b) {
@@ -371,7 +378,7 @@ mrh_status mrh_batch_create(mrh_map* const* maps, const mrh_pinhole* cams, int n
   }
   b->ray_tiles = ray_tiles;
   for (int sh = 0; sh < 4; ++sh) b->alloc_tiles[sh] = alloc_tiles[sh];
-  for (int k = 0; k < 4; ++k) cudaEventCreate(&b->ev[k]);
+  for (int k = 0; k < 5; ++k) cudaEventCreate(&b->ev[k]);
   b->tuned = !(flags & MRH_BATCH_AUTOTUNE);
   *out = b;
   return MRH_OK;
@@ -386,7 +393,7 @@ mrh_status mrh_batch_destroy(mrh_batch* b) {
   if (b->maps_dev) cudaFree(b->maps_dev);
   if (b->frames_dev) cudaFree(b->frames_dev);
   if (b->queue) cudaFree(b->queue);
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 5; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   delete b;
   return MRH_OK;
@@ -440,13 +447,13 @@ mrh_status mrh_batch_integrate(mrh_batch* b, const mrh_batch_frame* frames, void
                             cudaMemcpyHostToDevice, s));
   const bool use_graph = (b->flags & MRH_BATCH_GRAPH) && s != nullptr && b->tuned;
   if (trial) {
-    launch_step(b, as, fs, rs, s, b->ev);
+    launch_step(b, as, fs, rs, s, b->ev, false);
     MRH_BCUDA(cudaGetLastError());
-    MRH_BCUDA(cudaEventSynchronize(b->ev[3]));
+    MRH_BCUDA(cudaEventSynchronize(b->ev[4]));
     float t_alloc = 0, t_fuse = 0, t_ray = 0;
     cudaEventElapsedTime(&t_alloc, b->ev[0], b->ev[1]);
-    cudaEventElapsedTime(&t_fuse, b->ev[1], b->ev[2]);
-    cudaEventElapsedTime(&t_ray, b->ev[2], b->ev[3]);
+    cudaEventElapsedTime(&t_fuse, b->ev[1], b->ev[3]);
+    cudaEventElapsedTime(&t_ray, b->ev[3], b->ev[4]);
     b->trial_ms[0][as] += t_alloc;
     b->trial_n[0][as] += 1;
     b->trial_ms[1][fs] += t_fuse;
@@ -476,7 +483,7 @@ mrh_status mrh_batch_integrate(mrh_batch* b, const mrh_batch_frame* frames, void
     if (!b->exec || b->graph_stream != s) {
       destroy_graph(b);
       MRH_BCUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      launch_step(b, b->alloc_shape, b->fuse_shape, b->ray_shape, s, nullptr);
+      launch_step(b, b->alloc_shape, b->fuse_shape, b->ray_shape, s, b->ev, true);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -490,10 +497,18 @@ mrh_status mrh_batch_integrate(mrh_batch* b, const mrh_batch_frame* frames, void
     }
     MRH_BCUDA(cudaGraphLaunch(b->exec, s));
   } else {
-    launch_step(b, as, fs, rs, s, nullptr);
+    launch_step(b, as, fs, rs, s, b->ev, false);
     MRH_BCUDA(cudaGetLastError());
   }
   b->steps += 1;
+  return MRH_OK;
+}
+
+mrh_status mrh_batch_last_step_ms(const mrh_batch* b, float* ms_out4) {
+  if (!b || !ms_out4 || b->steps == 0) return MRH_ERR_INVALID_ARG;
+  BatchDeviceGuard guard(b->device);
+  MRH_BCUDA(cudaEventSynchronize(b->ev[4]));
+  for (int k = 0; k < 4; ++k) MRH_BCUDA(cudaEventElapsedTime(&ms_out4[k], b->ev[k], b->ev[k + 1]));
   return MRH_OK;
 }
 

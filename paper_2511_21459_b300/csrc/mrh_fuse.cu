@@ -31,12 +31,15 @@ __global__ void __launch_bounds__(32 * kLidarWarps) k_fuse_points(MapDev m) {
     if (t >= items) break;
     fuse_item<FP16, COLOR>(m, obs, warp, ic, t < coarse ? ic.it0 + t : t - coarse, my_obs, my_vox);
   }
+  uint32_t vmax = obs.vmax;
   for (int o = 16; o > 0; o >>= 1) {
     my_obs += __shfl_xor_sync(~0u, my_obs, o);
     my_vox += __shfl_xor_sync(~0u, my_vox, o);
+    vmax = max(vmax, __shfl_xor_sync(~0u, vmax, o));
   }
   if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
   if (lane == 0 && my_vox) atomicAdd(&m.st->updated_voxels, my_vox);
+  if (lane == 0 && vmax) atomicMax(&m.st->max_vox_obs, vmax);
 }
 
 // -------------------------------------------------------------------------------------------- LiDAR observation passes

@@ -196,6 +196,7 @@ template <bool FP16>
 struct LidarObs {
   LidarSmem* sm;
   uint2* recs;  // this warp's regrouped records: obs_bin + item base
+  mutable uint32_t vmax = 0;  // the most observations one of this lane's voxels received
 
   // warp-collective: regroup the item's observations per voxel (bin = group * nv + voxel), keeping for each voxel
   // its records contiguous
@@ -403,6 +404,7 @@ struct LidarObs {
       const uint32_t cnt = o[k + 1] - o[k];
       n_upd += (int)cnt;
       n_vox += cnt > 0 ? 1 : 0;
+      vmax = max(vmax, cnt);
       if (cnt <= 2) {
         const bool sw = cnt == 2 && a[k].x > b[k].x;
         const uint32_t d1 = sw ? b[k].y : a[k].y, d2 = sw ? a[k].y : b[k].y;
@@ -684,6 +686,7 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
         float* Sp = reinterpret_cast<float*>(io.blk + off_S2(nv, FP16, COLOR)) + bin;
         float D = Field<FP16>::get1(io.blk, (int)bin), W = *Wp, S2 = *Sp;
         Obs::apply_long(obs.recs + o0, cnt, D, W, S2);
+        obs.vmax = max(obs.vmax, cnt);
         Field<FP16>::store1(io.blk, (int)bin, D);
         *Wp = W;
         *Sp = S2;

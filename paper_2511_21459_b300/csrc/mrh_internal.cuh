@@ -88,6 +88,7 @@ struct DevState {
   uint32_t ar_used;            // streaming: archive slots handed out (each key keeps its slot)
   uint32_t ar_present;         // streaming: blocks currently in the archive
   uint32_t evict_go;           // streaming: this frame's capacity check (taken once, before any eviction)
+  uint32_t max_vox_obs;          // LiDAR: the most observations one voxel received in this scan
   unsigned long long mesh_tris;  // triangles counted by the last mesh extraction
   uint32_t mesh_next;            // mesh extraction: next chunk of 32 hash slots to hand out
 };

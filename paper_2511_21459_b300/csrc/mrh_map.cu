@@ -1193,6 +1193,7 @@ mrh_status mrh_get_stats(mrh_map* m, mrh_stats* out, void* stream) {
   out->observations = hs.observations;
   out->updated_voxels = hs.updated_voxels;
   out->lidar_restaged = hs.n_over;
+  out->lidar_max_voxel_obs = hs.max_vox_obs;
   out->evicted = hs.evicted;
   out->restored = hs.restored;
   out->archived = hs.ar_present;

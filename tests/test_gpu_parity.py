@@ -248,6 +248,40 @@ def test_lidar_map_raycast_normals_fp16():
         g.raycast(K_g, T, rgb=True)
 
 
+def test_lidar_dense_patch_many_points_per_block():
+    """Points on a 0.5 m x 0.5 m patch 1 m in front of the sensor (128 x 128 per scan, seeded range noise): a block
+    receives thousands of points and a voxel hundreds of observations per scan, far beyond the 16 that are ordered in
+    registers (the long lists are applied in passes of 8 smallest point indices), and with a high threshold the
+    blocks merge to the coarse levels, whose voxels collect more still. Counters after every scan and the whole map
+    against the oracle."""
+    wl = synth.lidar()
+    wl.fp16 = False
+    wl.min_obs = 2
+    wl.var_threshold = (5e-2, 2e-1)
+    wl.split_hysteresis = 0.0
+    g, o = gpu_map(wl), orc_map(wl)
+    rng = np.random.default_rng(17)
+    n = 128
+    a, b = np.meshgrid(np.linspace(-0.25, 0.25, n), np.linspace(-0.25, 0.25, n))
+    most = 0
+    for f in range(4):
+        dirs = np.stack([np.ones(n * n), a.ravel(), b.ravel()], -1)
+        dirs /= np.linalg.norm(dirs, axis=-1, keepdims=True)
+        rng_m = 1.0 / dirs[:, 0] + rng.normal(0.0, 0.01, n * n)
+        xyz = (dirs * rng_m[:, None]).astype(np.float32)
+        T = np.eye(4)
+        g.integrate_points(T, torch.from_numpy(xyz).cuda())
+        st_o = o.integrate_points(T, xyz)
+        st_g = g.stats()
+        assert st_g["status_code"] == 0, st_g
+        for k in ("valid_rays", "touched", "new_blocks", "merged", "split", "observations", "updated_voxels"):
+            assert st_g[k] == st_o[k], (f, k, st_g[k], st_o[k])
+        most = max(most, st_g["lidar_max_voxel_obs"])
+        compare_extracts(g.extract(), o.extract(), wl.truncation, wl.var_threshold[0], check_color=False)
+    assert most > 300, most
+    assert (o.block_stats()["levels"] > 0).sum() > 0
+
+
 def test_lidar_full_scans():
     """Six full 128 x 2048 scans of the benchmark's LiDAR configuration (FP16 storage)."""
     wl = synth.lidar()
