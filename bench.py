@@ -91,8 +91,12 @@ def profile_case(kind: str) -> int:
         wl.max_blocks = (1 << 17, 1 << 15, 1 << 15)
         m = mrh.Map(mrh.params_from(wl))
         K = mrh.pinhole_from(wl)
-        for d, c, T in camera_frames(wl, 0, wl.n_frames):
+        for k, (d, c, T) in enumerate(camera_frames(wl, 0, wl.n_frames)):
             m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+            if k >= wl.n_frames - 3:
+                st = m.stats()
+                print(json.dumps({"frame": k, "touched_level": st["touched_level"],
+                                  "fuse_algorithmic_bytes": fuse_bytes_camera(st, wl, voxel_bytes(wl))}))
         out = torch.empty((wl.height, wl.width), device="cuda")
         nrm = torch.empty((wl.height, wl.width, 3), device="cuda")
         col = torch.empty((wl.height, wl.width, 3), dtype=torch.uint8, device="cuda")

@@ -58,10 +58,13 @@ def test_bf16_copy_is_rounded_master():
     np.testing.assert_array_equal(wbf, mlp.bf16_bits(w.astype(np.float64)))
 
 
-@pytest.mark.parametrize("n", [1, 31, 777, 4096])
+@pytest.mark.parametrize("n", [1, 31, 777, 4096, 100_000])
 def test_loss_and_gradient_match_float64_oracle(n):
-    """Float sums and atomic accumulation against float64: relative error of order 1e-6; a rare flip of one BF16
-    activation rounding moves one sample's share by about 2^-8. Tolerance: 1e-4 of the largest gradient entry."""
+    """The tensor-core gradient against float64. Forward products are exact BF16 products summed in FP32; in the
+    backward products the FP32 gradient factor is split into a BF16 part and a BF16 remainder (16 of its 24 mantissa
+    bits, relative error below 2^-16 = 1.5e-5 per term); the sums and the atomic accumulation add errors of order
+    1e-6; a rare flip of one BF16 activation rounding moves one sample's share by about 2^-8. Tolerance: 1e-4 of the
+    largest gradient entry. 100 000 samples make every CTA loop over several tiles."""
     net = mrh().Mlp(_init(4))
     _, wbf = net.weights()
     rng = np.random.default_rng(5 + n)
