@@ -49,6 +49,10 @@ def parse_args():
     ap.add_argument("--no-lidar", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-epochs", type=int, default=12)
+    ap.add_argument("--learned-repeats", type=int, default=5, help="interleaved timed runs of plain and learned")
+    ap.add_argument("--learned-lidar-train-scans", type=int, default=500)
+    ap.add_argument("--learned-lidar-scans", type=int, default=500)
     ap.add_argument("--no-mesh", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
@@ -459,10 +463,142 @@ def chamfer_vs_truth(m, wl, views, poses=None):
     return metrics.chamfer(np.concatenate(rec), np.concatenate(gt))
 
 
-def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epochs=30):
-    """The learned level predictor against the plain rule on the same frames: train on the plain rule's levels of a
-    different seeded scene (features recorded by the library, labels = final levels), then time the same sequence
-    with the predictor set, and compare fused work, misclassification and Chamfer error."""
+def spread(xs):
+    """Mean, minimum, maximum and relative spread ((max - min) / mean) of repeated timings."""
+    xs = [float(x) for x in xs]
+    mean = sum(xs) / len(xs)
+    return {"mean": round(mean, 5), "min": round(min(xs), 5), "max": round(max(xs), 5),
+            "spread": round((max(xs) - min(xs)) / mean, 4), "n": len(xs)}
+
+
+def lidar_training_data(lw, n_scans):
+    """Features and plain-rule labels of every new block of a seeded LiDAR training street (another scene seed):
+    features recorded by the library as the scans are integrated, label = the block's level at the end."""
+    import torch
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import predictor
+    scene = lw.scene()
+    m = mrh.Map(mrh.params_from(lw), device=torch.cuda.current_device())
+    m.set_feature_capture(1 << 22)
+    for k in range(n_scans):
+        xyz, T = synth.render_lidar(lw, k, scene=scene)
+        m.integrate_points(T, torch.from_numpy(xyz).cuda())
+    st = m.stats()
+    keys, feats, seen = m.features()
+    ex = m.extract()
+    y = predictor.level_labels(keys.cpu().numpy(), ex["keys"].cpu().numpy(), ex["levels"].cpu().numpy())
+    ok = y >= 0
+    info = {"scene_seed": lw.seed, "scans": n_scans, "records": int(seen), "live_blocks": st["live_blocks"],
+            "status": st["status_code"]}
+    m.close()
+    return feats[torch.from_numpy(ok).cuda()].contiguous(), torch.from_numpy(y[ok]).cuda(), info
+
+
+def run_learned_lidar(lw, w_bf16, net, flush, n_scans=500, warmup=3, repeats=5,
+                      view_x=(25.0, 125.0, 225.0, 325.0, 425.0)):
+    """The learned predictor on a fresh LiDAR street against the plain rule: both maps integrate the same n_scans
+    scans (device-resident), each scan after the first `warmup` timed between CUDA events with L2 flushed before it;
+    `repeats` interleaved runs of each; Chamfer-L1 of the maps' raycast depth from pinhole views down the street
+    against noise-free renders; misclassification of the network against the plain rule's final levels."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import predictor
+    scene = lw.scene()
+    dev = []
+    for k in range(n_scans):
+        xyz, T = synth.render_lidar(lw, k, scene=scene)
+        dev.append((torch.from_numpy(xyz).cuda(), T))
+    stream = torch.cuda.current_stream()
+
+    def one(w, keep=False, capture=False):
+        m = mrh.Map(mrh.params_from(lw), device=torch.cuda.current_device())
+        if w is not None:
+            m.set_predictor(w)
+        if capture:
+            m.set_feature_capture(1 << 22)
+        ev, obs, rays = [], 0, 0
+        touched = [0, 0, 0]
+        for k, (x, T) in enumerate(dev):
+            if k < warmup:
+                m.integrate_points(T, x)
+                continue
+            flush.zero_()
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            e[0].record(stream)
+            m.integrate_points(T, x)
+            e[1].record(stream)
+            ev.append(e)
+            st = m.stats()
+            if st["status_code"] != 0:
+                raise RuntimeError(f"LiDAR map status {st['status_code']} at scan {k}")
+            obs += st["observations"]
+            rays += st["valid_rays"]
+            touched = [a + b for a, b in zip(touched, st["touched_level"])]
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        out = {"ms_per_scan": ms, "observations": obs, "rays": rays, "touched_level": touched,
+               "live_blocks": m.stats()["live_blocks"]}
+        if keep:
+            out["map"] = m
+        else:
+            m.close()
+        return out
+
+    plain_ms, learned_ms = [], []
+    for r in range(repeats):
+        plain_ms.append(one(None)["ms_per_scan"])
+        learned_ms.append(one(w_bf16)["ms_per_scan"])
+    p = one(None, keep=True, capture=True)
+    q = one(w_bf16, keep=True)
+    cam = dataclasses.replace(lw, sensor="camera", width=640, height=480, fx=400.0, fy=400.0, cx=319.5, cy=239.5,
+                              min_depth=0.5, max_depth=60.0, extra={"scene": "lidar"})
+    poses = [synth.look_at((x, 0.0, 1.8), (x + 10.0, 0.0, 1.5)) for x in view_x]
+    # the bound of any predictor: every new block started at one level (constant networks)
+    bound = {}
+    for lv in range(1, lw.n_levels):
+        c = one(predictor.constant_level_weights(lv), keep=True)
+        ch = chamfer_vs_truth(c["map"], cam, list(range(len(poses))), poses=poses)
+        c["map"].close()
+        bound[f"all_new_at_level_{lv}"] = {"ms_per_scan": round(c["ms_per_scan"], 5),
+                                           "chamfer_mm": round(1000 * ch["chamfer"], 4),
+                                           "live_blocks": c["live_blocks"]}
+    keys, feats, _ = p["map"].features()
+    ex = p["map"].extract()
+    y = predictor.level_labels(keys.cpu().numpy(), ex["keys"].cpu().numpy(), ex["levels"].cpu().numpy())
+    ok = y >= 0
+    xe = feats[torch.from_numpy(ok).cuda()].contiguous()
+    ye = torch.from_numpy(y[ok]).cuda()
+    pred = predictor.predicted_levels(net, xe)
+    misclass = float((pred != ye).float().mean().item())
+    ch_p = chamfer_vs_truth(p["map"], cam, list(range(len(poses))), poses=poses)
+    ch_l = chamfer_vs_truth(q["map"], cam, list(range(len(poses))), poses=poses)
+    p["map"].close()
+    q["map"].close()
+    pm, lm = spread(plain_ms), spread(learned_ms)
+    rays = p["rays"] / (n_scans - warmup)
+    return {"workload": f"lidar-128x2048-street, fresh scene seed {lw.seed}, {n_scans} scans ({warmup} warm-up)",
+            "value": rays / (lm["mean"] / 1000.0), "unit": "points/s", "plain_value": rays / (pm["mean"] / 1000.0),
+            "speedup_vs_plain": pm["mean"] / lm["mean"], "ms_per_scan": {"plain": pm, "learned": lm},
+            "misclassification": round(misclass, 4),
+            "label_histogram": np.bincount(ye.cpu().numpy(), minlength=3).tolist(),
+            "predicted_histogram": np.bincount(pred.cpu().numpy(), minlength=3).tolist(),
+            "fused_observations": {"plain": p["observations"], "learned": q["observations"]},
+            "touched_blocks_per_level": {"plain": p["touched_level"], "learned": q["touched_level"]},
+            "live_blocks": {"plain": p["live_blocks"], "learned": q["live_blocks"]},
+            "chamfer_mm": {"plain": round(1000 * ch_p["chamfer"], 4), "learned": round(1000 * ch_l["chamfer"], 4),
+                           "added": round(1000 * (ch_l["chamfer"] - ch_p["chamfer"]), 4)},
+            "fscore_10cm": {"plain": round(ch_p["fscore"], 5), "learned": round(ch_l["fscore"], 5)},
+            "upper_bound": bound}
+
+
+def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epochs=12, lidar_train_scans=500,
+                lidar_scans=500, repeats=5, cam_train_scenes=3, lidar_train_streets=2):
+    """The learned level predictor against the plain rule. One network is trained on the plain rule's levels of
+    other seeded RGB-D scenes and other seeded LiDAR streets (features recorded by the library, labels = final
+    levels); then the RGB-D bench sequence is timed with and without it (`repeats` interleaved runs each) and a fresh
+    LiDAR street likewise, comparing fused work, misclassification and Chamfer error, next to constant networks that
+    start every new block at one coarser level (the most a "go coarse" predictor could change)."""
     import dataclasses
     import torch
     import paper_2511_21459_b300 as mrh
@@ -482,14 +618,32 @@ def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epoch
         m.close()
         return feats[ok].contiguous(), torch.from_numpy(y[y >= 0]).cuda()
 
-    train_wl = dataclasses.replace(wl, seed=wl.seed + 10)
-    x, y = captured_run(train_wl, camera_frames(train_wl, 0, train_frames))
+    cam_seeds = [wl.seed + 10 + k for k in range(cam_train_scenes)]
+    parts = [captured_run(w, camera_frames(w, 0, train_frames))
+             for w in (dataclasses.replace(wl, seed=sd) for sd in cam_seeds)]
+    xc, yc = torch.cat([a for a, _ in parts]), torch.cat([b for _, b in parts])
+    lw = synth.lidar()
+    parts, linfo = [], []
+    for k in range(lidar_train_streets):
+        a, b, info = lidar_training_data(dataclasses.replace(lw, seed=lw.seed + 10 + k), lidar_train_scans)
+        parts.append((a, b))
+        linfo.append(info)
+    xl, yl = torch.cat([a for a, _ in parts]), torch.cat([b for _, b in parts])
+    x, y = torch.cat([xc, xl]), torch.cat([yc, yl])
+    tt = time.perf_counter()
     net, hist = predictor.train(x, y, epochs=epochs, batch=4096, lr=2e-3, seed=0)
-    train_err = float((predictor.predicted_levels(net, x) != y).float().mean().item())
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - tt
+    pred_c = predictor.predicted_levels(net, xc)
+    pred_l = predictor.predicted_levels(net, xl)
     _, w_bf16 = net.weights()
     # misclassification on the evaluation sequence: the features of its new blocks do not depend on levels
     xe, ye = captured_run(wl, frames[:max(timed) + 1])
     misclass = float((predictor.predicted_levels(net, xe) != ye).float().mean().item())
+    plain_ms, learned_ms = [], []
+    for r in range(repeats):
+        plain_ms.append(run_camera_gpu(wl, frames, warmup, timed, flush)["ms"] / len(timed))
+        learned_ms.append(run_camera_gpu(wl, frames, warmup, timed, flush, predictor=w_bf16)["ms"] / len(timed))
     learned = run_camera_gpu(wl, frames, warmup, timed, flush, predictor=w_bf16, keep=True)
     plain_map = run_camera_gpu(wl, frames, warmup, timed, flush, keep=True)
     steps = len(timed)
@@ -498,22 +652,39 @@ def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epoch
     ch_p = chamfer_vs_truth(plain_map["map"], wl, views)
     learned["map"].close()
     plain_map["map"].close()
-    return {"value": learned["rays"] / (learned["ms"] / 1000.0), "unit": "points/s",
-            "plain_value": plain["rays"] / (plain["ms"] / 1000.0),
-            "speedup_vs_plain": plain["ms"] / learned["ms"],
-            "ms_per_step": learned["ms"] / steps, "plain_ms_per_step": plain["ms"] / steps,
-            "misclassification": round(misclass, 4), "train": {"scene_seed": train_wl.seed, "frames": train_frames,
-                                                               "samples": int(x.shape[0]), "epochs": epochs,
-                                                               "loss": [round(hist[0], 4), round(hist[-1], 4)],
-                                                               "error": round(train_err, 4)},
+    bound = {}
+    for lv in range(1, wl.n_levels):
+        c = run_camera_gpu(wl, frames, warmup, timed, flush, predictor=predictor.constant_level_weights(lv), keep=True)
+        ch = chamfer_vs_truth(c["map"], wl, views)
+        c["map"].close()
+        bound[f"all_new_at_level_{lv}"] = {"ms_per_step": round(c["ms"] / steps, 5),
+                                           "chamfer_mm": round(1000 * ch["chamfer"], 4)}
+    pm, lm = spread(plain_ms), spread(learned_ms)
+    rays = plain["rays"] / steps
+    lid = run_learned_lidar(lw, w_bf16, net, flush, n_scans=lidar_scans, repeats=repeats)
+    return {"value": rays / (lm["mean"] / 1000.0), "unit": "points/s",
+            "plain_value": rays / (pm["mean"] / 1000.0),
+            "speedup_vs_plain": pm["mean"] / lm["mean"],
+            "ms_per_step": {"plain": pm, "learned": lm},
+            "misclassification": round(misclass, 4),
+            "train": {"rgbd": {"scene_seeds": cam_seeds, "frames": train_frames, "samples": int(xc.shape[0]),
+                               "error": round(float((pred_c != yc).float().mean().item()), 4),
+                               "labels": np.bincount(yc.cpu().numpy(), minlength=3).tolist()},
+                      "lidar": dict(streets=linfo, samples=int(xl.shape[0]),
+                                    error=round(float((pred_l != yl).float().mean().item()), 4),
+                                    labels=np.bincount(yl.cpu().numpy(), minlength=3).tolist()),
+                      "samples": int(x.shape[0]), "epochs": epochs, "batch": 4096, "train_s": round(train_s, 2),
+                      "loss": [round(hist[0], 4), round(hist[-1], 4)]},
             "label_histogram": np.bincount(ye.cpu().numpy(), minlength=3).tolist(),
-            "fused_observations": {"plain": plain["observations"], "learned": learned["observations"]},
-            "touched_blocks_per_level": {"plain": plain["touched_level"], "learned": learned["touched_level"]},
+            "fused_observations": {"plain": plain_map["observations"], "learned": learned["observations"]},
+            "touched_blocks_per_level": {"plain": plain_map["touched_level"], "learned": learned["touched_level"]},
             "chamfer_mm": {"plain": round(1000 * ch_p["chamfer"], 4), "learned": round(1000 * ch_l["chamfer"], 4),
                            "added": round(1000 * (ch_l["chamfer"] - ch_p["chamfer"]), 4)},
             "fscore_10cm": {"plain": round(ch_p["fscore"], 5), "learned": round(ch_l["fscore"], 5)},
-            "kernels_ms": {"plain": {g: round(v[0], 3) for g, v in plain["prof"].items() if v[1] > 0},
+            "kernels_ms": {"plain": {g: round(v[0], 3) for g, v in plain_map["prof"].items() if v[1] > 0},
                            "learned": {g: round(v[0], 3) for g, v in learned["prof"].items() if v[1] > 0}},
+            "upper_bound": bound,
+            "lidar": lid,
             "wall_s": round(time.perf_counter() - t0, 1)}
 
 
@@ -1220,7 +1391,9 @@ def main():
 
     learned = None
     if not args.no_learned:
-        learned = run_learned(wl, frames, args.warmup, timed, flush, res)
+        learned = run_learned(wl, frames, args.warmup, timed, flush, res, epochs=args.learned_epochs,
+                              lidar_train_scans=args.learned_lidar_train_scans,
+                              lidar_scans=args.learned_lidar_scans, repeats=args.learned_repeats)
 
     if rank == 0:
         final = res["final"]

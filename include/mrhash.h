@@ -184,13 +184,23 @@ mrh_status mrh_batch_destroy(mrh_batch* batch);
 
 /* ---- Learned level predictor (an addition to the paper's method; the paper has no counterpart).
  * A 16 -> 64 -> 64 -> 3 multilayer perceptron with GELU activations reads 16 features of a NEW block taken from the
- * current depth frame and predicts the level the variance rule of Sec. 3.2.1 would give that block after fusing the
- * sequence. With a predictor set, mrh_integrate_depth allocates each new block at the predicted level instead of the
- * finest one (Sec. 3.2.1 starts every block fine), so a block predicted coarse is never fused at the fine level. The
- * variance rule still runs on every touched block afterwards and re-levels any block the network got wrong. LiDAR
- * frames and batched integration always use the plain rule.
+ * current depth frame or LiDAR scan and predicts the level the variance rule of Sec. 3.2.1 would give that block after
+ * fusing the sequence. With a predictor set, mrh_integrate_depth and mrh_integrate_points allocate each new block at
+ * the predicted level instead of the finest one (Sec. 3.2.1 starts every block fine), so a block predicted coarse is
+ * never fused at the fine level. The variance rule still runs on every touched block afterwards and re-levels any
+ * block the network got wrong. Batched integration always uses the plain rule.
  *
- * Features (float32, in this order; computed on the device from the frame's range image rho = z |(q_x, q_y, 1)|,
+ * LiDAR features (float32, in this order; rounded to BF16): every valid point's end point p = T x (double) in fixed
+ * point gives its block and its position q in the block in units of E / 1024 (integers in [0, 1024)); a new block
+ * takes the moments of the q of its end points (count n, centroid m, covariance C, block units; none for a block that
+ * holds only the truncation band). With c the block centre relative to the sensor, r = |c|, u = c / r and o = m - 1/2
+ * the centroid's offset from the centre:
+ *   f0 r;  f1 S(o.u E / tau);  f2 S(sqrt(u^T C u) E / tau);  f3 sqrt(tr C - u^T C u);  f4 S(n / 16);  f5 E / r;
+ *   f6 sqrt(C_zz);  f7 |o - (o.u) u|;  f8 1 if n > 0 else 0;  f9 |u_z|;  f10 u_z;  f11 sqrt(tr C);  f12 1 / r;
+ *   f13 1 (LiDAR);  f14 tau / E;  f15 1;  all zero statistics when n = 0. c is formed in double and converted to
+ *   float; the rest is float arithmetic.
+ *
+ * Camera features (float32, in this order; computed on the device from the frame's range image rho = z |(q_x, q_y, 1)|,
  * q = ((u - cx)/fx, (v - cy)/fy), and rounded to BF16): with c the block centre in camera coordinates, r = |c|,
  * (u0, v0) its projection rounded to the nearest pixel, s = clamp(floor(fx E / (4 c_z)), 1, 16) pixels and a 5 x 5
  * grid of range samples p_ij at (u0 + (i-2) s, v0 + (j-2) s) (invalid or outside = missing):
@@ -217,9 +227,9 @@ mrh_status mrh_batch_destroy(mrh_batch* batch);
  * the map's device first (frames in flight read the previous weights). */
 mrh_status mrh_set_predictor(mrh_map* map, const uint16_t* bf16_weights_host, uint64_t n_params);
 
-/* Record the features of every new block of later depth frames (training data for the predictor): up to `capacity`
- * records of (key x, y, z; 16 features), in no particular order; later ones are counted but dropped. 0 turns
- * recording off and frees its buffers. Waits for all work on the map's device first. */
+/* Record the features of every new block of later depth frames and LiDAR scans (training data for the predictor):
+ * up to `capacity` records of (key x, y, z; 16 features), in no particular order; later ones are counted but dropped.
+ * 0 turns recording off and frees its buffers. Waits for all work on the map's device first. */
 mrh_status mrh_set_feature_capture(mrh_map* map, uint32_t capacity);
 
 /* Copy the recorded features out: keys_dev n x 3 int32, features_dev n x 16 float32 (device), n_out = n records

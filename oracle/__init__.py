@@ -130,6 +130,8 @@ def _load(path: str | None = None):
         lib.orc_block_features.restype = ctypes.c_int
         lib.orc_block_features.argtypes = [ctypes.POINTER(Pinhole), vp, vp, vp, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int, vp, vp]
+        lib.orc_lidar_block_features.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_int64,
+                                                 ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int, vp, vp]
         lib.orc_set_predictor.argtypes = [vp, vp, ctypes.c_int64]
         lib.orc_set_capture.argtypes = [vp, ctypes.c_int]
         lib.orc_get_features.restype = ctypes.c_int64
@@ -513,4 +515,19 @@ def block_features(K: Pinhole, R: np.ndarray, t: np.ndarray, rho: np.ndarray, E:
                                     int(key[2]), _p(w), n_levels, _p(f), ctypes.byref(lvl))
     if not ok:
         return None
+    return (f, lvl.value) if w is not None else f
+
+
+def lidar_block_features(moments, T_ws: np.ndarray, E: float, tau: float, key, w_bf16: np.ndarray | None = None,
+                         n_levels: int = 3):
+    """Features (16,) float32 of a new block of a LiDAR scan from its 10 end-point moments (n, sums of q_x, q_y,
+    q_z, of q_x^2, q_y^2, q_z^2, of q_x q_y, q_x q_z, q_y q_z; q = position in the block in units of E / 1024) and the
+    scan pose T_ws (4x4, double); and the predicted level when weights are given."""
+    mom = np.ascontiguousarray(moments, dtype=np.uint64).reshape(10)
+    T = np.ascontiguousarray(T_ws, dtype=np.float64).reshape(16)
+    f = np.zeros(MLP_IN, np.float32)
+    lvl = ctypes.c_int(-1)
+    w = None if w_bf16 is None else np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    _load().orc_lidar_block_features(_p(mom), _p(T), E, tau, int(key[0]), int(key[1]), int(key[2]), _p(w),
+                                     n_levels, _p(f), ctypes.byref(lvl))
     return (f, lvl.value) if w is not None else f

@@ -3,9 +3,10 @@
  * at the finest level, Sec. 3.2.1, and has no predictor).
  *
  * TEST INFRASTRUCTURE ONLY, like mrh_oracle.cpp, and shares no code with the CUDA library. It restates the
- * predictor's definition (16 features of a new block from the frame's range image, a 16-64-64-3 GELU network with
- * BF16 weights and activations, first argmax) in plain float arithmetic, one operation at a time in the order the
- * definition gives, so that its level decisions can be compared bit for bit. Compile with -ffp-contract=off.
+ * predictor's definition (16 features of a new block: from the frame's range image for a depth camera, from the
+ * moments of the scan's end points inside the block for a LiDAR scan; a 16-64-64-3 GELU network with BF16 weights and
+ * activations, first argmax) in plain float arithmetic, one operation at a time in the order the definition
+ * gives, so that its level decisions can be compared bit for bit. Compile with -ffp-contract=off.
  *
  * Published methods used (no library math in anything that decides a level):
  *   exp  Cody & Waite argument reduction x = k ln2 + r (ln2 split in a high part with trailing zero bits and a low
@@ -15,8 +16,9 @@
  *   BF16 round to nearest, ties to even, on the float32 bit pattern (inf / NaN passed through).
  *
  * Parity status: the exp / erf / GELU approximations are pinned to math library values within their published error
- * bounds; the forward pass is pinned to an independent float64 evaluation of the same network; the features are
- * pinned to closed forms on constant and linear range images (tests/test_oracle_predictor.py).
+ * bounds; the forward pass is pinned to an independent float64 evaluation of the same network; the camera features
+ * are pinned to closed forms on constant and linear range images, the LiDAR features to closed forms of point sets
+ * with known moments and to a brute-force numpy evaluation from the raw points (tests/test_oracle_predictor.py).
  */
 #include <cmath>
 #include <cstdint>
@@ -173,6 +175,66 @@ bool features(const Cam& K, const float* R, const float* t, const float* rho, fl
   return true;
 }
 
+// The 16 features of a new block of a LiDAR scan, from the moments of the scan's end points that fall inside it.
+// Each end point's position in the block is quantised to q in [0, 1024)^3 (units of E / 1024); mom holds
+// n, sum q_x, sum q_y, sum q_z, sum q_x^2, sum q_y^2, sum q_z^2, sum q_x q_y, sum q_x q_z, sum q_y q_z. T: the scan's
+// pose (world <- sensor, row-major 4 x 4, double). The block centre relative to the sensor is formed in double (the
+// pose's precision) and converted to float; everything after runs in float, like the camera features.
+void lidar_features(const uint64_t* mom, const double* T, float E, float tau, int64_t bx, int64_t by, int64_t bz,
+                    float* f) {
+  const double Ed = (double)E;
+  const float c0 = (float)(((double)bx + 0.5) * Ed - T[3]);
+  const float c1 = (float)(((double)by + 0.5) * Ed - T[7]);
+  const float c2 = (float)(((double)bz + 0.5) * Ed - T[11]);
+  // unit direction u from the sensor to the block centre, and its distance
+  const float r = std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  const float u[3] = {c0 / r, c1 / r, c2 / r};
+  const uint64_t cnt = mom[0];
+  float along = 0.0f, thick2 = 0.0f, total = 0.0f, czz = 0.0f, lateral_off = 0.0f;
+  if (cnt > 0) {
+    const float nf = (float)cnt;
+    float mean[3], off[3];
+    for (int a = 0; a < 3; ++a) {
+      mean[a] = (float)mom[1 + a] / nf;
+      off[a] = (mean[a] + 0.5f) / 1024.0f - 0.5f;  // centroid relative to the block centre, block units
+    }
+    // covariance of the end points, block units squared
+    const float cxx = ((float)mom[4] / nf - mean[0] * mean[0]) / 1048576.0f;
+    const float cyy = ((float)mom[5] / nf - mean[1] * mean[1]) / 1048576.0f;
+    czz = ((float)mom[6] / nf - mean[2] * mean[2]) / 1048576.0f;
+    const float cxy = ((float)mom[7] / nf - mean[0] * mean[1]) / 1048576.0f;
+    const float cxz = ((float)mom[8] / nf - mean[0] * mean[2]) / 1048576.0f;
+    const float cyz = ((float)mom[9] / nf - mean[1] * mean[2]) / 1048576.0f;
+    along = off[0] * u[0] + off[1] * u[1] + off[2] * u[2];
+    const float cu0 = cxx * u[0] + cxy * u[1] + cxz * u[2];
+    const float cu1 = cxy * u[0] + cyy * u[1] + cyz * u[2];
+    const float cu2 = cxz * u[0] + cyz * u[1] + czz * u[2];
+    thick2 = u[0] * cu0 + u[1] * cu1 + u[2] * cu2;  // spread along the viewing direction
+    total = cxx + cyy + czz;
+    const float l0 = off[0] - along * u[0], l1 = off[1] - along * u[1], l2 = off[2] - along * u[2];
+    lateral_off = std::sqrt(l0 * l0 + l1 * l1 + l2 * l2);
+  }
+  const float lat2 = total - thick2;
+  auto soft = [](float x) { return x / (1.0f + std::fabs(x)); };
+  f[0] = r;
+  f[1] = soft(along * E / tau);
+  f[2] = soft(std::sqrt(thick2 > 0.0f ? thick2 : 0.0f) * E / tau);
+  f[3] = std::sqrt(lat2 > 0.0f ? lat2 : 0.0f);
+  f[4] = soft((float)cnt / 16.0f);
+  f[5] = E / r;
+  f[6] = std::sqrt(czz > 0.0f ? czz : 0.0f);
+  f[7] = lateral_off;
+  f[8] = cnt > 0 ? 1.0f : 0.0f;
+  f[9] = std::fabs(u[2]);
+  f[10] = u[2];
+  f[11] = std::sqrt(total > 0.0f ? total : 0.0f);
+  f[12] = 1.0f / r;
+  f[13] = 1.0f;
+  f[14] = tau / E;
+  f[15] = 1.0f;
+  for (int q = 0; q < kIn; ++q) f[q] = round_bf16(f[q]);
+}
+
 // logits of one sample; x already BF16 values; w packed W1[16][64], b1, W2[64][64], b2, W3[64][3], b3 as BF16 bits
 void forward(const uint16_t* w, const float* x, float* logits) {
   const uint16_t* W1 = w;
@@ -243,6 +305,19 @@ int orc_block_features(const orc_pinhole* K, const float* R, const float* t, con
     *level = l < n_levels - 1 ? l : n_levels - 1;
   }
   return 1;
+}
+
+// Features of one new block of a LiDAR scan from its end-point moments (10 values, see lidar_features) and the
+// predicted level (level unset when w is null). T_ws: the scan pose, double, row-major 4 x 4.
+void orc_lidar_block_features(const uint64_t* mom, const double* T_ws, float E, float tau, int64_t bx, int64_t by,
+                              int64_t bz, const uint16_t* w, int n_levels, float* f, int* level) {
+  lidar_features(mom, T_ws, E, tau, bx, by, bz, f);
+  if (w && level) {
+    float z[kOut];
+    forward(w, f, z);
+    int l = first_argmax(z);
+    *level = l < n_levels - 1 ? l : n_levels - 1;
+  }
 }
 
 }  // extern "C"

@@ -258,6 +258,8 @@ struct orc_frame_stats {
 // learned level predictor (level_predictor.cpp)
 int orc_block_features(const orc_pinhole* K, const float* R, const float* t, const float* rho, float E, float tau,
                        int64_t bx, int64_t by, int64_t bz, const uint16_t* w, int n_levels, float* f, int* level);
+void orc_lidar_block_features(const uint64_t* mom, const double* T_ws, float E, float tau, int64_t bx, int64_t by,
+                              int64_t bz, const uint16_t* w, int n_levels, float* f, int* level);
 
 }  // extern "C"
 
@@ -786,6 +788,8 @@ struct Map : MapBase {
     std::vector<RayRec> rays;
     std::vector<int64_t> ray_index;
     std::set<Key> touched;
+    std::vector<Key> fresh;  // blocks created by this scan
+    std::vector<std::array<int64_t, 3>> ends;  // end points of the valid rays (fixed point), when one converts
     // (1) rays (double) and allocation
     for (int64_t j = 0; j < npts; ++j) {
       double xs[3] = {(double)xyz[3 * j], (double)xyz[3 * j + 1], (double)xyz[3 * j + 2]};
@@ -812,11 +816,51 @@ struct Map : MapBase {
       Key kb{floor_div(rr.B[0], kBlockUnit), floor_div(rr.B[1], kBlockUnit), floor_div(rr.B[2], kBlockUnit)};
       if (!key_in_range(ka) || !key_in_range(kb)) continue;
       st->valid_rays++;
-      allocate(cells_bruteforce(rr.A, rr.B, kBlockUnit), touched, st);
+      allocate(cells_bruteforce(rr.A, rr.B, kBlockUnit), touched, st, &fresh);
       rays.push_back(rr);
       ray_index.push_back(j);
+      std::array<int64_t, 3> e;
+      if (to_fixed_d(p[0], Sfix, &e[0]) && to_fixed_d(p[1], Sfix, &e[1]) && to_fixed_d(p[2], Sfix, &e[2]))
+        ends.push_back(e);
     }
     st->touched = (int64_t)touched.size();
+    // (1b) learned level predictor (not in the paper): a new block starts at the level predicted from the moments of
+    // the scan's end points inside it (position in the block quantised to 1/1024 of its edge) instead of the finest
+    // level; capture records the features as training data.
+    if (!pred_w.empty() || capture) {
+      std::map<Key, std::array<uint64_t, 10>> mom;
+      for (const Key& k : fresh) mom[k].fill(0);
+      for (const auto& e : ends) {
+        Key k{floor_div(e[0], kBlockUnit), floor_div(e[1], kBlockUnit), floor_div(e[2], kBlockUnit)};
+        auto it = mom.find(k);
+        if (it == mom.end()) continue;
+        const int64_t kc[3] = {k.x, k.y, k.z};
+        uint64_t q[3];  // 0 <= e - k E < E, in units of E / 1024
+        for (int a = 0; a < 3; ++a) q[a] = (uint64_t)((e[a] - kc[a] * kBlockUnit) / (kBlockUnit / 1024));
+        std::array<uint64_t, 10>& M = it->second;
+        M[0] += 1;
+        for (int a = 0; a < 3; ++a) M[1 + a] += q[a];
+        for (int a = 0; a < 3; ++a) M[4 + a] += q[a] * q[a];
+        M[7] += q[0] * q[1];
+        M[8] += q[0] * q[2];
+        M[9] += q[1] * q[2];
+      }
+      for (const Key& k : fresh) {
+        float f[16];
+        int lvl = -1;
+        orc_lidar_block_features(mom[k].data(), T, E_f, P.truncation, k.x, k.y, k.z,
+                                 pred_w.empty() ? nullptr : pred_w.data(), L, f, &lvl);
+        if (lvl > 0) {
+          Block<R, Sto>& b = blocks[k];
+          b.level = lvl;
+          b.resize(n[lvl], P.has_color != 0);
+        }
+        if (capture) {
+          cap_keys.push_back(k);
+          cap_feat.insert(cap_feat.end(), f, f + 16);
+        }
+      }
+    }
     // (2) ray-based fusion: each ray walks the voxels of its truncation band in ascending point index; a voxel at
     // level l is observed once per ray that crosses it (any of its finest-level cells).
     R Rm[9], t[3];

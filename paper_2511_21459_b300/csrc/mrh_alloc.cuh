@@ -197,12 +197,19 @@ __device__ inline void alloc_points_cta(const MapDev& m, const PoseD& P, const f
   const uint64_t j = first + threadIdx.x;
   if (j < n) {
     LidarRay ray;
-    double rho, rhat[3];
-    const bool ok = lidar_ray(m, P, xyz, j, ray.A, ray.B, &rho, rhat);
+    double rho, rhat[3], p[3];
+    const bool ok = lidar_ray(m, P, xyz, j, ray.A, ray.B, &rho, rhat, m.lidar_end ? p : nullptr);
     ray.rho = ok ? (float)rho : -1.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) ray.rh[a] = (float)rhat[a];
     m.rays[j] = ray;  // reused by the observation passes
+    if (m.lidar_end) {  // the end point in fixed point, for the learned predictor's moments
+      long long e[3];
+      const bool eok = ok && to_fixed_d(p[0], m.fix_scale64, &e[0]) && to_fixed_d(p[1], m.fix_scale64, &e[1]) &&
+                       to_fixed_d(p[2], m.fix_scale64, &e[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m.lidar_end[3 * j + a] = eok ? e[a] : kNoEndPoint;
+    }
     if (ok) {
       atomicAdd(s_valid, 1u);
       add_cells(m, s_set, ray.A, ray.B, frame);
@@ -333,6 +340,7 @@ __device__ inline void begin_frame(DevState* st) {
   st->updated_voxels = 0;
   st->n_over = 0;
   st->max_vox_obs = 0;
+  st->n_fresh = 0;
   st->item_next = 0;
   st->evicted = st->restored = st->n_restore = 0;
 }

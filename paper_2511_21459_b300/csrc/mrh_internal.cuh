@@ -38,6 +38,11 @@ constexpr int kMaxProbeWindows = 64;              // warp-cooperative probing: 6
 constexpr int kMaxProbes = 2048;                  // single-thread probing
 constexpr int kMaxSegmentCells = 64;
 constexpr int kMaxVoxelCells = 256;
+// End-point moments of a new block of a LiDAR scan (learned level predictor): n, sum q_x, sum q_y, sum q_z,
+// sum q_x^2, sum q_y^2, sum q_z^2, sum q_x q_y, sum q_x q_z, sum q_y q_z, with q the end point's position in the block
+// in units of E / 1024 (integers: the sums do not depend on the order of the atomic adds).
+constexpr int kLidarMoments = 10;
+constexpr long long kNoEndPoint = -0x7FFFFFFFFFFFFFFFLL - 1;  // lidar_end of a refused point
 constexpr int kRaycastMaxIter = 8192;
 constexpr int kBrickShift = 2;  // a brick is 4 x 4 x 4 blocks
 constexpr int kSuperShift = 2;  // a super-brick is 4 x 4 x 4 bricks
@@ -77,7 +82,7 @@ struct DevState {
   uint32_t frame;
   uint32_t status;
   uint32_t new_blocks, merged, split, rechecks, valid_rays;
-  uint32_t pad;
+  uint32_t n_fresh;  // LiDAR with the predictor or capture: new blocks listed for prediction this frame
   unsigned long long observations;
   unsigned long long updated_voxels;
   uint32_t obs_total;  // LiDAR: observation records allocated to segments this frame
@@ -139,6 +144,11 @@ struct MapDev {
   float* cap_feat;                 // 16 floats per record
   uint32_t* cap_count;
   uint32_t cap_max;
+  // LiDAR scans with the predictor or capture on (null otherwise), per touched entry i or fresh-list position f:
+  unsigned long long* lidar_mom;   // [i]: end-point moments of a new block
+  long long* lidar_end;            // [point]: end point in fixed point (x, y, z), written by the allocation pass
+  uint32_t* fresh;                 // [f]: touched index of the f-th new block
+  uint8_t* fresh_level;            // [i]: predicted level of a new block
   uint32_t brick_mask;
   float v[kMaxLevels];  // voxel edge per level
   float inv_v[kMaxLevels];  // 1 / v, as the float division computes it
@@ -360,7 +370,7 @@ struct __align__(16) LidarRay {
 // rho = |p - o|, n = (p - o) / rho; band end points o + max(rho - tau, 0) n and o + (rho + tau) n as fixed point.
 // Returns false for a point outside [min_range, max_range], non-finite, or out of key range.
 __device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* xyz, uint64_t j, long long A[3],
-                                 long long B[3], double* rho_out, double rhat[3]) {
+                                 long long B[3], double* rho_out, double rhat[3], double p_out[3] = nullptr) {
   double xs[3] = {(double)xyz[3 * j], (double)xyz[3 * j + 1], (double)xyz[3 * j + 2]};
   double n2 = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
   double rmin2 = (double)m.min_range * (double)m.min_range, rmax2 = (double)m.max_range * (double)m.max_range;
@@ -371,6 +381,7 @@ __device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* x
   for (int a = 0; a < 3; ++a) {
     double p = T[4 * a + 0] * xs[0] + T[4 * a + 1] * xs[1] + T[4 * a + 2] * xs[2] + T[4 * a + 3];
     dv[a] = p - T[4 * a + 3];
+    if (p_out) p_out[a] = p;
   }
   double rho = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
   double tau = (double)m.tau;
@@ -399,6 +410,7 @@ void launch_alloc_depth(const MapDev& m, const CamArgs& c, const float* depth, c
                         uint32_t* rgb_img, cudaStream_t s);
 void launch_alloc_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s);
 void launch_bin(const MapDev& m, cudaStream_t s, int sms);
+void launch_bin_points(const MapDev& m, const double* T, const float* xyz, uint64_t n, cudaStream_t s, int sms);
 // Record the failing call's text for mrh_last_cuda_error (calling thread) and return MRH_ERR_CUDA.
 mrh_status cuda_fail(cudaError_t e, const char* what);
 void launch_bin_camera(const MapDev& m, const CamArgs& c, const float* rho_img, cudaStream_t s, int sms);

@@ -54,6 +54,12 @@ struct mrh_map {
   size_t ray_cap = 0;
   // learned level predictor weights (BF16), owned; d.pred_w points here while the predictor is on
   uint16_t* pred_buf = nullptr;
+  // LiDAR scans with the predictor or capture: end-point moments, fresh list and levels of the new blocks
+  // (one allocation sized by max_touched, made by the first scan that needs it) and the scan's end points (grown to
+  // the largest scan)
+  void* lidar_pred = nullptr;
+  long long* lidar_end = nullptr;
+  size_t end_cap = 0;
 };
 
 namespace mrh {
@@ -343,8 +349,17 @@ void free_all(mrh_map* m) {
   if (m->rho_img) cudaFree(m->rho_img);
   if (m->rgb_img) cudaFree(m->rgb_img);
   if (m->pred_buf) cudaFree(m->pred_buf);
+  if (m->lidar_pred) cudaFree(m->lidar_pred);
+  if (m->lidar_end) cudaFree(m->lidar_end);
   free_capture(m);
   m->pred_buf = nullptr;
+  m->lidar_pred = nullptr;
+  m->lidar_end = nullptr;
+  m->end_cap = 0;
+  m->d.lidar_mom = nullptr;
+  m->d.lidar_end = nullptr;
+  m->d.fresh = nullptr;
+  m->d.fresh_level = nullptr;
   m->d.pred_w = nullptr;
   m->rho_img = nullptr;
   m->rgb_img = nullptr;
@@ -756,8 +771,34 @@ mrh_status mrh_integrate_points(mrh_map* m, const double* T_ws, const float* xyz
     KernelScope ks(m, MRH_K_STREAM, s, 1);
     launch_evict_lidar(m->d, T_ws, s, m->sms);
   }
+  const bool predict = m->d.pred_w || m->d.cap_feat;
+  if (predict) {
+    const size_t nt = m->d.max_touched;
+    if (!m->lidar_pred) {
+      const size_t bytes = nt * (sizeof(unsigned long long) * kLidarMoments + sizeof(uint32_t) + sizeof(uint8_t));
+      MRH_CUDA(cudaMalloc(&m->lidar_pred, bytes));
+    }
+    char* base = (char*)m->lidar_pred;  // moments, fresh list, levels
+    m->d.lidar_mom = (unsigned long long*)base;
+    m->d.fresh = (uint32_t*)(base + nt * sizeof(unsigned long long) * kLidarMoments);
+    m->d.fresh_level = (uint8_t*)((char*)m->d.fresh + nt * sizeof(uint32_t));
+    if (n > m->end_cap) {
+      if (m->lidar_end) cudaFreeAsync(m->lidar_end, s);
+      m->lidar_end = nullptr;
+      m->end_cap = 0;
+      MRH_CUDA(cudaMallocAsync(&m->lidar_end, n * 3 * sizeof(long long), s));
+      m->end_cap = n;
+    }
+  }
+  m->d.lidar_end = predict ? m->lidar_end : nullptr;  // the allocation pass writes end points only when set
   { KernelScope ks(m, MRH_K_ALLOC, s, n ? 1 : 0); launch_alloc_points(m->d, T_ws, xyz, n, s); }
-  { KernelScope ks(m, MRH_K_BIN, s, 1); launch_bin(m->d, s, m->sms); }
+  if (predict) {
+    KernelScope ks(m, MRH_K_BIN, s, n ? 4 : 3);
+    launch_bin_points(m->d, T_ws, xyz, n, s, m->sms);
+  } else {
+    KernelScope ks(m, MRH_K_BIN, s, 1);
+    launch_bin(m->d, s, m->sms);
+  }
   if (m->d.ar_keys) {
     KernelScope ks(m, MRH_K_STREAM, s, 1);
     launch_restore(m->d, s, m->sms);

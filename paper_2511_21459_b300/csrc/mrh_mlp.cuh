@@ -251,4 +251,61 @@ __device__ inline bool warp_block_features(const MapDev& m, const CamArgs& c, co
   return true;
 }
 
+// The 16 features of a new block of a LiDAR scan from its kLidarMoments end-point moments (one thread; the block
+// centre relative to the sensor in double, the pose's precision, then float in source order: the same values as the
+// CPU definition): distance r and unit direction u from the sensor to the block centre; centroid offset o from the
+// centre and covariance C of the end points in block units; f0 r; f1 S(o.u E / tau); f2 S(sqrt(u^T C u) E / tau);
+// f3 sqrt(tr C - u^T C u); f4 S(n / 16); f5 E / r; f6 sqrt(C_zz); f7 |o - (o.u) u|; f8 [n > 0]; f9 |u_z|; f10 u_z;
+// f11 sqrt(tr C); f12 1 / r; f13 1 (LiDAR); f14 tau / E; f15 1 (S(x) = x / (1 + |x|)); each rounded to BF16.
+__device__ inline void lidar_block_features(const unsigned long long* __restrict__ mom, const double* T, float E,
+                                            float tau, int bx, int by, int bz, float f[kMlpIn]) {
+  const double Ed = (double)E;
+  const float c0 = (float)(((double)bx + 0.5) * Ed - T[3]);
+  const float c1 = (float)(((double)by + 0.5) * Ed - T[7]);
+  const float c2 = (float)(((double)bz + 0.5) * Ed - T[11]);
+  const float r = sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+  const float u0 = c0 / r, u1 = c1 / r, u2 = c2 / r;
+  const unsigned long long cnt = mom[0];
+  float along = 0.0f, thick2 = 0.0f, total = 0.0f, czz = 0.0f, lateral_off = 0.0f;
+  if (cnt > 0) {
+    const float nf = (float)cnt;
+    const float mx = (float)mom[1] / nf, my = (float)mom[2] / nf, mz = (float)mom[3] / nf;
+    const float ox = (mx + 0.5f) / 1024.0f - 0.5f, oy = (my + 0.5f) / 1024.0f - 0.5f;
+    const float oz = (mz + 0.5f) / 1024.0f - 0.5f;
+    const float cxx = ((float)mom[4] / nf - mx * mx) / 1048576.0f;
+    const float cyy = ((float)mom[5] / nf - my * my) / 1048576.0f;
+    czz = ((float)mom[6] / nf - mz * mz) / 1048576.0f;
+    const float cxy = ((float)mom[7] / nf - mx * my) / 1048576.0f;
+    const float cxz = ((float)mom[8] / nf - mx * mz) / 1048576.0f;
+    const float cyz = ((float)mom[9] / nf - my * mz) / 1048576.0f;
+    along = ox * u0 + oy * u1 + oz * u2;
+    const float cu0 = cxx * u0 + cxy * u1 + cxz * u2;
+    const float cu1 = cxy * u0 + cyy * u1 + cyz * u2;
+    const float cu2 = cxz * u0 + cyz * u1 + czz * u2;
+    thick2 = u0 * cu0 + u1 * cu1 + u2 * cu2;
+    total = cxx + cyy + czz;
+    const float l0 = ox - along * u0, l1 = oy - along * u1, l2 = oz - along * u2;
+    lateral_off = sqrtf(l0 * l0 + l1 * l1 + l2 * l2);
+  }
+  const float lat2 = total - thick2;
+  f[0] = r;
+  f[1] = squash(along * E / tau);
+  f[2] = squash(sqrtf(thick2 > 0.0f ? thick2 : 0.0f) * E / tau);
+  f[3] = sqrtf(lat2 > 0.0f ? lat2 : 0.0f);
+  f[4] = squash((float)cnt / 16.0f);
+  f[5] = E / r;
+  f[6] = sqrtf(czz > 0.0f ? czz : 0.0f);
+  f[7] = lateral_off;
+  f[8] = cnt > 0 ? 1.0f : 0.0f;
+  f[9] = fabsf(u2);
+  f[10] = u2;
+  f[11] = sqrtf(total > 0.0f ? total : 0.0f);
+  f[12] = 1.0f / r;
+  f[13] = 1.0f;
+  f[14] = tau / E;
+  f[15] = 1.0f;
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) f[k] = bf16_round(f[k]);
+}
+
 }  // namespace mrh

@@ -25,6 +25,15 @@ def init_weights(seed: int) -> np.ndarray:
     return w
 
 
+def constant_level_weights(level: int) -> np.ndarray:
+    """BF16 bit patterns of a network that answers `level` for every input: zero weights, output bias 4 at `level`.
+    Set as a map's predictor it starts every new block at that level (the bound a perfect "go coarse" predictor can
+    reach at most)."""
+    w = np.zeros(MLP_PARAMS, dtype=np.uint16)
+    w[MLP_PARAMS - MLP_LEVELS + level] = 0x4080  # 4.0 in BF16
+    return w
+
+
 def _packed(keys: np.ndarray) -> np.ndarray:
     k = np.asarray(keys, dtype=np.int64) + (1 << 20)
     return (k[:, 0] << 42) | (k[:, 1] << 21) | k[:, 2]

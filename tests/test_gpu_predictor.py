@@ -215,6 +215,57 @@ def test_feature_capture_plain_rule_parity():
     assert np.all(omap.extract()["levels"] == 0)
 
 
+def _run_both_lidar(wl, n_scans, w_bf16, capture=True):
+    m = mrh()
+    gmap = m.Map(m.params_from(wl))
+    omap = oracle.OracleMap(oracle.params_from(wl, "f32s"))
+    if w_bf16 is not None:
+        gmap.set_predictor(w_bf16)
+        omap.set_predictor(w_bf16)
+    if capture:
+        gmap.set_feature_capture(1 << 21)
+        omap.set_capture(True)
+    sc = wl.scene()
+    for f in range(n_scans):
+        xyz, T = synth.render_lidar(wl, f, scene=sc)
+        gmap.integrate_points(T, torch.from_numpy(xyz).cuda())
+        st_o = omap.integrate_points(T, xyz)
+        st_g = gmap.stats()
+        assert st_g["status_code"] == 0, st_g
+        for k in ("valid_rays", "touched", "new_blocks", "merged", "split", "observations", "updated_voxels"):
+            assert st_g[k] == st_o[k], (f, k, st_g[k], st_o[k])
+    compare_extracts(gmap.extract(), omap.extract(), wl.truncation, wl.var_threshold[0], check_color=False)
+    return gmap, omap
+
+
+def test_learned_allocation_parity_lidar_small_scans():
+    """LiDAR scans with a predictor: the end-point moments, the features, the levels of the new blocks and the whole
+    map against the oracle (four 32 x 256 scans, FP16 storage, merges at two observations)."""
+    wl = synth.lidar()
+    wl.n_beams, wl.n_azimuth = 32, 256
+    wl.min_obs = 2
+    gmap, omap = _run_both_lidar(wl, 4, _spread_weights(12))
+    assert _compare_features(gmap, omap) > 10000
+    counts = np.bincount(omap.extract()["levels"], minlength=3)
+    assert np.all(counts > 0), counts
+
+
+def test_learned_allocation_parity_lidar_full_scans():
+    """Two full 128 x 2048 scans of the benchmark's LiDAR configuration with a predictor."""
+    wl = synth.lidar()
+    gmap, omap = _run_both_lidar(wl, 2, _spread_weights(12))
+    assert _compare_features(gmap, omap) > 50000
+
+
+def test_feature_capture_plain_rule_parity_lidar():
+    """LiDAR capture without a predictor (the training-data path): the plain rule's map and the recorded
+    features."""
+    wl = synth.lidar()
+    wl.n_beams, wl.n_azimuth = 64, 512
+    gmap, omap = _run_both_lidar(wl, 3, None)
+    assert _compare_features(gmap, omap) > 10000
+
+
 def test_capture_capacity_and_reset():
     wl = synth.tiny()
     m = mrh()

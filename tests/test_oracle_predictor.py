@@ -277,3 +277,172 @@ def test_predicted_level_in_oracle_map(level):
     for i in range(0, len(keys), max(1, len(keys) // 20)):
         f = oracle.block_features(K, Rf, tf, rho, float(E_f), float(np.float32(wl.truncation)), keys[i])
         np.testing.assert_array_equal(f, feats[i])
+
+
+# ---------------------------------------------------------------------------------------------- LiDAR features
+
+EL, TAUL = 0.5, 0.75  # LiDAR block edge and truncation (dyadic: block centres are exact in float and double)
+
+
+def _grid_moments(qs):
+    """The 10 end-point moments of integer positions qs (n, 3) in a block."""
+    q = np.asarray(qs, np.uint64)
+    x, y, z = q[:, 0], q[:, 1], q[:, 2]
+    return np.array([len(q), x.sum(), y.sum(), z.sum(), (x * x).sum(), (y * y).sum(), (z * z).sum(), (x * y).sum(),
+                     (x * z).sum(), (y * z).sum()], np.uint64)
+
+
+def _pose_at(o):
+    T = np.eye(4)
+    T[:3, 3] = o
+    return T
+
+
+def _grid_var(step, m):
+    """Population variance of the m equally spaced values 0, step, ..., (m - 1) step: step^2 (m^2 - 1) / 12."""
+    return step * step * (m * m - 1) / 12.0
+
+
+def test_lidar_features_horizontal_plane_seen_from_above():
+    """End points on an 8 x 8 grid of a horizontal plane, the sensor straight above the block centre: the spread along
+    the view (f2) and the vertical spread (f6) are zero, the lateral spread (f3, f11) is that of the grid in x and y,
+    and the centroid offsets follow from the grid's mean."""
+    key = (2, 3, -1)
+    c = (np.asarray(key, np.float64) + 0.5) * EL
+    h = 7.0
+    T = _pose_at(c + [0.0, 0.0, h])
+    step, m, qz = 128, 8, 300
+    qs = [(step * i, step * j, qz) for i in range(m) for j in range(m)]
+    f = oracle.lidar_block_features(_grid_moments(qs), T, EL, TAUL, key)
+    off_xy = (step * (m - 1) / 2 + 0.5) / 1024 - 0.5
+    off_z = (qz + 0.5) / 1024 - 0.5
+    lat = math.sqrt(2 * _grid_var(step, m)) / 1024
+    expect = [h, _soft(-off_z * EL / TAUL), 0.0, lat, _soft(64 / 16), EL / h, 0.0, math.sqrt(2) * abs(off_xy), 1.0,
+              1.0, -1.0, lat, 1.0 / h, 1.0, TAUL / EL, 1.0]
+    for i, (a, b) in enumerate(zip(f, expect)):
+        assert _near(float(a), _bf(b)), (i, a, b)
+
+
+def test_lidar_features_vertical_plane_seen_edge_on():
+    """End points on a grid of the plane y = const, viewed along +x (inside the plane): the spread along the view is
+    the grid's spread in x, the lateral spread its spread in z (a swapped axis or a transposed covariance fails)."""
+    key = (-4, 0, 1)
+    c = (np.asarray(key, np.float64) + 0.5) * EL
+    h = 12.0
+    T = _pose_at(c - [h, 0.0, 0.0])
+    qs = [(64 * i, 700, 32 * j) for i in range(16) for j in range(4)]
+    f = oracle.lidar_block_features(_grid_moments(qs), T, EL, TAUL, key)
+    sx, sz = math.sqrt(_grid_var(64, 16)) / 1024, math.sqrt(_grid_var(32, 4)) / 1024
+    off = np.array([(64 * 7.5 + 0.5) / 1024 - 0.5, 700.5 / 1024 - 0.5, (32 * 1.5 + 0.5) / 1024 - 0.5])
+    assert _near(float(f[0]), _bf(h))
+    assert _near(float(f[1]), _bf(_soft(off[0] * EL / TAUL)))
+    assert _near(float(f[2]), _bf(_soft(sx * EL / TAUL)))
+    assert _near(float(f[3]), _bf(sz))
+    assert _near(float(f[6]), _bf(sz))
+    assert _near(float(f[7]), _bf(math.hypot(off[1], off[2])))
+    assert _near(float(f[11]), _bf(math.hypot(sx, sz)))
+    assert float(f[9]) == 0.0 and float(f[10]) == 0.0
+
+
+def test_lidar_features_block_without_end_points():
+    """A block crossed only by free space: every end-point statistic is zero, the geometry features remain."""
+    key = (10, -2, 0)
+    c = (np.asarray(key, np.float64) + 0.5) * EL
+    o = np.array([1.0, 2.0, 3.0])
+    T = _pose_at(o)
+    f = oracle.lidar_block_features(np.zeros(10, np.uint64), T, EL, TAUL, key)
+    r = float(np.linalg.norm(c - o))
+    uz = (c[2] - o[2]) / r
+    assert all(float(f[i]) == 0.0 for i in (1, 2, 3, 4, 6, 7, 8, 11))
+    for i, b in ((0, r), (5, EL / r), (9, abs(uz)), (10, uz), (12, 1.0 / r), (13, 1.0), (14, TAUL / EL), (15, 1.0)):
+        assert _near(float(f[i]), _bf(b)), (i, f[i], b)
+
+
+def test_lidar_features_against_numpy_covariance():
+    """Random end points in random blocks seen from random sensor positions: the oracle's moment formulas (float)
+    against numpy's float64 mean and covariance of the quantised points, projected on the view direction by a matrix
+    product."""
+    rng = np.random.default_rng(5)
+    for trial in range(50):
+        key = tuple(int(k) for k in rng.integers(-50, 50, 3))
+        n = int(rng.integers(1, 400))
+        spread = rng.uniform(0.02, 1.0, 3)
+        q = np.clip(np.floor((0.5 + (rng.random((n, 3)) - 0.5) * spread) * 1024), 0, 1023).astype(np.int64)
+        o = rng.uniform(-30, 30, 3)
+        T = _pose_at(o)
+        f = oracle.lidar_block_features(_grid_moments(q), T, EL, TAUL, key)
+        c = (np.asarray(key, np.float64) + 0.5) * EL - o
+        r = np.linalg.norm(c)
+        u = c / r
+        pos = (q + 0.5) / 1024 - 0.5
+        mean = pos.mean(0)
+        C = np.cov(pos.T, bias=True) if n > 1 else np.zeros((3, 3))
+        along = mean @ u
+        thick = math.sqrt(max(u @ C @ u, 0.0))
+        lat = math.sqrt(max(np.trace(C) - u @ C @ u, 0.0))
+        expect = {0: r, 1: _soft(along * EL / TAUL), 2: _soft(thick * EL / TAUL), 3: lat, 4: _soft(n / 16),
+                  5: EL / r, 6: math.sqrt(max(C[2, 2], 0.0)), 7: np.linalg.norm(mean - along * u), 10: u[2],
+                  11: math.sqrt(max(np.trace(C), 0.0)), 12: 1.0 / r}
+        for i, b in expect.items():
+            # spreads are float differences of large moments (E[q^2] - E[q]^2): allow 1e-6 block units absolute
+            ok = _near(float(f[i]), _bf(b)) or abs(float(f[i]) - b) <= abs(b) * 2.0 ** -7 + 1e-6
+            assert ok, (trial, i, f[i], b)
+
+
+def _lidar_small():
+    wl = synth.lidar()
+    wl.n_beams, wl.n_azimuth = 32, 256
+    return wl
+
+
+def _end_point_moments(T, xyz, E_f, wl):
+    """Moments of every end point's block, from the raw points: p = R x + t evaluated left to right in float64 as
+    the map does, fixed point floor(p 65536 / E), block key floor(fixed / 65536), q = (fixed - key 65536) // 64."""
+    x = xyz.astype(np.float64)
+    n2 = (x * x).sum(1)
+    ok = np.isfinite(n2) & (n2 >= np.float64(np.float32(wl.r_min)) ** 2) & (n2 <= np.float64(np.float32(wl.r_max)) ** 2)
+    x = x[ok]
+    p = np.stack([((T[a, 0] * x[:, 0] + T[a, 1] * x[:, 1]) + T[a, 2] * x[:, 2]) + T[a, 3] for a in range(3)], 1)
+    fixed = np.floor(p * (65536.0 / float(E_f))).astype(np.int64)
+    keys = fixed // 65536
+    q = (fixed - keys * 65536) // 64
+    out = {}
+    for k in np.unique(keys, axis=0):
+        sel = np.all(keys == k, axis=1)
+        out[tuple(int(v) for v in k)] = _grid_moments(q[sel])
+    return out
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_predicted_level_in_oracle_map_lidar(level):
+    """LiDAR scans: a network that always answers `level` puts every block new to the scan at that level (blocks of
+    earlier scans keep theirs); the key set is the plain rule's; each captured record equals the features of the
+    block's end-point moments computed from the raw points."""
+    wl = _lidar_small()
+    sc = wl.scene()
+    scans = [synth.render_lidar(wl, k, scene=sc) for k in range(2)]
+    prm = dict(var_threshold=(-1.0, -1.0), split_hysteresis=0.0)
+    plain = oracle.OracleMap(oracle.params_from(wl, "f32s", **prm))
+    learned = oracle.OracleMap(oracle.params_from(wl, "f32s", **prm))
+    learned.set_predictor(_const_level_weights(level))
+    E_f = float(np.float32(np.float32(wl.base_voxel) / np.float32(2 ** (wl.n_levels - 1))) * np.float32(8))
+    total = 0
+    for xyz, T in scans:
+        learned.set_capture(True)  # records of this scan only
+        plain.integrate_points(T, xyz)
+        st = learned.integrate_points(T, xyz)
+        keys, feats = learned.features()
+        assert len(keys) == st["new_blocks"] > 0
+        total += len(keys)
+    a, b = plain.extract(), learned.extract()
+    np.testing.assert_array_equal(a["keys"], b["keys"])
+    assert np.all(b["levels"] == level)
+    assert total == len(b["keys"])  # every block was new to some scan
+    mom = _end_point_moments(scans[-1][1], scans[-1][0], E_f, wl)
+    seen = 0
+    for k, f in zip(keys, feats):
+        m = mom.get(tuple(int(v) for v in k), np.zeros(10, np.uint64))
+        g = oracle.lidar_block_features(m, scans[-1][1], E_f, float(np.float32(wl.truncation)), k)
+        np.testing.assert_array_equal(g, f)
+        seen += int(m[0] > 0)
+    assert seen > 0.1 * len(keys)  # most new blocks hold only the truncation band in front of or behind a surface
