@@ -93,10 +93,27 @@ __global__ void __launch_bounds__(256) k_batch_release(BatchDev b) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) release_one(m, i);
 }
 
+// Dynamic shared memory of k_batch_fuse: every map's MapDev and camera, copied once per CTA so that the fusion
+// reads them from shared memory (a global copy could alias the payload stores, which would keep them in registers).
+inline size_t fuse_smem_bytes(int n) { return (size_t)n * (sizeof(MapDev) + sizeof(CamArgs)); }
+
 template <bool FP16, bool COLOR, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch_fuse(BatchDev b) {
   __shared__ uint32_t s_end[kBatchMaxMaps];  // inclusive prefix of work items over maps
   __shared__ ItemCounts s_ic[kBatchMaxMaps];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  MapDev* s_maps = reinterpret_cast<MapDev*>(s_dyn);
+  CamArgs* s_cam = reinterpret_cast<CamArgs*>(s_dyn + sizeof(MapDev) * (size_t)b.n);
+  {
+    static_assert(sizeof(MapDev) % 8 == 0 && sizeof(CamArgs) % 4 == 0, "copied in words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.maps);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(s_maps);
+    const int words = b.n * (int)(sizeof(MapDev) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    constexpr int cw = (int)(sizeof(CamArgs) / 4);
+    for (int i = threadIdx.x; i < b.n * cw; i += blockDim.x)
+      reinterpret_cast<uint32_t*>(s_cam)[i] = reinterpret_cast<const uint32_t*>(&b.frames[i / cw].cam)[i % cw];
+  }
   if (threadIdx.x < 32) {
     uint32_t carry = 0;
     for (int base = 0; base < b.n; base += 32) {
@@ -125,9 +142,9 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch_fuse(BatchDev 
   for (uint32_t item = blockIdx.x * WARPS + warp; item < total; item += nwarps) {  // warp-uniform
     while (s_end[mi] <= item) ++mi;  // items rise, so the map index only moves forward
     const uint32_t local = item - (mi > 0 ? s_end[mi - 1] : 0u);
-    const MapDev& m = b.maps[mi];
+    const MapDev& m = s_maps[mi];
     const BatchFrame& f = b.frames[mi];
-    CameraObs<FP16, COLOR> obs{f.cam, f.rho_img, f.rgb ? f.rgb_img : nullptr};
+    CameraObs<FP16, COLOR, const CamArgs&> obs{s_cam[mi], f.rho_img, f.rgb ? f.rgb_img : nullptr};
     unsigned long long my_obs = 0, my_vox = 0;
     fuse_item<FP16, COLOR>(m, obs, warp, s_ic[mi], local, my_obs, my_vox);
     for (int o = 16; o > 0; o >>= 1) {
@@ -244,12 +261,13 @@ void launch_alloc(const mrh_batch* b, int shape, cudaStream_t s) {
 template <int WARPS>
 void launch_fuse_warps(const mrh_batch* b, int grid, cudaStream_t s) {
   const BatchDev d = batch_dev(b);
+  const size_t sm = fuse_smem_bytes(d.n);
   if (b->fp16) {
-    if (b->color) k_batch_fuse<true, true, WARPS><<<grid, 32 * WARPS, 0, s>>>(d);
-    else k_batch_fuse<true, false, WARPS><<<grid, 32 * WARPS, 0, s>>>(d);
+    if (b->color) k_batch_fuse<true, true, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
+    else k_batch_fuse<true, false, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
   } else {
-    if (b->color) k_batch_fuse<false, true, WARPS><<<grid, 32 * WARPS, 0, s>>>(d);
-    else k_batch_fuse<false, false, WARPS><<<grid, 32 * WARPS, 0, s>>>(d);
+    if (b->color) k_batch_fuse<false, true, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
+    else k_batch_fuse<false, false, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
   }
 }
 

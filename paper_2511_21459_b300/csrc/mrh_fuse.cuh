@@ -109,10 +109,11 @@ struct Ctx {
 
 // Reads the frame's range image (rho = z |K^-1 [u v 1]|, written by the allocation kernel with the same float
 // expression, -1 where the depth is invalid) and its colour packed as one 32-bit word per pixel, so a voxel costs one
-// 4-byte gather per image instead of recomputing the pixel ray.
-template <bool FP16, bool COLOR>
+// 4-byte gather per image instead of recomputing the pixel ray. CamT: the camera held by value (a kernel parameter)
+// or by reference (a copy in shared memory, batched path).
+template <bool FP16, bool COLOR, class CamT = CamArgs>
 struct CameraObs {
-  CamArgs c;
+  CamT c;
   const float* rho_img;
   const uint32_t* rgb_img;  // null when the frame has no colour
 

@@ -334,6 +334,7 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
   int jp = 0;
   float tp = 0.0f;
   int cb0 = 0x7FFFFFFF, cb1 = 0, cb2 = 0, jb = 0;  // the allocated block of the last sample and its first sample
+  float dmin_b = 0.0f;                              // and its least stored D
   // refine > 0: the loop evaluates the bracket's midpoint tm (the same code path as every grid sample, so the field
   // evaluation exists once in the kernel)
   int refine = 0;
@@ -386,8 +387,9 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       cb1 = bk[1];
       cb2 = bk[2];
       jb = j;
+      dmin_b = m.dmin[l][val & kPtrMask];  // read once per block: the samples of a block test a register
     }
-    if (!refine && m.dmin[l][val & kPtrMask] > 0.0f) {
+    if (!refine && dmin_b > 0.0f) {
       // inside the block's interior (every corner in the block)? then continue at the interior's last grid sample
       const float vl = m.v[l], in = (0.5f + 1e-3f) * vl;
       float t_out = t_far + 1.0f;
