@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-epochs", type=int, default=12)
+    ap.add_argument("--no-feature-study", action="store_true",
+                    help="skip the comparison of range-image and TSDF-statistics features for the learned level")
     ap.add_argument("--learned-repeats", type=int, default=5, help="interleaved timed runs of plain and learned")
     ap.add_argument("--learned-lidar-train-scans", type=int, default=500)
     ap.add_argument("--learned-lidar-scans", type=int, default=500)
@@ -590,6 +592,159 @@ def run_learned_lidar(lw, w_bf16, net, flush, n_scans=500, warmup=3, repeats=5,
                            "added": round(1000 * (ch_l["chamfer"] - ch_p["chamfer"]), 4)},
             "fscore_10cm": {"plain": round(ch_p["fscore"], 5), "learned": round(ch_l["fscore"], 5)},
             "upper_bound": bound}
+
+
+def _packed_keys(keys):
+    """Block keys (n, 3) int tensor -> one sortable int64 per key."""
+    import torch
+    k = keys.to(torch.int64) + (1 << 20)
+    return (k[:, 0] << 42) | (k[:, 1] << 21) | k[:, 2]
+
+
+def block_statistics(ex, rows, T, wl):
+    """The survey's 16 TSDF-statistics features of existing blocks (rows of an extract, CUDA): mean / min / max D
+    over observed voxels (/ tau), mean / max variance S2 / W (/ theta_0), mean / min / max W (W / (8 + W)), the
+    observed fraction, the normal spread 1 - |mean unit gradient| over observed voxels with |D| < tau, the largest W
+    (frames that observed the block, W / (8 + W)), the distance r of the block centre to the sensor, the cosine
+    between the viewing ray and the mean gradient, the level, E / r, the sensor type (0). Measurement code for the
+    feature study; the library's own predictor reads the range image."""
+    import torch
+    E = float(np.float32(wl.base_voxel) / np.float32(2 ** (wl.n_levels - 1))) * 8.0
+    tau, th0 = float(wl.truncation), float(wl.var_threshold[0])
+    out = torch.zeros((len(rows), 16), dtype=torch.float32, device=ex["D"].device)
+    lv = ex["levels"][rows].long()
+    off = ex["offsets"]
+    o = torch.as_tensor(T[:3, 3], dtype=torch.float32, device=out.device)
+    for l in range(wl.n_levels):
+        sel = (lv == l).nonzero().flatten()
+        if len(sel) == 0:
+            continue
+        n = 8 >> l
+        b = rows[sel]
+        idx = off[b][:, None] + torch.arange(n ** 3, device=out.device)[None, :]
+        D, W, S2 = ex["D"][idx], ex["W"][idx], ex["S2"][idx]
+        obs = W > 0
+        cnt = obs.sum(1).clamp(min=1).float()
+        Dm = torch.where(obs, D, torch.zeros_like(D))
+        var = torch.where(obs, S2 / W.clamp(min=1e-30), torch.zeros_like(D))
+        big = torch.full_like(D, 1e30)
+        f = torch.zeros((len(sel), 16), dtype=torch.float32, device=out.device)
+        f[:, 0] = Dm.sum(1) / cnt / tau
+        f[:, 1] = torch.where(obs, D, big).min(1).values.clamp(max=tau) / tau
+        f[:, 2] = torch.where(obs, D, -big).max(1).values.clamp(min=-tau) / tau
+        f[:, 3] = var.sum(1) / cnt / th0
+        f[:, 4] = var.max(1).values / th0
+        Wobs = torch.where(obs, W, torch.zeros_like(W))
+        f[:, 5] = (Wobs.sum(1) / cnt) / (8.0 + Wobs.sum(1) / cnt)
+        wmin = torch.where(obs, W, big).min(1).values
+        wmin = torch.where(obs.any(1), wmin, torch.zeros_like(wmin))
+        f[:, 6] = wmin / (8.0 + wmin)
+        wmax = Wobs.max(1).values
+        f[:, 7] = wmax / (8.0 + wmax)
+        f[:, 8] = obs.float().mean(1)
+        g = Dm.view(-1, n, n, n)  # z, y, x
+        gx = torch.zeros_like(g)
+        gy = torch.zeros_like(g)
+        gz = torch.zeros_like(g)
+        if n > 1:
+            gx[:, :, :, :-1] = g[:, :, :, 1:] - g[:, :, :, :-1]
+            gy[:, :, :-1, :] = g[:, :, 1:, :] - g[:, :, :-1, :]
+            gz[:, :-1, :, :] = g[:, 1:, :, :] - g[:, :-1, :, :]
+        gv = torch.stack([gx, gy, gz], -1).view(len(sel), -1, 3)
+        gn = gv / gv.norm(dim=-1, keepdim=True).clamp(min=1e-12)
+        band = (obs & (D.abs() < tau)).float()[..., None]
+        mg = (gn * band).sum(1) / band.sum(1).clamp(min=1)
+        f[:, 9] = 1.0 - mg.norm(dim=-1)
+        f[:, 10] = f[:, 7]
+        centre = (ex["keys"][b].float() + 0.5) * E - o
+        r = centre.norm(dim=-1)
+        f[:, 11] = r
+        mgn = mg / mg.norm(dim=-1, keepdim=True).clamp(min=1e-12)
+        f[:, 12] = ((centre / r[:, None]) * mgn).sum(-1)
+        f[:, 13] = float(l)
+        f[:, 14] = E / r
+        f[:, 15] = 0.0
+        out[sel] = f
+    return out
+
+
+def run_feature_study(wl, train_seeds=(11, 12), eval_seed=1, n_frames=100, epochs=30, obs_frames=4):
+    """Which features predict a block's final level (the plain rule's) best? For every new block of each sequence:
+    (a) the library's range-image features at creation; (b) TSDF statistics of the block after the frame that
+    created it; (c) TSDF statistics when it has first been observed by `obs_frames` frames (an existing block). One
+    network per feature set, trained by the library's kernels on the training sequences, scored on the evaluation
+    sequence's blocks against the plain rule's final levels (with the all-finest answer as the baseline)."""
+    import dataclasses
+    import torch
+    import paper_2511_21459_b300 as mrh
+    from paper_2511_21459_b300 import predictor
+    t0 = time.perf_counter()
+    K = mrh.pinhole_from(wl)
+
+    def sequence(seed):
+        w = dataclasses.replace(wl, seed=seed)
+        frs = camera_frames(w, 0, n_frames)
+        m = mrh.Map(mrh.params_from(w))
+        m.set_feature_capture(1 << 20)
+        ka, fa, kb, fb, kc, fc = [], [], [], [], [], []
+        done = torch.empty(0, dtype=torch.int64, device="cuda")
+        for d, c, T in frs:
+            m.integrate_depth(K, T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda())
+            keys, feats, _ = m.features(reset=True)
+            ex = m.extract()
+            pk = _packed_keys(ex["keys"])  # extract is sorted by key
+            if len(keys):
+                rows = torch.searchsorted(pk, _packed_keys(keys))
+                rows = rows.clamp(max=len(pk) - 1)
+                ok = pk[rows] == _packed_keys(keys)
+                ka.append(keys[ok])
+                fa.append(feats[ok])
+                kb.append(keys[ok])
+                fb.append(block_statistics(ex, rows[ok], T, w))
+            # blocks whose most-observed voxel has reached obs_frames observations, first time
+            nb = len(pk)
+            seg = torch.repeat_interleave(torch.arange(nb, device="cuda"), ex["offsets"][1:] - ex["offsets"][:-1])
+            wmax = torch.zeros(nb, device="cuda").scatter_reduce_(0, seg, ex["W"], "amax")
+            cand = (wmax >= obs_frames).nonzero().flatten()
+            cand = cand[~torch.isin(pk[cand], done)]
+            if len(cand):
+                done = torch.cat([done, pk[cand]])
+                kc.append(ex["keys"][cand])
+                fc.append(block_statistics(ex, cand, T, w))
+        ex = m.extract()
+        fk, fl = ex["keys"].cpu().numpy(), ex["levels"].cpu().numpy()
+        m.close()
+
+        def lab(ks, fs):
+            ks = torch.cat(ks)
+            fs = torch.cat(fs)
+            y = predictor.level_labels(ks.cpu().numpy(), fk, fl)
+            ok = torch.from_numpy(y >= 0).cuda()
+            return fs[ok].contiguous(), torch.from_numpy(y[y >= 0]).cuda()
+
+        return {"a": lab(ka, fa), "b": lab(kb, fb), "c": lab(kc, fc)}
+
+    train = [sequence(sd) for sd in train_seeds]
+    ev = sequence(eval_seed)
+    out = {}
+    names = {"a": "range image at creation (the library's predictor)", "b": "TSDF statistics after the creating frame",
+             "c": f"TSDF statistics once observed by {obs_frames} frames"}
+    for key, name in names.items():
+        x = torch.cat([t[key][0] for t in train])
+        y = torch.cat([t[key][1] for t in train])
+        net, hist = predictor.train(x, y, epochs=epochs, batch=4096, lr=2e-3, seed=0)
+        xe, ye = ev[key]
+        pred = predictor.predicted_levels(net, xe)
+        out[key] = {"features": name, "train_samples": int(x.shape[0]), "eval_samples": int(xe.shape[0]),
+                    "misclassification": round(float((pred != ye).float().mean().item()), 4),
+                    "all_finest_misclassification": round(float((ye != 0).float().mean().item()), 4),
+                    "coarse_recall": round(float(((pred > 0) & (ye > 0)).sum().item() / max(1, (ye > 0).sum().item())), 4),
+                    "train_loss": [round(hist[0], 4), round(hist[-1], 4)]}
+    out["frames_per_sequence"] = n_frames
+    out["train_seeds"] = list(train_seeds)
+    out["eval_seed"] = eval_seed
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def run_learned(wl, frames, warmup, timed, flush, plain, train_frames=150, epochs=12, lidar_train_scans=500,
@@ -1394,6 +1549,8 @@ def main():
         learned = run_learned(wl, frames, args.warmup, timed, flush, res, epochs=args.learned_epochs,
                               lidar_train_scans=args.learned_lidar_train_scans,
                               lidar_scans=args.learned_lidar_scans, repeats=args.learned_repeats)
+        if rank == 0 and not args.no_feature_study:
+            learned["feature_study"] = run_feature_study(wl)
 
     if rank == 0:
         final = res["final"]
