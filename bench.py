@@ -349,15 +349,48 @@ def fuse_bytes_lidar(stats, n_points, s_v):
     return 12 * n_points + 2 * s_v * stats["updated_voxels"] + 16 * stats["touched"]
 
 
-def fusion_source_sha256() -> str:
-    """Hash of the sources the camera fusion kernel is compiled from (a stored ncu capture is used only while it
-    matches)."""
+def source_sha256(files=("mrh_fuse.cu", "mrh_fuse.cuh", "mrh_internal.cuh"), with_build=False) -> str:
+    """Hash of the sources a kernel is compiled from, and optionally of the build script that holds the compiler
+    flags (a stored ncu capture is used only while it matches)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("mrh_fuse.cu", "mrh_fuse.cuh", "mrh_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2511_21459_b300", "csrc", f), "rb") as fh:
+    paths = [os.path.join(ROOT, "paper_2511_21459_b300", "csrc", f) for f in files]
+    if with_build:
+        paths.append(os.path.join(ROOT, "paper_2511_21459_b300", "build.py"))
+    for path in paths:
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def fusion_source_sha256() -> str:
+    return source_sha256()
+
+
+RAYCAST_SOURCES = ("mrh_raycast.cu", "mrh_raycast.cuh", "mrh_internal.cuh")
+
+
+def raycast_roofline(ray_ms_avg, rays_per_launch, clk, n_sms):
+    """The raycast against the instruction-issue roofline: it is bound by issue and dependent latency (0.5 % of
+    HBM). achieved = warp instructions per launch / launch time, the instructions per ray taken from one ncu capture
+    of the same kernel on a view of the grown map (profiles/raycast_rgbd.json) times this run's rays per launch;
+    peak = SMs x 4 schedulers x one warp instruction per cycle at the highest SM clock sampled under load."""
+    path = os.path.join(ROOT, "profiles", "raycast_rgbd.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        pr = json.load(f)
+    if pr.get("source_sha256") != source_sha256(RAYCAST_SOURCES, with_build=True):
+        return None
+    mhz = float((clk or {}).get("sm_max_mhz") or pr["sm_mhz"])
+    peak = n_sms * 4 * mhz * 1e6 / 1e9  # G warp instructions / s
+    instr = pr["warp_instructions_per_ray"] * rays_per_launch
+    ach = instr / (ray_ms_avg / 1000.0) / 1e9
+    return {"kernel": "k_raycast (depth, normal, colour)", "bound": "alu", "achieved": round(ach, 1),
+            "peak": round(peak, 1), "unit": "G warp instructions/s", "frac": round(ach / peak, 4),
+            "peak_kind": "derived: SMs x 4 schedulers x SM clock", "traffic": None,
+            "warp_instructions_per_launch": int(instr), "active_threads_per_instruction": pr["active_threads"],
+            "launch_ms_avg": round(ray_ms_avg, 5)}
 
 
 def voxel_bytes(wl):
@@ -1464,6 +1497,10 @@ def main():
             # one ncu capture of a full-size frame of the same sequence, scaled to this run's launches by the
             # algorithmic bytes (units) they process
             traffic = int(tr["dram_bytes_per_algorithmic_byte"] * res["fuse_bytes"] / args.steps)
+    roofline_ray = None
+    if prof.get("raycast", (0, 0))[1] > 0:
+        n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        roofline_ray = raycast_roofline(prof["raycast"][0] / prof["raycast"][1], wl.width * wl.height, clk, n_sms)
     roofline = {"kernel": "k_fuse_depth (fusion + block variance + re-level)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "peak_kind": peak_kind, "traffic": traffic,
@@ -1565,7 +1602,8 @@ def main():
                                      f"frames, every other frame integrated untimed in sequence order",
                            "l2": "flushed between steps (256 MiB write outside the timed events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "frames_per_s": fps, "roofline": roofline, "roofline_lidar": roofline_lidar, "cpu_baseline": cpu,
+                "frames_per_s": fps, "roofline": roofline, "roofline_raycast": roofline_ray,
+                "roofline_lidar": roofline_lidar, "cpu_baseline": cpu,
                 "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
                 "map": {"live_blocks": final["live_blocks"], "touched_last": final["touched"]},
