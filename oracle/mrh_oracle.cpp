@@ -800,9 +800,15 @@ struct Map : MapBase {
         p[a] = T[4 * a + 0] * xs[0] + T[4 * a + 1] * xs[1] + T[4 * a + 2] * xs[2] + T[4 * a + 3];
         dv[a] = p[a] - T[4 * a + 3];
       }
+      // length and direction of the ray in float (reading: FP64 is confined to the pose composition above and the
+      // fixed-point band ends below)
       RayRec rr;
-      rr.rho = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-      for (int a = 0; a < 3; ++a) rr.rhat[a] = dv[a] / rr.rho;
+      const float d0 = (float)dv[0], d1 = (float)dv[1], d2 = (float)dv[2];
+      const float rf = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      rr.rho = (double)rf;
+      rr.rhat[0] = (double)(d0 / rf);
+      rr.rhat[1] = (double)(d1 / rf);
+      rr.rhat[2] = (double)(d2 / rf);
       double t0 = rr.rho - tau_d;
       if (t0 < 0.0) t0 = 0.0;
       double t1 = rr.rho + tau_d;

@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(256) k_batch_release(BatchDev b) {
 // reads them from shared memory (a global copy could alias the payload stores, which would keep them in registers).
 inline size_t fuse_smem_bytes(int n) { return (size_t)n * (sizeof(MapDev) + sizeof(CamArgs)); }
 
-template <bool FP16, bool COLOR, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch_fuse(BatchDev b) {
+template <bool FP16, bool COLOR, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_batch_fuse(BatchDev b) {
   __shared__ uint32_t s_end[kBatchMaxMaps];  // inclusive prefix of work items over maps
   __shared__ ItemCounts s_ic[kBatchMaxMaps];
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -186,9 +186,9 @@ struct AllocShape {
 };
 constexpr AllocShape kAllocShapes[] = {{32, 8, 8}, {16, 16, 8}, {32, 8, 4}, {16, 16, 4}};
 struct FuseShape {
-  int warps, per_sm;
+  int warps, per_sm;  // warps per CTA, CTAs per SM in the persistent grid (also the residency the registers allow)
 };
-constexpr FuseShape kFuseShapes[] = {{8, 4}, {8, 8}, {4, 8}, {4, 16}};
+constexpr FuseShape kFuseShapes[] = {{8, 4}, {8, 8}, {4, 8}, {8, 3}};
 constexpr int kRayShapes = 2;  // warp tile 8 x 4, 16 x 2
 constexpr int kTrials = 4;
 
@@ -258,24 +258,27 @@ void launch_alloc(const mrh_batch* b, int shape, cudaStream_t s) {
   }
 }
 
-template <int WARPS>
+template <int WARPS, int MINB>
 void launch_fuse_warps(const mrh_batch* b, int grid, cudaStream_t s) {
   const BatchDev d = batch_dev(b);
   const size_t sm = fuse_smem_bytes(d.n);
   if (b->fp16) {
-    if (b->color) k_batch_fuse<true, true, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
-    else k_batch_fuse<true, false, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
+    if (b->color) k_batch_fuse<true, true, WARPS, MINB><<<grid, 32 * WARPS, sm, s>>>(d);
+    else k_batch_fuse<true, false, WARPS, MINB><<<grid, 32 * WARPS, sm, s>>>(d);
   } else {
-    if (b->color) k_batch_fuse<false, true, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
-    else k_batch_fuse<false, false, WARPS><<<grid, 32 * WARPS, sm, s>>>(d);
+    if (b->color) k_batch_fuse<false, true, WARPS, MINB><<<grid, 32 * WARPS, sm, s>>>(d);
+    else k_batch_fuse<false, false, WARPS, MINB><<<grid, 32 * WARPS, sm, s>>>(d);
   }
 }
 
+// 64 registers a thread at 32 warps per SM; the 3-CTA shape trades a quarter of the warps for 80 registers and no
+// spills
 void launch_fuse(const mrh_batch* b, int shape, cudaStream_t s) {
   const FuseShape fs = kFuseShapes[shape];
   const int grid = b->sms * fs.per_sm;
-  if (fs.warps == 8) launch_fuse_warps<8>(b, grid, s);
-  else launch_fuse_warps<4>(b, grid, s);
+  if (fs.warps == 8 && fs.per_sm == 3) launch_fuse_warps<8, 3>(b, grid, s);
+  else if (fs.warps == 8) launch_fuse_warps<8, 4>(b, grid, s);
+  else launch_fuse_warps<4, 8>(b, grid, s);
 }
 
 void launch_raycast_shape(const mrh_batch* b, int shape, cudaStream_t s) {

@@ -383,15 +383,20 @@ __device__ inline bool lidar_ray(const MapDev& m, const PoseD& P, const float* x
     dv[a] = p - T[4 * a + 3];
     if (p_out) p_out[a] = p;
   }
-  double rho = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-  double tau = (double)m.tau;
+  // the ray's length and direction in float: double is kept for the pose composition above and for the fixed-point
+  // band ends below, whose block keys must not lose precision at 80 m
+  const float d0 = (float)dv[0], d1 = (float)dv[1], d2 = (float)dv[2];
+  const float rf = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  rhat[0] = (double)(d0 / rf);
+  rhat[1] = (double)(d1 / rf);
+  rhat[2] = (double)(d2 / rf);
+  const double rho = (double)rf, tau = (double)m.tau;
   double t0 = rho - tau;
   if (t0 < 0.0) t0 = 0.0;
   double t1 = rho + tau;
   bool ok = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    rhat[a] = dv[a] / rho;
     ok = ok && to_fixed_d(T[4 * a + 3] + t0 * rhat[a], m.fix_scale64, &A[a]);
     ok = ok && to_fixed_d(T[4 * a + 3] + t1 * rhat[a], m.fix_scale64, &B[a]);
   }
