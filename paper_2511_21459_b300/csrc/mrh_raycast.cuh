@@ -199,8 +199,9 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
     *out = acc;
     return true;
   }
-  // corners in blocks of different levels
-  float acc = 0.0f;
+  // corners in blocks of different levels: every corner's block and voxel first, the 16 loads issued together (no
+  // early exit between them), then the observed test and the sum in corner order
+  float w[8], d[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
@@ -221,11 +222,20 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
       for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
       idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
     }
-    if (!(read_W<FP16, COLOR>(blk, nb * nb * nb, idx) > 0.0f)) return false;
-    const float wx = ax ? fr[0] : 1.0f - fr[0];
-    const float wy = ay ? fr[1] : 1.0f - fr[1];
-    const float wz = az ? fr[2] : 1.0f - fr[2];
-    acc = fmaf(wx * wy * wz, read_D<FP16>(blk, idx), acc);
+    w[k] = read_W<FP16, COLOR>(blk, nb * nb * nb, idx);
+    d[k] = read_D<FP16>(blk, idx);
+  }
+  bool all = true;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) all = all && w[k] > 0.0f;
+  if (!all) return false;
+  float acc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float wx = (k & 1) ? fr[0] : 1.0f - fr[0];
+    const float wy = ((k >> 1) & 1) ? fr[1] : 1.0f - fr[1];
+    const float wz = (k >> 2) ? fr[2] : 1.0f - fr[2];
+    acc = fmaf(wx * wy * wz, d[k], acc);
   }
   *out = acc;
   return true;
@@ -234,8 +244,8 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
 // Surface attributes at a hit x in a block of level l, over the 8 corners field() uses (each corner's block and voxel
 // found the same way): g = the interpolant's gradient times v_l (the x weight's derivative is +1 for the upper
 // corner, -1 for the lower), col = the trilinear mean of the stored colour, both summed in corner order. False when a
-// corner's block is unallocated or a corner is unobserved. Runs once per hit pixel, so it takes the generic corner
-// path only.
+// corner's block is unallocated or a corner is unobserved. Runs once per hit pixel; the corners' weights and
+// distances are loaded together before they are tested.
 template <bool FP16, bool COLOR>
 __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, float g[3], float col[3]) {
   const float inv = m.inv_v[l];
@@ -251,8 +261,11 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
     col[a] = 0.0f;
   }
   const int sh = 3 - l, nl = 1 << sh, mask = nl - 1;
+  const uint8_t* blk[8];
+  int nvs[8], idx[8];
   int lb0 = 0x7FFFFFFF, lb1 = 0, lb2 = 0;  // the last corner's block and its heap value (corners share blocks)
   uint32_t lval = kValPending;
+#pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
     const int j[3] = {j0[0] + ax, j0[1] + ay, j0[2] + az};
@@ -263,33 +276,44 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
       lb2 = c2;
       lval = find_block(m.slots, m.slot_mask, c0, c1, c2);
     }
-    const uint32_t val = lval;
-    if (val == kValPending) return false;
-    const int lb = (int)((val >> 28) & 3u);
-    const int nb = kFineDim >> lb, nv = nb * nb * nb;
-    const uint8_t* blk = block_ptr(m, val);
-    int idx;
+    if (lval == kValPending) return false;
+    const int lb = (int)((lval >> 28) & 3u);
+    const int nb = kFineDim >> lb;
+    blk[k] = block_ptr(m, lval);
+    nvs[k] = nb * nb * nb;
     if (lb == l) {
-      idx = (j[0] & mask) + nl * ((j[1] & mask) + nl * (j[2] & mask));
+      idx[k] = (j[0] & mask) + nl * ((j[1] & mask) + nl * (j[2] & mask));
     } else {
       int cc[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) cc[a] = (l == 0 ? j[a] : (j[a] << l) + (1 << (l - 1))) >> lb;
-      idx = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
+      idx[k] = (cc[0] & (nb - 1)) + nb * ((cc[1] & (nb - 1)) + nb * (cc[2] & (nb - 1)));
     }
-    if (!(read_W<FP16, COLOR>(blk, nv, idx) > 0.0f)) return false;
+  }
+  float w[8], d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    w[k] = read_W<FP16, COLOR>(blk[k], nvs[k], idx[k]);
+    d[k] = read_D<FP16>(blk[k], idx[k]);
+  }
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ok = ok && w[k] > 0.0f;
+  if (!ok) return false;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int ax = k & 1, ay = (k >> 1) & 1, az = k >> 2;
     const float wx = ax ? fr[0] : 1.0f - fr[0];
     const float wy = ay ? fr[1] : 1.0f - fr[1];
     const float wz = az ? fr[2] : 1.0f - fr[2];
-    const float d = read_D<FP16>(blk, idx);
-    const float tx = (wy * wz) * d, ty = (wx * wz) * d, tz = (wx * wy) * d;
+    const float tx = (wy * wz) * d[k], ty = (wx * wz) * d[k], tz = (wx * wy) * d[k];
     g[0] = ax ? g[0] + tx : g[0] - tx;
     g[1] = ay ? g[1] + ty : g[1] - ty;
     g[2] = az ? g[2] + tz : g[2] - tz;
     if (COLOR) {
-      const float w = (wx * wy) * wz;
+      const float wt = (wx * wy) * wz;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) col[q] = col[q] + w * read_C<FP16>(blk, nv, idx, q);
+      for (int q = 0; q < 3; ++q) col[q] = col[q] + wt * read_C<FP16>(blk[k], nvs[k], idx[k], q);
     }
   }
   return true;
@@ -475,8 +499,7 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     bool ok = false;
     if (hit) {
       const float xh[3] = {fmaf(t_hit, r[0], o[0]), fmaf(t_hit, r[1], o[1]), fmaf(t_hit, r[2], o[2])};
-      const uint32_t val = find_block(m.slots, m.slot_mask, ifloor(xh[0] * invE), ifloor(xh[1] * invE),
-                                      ifloor(xh[2] * invE));
+      const uint32_t val = bc.get(m, ifloor(xh[0] * invE), ifloor(xh[1] * invE), ifloor(xh[2] * invE));
       ok = val != kValPending && shade<FP16, COLOR>(m, xh, (int)((val >> 28) & 3u), g, col);
     }
     if (out.normal) {
