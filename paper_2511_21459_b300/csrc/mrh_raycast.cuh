@@ -136,15 +136,19 @@ __device__ bool field(const MapDev& m, BlockCache& bc, const float x[3], int l, 
   const bool sx = (j0[0] & mask) == mask, sy = (j0[1] & mask) == mask, sz = (j0[2] & mask) == mask;
   // distinct blocks of the corners, in registers: v<zyx> for the block offset (x, y, z) in {0, 1}^3
   uint32_t v000, v100 = 0, v010 = 0, v110 = 0, v001 = 0, v101 = 0, v011 = 0, v111 = 0;
+  // every needed block is looked up before any is tested (a missing one only ends the sample afterwards)
   v000 = bc.get(m, b0[0], b0[1], b0[2]);
-  bool ok = v000 != kValPending;
-  if (ok && sx) { v100 = bc.get(m, b0[0] + 1, b0[1], b0[2]); ok = v100 != kValPending; }
-  if (ok && sy) { v010 = bc.get(m, b0[0], b0[1] + 1, b0[2]); ok = v010 != kValPending; }
-  if (ok && sx && sy) { v110 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2]); ok = v110 != kValPending; }
-  if (ok && sz) { v001 = bc.get(m, b0[0], b0[1], b0[2] + 1); ok = v001 != kValPending; }
-  if (ok && sx && sz) { v101 = bc.get(m, b0[0] + 1, b0[1], b0[2] + 1); ok = v101 != kValPending; }
-  if (ok && sy && sz) { v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1); ok = v011 != kValPending; }
-  if (ok && sx && sy && sz) { v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1); ok = v111 != kValPending; }
+  if (sx) v100 = bc.get(m, b0[0] + 1, b0[1], b0[2]);
+  if (sy) v010 = bc.get(m, b0[0], b0[1] + 1, b0[2]);
+  if (sx && sy) v110 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2]);
+  if (sz) v001 = bc.get(m, b0[0], b0[1], b0[2] + 1);
+  if (sx && sz) v101 = bc.get(m, b0[0] + 1, b0[1], b0[2] + 1);
+  if (sy && sz) v011 = bc.get(m, b0[0], b0[1] + 1, b0[2] + 1);
+  if (sx && sy && sz) v111 = bc.get(m, b0[0] + 1, b0[1] + 1, b0[2] + 1);
+  const bool ok = v000 != kValPending && (!sx || v100 != kValPending) && (!sy || v010 != kValPending) &&
+                  (!(sx && sy) || v110 != kValPending) && (!sz || v001 != kValPending) &&
+                  (!(sx && sz) || v101 != kValPending) && (!(sy && sz) || v011 != kValPending) &&
+                  (!(sx && sy && sz) || v111 != kValPending);
   if (!ok) return false;
   const uint32_t lvl = (uint32_t)l;
   const bool same = ((v000 >> 28) & 3u) == lvl && (!sx || ((v100 >> 28) & 3u) == lvl) &&
