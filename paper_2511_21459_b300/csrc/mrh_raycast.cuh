@@ -18,6 +18,8 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include <cstddef>
+
 #include "mrh_internal.cuh"
 
 namespace mrh {
@@ -40,16 +42,37 @@ __device__ inline int ifloor(float v) {
 
 // heap value of block (x, y, z), or kValPending when the block is not allocated or has no storage. Not inlined:
 // the probe loop is the cache-miss path of several call sites, and one copy keeps the kernel's code small.
+static_assert(sizeof(Slot) == 16 && offsetof(Slot, val) == 8, "find_block reads a slot as one ulonglong2");
+
+// Linear probing as lookup_slot, each probe one 16-byte load of the whole slot (key and heap value together, so a
+// hit costs no second dependent load).
 __device__ __noinline__ uint32_t find_block(const Slot* __restrict__ slots, uint32_t slot_mask, int x, int y, int z) {
   if (!key_ok32(x, y, z)) return kValPending;
-  const int s = lookup_slot(slots, slot_mask, pack_key(x, y, z));
-  return s >= 0 ? slots[s].val : kValPending;
+  const unsigned long long key = pack_key(x, y, z);
+  const uint32_t h = hash_key(key, slot_mask);
+  const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(slots);
+  for (int p = 0; p < kMaxProbes; ++p) {
+    const ulonglong2 e = sl[(h + (uint32_t)p) & slot_mask];
+    if (e.x == key) return (uint32_t)e.y;  // Slot::val: the low word after the key
+    if (e.x == kEmptyKey) return kValPending;
+  }
+  return kValPending;
 }
 
+// occupancy_bits with the mask word loaded next to each probed key (no second dependent load on a hit)
 __device__ __noinline__ unsigned long long find_bits(const unsigned long long* __restrict__ keys,
                                                      const unsigned long long* __restrict__ vals, uint32_t mask,
                                                      int x, int y, int z) {
-  return key_ok32(x, y, z) ? occupancy_bits(keys, vals, mask, x, y, z) : 0ull;
+  if (!key_ok32(x, y, z)) return 0ull;
+  const unsigned long long key = pack_key(x, y, z);
+  const uint32_t h = hash_xyz(x, y, z, mask);
+  for (int p = 0; p < kMaxProbes; ++p) {
+    const uint32_t s = (h + (uint32_t)p) & mask;
+    const unsigned long long c = keys[s], b = vals[s];
+    if (c == key) return b;
+    if (c == kEmptyKey) return 0ull;
+  }
+  return 0ull;
 }
 
 // Two most recent block lookups, keyed by coordinates, in registers (static indices only).
