@@ -1,8 +1,28 @@
 // Kernels and launchers of fusion for one map, and the LiDAR observation passes (device code in mrh_fuse.cuh).
+#include <cstddef>
+
 #include "mrh_fuse.cuh"
 
 namespace mrh {
 namespace {
+
+// lookup_slot reading each probed slot with one 16-byte load, so that the heap value of a hit comes with its key.
+// Returns the slot index or -1; *val = the slot's heap value on a hit.
+__device__ inline int probe_slot(const Slot* __restrict__ slots, uint32_t mask, unsigned long long key, uint32_t* val) {
+  static_assert(sizeof(Slot) == 16 && offsetof(Slot, val) == 8, "a slot is read as one ulonglong2");
+  const uint32_t h = hash_key(key, mask);
+  const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(slots);
+  for (int p = 0; p < kMaxProbes; ++p) {
+    const uint32_t s = (h + (uint32_t)p) & mask;
+    const ulonglong2 e = sl[s];
+    if (e.x == key) {
+      *val = (uint32_t)e.y;
+      return (int)s;
+    }
+    if (e.x == kEmptyKey) return -1;
+  }
+  return -1;
+}
 
 constexpr int kCamWarps = 8;
 
@@ -96,9 +116,9 @@ __device__ inline void lidar_point(const MapDev& m, const PoseD& P, uint64_t j) 
       cb[0] = bk[0]; cb[1] = bk[1]; cb[2] = bk[2];
       have_last = false;
       cur_ok = false;
-      int s = lookup_slot(m.slots, m.slot_mask, pack_key(bk[0], bk[1], bk[2]));
+      uint32_t val = kValPending;
+      const int s = probe_slot(m.slots, m.slot_mask, pack_key(bk[0], bk[1], bk[2]), &val);
       if (s >= 0) {
-        uint32_t val = m.slots[s].val;
         if (val != kValPending) {
           uint32_t sp = m.slot_pos[s];
           uint32_t lv = sp >> 28, jj = sp & kPtrMask;
