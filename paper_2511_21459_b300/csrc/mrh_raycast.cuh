@@ -357,8 +357,9 @@ __device__ __noinline__ bool shade(const MapDev& m, const float x[3], int l, flo
 //     continues at the first grid sample past the cell's exit face;
 //   - in a block whose observed voxels all hold D > 0 (dmin, kept by the fusion epilogue), every sample whose 8
 //     corners lie in the block (the block shrunk by half a voxel, and by a further 1e-3 voxel so that float rounding
-//     of the position cannot move a sample across) has F > 0 or no field: the march continues at the last grid
-//     sample of that interior (of the block's pitch), which it evaluates, since it may begin a bracket;
+//     of the position cannot move a sample across) has F > 0 or no field: after the first such sample the march
+//     continues at the last grid sample of that interior (of the block's pitch), which it evaluates, since it may
+//     begin a bracket;
 //   - the bracket (1 to 4 grid steps wide) is narrowed by bisections (the definition's own first steps) down to h / 8
 //     and the linear root of the last bracket: the result lies within h / 8 of the fully converged crossing of the
 //     same bracket.
@@ -440,8 +441,10 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       jb = j;
       dmin_b = m.dmin[l][val & kPtrMask];  // read once per block: the samples of a block test a register
     }
+    int j_skip = -1;  // the interior's last grid sample, when this sample lies in a positive block's interior
     if (!refine && dmin_b > 0.0f) {
-      // inside the block's interior (every corner in the block)? then continue at the interior's last grid sample
+      // inside the block's interior (every corner in the block)? then the march continues at the interior's last
+      // grid sample after this one (evaluated first, so that the least-D load overlaps the corner loads)
       const float vl = m.v[l], in = (0.5f + 1e-3f) * vl;
       float t_out = t_far + 1.0f;
       bool inside = true;
@@ -458,11 +461,7 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
         const float jf = floorf((t_out - t0) * inv_h);
         int jl = jf < 1073741824.0f ? (int)jf : 1073741824;
         jl = jb + (((jl - jb) >> l) << l);  // a sample of the block's pitch
-        if (jl > j) {
-          j = jl;
-          pv = false;  // the samples left out were positive or had no field: none can end a bracket at sample jl
-          continue;
-        }
+        if (jl > j) j_skip = jl;
       }
     }
     float F = 0.0f;
@@ -517,7 +516,12 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       const int jn = jf < 1073741824.0f ? (int)jf : 1073741824;
       step = min(1 << l, jn > j ? jn - j : 1);
     }
-    j += step;
+    if (j_skip > j + step) {
+      j = j_skip;
+      pv = false;  // the samples left out were positive or had no field: none can end a bracket at sample j_skip
+    } else {
+      j += step;
+    }
   }
   const size_t px = (size_t)v * c.width + u;
   out.depth[px] = hit ? t_hit * rc[2] : 0.0f;
