@@ -387,6 +387,7 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
   float tp = 0.0f;
   int cb0 = 0x7FFFFFFF, cb1 = 0, cb2 = 0, jb = 0;  // the allocated block of the last sample and its first sample
   float dmin_b = 0.0f;                              // and its least stored D
+  int jn_b = 0;                                     // and, at a coarse level, the first sample beyond its exit face
   // refine > 0: the loop evaluates the bracket's midpoint tm (the same code path as every grid sample, so the field
   // evaluation exists once in the kernel)
   int refine = 0;
@@ -440,6 +441,19 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
       cb2 = bk[2];
       jb = j;
       dmin_b = m.dmin[l][val & kPtrMask];  // read once per block: the samples of a block test a register
+      if (l > 0) {
+        // a coarse block's samples stop at the first grid sample beyond its exit face (also computed once)
+        float t_exit = t_far + 1.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (r[a] == 0.0f) continue;
+          const float face = (float)(r[a] > 0.0f ? bk[a] + 1 : bk[a]) * E;
+          const float tf = (face - o[a]) * inv_r[a];
+          if (tf < t_exit) t_exit = tf;
+        }
+        const float jf = ceilf((t_exit - t0) * inv_h);
+        jn_b = jf < 1073741824.0f ? (int)jf : 1073741824;
+      }
     }
     int j_skip = -1;  // the interior's last grid sample, when this sample lies in a positive block's interior
     if (!refine && dmin_b > 0.0f) {
@@ -501,21 +515,8 @@ __device__ inline void cast_ray(const MapDev& m, const CamArgs& c, int u, int v,
     Fp = F;
     jp = j;
     tp = t;
-    int step = 1;
-    if (l > 0) {
-      // the block's pitch, but not past the first grid sample beyond its exit face
-      float t_exit = t_far + 1.0f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (r[a] == 0.0f) continue;
-        const float face = (float)(r[a] > 0.0f ? bk[a] + 1 : bk[a]) * E;
-        const float tf = (face - o[a]) * inv_r[a];
-        if (tf < t_exit) t_exit = tf;
-      }
-      const float jf = ceilf((t_exit - t0) * inv_h);
-      const int jn = jf < 1073741824.0f ? (int)jf : 1073741824;
-      step = min(1 << l, jn > j ? jn - j : 1);
-    }
+    // the block's pitch, but not past the first grid sample beyond its exit face
+    const int step = l > 0 ? min(1 << l, jn_b > j ? jn_b - j : 1) : 1;
     if (j_skip > j + step) {
       j = j_skip;
       pv = false;  // the samples left out were positive or had no field: none can end a bracket at sample j_skip
