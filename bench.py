@@ -635,7 +635,7 @@ def _packed_keys(keys):
 
 
 def block_statistics(ex, rows, T, wl):
-    """The survey's 16 TSDF-statistics features of existing blocks (rows of an extract, CUDA): mean / min / max D
+    """The 16 TSDF-statistics features of existing blocks (rows of an extract, CUDA): mean / min / max D
     over observed voxels (/ tau), mean / max variance S2 / W (/ theta_0), mean / min / max W (W / (8 + W)), the
     observed fraction, the normal spread 1 - |mean unit gradient| over observed voxels with |D| < tau, the largest W
     (frames that observed the block, W / (8 + W)), the distance r of the block centre to the sensor, the cosine

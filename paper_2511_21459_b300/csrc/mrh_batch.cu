@@ -1,5 +1,5 @@
 // Batched multi-scene integration: one frame for each of up to 64 maps per step, with one launch per phase for all
-// maps together (spec add-on (2); the paper integrates one map).
+// maps together (an addition to the paper's method, which integrates one map).
 //
 //   k_batch_begin     per-map frame counters
 //   k_batch_alloc     one grid over every map's pixel tiles (a CTA finds its map from the tile offsets)

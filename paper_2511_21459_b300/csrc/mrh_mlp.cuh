@@ -1,7 +1,7 @@
-// Learned level predictor (spec add-on (4); not in the paper): a 16 -> 64 -> 64 -> 3 MLP with GELU that
-// predicts, from features of a new block's neighbourhood in the current range image, the level the block will end at
-// under the variance rule, so it can be allocated and fused at that level from its first frame. The variance rule
-// still runs afterwards and re-levels any block the network got wrong.
+// Learned level predictor (an addition; not in the paper): a 16 -> 64 -> 64 -> 3 MLP with GELU that predicts, from
+// features of a new block (its neighbourhood in the current range image, or the moments of a LiDAR scan's end points
+// inside it), the level the block will end at under the variance rule, so it can be allocated and fused at that level
+// from its first frame. The variance rule still runs afterwards and re-levels any block the network got wrong.
 //
 // Everything that decides a level is computed with +, -, *, / and sqrt only (compiled without multiply-add
 // contraction), in a fixed order, so that the CPU oracle reproduces every decision bit for bit:
