@@ -9,8 +9,9 @@
 //
 // The B300 form of Algorithm 1's breadth-first loop: the sums of any rectangle come from integral images of the bytes
 // and of their squares (64-bit, built once per image), so a node's contrast is 24 loads instead of a reduction over its
-// pixels. The levels run as one launch each over the previous level's node list; every launch reads its node count
-// from device memory, so the whole tree is queued without a host round trip.
+// pixels. The top levels run as one launch each over the previous level's node list (every launch reads its node count
+// from device memory, so the whole tree is queued without a host round trip); once nodes are at most 64 pixels on a
+// side, one launch expands every remaining subtree, one CTA per subtree with its level lists in shared memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -184,6 +185,91 @@ __global__ void __launch_bounds__(256) k_qt_level(QtArgs a, int level) {
   }
 }
 
+// The subtrees below level T, one CTA per level-T node: its nodes are at most kQtSubSide x kQtSubSide pixels, so no
+// level of its subtree holds more than kQtSubSide^2 nodes (they are disjoint non-empty rectangles of its pixels). The
+// CTA expands the subtree breadth-first with its two level lists in shared memory (8-byte nodes) and a CTA barrier
+// between levels, instead of one launch per level; decisions and children are those of k_qt_level.
+constexpr int kQtSubSide = 64, kQtSubCap = kQtSubSide * kQtSubSide;
+
+struct QtNode8 {
+  uint16_t x, y, w, h;
+};
+
+__global__ void __launch_bounds__(256) k_qt_subtrees(QtArgs a, int level) {
+  extern __shared__ QtNode8 s_list[];  // [2][kQtSubCap]
+  __shared__ uint32_t s_n[2];
+  const uint32_t n_roots = a.count[level];
+  const QtNode* roots = a.queue[level & 1];
+  const int lane = threadIdx.x & 31;
+  for (uint32_t root = blockIdx.x; root < n_roots; root += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const QtNode q = roots[root];
+      s_list[0] = QtNode8{(uint16_t)q.x, (uint16_t)q.y, (uint16_t)q.w, (uint16_t)q.h};
+      s_n[0] = 1;
+      s_n[1] = 0;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (;;) {
+      const uint32_t n = s_n[cur];
+      if (n == 0) break;  // the same value in every thread (read after a barrier)
+      const QtNode8* in = s_list + cur * kQtSubCap;
+      QtNode8* out = s_list + (cur ^ 1) * kQtSubCap;
+      for (uint32_t base = threadIdx.x & ~31u; base < n; base += blockDim.x) {  // warp-uniform
+        const uint32_t i = base + lane;
+        QtNode q{0, 0, 0, 0};
+        bool live = i < n, split = false;
+        if (live) {
+          const QtNode8 c = in[i];
+          q = QtNode{c.x, c.y, c.w, c.h};
+          const int size = q.w > q.h ? q.w : q.h;
+          double n2 = 0.0;
+          split = size > a.min_size && scaled_contrast(a, q, &n2) > a.threshold * n2;
+        }
+        const int hw = q.w / 2, hh = q.h / 2;
+        const int kids = split ? (hw > 0 ? 2 : 1) * (hh > 0 ? 2 : 1) : 0;
+        int incl = kids;
+        for (int d = 1; d < 32; d <<= 1) {
+          const int t = __shfl_up_sync(~0u, incl, d);
+          if (lane >= d) incl += t;
+        }
+        uint32_t first = 0;
+        if (lane == 31 && incl > 0) first = atomicAdd(&s_n[cur ^ 1], (uint32_t)incl);
+        first = __shfl_sync(~0u, first, 31) + (uint32_t)(incl - kids);
+        if (split)
+          for (int j = 0; j < 2; ++j)
+            for (int r = 0; r < 2; ++r) {
+              const int cw = r ? q.w - hw : hw, ch = j ? q.h - hh : hh;
+              if (cw > 0 && ch > 0) {
+                if (first < (uint32_t)kQtSubCap)
+                  out[first] = QtNode8{(uint16_t)(r ? q.x + hw : q.x), (uint16_t)(j ? q.y + hh : q.y), (uint16_t)cw,
+                                       (uint16_t)ch};
+                ++first;
+              }
+            }
+        const bool leaf = live && !split;
+        const unsigned bal = __ballot_sync(~0u, leaf);
+        unsigned long long lbase = 0;
+        if (lane == 0 && bal) lbase = atomicAdd(a.n_leaves, (unsigned long long)__popc(bal));
+        lbase = __shfl_sync(~0u, lbase, 0);
+        if (leaf) {
+          const unsigned long long slot = lbase + __popc(bal & ((1u << lane) - 1u));
+          if (slot < a.cap) {
+            a.leaves[4 * slot] = q.x;
+            a.leaves[4 * slot + 1] = q.y;
+            a.leaves[4 * slot + 2] = q.w;
+            a.leaves[4 * slot + 3] = q.h;
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_n[cur] = 0;
+      cur ^= 1;
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
 
 size_t quadtree_scratch_bytes(int width, int height) {
@@ -224,7 +310,17 @@ cudaError_t launch_quadtree(const uint8_t* rgb, int width, int height, double th
   k_qt_col_sums<<<(col_threads + 255) / 256, 256, 0, s>>>(a, seg);
   k_qt_cols<<<(col_threads + 255) / 256, 256, 0, s>>>(a, seg);
   k_qt_root<<<1, 32, 0, s>>>(a, levels + 1);
-  for (int l = 0; l <= levels; ++l) k_qt_level<<<sms * 2, 256, 0, s>>>(a, l);
+  // one launch per level while nodes are larger than kQtSubSide on a side, then every remaining subtree in one launch
+  int top = 0;
+  for (int side = width > height ? width : height; side > kQtSubSide; side = (side + 1) / 2) ++top;
+  if (top > levels || width > 65535 || height > 65535) top = levels + 1;
+  for (int l = 0; l < top; ++l) k_qt_level<<<sms * 2, 256, 0, s>>>(a, l);
+  if (top <= levels) {
+    const int smem = 2 * kQtSubCap * (int)sizeof(QtNode8);
+    cudaError_t e = cudaFuncSetAttribute(k_qt_subtrees, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_qt_subtrees<<<sms * 3, 256, smem, s>>>(a, top);
+  }
   *n_leaves_dev = a.n_leaves;
   return cudaGetLastError();
 }
