@@ -1582,11 +1582,11 @@ def main():
                                    "launch_ms_avg": round(bf["ms"] / bf["steps"], 5)}
 
     learned = None
-    if not args.no_learned:
+    if rank == 0 and not args.no_learned:  # a comparison on one GPU (its synthetic scans render on the host cores)
         learned = run_learned(wl, frames, args.warmup, timed, flush, res, epochs=args.learned_epochs,
                               lidar_train_scans=args.learned_lidar_train_scans,
                               lidar_scans=args.learned_lidar_scans, repeats=args.learned_repeats)
-        if rank == 0 and not args.no_feature_study:
+        if not args.no_feature_study:
             learned["feature_study"] = run_feature_study(wl)
 
     if rank == 0:
