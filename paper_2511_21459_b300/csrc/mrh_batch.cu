@@ -136,23 +136,27 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_batch_fuse(BatchDev b) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t total = s_end[b.n - 1];
   const uint32_t nwarps = gridDim.x * WARPS;
-  int mi = 0;
-  for (uint32_t item = blockIdx.x * WARPS + warp; item < total; item += nwarps) {  // warp-uniform
-    while (s_end[mi] <= item) ++mi;  // items rise, so the map index only moves forward
-    const uint32_t local = item - (mi > 0 ? s_end[mi - 1] : 0u);
+  // Map by map, the warp takes the items it would take in a grid-stride loop over all maps' items in order (item
+  // s_end[mi - 1] + local of map mi goes to warp (s_end[mi - 1] + local) mod nwarps), with the map's counters in
+  // 32 bits and added to its DevState once (a map's observations in one frame stay far below 2^32).
+  const uint32_t gw = blockIdx.x * WARPS + warp;
+  for (int mi = 0; mi < b.n; ++mi) {
+    const uint32_t first = mi > 0 ? s_end[mi - 1] : 0u, items = s_end[mi] - first;
+    const uint32_t start = (gw + nwarps - first % nwarps) % nwarps;
+    if (start >= items) continue;
     const MapDev& m = s_maps[mi];
     const BatchFrame& f = b.frames[mi];
     CameraObs<FP16, COLOR, const CamArgs&> obs{s_cam[mi], f.rho_img, f.rgb ? f.rgb_img : nullptr};
-    unsigned long long my_obs = 0, my_vox = 0;
-    fuse_item<FP16, COLOR>(m, obs, warp, s_ic[mi], local, my_obs, my_vox);
+    uint32_t my_obs = 0, my_vox = 0;
+    for (uint32_t local = start; local < items; local += nwarps)  // warp-uniform
+      fuse_item<FP16, COLOR>(m, obs, warp, s_ic[mi], local, my_obs, my_vox);
     for (int o = 16; o > 0; o >>= 1) {
       my_obs += __shfl_xor_sync(~0u, my_obs, o);
       my_vox += __shfl_xor_sync(~0u, my_vox, o);
     }
-    if (lane == 0 && my_obs) atomicAdd(&m.st->observations, my_obs);
-    if (lane == 0 && my_vox) atomicAdd(&m.st->updated_voxels, my_vox);
+    if (lane == 0 && my_obs) atomicAdd(&m.st->observations, (unsigned long long)my_obs);
+    if (lane == 0 && my_vox) atomicAdd(&m.st->updated_voxels, (unsigned long long)my_vox);
   }
 }
 

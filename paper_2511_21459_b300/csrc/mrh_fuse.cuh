@@ -170,7 +170,7 @@ struct CameraObs {
           for (int q = 0; q < 3; ++q) {
             const float col = (float)((packed >> (8 * q)) & 255u);
             const float Cn = ch.C[q][k] + (col - ch.C[q][k]) * inv;
-            if (ok) ch.C[q][k] = Field<FP16>::kept(Cn);
+            if (ok) ch.C[q][k] = Cn;  // rounded to the storage format by the store (nothing reads it before)
           }
         }
       }
@@ -586,10 +586,11 @@ __device__ inline ItemCounts item_counts(const MapDev& m) {
   return c;
 }
 
-// One work item, processed by the whole warp (warp-uniform control flow).
-template <bool FP16, bool COLOR, class Obs>
+// One work item, processed by the whole warp (warp-uniform control flow). my_obs / my_vox: the lane's running
+// counts of observations and updated voxels (Acc: 32 bits where a caller flushes them per map and frame).
+template <bool FP16, bool COLOR, class Obs, class Acc = unsigned long long>
 __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, const ItemCounts& ic, uint32_t item,
-                                 unsigned long long& my_obs, unsigned long long& my_vox) {
+                                 Acc& my_obs, Acc& my_vox) {
   const int lane = threadIdx.x & 31;
   const uint32_t n0 = ic.n0, n1 = ic.n1, n2 = ic.n2, it0 = ic.it0, it1 = ic.it1;
   {
@@ -637,8 +638,8 @@ __device__ inline void fuse_item(const MapDev& m, Obs& obs, int warp_in_cta, con
       int n_def = 0;
       if (x.active) {
         int n_vox = 0;
-        my_obs += (unsigned long long)obs.apply(m, x, 4 * (c * G + li), cur, n_vox, n_def);
-        my_vox += (unsigned long long)n_vox;
+        my_obs += (Acc)obs.apply(m, x, 4 * (c * G + li), cur, n_vox, n_def);
+        my_vox += (Acc)n_vox;
         // a chunk without an update is unchanged in memory, unless the block is new (zero state to write)
         if (n_vox > 0 || isnew) io.store(c * G + li, cur);
       }
