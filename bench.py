@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "integrated points/s & frames/s (RGB-D 640x480, LiDAR 262k pts) vs HBM roofline"
+RGBD_WORKLOAD = ("rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm, 2^20 hash, colour, FP32 storage) + 640x480 "
+                 "raycast (depth, normal, colour) per frame")
 FALLBACK_HBM_GBS = 6400.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -1424,8 +1426,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
                 "steps": n, "warmup": warm, "ms_per_step": 1000.0 * t_total / n, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm) + 640x480 raycast "
-                                       "(depth, normal, colour)"},
+                "config": {"workload": RGBD_WORKLOAD},
                 "frames_per_s": n / t_total,
                 "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": sample,
                                  "host": host_cpu()},
@@ -1595,8 +1596,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded procedural RGB-D room sequence; stands in for ScanNet/Replica)",
-                "config": {"workload": "rgbd-640x480-seq300 (3 levels 1/2/4 cm, tau 12 cm, 2^20 hash, colour, FP32 "
-                                       "storage) + 640x480 raycast (depth, normal, colour) per frame",
+                "config": {"workload": RGBD_WORKLOAD,
                            "frames": f"{len(timed)} timed frames spread over the {n_frames}-frame orbit ({timed[0]}, "
                                      f"{timed[1] if len(timed) > 1 else ''}, ... {timed[-1]}); {args.warmup} warm-up "
                                      f"frames, every other frame integrated untimed in sequence order",
