@@ -4,9 +4,9 @@
 //   k_batch_begin     per-map frame counters
 //   k_batch_alloc     one grid over every map's pixel tiles (a CTA finds its map from the tile offsets)
 //   k_batch_bin       one grid row per map
-//   k_batch_fuse      persistent warps stride over the work items of all maps laid end to end (a warp finds an
-//                     item's map from the running totals), so maps with large and small frames share the GPU without
-//                     per-map launches or idle tails
+//   k_batch_fuse      persistent warps share the work items of all maps laid end to end as a grid-stride loop would
+//                     (each warp walks the maps in order and takes, in each, the items that loop gives it), so maps
+//                     with large and small frames share the GPU without per-map launches or idle tails
 //   k_batch_release   one grid row per map
 //   k_batch_raycast   one grid over every map's pixel tiles (maps without a raycast output skip)
 //
@@ -48,7 +48,6 @@ struct BatchDev {
   const MapDev* maps;
   const BatchFrame* frames;
   int n;
-  uint32_t* queue;  // fusion work counter (reset by k_batch_begin)
 };
 
 namespace {
@@ -63,7 +62,6 @@ __device__ inline int find_map(const BatchFrame* frames, int n, uint32_t tile, b
 __global__ void k_batch_begin(BatchDev b) {
   const int i = threadIdx.x;
   if (i < b.n) begin_frame(b.maps[i].st);
-  if (i == 0) *b.queue = 0;
 }
 
 template <int TW, int TH, int PW>
@@ -208,7 +206,6 @@ struct mrh_batch {
   std::vector<mrh_pinhole> cams;
   MapDev* maps_dev = nullptr;
   BatchFrame* frames_dev = nullptr;
-  uint32_t* queue = nullptr;
   std::vector<void*> images;
   std::vector<BatchFrame> frames_host;
   uint32_t alloc_tiles[4] = {0, 0, 0, 0};  // per allocation shape
@@ -245,7 +242,7 @@ struct BatchDeviceGuard {
   }
 };
 
-BatchDev batch_dev(const mrh_batch* b) { return BatchDev{b->maps_dev, b->frames_dev, b->n, b->queue}; }
+BatchDev batch_dev(const mrh_batch* b) { return BatchDev{b->maps_dev, b->frames_dev, b->n}; }
 
 template <int TW, int TH, int PW>
 void launch_alloc_shape(const mrh_batch* b, cudaStream_t s, uint32_t tiles) {
@@ -373,8 +370,6 @@ mrh_status mrh_batch_create(mrh_map* const* maps, const mrh_pinhole* cams, int n
   if (e != cudaSuccess) return fail(e, "cudaMalloc");
   e = cudaMalloc(&b->frames_dev, sizeof(BatchFrame) * n);
   if (e != cudaSuccess) return fail(e, "cudaMalloc");
-  e = cudaMalloc(&b->queue, sizeof(uint32_t));
-  if (e != cudaSuccess) return fail(e, "cudaMalloc");
   e = cudaMemcpy(b->maps_dev, mdev.data(), sizeof(MapDev) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(e, "cudaMemcpy");
   b->frames_host.resize(n);
@@ -417,7 +412,6 @@ mrh_status mrh_batch_destroy(mrh_batch* b) {
   for (void* p : b->images) cudaFree(p);
   if (b->maps_dev) cudaFree(b->maps_dev);
   if (b->frames_dev) cudaFree(b->frames_dev);
-  if (b->queue) cudaFree(b->queue);
   for (int k = 0; k < 5; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   delete b;
