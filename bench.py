@@ -168,6 +168,9 @@ def profile_case(kind: str) -> int:
         for k in range(4):
             xyz, T = synth.render_lidar(wl, k, scene=scene)
             m.integrate_points(T, torch.from_numpy(xyz).cuda())
+            st = m.stats()
+            print(json.dumps({"scan": k, "fuse_algorithmic_bytes":
+                              fuse_bytes_lidar(st, wl.n_beams * wl.n_azimuth, voxel_bytes(wl))}))
     elif kind == "batched":
         # the first 8 of the 16 batched maps, 4 steps, reduced heaps (about 2 GB on the device)
         wls = synth.batched()[:8]
@@ -181,6 +184,8 @@ def profile_case(kind: str) -> int:
             fr = [synth.render_depth(w, k, scene=sc) for w, sc in zip(wls, scenes)]
             batch.integrate([(T, torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), o)
                              for (d, c, T), o in zip(fr, outs)])
+            print(json.dumps({"step": k, "fuse_algorithmic_bytes":
+                              sum(fuse_bytes_camera(mm.stats(), w, voxel_bytes(w)) for mm, w in zip(maps, wls))}))
         torch.cuda.synchronize()
         batch.close()
         m = maps[0]
@@ -367,6 +372,24 @@ def source_sha256(files=("mrh_fuse.cu", "mrh_fuse.cuh", "mrh_internal.cuh"), wit
 
 def fusion_source_sha256() -> str:
     return source_sha256()
+
+
+LIDAR_FUSION_SOURCES = ("mrh_fuse.cu", "mrh_fuse.cuh", "mrh_internal.cuh")
+BATCH_FUSE_SOURCES = ("mrh_batch.cu", "mrh_fuse.cuh", "mrh_internal.cuh")
+
+
+def stored_traffic(name, files, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch from a stored ncu capture (profiles/<name>.json: DRAM bytes per algorithmic byte of the
+    captured launches), scaled to this run's algorithmic bytes per launch; None unless the capture was taken from the
+    same kernel sources."""
+    path = os.path.join(ROOT, "profiles", name + ".json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        tr = json.load(f)
+    if tr.get("source_sha256") != source_sha256(files):
+        return None
+    return int(tr["dram_bytes_per_algorithmic_byte"] * algorithmic_bytes_per_launch)
 
 
 RAYCAST_SOURCES = ("mrh_raycast.cu", "mrh_raycast.cuh", "mrh_internal.cuh")
@@ -1545,7 +1568,9 @@ def main():
         l_ach = lres["fuse_bytes"] / (l_fuse_ms / 1000.0) / 1e9
         roofline_lidar = {"kernel": "LiDAR fusion: observation passes + k_fuse_points (fusion + block variance + "
                                     "re-level)", "bound": "hbm", "achieved": round(l_ach, 1), "peak": hbm,
-                          "unit": "GB/s", "frac": round(l_ach / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                          "unit": "GB/s", "frac": round(l_ach / hbm, 4), "peak_kind": peak_kind,
+                          "traffic": stored_traffic("lidar_fusion_traffic", LIDAR_FUSION_SOURCES,
+                                                    lres["fuse_bytes"] / lres["steps"]),
                           "algorithmic_bytes_per_launch": int(lres["fuse_bytes"] / lres["steps"]),
                           "launch_ms_avg": round(l_fuse_ms / lres["steps"], 5),
                           "bytes_formula": "12 N_points + 2 s_v updated_voxels + 16 touched (s_v = 10 B, FP16, no "
@@ -1578,7 +1603,9 @@ def main():
             b_ach = bf["bytes"] / (bf["ms"] / 1000.0) / 1e9
             batched["roofline"] = {"kernel": "k_batch_fuse (all maps' fusion + block variance + re-level, one launch)",
                                    "bound": "hbm", "achieved": round(b_ach, 1), "peak": hbm, "unit": "GB/s",
-                                   "frac": round(b_ach / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                                   "frac": round(b_ach / hbm, 4), "peak_kind": peak_kind,
+                                   "traffic": stored_traffic("batch_fuse_traffic", BATCH_FUSE_SOURCES,
+                                                             bf["bytes"] / bf["steps"]),
                                    "algorithmic_bytes_per_launch": int(bf["bytes"] / bf["steps"]),
                                    "launch_ms_avg": round(bf["ms"] / bf["steps"], 5)}
 

@@ -1,5 +1,6 @@
 """Host-side logic of the benchmark (no GPU): the timing spread summary, the raycast's instruction-issue roofline and
-its gate on the stored capture's source hash, and the constant-level networks that bound the learned predictor."""
+its gate on the stored capture's source hash, the stored DRAM-traffic ratios and their gate, and the constant-level
+networks that bound the learned predictor."""
 import json
 
 import numpy as np
@@ -38,6 +39,24 @@ def test_raycast_roofline_arithmetic(tmp_path, monkeypatch):
     # a source or flag change since the capture: no roofline from a stale count
     (tmp_path / "paper_2511_21459_b300" / "build.py").write_text("other flags")
     assert bench.raycast_roofline(0.5, 100_000, {"sm_max_mhz": 2000.0}, 100) is None
+
+
+def test_stored_traffic_scales_and_gates(tmp_path, monkeypatch):
+    """traffic = the capture's DRAM bytes per algorithmic byte x this run's algorithmic bytes per launch, only while
+    the kernel sources hash as they did when the capture was taken."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2511_21459_b300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.BATCH_FUSE_SOURCES:
+        (csrc / f).write_text("source " + f)
+    rec = {"source_sha256": bench.source_sha256(bench.BATCH_FUSE_SOURCES), "dram_bytes_per_algorithmic_byte": 0.8}
+    (prof / "batch_fuse_traffic.json").write_text(json.dumps(rec))
+    assert bench.stored_traffic("batch_fuse_traffic", bench.BATCH_FUSE_SOURCES, 1_000_000) == 800_000
+    assert bench.stored_traffic("missing_traffic", bench.BATCH_FUSE_SOURCES, 1_000_000) is None
+    (csrc / "mrh_batch.cu").write_text("changed")
+    assert bench.stored_traffic("batch_fuse_traffic", bench.BATCH_FUSE_SOURCES, 1_000_000) is None
 
 
 @pytest.mark.parametrize("level", range(MLP_LEVELS))
